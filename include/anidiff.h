@@ -1,0 +1,188 @@
+/*
+ * anidiff.h -- C ABI of the GB300 (sm_103a) exponential-integrator library for
+ * the 2-D anisotropic diffusion-advection equation with sources
+ *
+ *     du/dt = div(D grad u) + div(a u) + S(x, y, t)              (Eq. anidiff)
+ *
+ * of Deka, Kissmann & Einkemmer, "Efficient numerical methods for Anisotropic
+ * Diffusion of Galactic Cosmic Rays" (ICRC 2023).  The matrix functions
+ * phi_l(dt A) are applied by Newton interpolation at Leja points on [-2, 2]
+ * (Section 2), inside exponential quadrature steps (Eqs. exp_quad,
+ * exp_midpoint, exp_quad_Gauss); Crank-Nicolson is the comparison solver.
+ *
+ * Conventions shared by every call
+ *   - Grid: nx x ny cells on [x0, x1] x [y0, y1], cell centred.  Every field and
+ *     vector is row-major [ny][nx] (x fastest), contiguous, no padding.
+ *   - Coefficient fields passed to ad_create_operator are float64 DEVICE
+ *     pointers; they are read during the call only (the library packs its own
+ *     copy).  Vectors (u, v, out) have the operator's storage type: float64
+ *     for AD_FP64, float32 for AD_FP32_STORAGE.  A vector argument may be a
+ *     device pointer or a host pointer; host data is staged through
+ *     library-owned device buffers with copies on the operator's stream.
+ *   - Ownership: the caller owns every buffer it passes.  The library owns the
+ *     operator (packed coefficients, workspace, CUDA graphs), allocated in
+ *     ad_create_operator and released by ad_destroy_operator; no call
+ *     allocates device memory after creation, except the lazily built device
+ *     buffers for host-pointer staging (once per operator).
+ *   - Streams: all work is enqueued on the CUDA stream given at creation.
+ *     Calls that report statistics or a convergence status synchronise that
+ *     stream before returning.
+ *   - Errors: every call returns an ad_status; ad_last_error() gives a
+ *     thread-local message for the last failure.  No C++ exception crosses
+ *     the ABI.  A CUDA error is reported as AD_ERR_CUDA.
+ */
+#ifndef ANIDIFF_H
+#define ANIDIFF_H
+
+#if defined(__GNUC__)
+#define AD_API __attribute__((visibility("default")))
+#else
+#define AD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AD_OK = 0,
+  AD_ERR_INVALID = 1,        /* bad argument (sizes, pointers, s, c, tolerances) */
+  AD_ERR_CUDA = 2,           /* a CUDA runtime call or kernel launch failed */
+  AD_ERR_NOT_CONVERGED = 3,  /* Leja series or GMRES hit its iteration cap */
+  AD_ERR_TIMEOUT = 4,        /* a bounded device-side wait gave up */
+  AD_ERR_NOMEM = 5           /* device allocation failed */
+} ad_status;
+
+typedef enum { AD_BC_PERIODIC = 0, AD_BC_DIRICHLET0 = 1 } ad_bc;
+typedef enum { AD_FP64 = 0, AD_FP32_STORAGE = 1 } ad_precision;
+typedef enum { AD_BOUND_GERSHGORIN = 0, AD_BOUND_POWER = 1 } ad_bound_method;
+
+typedef struct {
+  int nx, ny;                /* cells; nx, ny >= 1 */
+  double x0, x1, y0, y1;     /* domain; x1 > x0, y1 > y0 */
+  int bc;                    /* ad_bc */
+} ad_grid;
+
+typedef struct {
+  int iters;                 /* Leja (or GMRES) iterations, summed over substeps */
+  int matvecs;               /* all applications of A, including A u and substep couplings */
+  int substeps;              /* K: the step was split into K equal substeps */
+  int converged;             /* 1 if every series met its stopping rule */
+  double err_est;            /* largest |d_{m+1}| ||y_{m+1}|| / ||p_{m+1}|| (GMRES: relative residual) */
+  double alpha;              /* spectral bound used */
+  int kernel_launches;       /* device kernels this call enqueued (graph-loop bodies included) */
+  int pad_;
+} ad_stats;
+
+/* Time profile h_k(t) of a separable source S(x, y, t) = sum_k h_k(t) g_k(x, y).
+ * Called on the host, from the calling thread, during the step call. */
+typedef double (*ad_time_profile)(int k, double t, void* ctx);
+
+typedef struct {
+  int nterms;                /* 0 <= nterms <= 16 */
+  const void* const* g;      /* host array of nterms DEVICE pointers, storage type, [ny][nx] */
+  ad_time_profile h;         /* NULL: every h_k(t) = 1 (time-independent source) */
+  void* ctx;
+} ad_source;
+
+typedef struct ad_operator ad_operator;
+
+/* Build the discretised operator A = div(D grad .) + div(a .) of Eq. anidiff
+ * (A is defined below Eq. exp_quad; the tensor D = [[Dxx, Dxy], [Dxy, Dyy]] in
+ * Section 1).  The paper gives no spatial scheme: the library uses the
+ * conservative 9-point flux form on the cell-centred grid (face coefficients
+ * are means of the two adjacent cells; centred advective flux; periodic
+ * wrap or zero Dirichlet by odd-reflection ghosts).
+ *   Dxx, Dxy, Dyy : float64 device fields [ny][nx] (required).
+ *   ax, ay        : float64 device fields, or NULL to use the constants ax_c, ay_c.
+ *   precision     : AD_FP64 (9 packed float64 weights per cell) or
+ *                   AD_FP32_STORAGE (float32 fields, float32 stencil arithmetic,
+ *                   float64 Leja scalars and norm accumulation).
+ *   cuda_stream   : cudaStream_t (NULL = legacy default stream) for all work.
+ *   out           : receives the handle.
+ * Errors: AD_ERR_INVALID for null pointers or a bad grid, AD_ERR_NOMEM,
+ * AD_ERR_CUDA.  The spectral bound is computed here by Gershgorin (Section 2);
+ * override it with ad_spectral_bound or ad_set_spectral_bound. */
+AD_API int ad_create_operator(const ad_grid* grid, const double* Dxx, const double* Dxy,
+                       const double* Dyy, const double* ax, const double* ay,
+                       double ax_c, double ay_c, int precision, void* cuda_stream,
+                       ad_operator** out);
+
+/* Release the operator and everything it owns.  NULL is accepted. */
+AD_API int ad_destroy_operator(ad_operator* op);
+
+/* Leja series options: rho_max is the largest gamma*dt per substep (a step
+ * with rho = gamma dt > rho_max is split into ceil(rho / rho_max) substeps);
+ * max_iters caps the number of Leja iterations per series (<= 500).
+ * Values <= 0 keep the current setting.  Defaults: rho_max 200, max_iters 500. */
+AD_API int ad_set_options(ad_operator* op, double rho_max, int max_iters);
+
+/* Estimate alpha, the largest-magnitude (negative) eigenvalue of A (Section 2:
+ * Gershgorin's disc theorem, smallest eigenvalue taken as 0), store it in the
+ * operator and return it in *alpha.
+ *   method AD_BOUND_GERSHGORIN: alpha = min_i (a_ii - sum_{j!=i} |a_ij|).
+ *   method AD_BOUND_POWER: power iteration, x <- A x / ||A x|| for power_iters
+ *     steps from x0 (device vector of the storage type) or, with x0 == NULL,
+ *     from the counter-based SplitMix64 sequence with the given seed mapped to
+ *     [-0.5, 0.5); alpha = -safety * ||A x_last||.  */
+AD_API int ad_spectral_bound(ad_operator* op, int method, const void* x0, unsigned long long seed,
+                      int power_iters, double safety, double* alpha);
+
+/* Set alpha directly (alpha < 0); c = alpha/2 and gamma = -alpha/4 follow. */
+AD_API int ad_set_spectral_bound(ad_operator* op, double alpha);
+AD_API int ad_get_spectral_bound(const ad_operator* op, double* alpha);
+
+/* Au = A u (one matrix-free 9-point stencil pass).  u and Au: storage type. */
+AD_API int ad_apply(ad_operator* op, const void* u, void* Au);
+
+/* out = phi_1(dt A) v by Leja interpolation (Section 2): Leja points on
+ * [-2, 2] with xi_0 = 2, divided differences of xi -> phi_1((c + gamma xi) dt),
+ * and the recurrence y_{m+1} = ((A - c)/gamma - xi_m) y_m,
+ * p_{m+1} = p_m + d_{m+1} y_{m+1}, each iteration one fused device pass.
+ * Stopping rule: after term m+1 >= 2, stop when |d_{m+1}| ||y_{m+1}|| <=
+ * tol ||p_{m+1}||.  force_iters > 0 runs exactly that many iterations per
+ * substep (no test); force_iters == 0 returns d_0 v.  tol > 0 unless forced.
+ * v and out may alias.  Returns AD_ERR_NOT_CONVERGED when a series reaches
+ * max_iters (out then holds the partial sum).  stats may be NULL. */
+AD_API int ad_leja_phi1(ad_operator* op, const void* v, void* out, double dt, double tol,
+                 int force_iters, ad_stats* stats);
+
+/* One exponential quadrature step, Eq. exp_quad, in place on u (t -> t + dt):
+ *   s = 1: u += dt phi_1(dt A)(A u + S(t + c[0] dt))   (Eq. exp_midpoint for c = 1/2);
+ *   s = 2: weights b_1, b_2 of Section 2, collected as
+ *          u += dt phi_1(dt A) w1 + dt^2 phi_2(dt A) w2,
+ *          w1 = A u + (c2 S1 - c1 S2)/(c2 - c1), w2 = (S2 - S1)/((c2 - c1) dt),
+ *          evaluated as the exponential of the augmented matrix (Section 2)
+ *          by one Leja series (Eq. exp_quad_Gauss for c = (1 -+ 1/sqrt 3)/2).
+ * c: host array of s nodes with c[0] != c[1] for s = 2.  src may be NULL (S = 0).
+ * force_iters as in ad_leja_phi1.  stats may be NULL. */
+AD_API int ad_expquad_step(ad_operator* op, void* u, double t, double dt, int s, const double* c,
+                    const ad_source* src, double tol, int force_iters, ad_stats* stats);
+
+/* One Crank-Nicolson step (the paper's comparison solver; its linear solver
+ * is unspecified): (I - dt/2 A) u+ = (I + dt/2 A) u + dt (S(t) + S(t+dt))/2,
+ * solved by restarted GMRES(restart) from x0 = u to relative residual
+ * gmres_tol.  force_iters > 0 runs exactly that many Arnoldi steps in one
+ * cycle (force_iters <= restart <= 200).  AD_FP64 operators only. */
+AD_API int ad_cn_step(ad_operator* op, void* u, double t, double dt, const ad_source* src,
+               double gmres_tol, int restart, int force_iters, ad_stats* stats);
+
+/* Measurement helper (no counterpart in the paper): time the fused Leja
+ * iteration kernel alone.  Runs `reps` iterations of the series kernel
+ * (aug = 0: phi_1 form, 1: augmented form) on the operator's stream with a
+ * CUDA event pair around each kernel launch (the control kernel between
+ * them is not timed) and returns the mean kernel duration in *ms_per_launch.
+ * Overwrites the operator's series workspace; results of earlier calls are
+ * unaffected.  1 <= reps <= 500. */
+AD_API int ad_profile_leja_iteration(ad_operator* op, int aug, int reps, double* ms_per_launch);
+
+/* Thread-local message for the last error of this thread ("" if none). */
+AD_API const char* ad_last_error(void);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+AD_API int ad_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ANIDIFF_H */

@@ -1,0 +1,283 @@
+"""Python binding of libanidiff (include/anidiff.h): argument marshalling only.
+
+Every computation runs in the CUDA kernels of the shared library; this module
+converts tensors and arrays to pointers, checks shapes and types, and turns
+status codes into exceptions.  Function names are those of the C ABI without
+the ``ad_`` prefix.  There is no fallback: if the library is missing or does
+not load, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Callable, Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libanidiff.so")
+
+AD_OK, AD_ERR_INVALID, AD_ERR_CUDA, AD_ERR_NOT_CONVERGED, AD_ERR_TIMEOUT, AD_ERR_NOMEM = range(6)
+BC_PERIODIC, BC_DIRICHLET0 = 0, 1
+FP64, FP32_STORAGE = 0, 1
+BOUND_GERSHGORIN, BOUND_POWER = 0, 1
+MAX_SOURCES = 16
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() (nvcc, sm_103a) first")
+_lib = C.CDLL(LIB_PATH)
+
+
+class _Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("x0", C.c_double), ("x1", C.c_double),
+                ("y0", C.c_double), ("y1", C.c_double), ("bc", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("matvecs", C.c_int), ("substeps", C.c_int),
+                ("converged", C.c_int), ("err_est", C.c_double), ("alpha", C.c_double),
+                ("kernel_launches", C.c_int), ("pad_", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+_PROFILE = C.CFUNCTYPE(C.c_double, C.c_int, C.c_double, C.c_void_p)
+
+
+class _Source(C.Structure):
+    _fields_ = [("nterms", C.c_int), ("g", C.POINTER(C.c_void_p)), ("h", _PROFILE),
+                ("ctx", C.c_void_p)]
+
+
+_vp, _dp, _i, _d = C.c_void_p, C.c_double, C.c_int, C.c_double
+_sig = {
+    "ad_create_operator": (_i, [C.POINTER(_Grid), _vp, _vp, _vp, _vp, _vp, _d, _d, _i, _vp,
+                                C.POINTER(_vp)]),
+    "ad_destroy_operator": (_i, [_vp]),
+    "ad_set_options": (_i, [_vp, _d, _i]),
+    "ad_spectral_bound": (_i, [_vp, _i, _vp, C.c_ulonglong, _i, _d, C.POINTER(_d)]),
+    "ad_set_spectral_bound": (_i, [_vp, _d]),
+    "ad_get_spectral_bound": (_i, [_vp, C.POINTER(_d)]),
+    "ad_apply": (_i, [_vp, _vp, _vp]),
+    "ad_leja_phi1": (_i, [_vp, _vp, _vp, _d, _d, _i, C.POINTER(Stats)]),
+    "ad_expquad_step": (_i, [_vp, _vp, _d, _d, _i, C.POINTER(_d), C.POINTER(_Source), _d, _i,
+                             C.POINTER(Stats)]),
+    "ad_cn_step": (_i, [_vp, _vp, _d, _d, C.POINTER(_Source), _d, _i, _i, C.POINTER(Stats)]),
+    "ad_profile_leja_iteration": (_i, [_vp, _i, _i, C.POINTER(_d)]),
+    "ad_last_error": (C.c_char_p, []),
+    "ad_version": (_i, []),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sig)
+
+
+class AdError(RuntimeError):
+    def __init__(self, status: int, msg: str, stats: Optional[dict] = None):
+        super().__init__(f"anidiff status {status}: {msg}")
+        self.status = status
+        self.stats = stats
+
+
+class NotConverged(AdError):
+    pass
+
+
+def last_error() -> str:
+    return _lib.ad_last_error().decode()
+
+
+def version() -> int:
+    return _lib.ad_version()
+
+
+def _check(status: int, stats: Optional[Stats] = None):
+    if status == AD_OK:
+        return
+    d = stats.as_dict() if stats is not None else None
+    cls = NotConverged if status == AD_ERR_NOT_CONVERGED else AdError
+    raise cls(status, last_error(), d)
+
+
+def _ptr(x, dtype_name: str, n: int, what: str):
+    """Pointer of a contiguous tensor/array with n elements of the given dtype."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            want = {"float64": torch.float64, "float32": torch.float32}[dtype_name]
+            if x.dtype != want:
+                raise TypeError(f"{what}: expected {dtype_name}, got {x.dtype}")
+            if not x.is_contiguous():
+                raise ValueError(f"{what}: tensor must be contiguous")
+            if x.numel() != n:
+                raise ValueError(f"{what}: expected {n} elements, got {x.numel()}")
+            return x.data_ptr()
+    except ImportError:
+        pass
+    import numpy as np
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.dtype(dtype_name):
+            raise TypeError(f"{what}: expected {dtype_name}, got {x.dtype}")
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{what}: array must be C-contiguous")
+        if x.size != n:
+            raise ValueError(f"{what}: expected {n} elements, got {x.size}")
+        return x.ctypes.data
+    raise TypeError(f"{what}: unsupported type {type(x)}")
+
+
+@dataclass
+class Source:
+    """S(x, y, t) = sum_k h_k(t) g_k(x, y); g: device tensors of the storage type,
+    h: callables of t (None: time-independent, every h_k = 1)."""
+    g: Sequence
+    h: Optional[Sequence[Callable[[float], float]]] = None
+
+
+class Operator:
+    """Handle of an ad_operator (see include/anidiff.h for the semantics)."""
+
+    def __init__(self, handle: int, nx: int, ny: int, precision: int, keep=()):
+        self.handle = handle
+        self.nx, self.ny, self.precision = nx, ny, precision
+        self.n = nx * ny
+        self.dtype_name = "float64" if precision == FP64 else "float32"
+        self._keep = keep
+
+    def close(self):
+        if self.handle:
+            _lib.ad_destroy_operator(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def vec(self, x, what):
+        return _ptr(x, self.dtype_name, self.n, what)
+
+
+def create_operator(nx: int, ny: int, bc: int, Dxx, Dxy, Dyy, ax=0.0, ay=0.0,
+                    precision: int = FP64, stream=None, x0=-1.0, x1=1.0, y0=-1.0,
+                    y1=1.0) -> Operator:
+    """ad_create_operator.  Dxx/Dxy/Dyy: float64 device tensors [ny][nx];
+    ax/ay: float constants or float64 device tensors."""
+    g = _Grid(nx, ny, x0, x1, y0, y1, bc)
+    n = nx * ny
+    pf = [_ptr(f, "float64", n, name) for f, name in ((Dxx, "Dxx"), (Dxy, "Dxy"), (Dyy, "Dyy"))]
+    axp = None if isinstance(ax, (int, float)) else _ptr(ax, "float64", n, "ax")
+    ayp = None if isinstance(ay, (int, float)) else _ptr(ay, "float64", n, "ay")
+    axc = float(ax) if isinstance(ax, (int, float)) else 0.0
+    ayc = float(ay) if isinstance(ay, (int, float)) else 0.0
+    sptr = _stream_ptr(stream)
+    h = _vp()
+    _check(_lib.ad_create_operator(C.byref(g), pf[0], pf[1], pf[2], axp, ayp, axc, ayc,
+                                   precision, sptr, C.byref(h)))
+    return Operator(h.value, nx, ny, precision)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def destroy_operator(op: Operator):
+    op.close()
+
+
+def set_options(op: Operator, rho_max: float = 0.0, max_iters: int = 0):
+    _check(_lib.ad_set_options(op.handle, rho_max, max_iters))
+
+
+def spectral_bound(op: Operator, method: int = BOUND_GERSHGORIN, x0=None, seed: int = 0,
+                   power_iters: int = 30, safety: float = 1.1) -> float:
+    a = _d()
+    _check(_lib.ad_spectral_bound(op.handle, method, op.vec(x0, "x0"), seed, power_iters,
+                                  safety, C.byref(a)))
+    return a.value
+
+
+def set_spectral_bound(op: Operator, alpha: float):
+    _check(_lib.ad_set_spectral_bound(op.handle, alpha))
+
+
+def get_spectral_bound(op: Operator) -> float:
+    a = _d()
+    _check(_lib.ad_get_spectral_bound(op.handle, C.byref(a)))
+    return a.value
+
+
+def apply(op: Operator, u, out):
+    _check(_lib.ad_apply(op.handle, op.vec(u, "u"), op.vec(out, "out")))
+
+
+def leja_phi1(op: Operator, v, out, dt: float, tol: float = 1e-10, force_iters: int = -1) -> dict:
+    st = Stats()
+    _check(_lib.ad_leja_phi1(op.handle, op.vec(v, "v"), op.vec(out, "out"), dt, tol,
+                             force_iters, C.byref(st)), st)
+    return st.as_dict()
+
+
+def _source_struct(op: Operator, src: Optional[Source]):
+    if src is None or len(src.g) == 0:
+        return None, ()
+    if len(src.g) > MAX_SOURCES:
+        raise ValueError("at most 16 source terms")
+    arr = (C.c_void_p * len(src.g))(*[op.vec(gk, f"g[{k}]") for k, gk in enumerate(src.g)])
+    cb = _PROFILE(0)
+    if src.h is not None:
+        hs = list(src.h)
+
+        def _h(k, t, ctx):
+            return float(hs[k](t))
+        cb = _PROFILE(_h)
+    s = _Source(len(src.g), C.cast(arr, C.POINTER(C.c_void_p)), cb, None)
+    return s, (arr, cb)
+
+
+def expquad_step(op: Operator, u, t: float, dt: float, s: int = 1, c: Sequence[float] = (0.5,),
+                 source: Optional[Source] = None, tol: float = 1e-10,
+                 force_iters: int = -1) -> dict:
+    st = Stats()
+    carr = (C.c_double * max(2, len(c)))(*list(c) + [0.0] * (max(2, len(c)) - len(c)))
+    srcs, keep = _source_struct(op, source)
+    _check(_lib.ad_expquad_step(op.handle, op.vec(u, "u"), t, dt, s, carr,
+                                C.byref(srcs) if srcs is not None else None, tol, force_iters,
+                                C.byref(st)), st)
+    del keep
+    return st.as_dict()
+
+
+def cn_step(op: Operator, u, t: float, dt: float, source: Optional[Source] = None,
+            gmres_tol: float = 1e-10, restart: int = 50, force_iters: int = 0) -> dict:
+    st = Stats()
+    srcs, keep = _source_struct(op, source)
+    _check(_lib.ad_cn_step(op.handle, op.vec(u, "u"), t, dt,
+                           C.byref(srcs) if srcs is not None else None, gmres_tol, restart,
+                           force_iters, C.byref(st)), st)
+    del keep
+    return st.as_dict()
+
+
+def profile_leja_iteration(op: Operator, aug: int = 0, reps: int = 200) -> float:
+    """Mean duration (ms) of the fused Leja iteration kernel, CUDA events on
+    the operator's stream (ad_profile_leja_iteration)."""
+    ms = _d()
+    _check(_lib.ad_profile_leja_iteration(op.handle, aug, reps, C.byref(ms)))
+    return ms.value

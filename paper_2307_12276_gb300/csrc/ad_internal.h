@@ -1,0 +1,139 @@
+// Internal declarations shared by the library's translation units.
+// Not part of the public ABI (that is include/anidiff.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace ad {
+
+constexpr int kMaxIters = 500;      // cap on Leja iterations per series
+constexpr int kMaxSources = 16;     // separable source terms per step
+constexpr int kThreads = 256;       // threads per block of the streaming kernels
+constexpr int kMaxGmres = 200;      // largest GMRES restart length
+
+// Per-iteration scalars of the Newton series, uploaded once per series
+// configuration.  Iteration m (0-based) produces term m+1.
+struct LejaCoef {
+  double xi;      // xi_m
+  double d;       // d_{m+1}
+  double absd;    // |d_{m+1}|
+  double e1;      // eta1_m / gamma  (augmented coupling with w2)
+  double e2;      // eta2_m / gamma  (augmented coupling with w1)
+  double pad[3];
+};
+
+// Device-side control block of one Newton series.
+struct Ctrl {
+  int m;          // iteration about to run (0-based)
+  int stop;       // 1 once the series has finished
+  int iters;      // iterations done
+  int status;     // 0 ok, 3 not converged
+  int force;      // > 0: exact iteration count, no stopping test
+  int max_iters;
+  int pad0, pad1;
+  double tol;
+  double err_est;
+  double ynorm2;  // last ||y_{m+1}||^2
+  double pnorm2;  // last ||p_{m+1}||^2
+};
+
+struct Sources {
+  const void* g[kMaxSources];
+  double a[kMaxSources];    // coefficients of the first combination
+  double b[kMaxSources];    // coefficients of the second combination
+  int n;
+};
+
+struct GridDev {
+  int nx, ny, bc;
+  long long n;
+};
+
+// ---------------------------------------------------------------- FP64 path
+// W: 9 planes [9][n] of folded stencil weights, slot k = (dj+1)*3 + (di+1).
+void pack_weights_f64(const GridDev& g, double dx, double dy, const double* Dxx, const double* Dxy,
+                      const double* Dyy, const double* ax, const double* ay, double ax_c,
+                      double ay_c, double* W, cudaStream_t s);
+void scale_weights_f64(const GridDev& g, const double* W, double c, double gamma, double* Ws,
+                       cudaStream_t s);
+void gershgorin_partials_f64(const GridDev& g, const double* W, double* partials, int nblocks,
+                             cudaStream_t s);
+// out1 = A u + sum_k a_k g_k ; if out2: out2 = sum_k b_k g_k.
+void apply_f64(const GridDev& g, const double* W, const double* u, double* out1, double* out2,
+               const Sources& src, cudaStream_t s);
+
+// ---------------------------------------------------------------- FP32 storage path
+// F: packed fields float [3][n] = Dxx/(2 dx^2), Dyy/(2 dy^2), Dxy/(8 dx dy) (the factors 1/2
+// of the face means are folded in), plus [2][n] = ax/(4 dx), ay/(4 dy) when advection is a field.
+// adv: 0 none, 1 constant (abx = ax/(2 dx), aby = ay/(2 dy)), 2 fields.
+void pack_fields_f32(const GridDev& g, double dx, double dy, const double* Dxx, const double* Dxy,
+                     const double* Dyy, const double* ax, const double* ay, double ax_c,
+                     double ay_c, float* F, cudaStream_t s);
+void gershgorin_partials_f32(const GridDev& g, const float* F, int adv, float abx, float aby,
+                             double* partials, int nblocks, cudaStream_t s);
+void apply_f32(const GridDev& g, const float* F, int adv, float abx, float aby, const float* u,
+               float* out1, float* out2, const Sources& src, cudaStream_t s);
+void apply_shifted_f64(const GridDev& g, const double* W, const double* u, double* out, double s0,
+                       double s1, cudaStream_t s);
+
+// ---------------------------------------------------------------- Leja series
+struct SeriesArgs {
+  GridDev g;
+  int prec;                 // 0 fp64, 1 fp32
+  const void* coef;         // Ws (fp64) or F (fp32)
+  double c, gamma;          // spectral shift/scale (fp32 path applies them per cell)
+  void* y[2];               // ping-pong Newton basis vectors
+  void* p;                  // partial sum
+  const void* w1;           // augmented couplings (may be null)
+  const void* w2;
+  const LejaCoef* lc;       // device [kMaxIters]
+  Ctrl* ctrl;               // device
+  double* partials;         // device [2 * nblocks]
+  int nblocks;
+  int aug;
+  int adv;                  // fp32 advection mode (see pack_fields_f32)
+  float abx, aby;
+};
+// y[0] = src (or 0 if src == null), p = d0 * y[0]; resets ctrl.
+void series_init(const SeriesArgs& a, const void* src, double d0, int force, int max_iters,
+                 double tol, cudaStream_t s);
+void series_iteration(const SeriesArgs& a, cudaStream_t s);
+// control kernel: reduce partials, apply stopping rule, advance m; when
+// has_handle, set the graph conditional to "continue".
+void series_control(const SeriesArgs& a, unsigned long long handle, int has_handle,
+                    cudaStream_t s);
+
+// ---------------------------------------------------------------- vector helpers
+// z = a*x + b*y (x or y may be null = 0), elementwise, storage type prec.
+void axpby(int prec, long long n, double a, const void* x, double b, const void* y, void* z,
+           cudaStream_t s);
+// partial sums of squares of x into partials[nblocks]; then finalize to out[0] = sqrt(sum).
+void norm2_partials(int prec, long long n, const void* x, double* partials, int nblocks,
+                    cudaStream_t s);
+void reduce_partials(const double* partials, int nblocks, int op /*0 sum,1 min,2 sqrt-sum*/,
+                     double* out, cudaStream_t s);
+// x = y / dev_scalar[0] (power iteration normalisation).
+void scale_by_inv(int prec, long long n, const void* y, const double* dev_scalar, void* x,
+                  cudaStream_t s);
+void splitmix_fill(int prec, long long n, unsigned long long seed, void* x, cudaStream_t s);
+
+// ---------------------------------------------------------------- GMRES (FP64)
+// h[i] = <V_i, w> for i < k (partials per block: [k][nblocks]).
+void multi_dot_partials(long long n, const double* V, long long ldv, int k, const double* w,
+                        double* partials, int nblocks, cudaStream_t s);
+void multi_dot_finalize(const double* partials, int nblocks, int k, double* h, cudaStream_t s);
+// w -= sum_i h[i] V_i ; also partial sums of ||w||^2 into partials.
+void multi_axpy_norm(long long n, const double* V, long long ldv, int k, const double* h,
+                     double* w, double* partials, int nblocks, cudaStream_t s);
+// x += sum_i y[i] V_i
+void multi_axpy_add(long long n, const double* V, long long ldv, int k, const double* y, double* x,
+                    cudaStream_t s);
+
+int stream_blocks(long long n);   // grid size of the streaming kernels
+
+// Kernels enqueued from the host by this thread (every launcher adds one);
+// kernels run inside graph loops are counted by the caller.
+long long& launch_counter();
+
+}  // namespace ad

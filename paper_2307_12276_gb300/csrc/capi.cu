@@ -1,0 +1,914 @@
+// C ABI of the library (include/anidiff.h): operator lifecycle, spectral
+// bounds, the Leja phi_1 action, exponential quadrature steps and the
+// Crank-Nicolson comparison step.  Host code here does only the scalar work
+// of the method (Leja points, divided differences, the scalar eta recurrence
+// of the augmented matrix, the GMRES Hessenberg solve) and orchestration;
+// every per-cell pass runs in the kernels of stencil_kernels.cu and
+// vec_kernels.cu.
+//
+// Each Newton series (Section 2) runs as one CUDA graph launch: a
+// conditional WHILE node whose body is [fused Leja iteration, one-block
+// control kernel].  The control kernel evaluates the stopping rule on the
+// device and sets the loop condition, so the host neither polls nor syncs per
+// iteration; the loop is bounded by the iteration cap (<= 500).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "anidiff.h"
+#include "ad_internal.h"
+#include "leja_host.h"
+
+using namespace ad;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                    \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(AD_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));       \
+  } while (0)
+
+#define AD_TRY(expr)              \
+  do {                            \
+    int r_ = (expr);              \
+    if (r_ != AD_OK) return r_;   \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct SeriesGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool ok = false;
+  bool tried = false;
+};
+
+struct ad_operator {
+  ad_grid grid{};
+  GridDev g{};
+  int prec = 0;
+  size_t esz = 8;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int dev = 0;
+  // coefficients
+  double* W = nullptr;   // fp64 [9][n]
+  double* Ws = nullptr;  // fp64 [9][n], (W - c)/gamma
+  float* F = nullptr;    // fp32 [3 or 5][n]
+  int adv = 0;
+  double ax_c = 0, ay_c = 0;
+  float abx = 0, aby = 0;
+  // workspace vectors (storage type)
+  void* Y0 = nullptr; void* Y1 = nullptr; void* P = nullptr;
+  void* W1 = nullptr; void* W2 = nullptr;
+  void* T1 = nullptr; void* T2 = nullptr; void* T3 = nullptr;
+  void* S0 = nullptr; void* S1 = nullptr;      // host staging (lazy)
+  double* Vk = nullptr; int vk_cols = 0;       // GMRES basis (lazy)
+  LejaCoef* lc = nullptr;
+  Ctrl* ctrl = nullptr;
+  double* partials = nullptr;                  // >= 2 * nblocks and >= kMaxGmres+1 rows for GMRES
+  size_t partials_len = 0;
+  double* dscal = nullptr;                     // device scalars [64]
+  int nblocks = 1;
+  // pinned host mirrors
+  LejaCoef* h_lc = nullptr;
+  Ctrl* h_ctrl = nullptr;
+  double* h_scal = nullptr;                    // [4 * (kMaxGmres + 2)]
+  // method state
+  double alpha = 0.0, c = 0.0, gamma = 0.0;
+  bool have_alpha = false;
+  double rho_max = 200.0;
+  int max_iters = kMaxIters;
+  SeriesGraph graphs[2];                       // [aug]
+  // cache of the coefficient upload
+  int cache_kind = -1;
+  double cache_h = 0.0, cache_alpha = 0.0;
+  std::vector<double> d_host;                  // divided differences of the current series
+};
+
+namespace {
+
+SeriesArgs series_args(ad_operator* op, int aug) {
+  SeriesArgs a{};
+  a.g = op->g;
+  a.prec = op->prec;
+  a.coef = op->prec == 0 ? (const void*)op->Ws : (const void*)op->F;
+  a.c = op->c;
+  a.gamma = op->gamma;
+  a.y[0] = op->Y0;
+  a.y[1] = op->Y1;
+  a.p = op->P;
+  a.w1 = op->W1;
+  a.w2 = op->W2;
+  a.lc = op->lc;
+  a.ctrl = op->ctrl;
+  a.partials = op->partials;
+  a.nblocks = op->nblocks;
+  a.aug = aug;
+  a.adv = op->adv;
+  a.abx = op->abx;
+  a.aby = op->aby;
+  return a;
+}
+
+void destroy_graphs(ad_operator* op) {
+  for (auto& sg : op->graphs) {
+    if (sg.exec) cudaGraphExecDestroy(sg.exec);
+    if (sg.graph) cudaGraphDestroy(sg.graph);
+    sg = SeriesGraph{};
+  }
+}
+
+// Build the WHILE-loop graph of one series variant.  Returns false (and the
+// caller falls back to launching iterations from the host) if the runtime
+// refuses any step.
+bool build_graph(ad_operator* op, int aug) {
+  SeriesGraph& sg = op->graphs[aug];
+  sg.tried = true;
+  if (getenv("AD_NO_GRAPH")) return false;
+  if (!op->cap_stream && cudaStreamCreateWithFlags(&op->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaGraph_t graph = nullptr;
+  if (cudaGraphCreate(&graph, 0) != cudaSuccess) { cudaGetLastError(); return false; }
+  cudaGraphConditionalHandle handle;
+  if (cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    return false;
+  }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    return false;
+  }
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if (cudaStreamBeginCaptureToGraph(op->cap_stream, body, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    return false;
+  }
+  SeriesArgs a = series_args(op, aug);
+  series_iteration(a, op->cap_stream);
+  series_control(a, (unsigned long long)handle, 1, op->cap_stream);
+  cudaGraph_t captured = nullptr;
+  if (cudaStreamEndCapture(op->cap_stream, &captured) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    return false;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    return false;
+  }
+  sg.graph = graph;
+  sg.exec = exec;
+  sg.ok = true;
+  return true;
+}
+
+int set_alpha(ad_operator* op, double alpha) {
+  if (!(alpha < 0.0) || !std::isfinite(alpha))
+    return fail(AD_ERR_INVALID, "spectral bound alpha must be finite and negative");
+  op->alpha = alpha;
+  op->c = alpha / 2.0;       // Section 2: c = alpha/2, gamma = -alpha/4
+  op->gamma = -alpha / 4.0;
+  op->have_alpha = true;
+  op->cache_kind = -1;
+  if (op->prec == 0) {
+    scale_weights_f64(op->g, op->W, op->c, op->gamma, op->Ws, op->stream);
+    CUDA_TRY(cudaGetLastError());
+  }
+  destroy_graphs(op);        // kernel arguments hold c and gamma
+  return AD_OK;
+}
+
+int gershgorin(ad_operator* op, double* out) {
+  if (op->prec == 0)
+    gershgorin_partials_f64(op->g, op->W, op->partials, op->nblocks, op->stream);
+  else
+    gershgorin_partials_f32(op->g, op->F, op->adv, op->abx, op->aby, op->partials, op->nblocks,
+                            op->stream);
+  reduce_partials(op->partials, op->nblocks, 1, op->dscal, op->stream);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(op->h_scal, op->dscal, sizeof(double), cudaMemcpyDeviceToHost, op->stream));
+  CUDA_TRY(cudaStreamSynchronize(op->stream));
+  *out = op->h_scal[0];
+  return AD_OK;
+}
+
+// A x (+ sources) in the storage type.
+void apply(ad_operator* op, const void* u, void* out1, void* out2, const Sources& src) {
+  if (op->prec == 0)
+    apply_f64(op->g, op->W, (const double*)u, (double*)out1, (double*)out2, src, op->stream);
+  else
+    apply_f32(op->g, op->F, op->adv, op->abx, op->aby, (const float*)u, (float*)out1,
+              (float*)out2, src, op->stream);
+}
+
+// Upload the per-iteration scalars of a series.
+//   kind 0: phi_1 at step h (no augmented coupling);
+//   kind 1: exp at step h, augmented coupling from eta0 (e1_m, e2_m filled).
+// Returns d_0 in *d0 and, for kind 1, the eta part of the series sum in eta_out.
+int upload_series(ad_operator* op, int kind, double h, const double eta0[2], double* d0,
+                  double eta_out[2]) {
+  const std::vector<double>& xi = leja_points();
+  const int M = kMaxIters + 1;
+  const bool cached = op->cache_kind == kind && op->cache_h == h && op->cache_alpha == op->alpha;
+  if (!cached) {
+    std::vector<double> f(M);
+    for (int m = 0; m < M; ++m) {
+      const double z = (op->c + op->gamma * xi[m]) * h;
+      f[m] = kind == 0 ? phi1(z) : std::exp(z);
+    }
+    op->d_host.assign(M, 0.0);
+    divided_differences(xi.data(), f.data(), M, op->d_host.data());
+  }
+  const std::vector<double>& d = op->d_host;
+  double e1 = 0.0, e2 = 0.0, pe1 = 0.0, pe2 = 0.0;
+  if (kind == 1) {
+    e1 = eta0[0];
+    e2 = eta0[1];
+    pe1 = d[0] * e1;
+    pe2 = d[0] * e2;
+  }
+  for (int m = 0; m < kMaxIters; ++m) {
+    LejaCoef& L = op->h_lc[m];
+    L.xi = xi[m];
+    L.d = d[m + 1];
+    L.absd = std::fabs(d[m + 1]);
+    L.e1 = kind == 1 ? e1 / op->gamma : 0.0;
+    L.e2 = kind == 1 ? e2 / op->gamma : 0.0;
+    if (kind == 1) {
+      // eta_{m+1} = ((J - c)/gamma - xi_m) eta_m with J = [[0, 1], [0, 0]]
+      const double n1 = (e2 - op->c * e1) / op->gamma - xi[m] * e1;
+      const double n2 = (-op->c * e2) / op->gamma - xi[m] * e2;
+      e1 = n1;
+      e2 = n2;
+    }
+  }
+  CUDA_TRY(cudaMemcpyAsync(op->lc, op->h_lc, sizeof(LejaCoef) * kMaxIters, cudaMemcpyHostToDevice,
+                           op->stream));
+  op->cache_kind = kind;
+  op->cache_h = h;
+  op->cache_alpha = op->alpha;
+  *d0 = d[0];
+  if (kind == 1) {
+    eta_out[0] = pe1;
+    eta_out[1] = pe2;
+  }
+  return AD_OK;
+}
+
+// Run one Newton series from src (device vector of the storage type, or null
+// for a zero start); the result is left in op->P.  *iters receives the
+// number of iterations; the eta part (augmented series) is accumulated on
+// the host into eta_sum using the uploaded d.
+int run_series(ad_operator* op, int aug, const void* src, double d0, int force, double tol,
+               ad_stats* st, int* iters_out) {
+  SeriesArgs a = series_args(op, aug);
+  series_init(a, src, d0, force, op->max_iters, tol, op->stream);
+  CUDA_TRY(cudaGetLastError());
+  int iters = 0;
+  bool graph_used = false;
+  if (force == 0) {
+    iters = 0;
+    op->h_ctrl->status = 0;
+    op->h_ctrl->err_est = 0.0;
+  } else {
+    SeriesGraph& sg = op->graphs[aug];
+    if (!sg.tried) build_graph(op, aug);
+    if (sg.ok) {
+      CUDA_TRY(cudaGraphLaunch(sg.exec, op->stream));
+      graph_used = true;
+    } else {  // host-driven fallback: chunks of iterations, poll the stop flag
+      int launched = 0;
+      for (;;) {
+        const int chunk = 16;
+        for (int k = 0; k < chunk; ++k) {
+          series_iteration(a, op->stream);
+          series_control(a, 0ULL, 0, op->stream);
+        }
+        launched += chunk;
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaMemcpyAsync(op->h_ctrl, op->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, op->stream));
+        CUDA_TRY(cudaStreamSynchronize(op->stream));
+        if (op->h_ctrl->stop || launched >= kMaxIters + chunk) break;
+      }
+    }
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(op->h_ctrl, op->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, op->stream));
+    CUDA_TRY(cudaStreamSynchronize(op->stream));
+    iters = op->h_ctrl->iters;
+    if (!op->h_ctrl->stop) return fail(AD_ERR_TIMEOUT, "Leja series did not reach its stop state");
+    // graph bodies: fused iteration + control kernel per iteration (host launches
+    // are counted by the launchers themselves)
+    if (st && graph_used) st->kernel_launches += 2 * iters;
+  }
+  if (st) {
+    st->iters += iters;
+    st->matvecs += iters;
+    st->err_est = std::max(st->err_est, op->h_ctrl->err_est);
+    if (op->h_ctrl->status != 0) st->converged = 0;
+  }
+  *iters_out = iters;
+  return op->h_ctrl->status == 0 ? AD_OK : AD_ERR_NOT_CONVERGED;
+}
+
+int n_substeps(const ad_operator* op, double dt) {
+  const double rho = op->gamma * dt;
+  if (rho <= op->rho_max) return 1;
+  return (int)std::ceil(rho / op->rho_max);
+}
+
+int ensure_staging(ad_operator* op) {
+  const size_t bytes = (size_t)op->g.n * op->esz;
+  if (!op->S0) {
+    if (cudaMalloc(&op->S0, bytes) != cudaSuccess) { cudaGetLastError(); return fail(AD_ERR_NOMEM, "staging buffer"); }
+    if (cudaMalloc(&op->S1, bytes) != cudaSuccess) { cudaGetLastError(); return fail(AD_ERR_NOMEM, "staging buffer"); }
+  }
+  return AD_OK;
+}
+
+// Bring a caller vector to the device: returns the device pointer to use and
+// whether the result must be copied back.
+int stage_in(ad_operator* op, const void* user, void* slot, const void** dev, bool copy) {
+  if (is_device_ptr(user)) { *dev = user; return AD_OK; }
+  AD_TRY(ensure_staging(op));
+  if (copy)
+    CUDA_TRY(cudaMemcpyAsync(slot, user, (size_t)op->g.n * op->esz, cudaMemcpyHostToDevice, op->stream));
+  *dev = slot;
+  return AD_OK;
+}
+
+int finish_out(ad_operator* op, void* user, const void* dev) {
+  if (dev != user)
+    CUDA_TRY(cudaMemcpyAsync(user, dev, (size_t)op->g.n * op->esz, cudaMemcpyDeviceToHost, op->stream));
+  CUDA_TRY(cudaStreamSynchronize(op->stream));
+  return AD_OK;
+}
+
+int fill_sources(const ad_source* src, int nterms_max, Sources* out) {
+  *out = Sources{};
+  if (!src) return AD_OK;
+  if (src->nterms < 0 || src->nterms > nterms_max)
+    return fail(AD_ERR_INVALID, "source: nterms out of range [0, 16]");
+  if (src->nterms > 0 && !src->g) return fail(AD_ERR_INVALID, "source: g is NULL");
+  for (int k = 0; k < src->nterms; ++k) {
+    if (!is_device_ptr(src->g[k])) return fail(AD_ERR_INVALID, "source: g[k] must be a device pointer");
+    out->g[k] = src->g[k];
+  }
+  out->n = src->nterms;
+  return AD_OK;
+}
+
+double h_at(const ad_source* src, int k, double t) {
+  return (src && src->h) ? src->h(k, t, src->ctx) : 1.0;
+}
+
+// out_dev (storage type) = phi_1(dt A) v_dev; v_dev must not alias T1/T2/T3.
+int phi1_device(ad_operator* op, const void* v_dev, void* out_dev, double dt, double tol,
+                int force, ad_stats* st) {
+  const int K = n_substeps(op, dt);
+  const double h = dt / K;
+  double d0;
+  AD_TRY(upload_series(op, 0, h, nullptr, &d0, nullptr));
+  if (st) st->substeps = K;
+  int status = AD_OK, it = 0;
+  const long long n = op->g.n;
+  if (K == 1) {
+    int r = run_series(op, 0, v_dev, d0, force, tol, st, &it);
+    if (r != AD_OK && r != AD_ERR_NOT_CONVERGED) return r;
+    status = r;
+    axpby(op->prec, n, 1.0, op->P, 0.0, nullptr, out_dev, op->stream);
+  } else {
+    // w_{k+1} = w_k + h phi_1(h A)(A w_k + v), w_0 = 0; out = w_K / dt
+    axpby(op->prec, n, 1.0, v_dev, 0.0, nullptr, op->T1, op->stream);   // v
+    axpby(op->prec, n, 0.0, nullptr, 0.0, nullptr, op->T2, op->stream); // w
+    Sources none{};
+    for (int k = 0; k < K; ++k) {
+      const void* rhs = op->T1;
+      if (k > 0) {
+        apply(op, op->T2, op->T3, nullptr, none);
+        axpby(op->prec, n, 1.0, op->T3, 1.0, op->T1, op->T3, op->stream);
+        rhs = op->T3;
+        if (st) st->matvecs += 1;
+      }
+      int r = run_series(op, 0, rhs, d0, force, tol, st, &it);
+      if (r != AD_OK && r != AD_ERR_NOT_CONVERGED) return r;
+      if (r != AD_OK) status = r;
+      axpby(op->prec, n, 1.0, op->T2, h, op->P, op->T2, op->stream);
+    }
+    axpby(op->prec, n, 1.0 / dt, op->T2, 0.0, nullptr, out_dev, op->stream);
+  }
+  CUDA_TRY(cudaGetLastError());
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ad_version(void) { return 10000; }
+
+const char* ad_last_error(void) { return g_err.c_str(); }
+
+int ad_create_operator(const ad_grid* grid, const double* Dxx, const double* Dxy, const double* Dyy,
+                       const double* ax, const double* ay, double ax_c, double ay_c, int precision,
+                       void* cuda_stream, ad_operator** out) {
+  g_err.clear();
+  if (!out) return fail(AD_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!grid || !Dxx || !Dxy || !Dyy) return fail(AD_ERR_INVALID, "grid or D field is NULL");
+  if (grid->nx < 1 || grid->ny < 1) return fail(AD_ERR_INVALID, "grid: nx, ny must be >= 1");
+  if ((long long)grid->nx * grid->ny > (1LL << 31) - 1) return fail(AD_ERR_INVALID, "grid: too many cells");
+  if (!(grid->x1 > grid->x0) || !(grid->y1 > grid->y0)) return fail(AD_ERR_INVALID, "grid: empty domain");
+  if (grid->bc != AD_BC_PERIODIC && grid->bc != AD_BC_DIRICHLET0) return fail(AD_ERR_INVALID, "grid: bad bc");
+  if (precision != AD_FP64 && precision != AD_FP32_STORAGE) return fail(AD_ERR_INVALID, "bad precision");
+  for (const void* p : {(const void*)Dxx, (const void*)Dxy, (const void*)Dyy})
+    if (!is_device_ptr(p)) return fail(AD_ERR_INVALID, "coefficient fields must be device pointers");
+  if ((ax && !is_device_ptr(ax)) || (ay && !is_device_ptr(ay)))
+    return fail(AD_ERR_INVALID, "advection fields must be device pointers");
+  if (!std::isfinite(ax_c) || !std::isfinite(ay_c)) return fail(AD_ERR_INVALID, "advection constants");
+
+  ad_operator* op = new ad_operator();
+  op->grid = *grid;
+  op->g.nx = grid->nx;
+  op->g.ny = grid->ny;
+  op->g.bc = grid->bc;
+  op->g.n = (long long)grid->nx * grid->ny;
+  op->prec = precision;
+  op->esz = precision == AD_FP64 ? 8 : 4;
+  op->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&op->dev);
+  const double dx = (grid->x1 - grid->x0) / grid->nx, dy = (grid->y1 - grid->y0) / grid->ny;
+  const long long n = op->g.n;
+  op->nblocks = stream_blocks(n);
+  op->ax_c = ax_c;
+  op->ay_c = ay_c;
+  op->adv = (ax || ay) ? 2 : ((ax_c != 0.0 || ay_c != 0.0) ? 1 : 0);
+  op->abx = (float)(ax_c / (2.0 * dx));
+  op->aby = (float)(ay_c / (2.0 * dy));
+
+  auto alloc = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes) != cudaSuccess) { cudaGetLastError(); return false; }
+    return true;
+  };
+  bool ok = true;
+  if (precision == AD_FP64) {
+    ok = ok && alloc((void**)&op->W, sizeof(double) * 9 * n);
+    ok = ok && alloc((void**)&op->Ws, sizeof(double) * 9 * n);
+  } else {
+    ok = ok && alloc((void**)&op->F, sizeof(float) * (op->adv == 2 ? 5 : 3) * n);
+  }
+  for (void** v : {&op->Y0, &op->Y1, &op->P, &op->W1, &op->W2, &op->T1, &op->T2, &op->T3})
+    ok = ok && alloc(v, op->esz * n);
+  op->partials_len = std::max<size_t>(2 * (size_t)op->nblocks, (size_t)(kMaxGmres + 2) * op->nblocks);
+  ok = ok && alloc((void**)&op->partials, sizeof(double) * op->partials_len);
+  ok = ok && alloc((void**)&op->lc, sizeof(LejaCoef) * kMaxIters);
+  ok = ok && alloc((void**)&op->ctrl, sizeof(Ctrl));
+  ok = ok && alloc((void**)&op->dscal, sizeof(double) * 4 * (kMaxGmres + 2));
+  if (ok) ok = cudaMallocHost((void**)&op->h_lc, sizeof(LejaCoef) * kMaxIters) == cudaSuccess;
+  if (ok) ok = cudaMallocHost((void**)&op->h_ctrl, sizeof(Ctrl)) == cudaSuccess;
+  if (ok) ok = cudaMallocHost((void**)&op->h_scal, sizeof(double) * 4 * (kMaxGmres + 2)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    ad_destroy_operator(op);
+    return fail(AD_ERR_NOMEM, "device allocation failed");
+  }
+  std::memset(op->h_ctrl, 0, sizeof(Ctrl));
+  cudaMemsetAsync(op->ctrl, 0, sizeof(Ctrl), op->stream);
+  if (precision == AD_FP64)
+    pack_weights_f64(op->g, dx, dy, Dxx, Dxy, Dyy, ax, ay, ax_c, ay_c, op->W, op->stream);
+  else
+    pack_fields_f32(op->g, dx, dy, Dxx, Dxy, Dyy, ax, ay, ax_c, ay_c, op->F, op->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ad_destroy_operator(op);
+    return fail(AD_ERR_CUDA, std::string("pack kernel: ") + cudaGetErrorString(e));
+  }
+  (void)leja_points();  // computed once per process
+  double alpha = 0.0;
+  int r = gershgorin(op, &alpha);
+  if (r == AD_OK) {
+    if (!(alpha < 0.0)) alpha = -1.0;  // A == 0: any negative bound serves
+    r = set_alpha(op, alpha);
+  }
+  if (r != AD_OK) {
+    std::string msg = g_err;
+    ad_destroy_operator(op);
+    return fail(r, msg);
+  }
+  *out = op;
+  return AD_OK;
+}
+
+int ad_destroy_operator(ad_operator* op) {
+  if (!op) return AD_OK;
+  if (op->stream) cudaStreamSynchronize(op->stream);
+  destroy_graphs(op);
+  if (op->cap_stream) cudaStreamDestroy(op->cap_stream);
+  for (void* p : {(void*)op->W, (void*)op->Ws, (void*)op->F, op->Y0, op->Y1, op->P, op->W1, op->W2,
+                  op->T1, op->T2, op->T3, op->S0, op->S1, (void*)op->Vk, (void*)op->lc,
+                  (void*)op->ctrl, (void*)op->partials, (void*)op->dscal})
+    if (p) cudaFree(p);
+  if (op->h_lc) cudaFreeHost(op->h_lc);
+  if (op->h_ctrl) cudaFreeHost(op->h_ctrl);
+  if (op->h_scal) cudaFreeHost(op->h_scal);
+  delete op;
+  return AD_OK;
+}
+
+int ad_set_options(ad_operator* op, double rho_max, int max_iters) {
+  g_err.clear();
+  if (!op) return fail(AD_ERR_INVALID, "op is NULL");
+  if (max_iters > kMaxIters) return fail(AD_ERR_INVALID, "max_iters > 500");
+  if (rho_max > 0) op->rho_max = rho_max;
+  if (max_iters > 0) op->max_iters = max_iters;
+  return AD_OK;
+}
+
+int ad_set_spectral_bound(ad_operator* op, double alpha) {
+  g_err.clear();
+  if (!op) return fail(AD_ERR_INVALID, "op is NULL");
+  return set_alpha(op, alpha);
+}
+
+int ad_get_spectral_bound(const ad_operator* op, double* alpha) {
+  if (!op || !alpha) return fail(AD_ERR_INVALID, "NULL argument");
+  *alpha = op->alpha;
+  return AD_OK;
+}
+
+int ad_spectral_bound(ad_operator* op, int method, const void* x0, unsigned long long seed,
+                      int power_iters, double safety, double* alpha) {
+  g_err.clear();
+  if (!op || !alpha) return fail(AD_ERR_INVALID, "NULL argument");
+  double a = 0.0;
+  if (method == AD_BOUND_GERSHGORIN) {
+    AD_TRY(gershgorin(op, &a));
+  } else if (method == AD_BOUND_POWER) {
+    if (power_iters < 1 || !(safety > 0)) return fail(AD_ERR_INVALID, "power_iters >= 1, safety > 0");
+    const long long n = op->g.n;
+    const void* x0d = nullptr;
+    if (x0) AD_TRY(stage_in(op, x0, op->T3, &x0d, true));
+    if (x0d) axpby(op->prec, n, 1.0, x0d, 0.0, nullptr, op->T1, op->stream);
+    else splitmix_fill(op->prec, n, seed, op->T1, op->stream);
+    // x <- x0 / ||x0||
+    norm2_partials(op->prec, n, op->T1, op->partials, op->nblocks, op->stream);
+    reduce_partials(op->partials, op->nblocks, 2, op->dscal, op->stream);
+    scale_by_inv(op->prec, n, op->T1, op->dscal, op->T1, op->stream);
+    Sources none{};
+    for (int it = 0; it < power_iters; ++it) {
+      apply(op, op->T1, op->T2, nullptr, none);                          // y = A x
+      norm2_partials(op->prec, n, op->T2, op->partials, op->nblocks, op->stream);
+      reduce_partials(op->partials, op->nblocks, 2, op->dscal, op->stream);  // est = ||y||
+      scale_by_inv(op->prec, n, op->T2, op->dscal, op->T1, op->stream);      // x = y / est
+    }
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(op->h_scal, op->dscal, sizeof(double), cudaMemcpyDeviceToHost, op->stream));
+    CUDA_TRY(cudaStreamSynchronize(op->stream));
+    a = -safety * op->h_scal[0];
+  } else {
+    return fail(AD_ERR_INVALID, "unknown spectral bound method");
+  }
+  if (!(a < 0.0)) return fail(AD_ERR_INVALID, "spectral bound is not negative (A == 0?)");
+  AD_TRY(set_alpha(op, a));
+  *alpha = a;
+  return AD_OK;
+}
+
+int ad_apply(ad_operator* op, const void* u, void* Au) {
+  g_err.clear();
+  if (!op || !u || !Au) return fail(AD_ERR_INVALID, "NULL argument");
+  const void* ud;
+  AD_TRY(stage_in(op, u, op->T3, &ud, true));
+  void* od = is_device_ptr(Au) ? Au : nullptr;
+  if (!od) { AD_TRY(ensure_staging(op)); od = op->S1; }
+  Sources none{};
+  apply(op, ud, od, nullptr, none);
+  CUDA_TRY(cudaGetLastError());
+  return finish_out(op, Au, od);
+}
+
+int ad_leja_phi1(ad_operator* op, const void* v, void* out, double dt, double tol, int force_iters,
+                 ad_stats* stats) {
+  g_err.clear();
+  if (!op || !v || !out) return fail(AD_ERR_INVALID, "NULL argument");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(AD_ERR_INVALID, "dt must be positive");
+  if (force_iters < 0 && !(tol > 0)) return fail(AD_ERR_INVALID, "tol must be positive");
+  if (force_iters > op->max_iters) return fail(AD_ERR_INVALID, "force_iters > max_iters");
+  ad_stats st{};
+  st.converged = 1;
+  st.alpha = op->alpha;
+  const long long l0 = launch_counter();
+  const void* vd;
+  AD_TRY(stage_in(op, v, op->S0, &vd, true));
+  void* od = is_device_ptr(out) ? out : nullptr;
+  if (!od) { AD_TRY(ensure_staging(op)); od = op->S1; }
+  int r = phi1_device(op, vd, od, dt, tol, force_iters < 0 ? -1 : force_iters, &st);
+  if (r != AD_OK && r != AD_ERR_NOT_CONVERGED) return r;
+  AD_TRY(finish_out(op, out, od));
+  st.kernel_launches += (int)(launch_counter() - l0);
+  if (stats) *stats = st;
+  if (r == AD_ERR_NOT_CONVERGED) return fail(r, "Leja series reached max_iters");
+  return AD_OK;
+}
+
+int ad_expquad_step(ad_operator* op, void* u, double t, double dt, int s, const double* c,
+                    const ad_source* src, double tol, int force_iters, ad_stats* stats) {
+  g_err.clear();
+  if (!op || !u || !c) return fail(AD_ERR_INVALID, "NULL argument");
+  if (!(dt > 0) || !std::isfinite(dt) || !std::isfinite(t)) return fail(AD_ERR_INVALID, "bad t or dt");
+  if (s != 1 && s != 2) return fail(AD_ERR_INVALID, "s must be 1 or 2");
+  if (s == 2 && !(c[0] != c[1])) return fail(AD_ERR_INVALID, "s = 2 needs c[0] != c[1]");
+  if (force_iters < 0 && !(tol > 0)) return fail(AD_ERR_INVALID, "tol must be positive");
+  if (force_iters > op->max_iters) return fail(AD_ERR_INVALID, "force_iters > max_iters");
+  Sources S;
+  AD_TRY(fill_sources(src, kMaxSources, &S));
+  ad_stats st{};
+  st.converged = 1;
+  st.alpha = op->alpha;
+  const long long l0 = launch_counter();
+  const void* ud_c;
+  AD_TRY(stage_in(op, u, op->S0, &ud_c, true));
+  void* ud = const_cast<void*>(ud_c);
+  const long long n = op->g.n;
+  const int force = force_iters < 0 ? -1 : force_iters;
+  int status = AD_OK;
+  if (s == 1) {
+    // v = A u + S(t + c1 dt);  u += dt phi_1(dt A) v   (Eq. exp_midpoint for c1 = 1/2)
+    for (int k = 0; k < S.n; ++k) S.a[k] = h_at(src, k, t + c[0] * dt);
+    apply(op, ud, op->W1, nullptr, S);
+    st.matvecs += 1;
+    const int r = phi1_device(op, op->W1, op->W2, dt, tol, force, &st);
+    if (r != AD_OK && r != AD_ERR_NOT_CONVERGED) return r;
+    status = r;
+    axpby(op->prec, n, 1.0, ud, dt, op->W2, ud, op->stream);
+  } else {
+    // w1 = A u + (c2 S1 - c1 S2)/(c2 - c1), w2 = (S2 - S1)/((c2 - c1) dt);
+    // u += top block of exp(dt [[A, W], [0, J]]) [0; 0; 1]
+    const double c1 = c[0], c2 = c[1];
+    for (int k = 0; k < S.n; ++k) {
+      const double h1 = h_at(src, k, t + c1 * dt), h2 = h_at(src, k, t + c2 * dt);
+      S.a[k] = (c2 * h1 - c1 * h2) / (c2 - c1);
+      S.b[k] = (h2 - h1) / ((c2 - c1) * dt);
+    }
+    apply(op, ud, op->W1, op->W2, S);
+    st.matvecs += 1;
+    const int K = n_substeps(op, dt);
+    const double h = dt / K;
+    st.substeps = K;
+    double eta[2] = {0.0, 1.0};
+    for (int k = 0; k < K; ++k) {
+      double d0, eta_next[2];
+      AD_TRY(upload_series(op, 1, h, eta, &d0, eta_next));
+      int it = 0;
+      const int r = run_series(op, 1, k == 0 ? nullptr : op->T2, d0, force, tol, &st, &it);
+      if (r != AD_OK && r != AD_ERR_NOT_CONVERGED) return r;
+      if (r != AD_OK) status = r;
+      // eta part of the series sum: sum_m d_m eta_m (scalar, host)
+      {
+        const std::vector<double>& d = op->d_host;
+        double e1 = eta[0], e2 = eta[1];
+        double s1 = d[0] * e1, s2 = d[0] * e2;
+        const std::vector<double>& xi = leja_points();
+        for (int m = 0; m < it; ++m) {
+          const double n1 = (e2 - op->c * e1) / op->gamma - xi[m] * e1;
+          const double n2 = (-op->c * e2) / op->gamma - xi[m] * e2;
+          e1 = n1;
+          e2 = n2;
+          s1 += d[m + 1] * e1;
+          s2 += d[m + 1] * e2;
+        }
+        eta[0] = s1;
+        eta[1] = s2;
+        (void)eta_next;
+      }
+      if (K > 1) axpby(op->prec, n, 1.0, op->P, 0.0, nullptr, op->T2, op->stream);
+    }
+    axpby(op->prec, n, 1.0, ud, 1.0, K > 1 ? op->T2 : op->P, ud, op->stream);
+  }
+  CUDA_TRY(cudaGetLastError());
+  AD_TRY(finish_out(op, u, ud));
+  st.kernel_launches += (int)(launch_counter() - l0);
+  if (stats) *stats = st;
+  if (status == AD_ERR_NOT_CONVERGED) return fail(status, "Leja series reached max_iters");
+  return AD_OK;
+}
+
+int ad_cn_step(ad_operator* op, void* u, double t, double dt, const ad_source* src,
+               double gmres_tol, int restart, int force_iters, ad_stats* stats) {
+  g_err.clear();
+  if (!op || !u) return fail(AD_ERR_INVALID, "NULL argument");
+  if (op->prec != AD_FP64) return fail(AD_ERR_INVALID, "ad_cn_step needs an AD_FP64 operator");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(AD_ERR_INVALID, "dt must be positive");
+  if (restart < 1 || restart > kMaxGmres) return fail(AD_ERR_INVALID, "restart must be in [1, 200]");
+  if (force_iters > restart) return fail(AD_ERR_INVALID, "force_iters > restart");
+  if (force_iters <= 0 && !(gmres_tol > 0)) return fail(AD_ERR_INVALID, "gmres_tol must be positive");
+  Sources S;
+  AD_TRY(fill_sources(src, kMaxSources, &S));
+  const long long n = op->g.n;
+  const int m = force_iters > 0 ? force_iters : restart;
+  if (op->vk_cols < m + 1) {
+    if (op->Vk) cudaFree(op->Vk);
+    op->Vk = nullptr;
+    op->vk_cols = 0;
+    if (cudaMalloc(&op->Vk, sizeof(double) * (size_t)(m + 1) * n) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(AD_ERR_NOMEM, "GMRES basis");
+    }
+    op->vk_cols = m + 1;
+  }
+  ad_stats st{};
+  st.converged = 1;
+  st.alpha = op->alpha;
+  const long long l0 = launch_counter();
+  const void* ud_c;
+  AD_TRY(stage_in(op, u, op->S0, &ud_c, true));
+  double* x = (double*)const_cast<void*>(ud_c);
+  double* b = (double*)op->T1;
+  double* w = (double*)op->T2;
+  double* V = op->Vk;
+  const int nb = op->nblocks;
+  cudaStream_t s = op->stream;
+  // b = u + dt/2 A u + dt/2 (S(t) + S(t + dt))
+  for (int k = 0; k < S.n; ++k) S.a[k] = 0.5 * dt * (h_at(src, k, t) + h_at(src, k, t + dt));
+  {
+    Sources none{};
+    apply_shifted_f64(op->g, op->W, x, b, 1.0, 0.5 * dt, s);
+    if (S.n > 0) {
+      // add the source combination: b += sum a_k g_k  (apply with zero field -> sources only)
+      for (int k = 0; k < S.n; ++k)
+        axpby(0, n, S.a[k], S.g[k], 1.0, b, b, s);
+    }
+    (void)none;
+  }
+  st.matvecs += 1;
+  auto read_scalars = [&](int count) -> int {
+    CUDA_TRY(cudaMemcpyAsync(op->h_scal, op->dscal, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return AD_OK;
+  };
+  norm2_partials(0, n, b, op->partials, nb, s);
+  reduce_partials(op->partials, nb, 2, op->dscal, s);
+  AD_TRY(read_scalars(1));
+  const double bnorm = op->h_scal[0];
+  if (bnorm == 0.0) {
+    axpby(0, n, 0.0, nullptr, 0.0, nullptr, x, s);
+    AD_TRY(finish_out(op, u, x));
+    if (stats) *stats = st;
+    return AD_OK;
+  }
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  auto Hc = [&](int i, int k) -> double& { return H[(size_t)i * m + k]; };
+  int total_iters = 0;
+  const int max_total = force_iters > 0 ? force_iters : 5000;
+  for (;;) {
+    // r = b - M x, M = I - dt/2 A
+    apply_shifted_f64(op->g, op->W, x, w, 1.0, -0.5 * dt, s);
+    axpby(0, n, 1.0, b, -1.0, w, V, s);
+    st.matvecs += 1;
+    norm2_partials(0, n, V, op->partials, nb, s);
+    reduce_partials(op->partials, nb, 2, op->dscal, s);
+    AD_TRY(read_scalars(1));
+    const double beta = op->h_scal[0];
+    st.err_est = beta / bnorm;
+    if (force_iters <= 0 && (beta / bnorm <= gmres_tol || total_iters >= max_total)) {
+      st.converged = beta / bnorm <= gmres_tol;
+      break;
+    }
+    axpby(0, n, 1.0 / beta, V, 0.0, nullptr, V, s);
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int kused = 0;
+    for (int k = 0; k < m; ++k) {
+      double* Vk = V + (size_t)k * n;
+      double* Vn = V + (size_t)(k + 1) * n;
+      apply_shifted_f64(op->g, op->W, Vk, Vn, 1.0, -0.5 * dt, s);
+      st.matvecs += 1;
+      ++total_iters;
+      // classical Gram-Schmidt, twice
+      multi_dot_partials(n, V, n, k + 1, Vn, op->partials, nb, s);
+      multi_dot_finalize(op->partials, nb, k + 1, op->dscal, s);
+      multi_axpy_norm(n, V, n, k + 1, op->dscal, Vn, op->partials, nb, s);
+      multi_dot_partials(n, V, n, k + 1, Vn, op->partials, nb, s);
+      multi_dot_finalize(op->partials, nb, k + 1, op->dscal + (k + 1), s);
+      multi_axpy_norm(n, V, n, k + 1, op->dscal + (k + 1), Vn, op->partials, nb, s);
+      reduce_partials(op->partials, nb, 2, op->dscal + 2 * (k + 1), s);
+      CUDA_TRY(cudaGetLastError());
+      AD_TRY(read_scalars(2 * (k + 1) + 1));
+      for (int i = 0; i <= k; ++i) Hc(i, k) = op->h_scal[i] + op->h_scal[k + 1 + i];
+      const double hk1 = op->h_scal[2 * (k + 1)];
+      Hc(k + 1, k) = hk1;
+      if (hk1 != 0.0) axpby(0, n, 1.0 / hk1, Vn, 0.0, nullptr, Vn, s);
+      for (int i = 0; i < k; ++i) {
+        const double tmp = cs[i] * Hc(i, k) + sn[i] * Hc(i + 1, k);
+        Hc(i + 1, k) = -sn[i] * Hc(i, k) + cs[i] * Hc(i + 1, k);
+        Hc(i, k) = tmp;
+      }
+      const double den = std::hypot(Hc(k, k), Hc(k + 1, k));
+      cs[k] = Hc(k, k) / den;
+      sn[k] = Hc(k + 1, k) / den;
+      Hc(k, k) = den;
+      Hc(k + 1, k) = 0.0;
+      g[k + 1] = -sn[k] * g[k];
+      g[k] = cs[k] * g[k];
+      kused = k + 1;
+      if (force_iters <= 0 && (std::fabs(g[k + 1]) <= gmres_tol * bnorm || total_iters >= max_total))
+        break;
+    }
+    for (int i = kused - 1; i >= 0; --i) {      // back substitution
+      double r = g[i];
+      for (int j = i + 1; j < kused; ++j) r -= Hc(i, j) * y[j];
+      y[i] = r / Hc(i, i);
+    }
+    CUDA_TRY(cudaMemcpyAsync(op->dscal, y.data(), sizeof(double) * kused, cudaMemcpyHostToDevice, s));
+    multi_axpy_add(n, V, n, kused, op->dscal, x, s);
+    CUDA_TRY(cudaStreamSynchronize(s));     // y lives on the host stack
+    if (force_iters > 0) {
+      st.err_est = std::fabs(g[kused]) / bnorm;
+      break;
+    }
+  }
+  st.iters = total_iters;
+  CUDA_TRY(cudaGetLastError());
+  AD_TRY(finish_out(op, u, x));
+  st.kernel_launches += (int)(launch_counter() - l0);
+  if (stats) *stats = st;
+  if (!st.converged) return fail(AD_ERR_NOT_CONVERGED, "GMRES reached its iteration cap");
+  return AD_OK;
+}
+
+int ad_profile_leja_iteration(ad_operator* op, int aug, int reps, double* ms_per_launch) {
+  g_err.clear();
+  if (!op || !ms_per_launch) return fail(AD_ERR_INVALID, "NULL argument");
+  if (aug != 0 && aug != 1) return fail(AD_ERR_INVALID, "aug must be 0 or 1");
+  if (reps < 1 || reps > kMaxIters) return fail(AD_ERR_INVALID, "reps must be in [1, 500]");
+  // a forced series on a SplitMix64 start vector with couplings w1 = w2 = start
+  double d0 = 0.0, eta[2] = {0.0, 1.0}, eta_out[2];
+  AD_TRY(upload_series(op, aug, 1e-3 / op->gamma, eta, &d0, eta_out));
+  splitmix_fill(op->prec, op->g.n, 7ULL, op->W1, op->stream);
+  splitmix_fill(op->prec, op->g.n, 8ULL, op->W2, op->stream);
+  SeriesArgs a = series_args(op, aug);
+  series_init(a, op->W1, d0, reps, op->max_iters, 0.0, op->stream);
+  std::vector<cudaEvent_t> ev(2 * reps);
+  for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
+  for (int r = 0; r < reps; ++r) {
+    CUDA_TRY(cudaEventRecord(ev[2 * r], op->stream));
+    series_iteration(a, op->stream);
+    CUDA_TRY(cudaEventRecord(ev[2 * r + 1], op->stream));
+    series_control(a, 0ULL, 0, op->stream);
+  }
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(op->stream));
+  double total = 0.0;
+  for (int r = 0; r < reps; ++r) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]));
+    total += ms;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  op->cache_kind = -1;
+  *ms_per_launch = total / reps;
+  return AD_OK;
+}
+
+}  // extern "C"
