@@ -21,8 +21,8 @@ def _declared():
 def ad():
     lib = os.path.join(ROOT, "paper_2307_12276_gb300", "libanidiff.so")
     if not os.path.exists(lib):
-        from paper_2307_12276_gb300 import build as b
-        b.build()
+        import __graft_entry__
+        __graft_entry__._builder().build()
     import paper_2307_12276_gb300 as mod
     return mod
 
