@@ -62,9 +62,11 @@ def problem(name):
 
 
 # --------------------------------------------------------------------------- oracle leg
-def oracle_sample(workload: str, seconds: float, max_steps: int, out_npy: str | None):
+def oracle_sample(workload: str, seconds: float, max_steps: int, out_npy: str | None,
+                  warmup: int = 0):
     """Run the CPU oracle from the workload's initial state for about
-    ``seconds`` (at least one step); returns a dict with its throughput."""
+    ``seconds`` (at least one step) after ``warmup`` untimed steps; returns a
+    dict with its throughput."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = f"""
 import json, sys, time
@@ -77,6 +79,9 @@ A = oop.assemble(p.grid, p.Dxx, p.Dxy, p.Dyy, p.ax_arr(), p.ay_arr())
 alpha = spectral.gershgorin(A)
 S = lambda t: p.source_at(t).ravel()
 u, t, steps, iters = p.u0.ravel().copy(), 0.0, 0, 0
+for _ in range({warmup}):
+    u, st = integrators.expquad_step(A, u, t, p.dt, p.s, p.c, S, alpha, tol=p.tol)
+    t += p.dt
 t0 = time.perf_counter()
 while True:
     u, st = integrators.expquad_step(A, u, t, p.dt, p.s, p.c, S, alpha, tol=p.tol)
@@ -102,13 +107,14 @@ def run_reference(args):
     if rank != 0:
         return
     # each of the K steps is one oracle step of the same workload (about 0.5 s each)
-    d = oracle_sample(args.workload, seconds=1e9, max_steps=max(1, args.steps), out_npy=None)
+    d = oracle_sample(args.workload, seconds=1e9, max_steps=max(1, args.steps), out_npy=None,
+                      warmup=args.warmup)
     line = {
         "impl": "reference", "metric": "Mcell-steps/s", "value": round(d["value"], 6),
-        "unit": "Mcell-steps/s", "n_gpus": args.gpus, "steps": d["steps"], "warmup": 0,
+        "unit": "Mcell-steps/s", "n_gpus": args.gpus, "steps": d["steps"],
         "ms_per_step": 1e3 * d["seconds"] / d["steps"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "cells": d["cells"]},
+        "config": {"workload": args.workload, "cells": d["cells"]}, "warmup": args.warmup,
         "cpu_baseline": {"value": round(d["value"], 6), "unit": "Mcell-steps/s", "cores": 1,
                          "kind": "oracle",
                          "sample": f"{d['steps']} full exponential quadrature steps from t=0"},

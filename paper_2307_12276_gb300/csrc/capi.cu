@@ -36,11 +36,15 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+// On failure the runtime's pending (non-sticky) error is cleared so that it is
+// not reported again by a later, unrelated call.
 #define CUDA_TRY(expr)                                                                    \
   do {                                                                                    \
     cudaError_t e_ = (expr);                                                              \
-    if (e_ != cudaSuccess)                                                                \
+    if (e_ != cudaSuccess) {                                                              \
+      cudaGetLastError();                                                                 \
       return fail(AD_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));       \
+    }                                                                                     \
   } while (0)
 
 #define AD_TRY(expr)              \
@@ -368,9 +372,10 @@ int ensure_staging(ad_operator* op) {
 
 // Bring a caller vector to the device: returns the device pointer to use and
 // whether the result must be copied back.
-int stage_in(ad_operator* op, const void* user, void* slot, const void** dev, bool copy) {
+int stage_in(ad_operator* op, const void* user, int which, const void** dev, bool copy) {
   if (is_device_ptr(user)) { *dev = user; return AD_OK; }
   AD_TRY(ensure_staging(op));
+  void* slot = which == 0 ? op->S0 : (which == 1 ? op->S1 : op->T3);
   if (copy)
     CUDA_TRY(cudaMemcpyAsync(slot, user, (size_t)op->g.n * op->esz, cudaMemcpyHostToDevice, op->stream));
   *dev = slot;
@@ -453,6 +458,7 @@ int ad_create_operator(const ad_grid* grid, const double* Dxx, const double* Dxy
                        const double* ax, const double* ay, double ax_c, double ay_c, int precision,
                        void* cuda_stream, ad_operator** out) {
   g_err.clear();
+  cudaGetLastError();  // a pending error of the caller's own runtime use is not ours
   if (!out) return fail(AD_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (!grid || !Dxx || !Dxy || !Dyy) return fail(AD_ERR_INVALID, "grid or D field is NULL");
@@ -587,7 +593,7 @@ int ad_spectral_bound(ad_operator* op, int method, const void* x0, unsigned long
     if (power_iters < 1 || !(safety > 0)) return fail(AD_ERR_INVALID, "power_iters >= 1, safety > 0");
     const long long n = op->g.n;
     const void* x0d = nullptr;
-    if (x0) AD_TRY(stage_in(op, x0, op->T3, &x0d, true));
+    if (x0) AD_TRY(stage_in(op, x0, 2, &x0d, true));
     if (x0d) axpby(op->prec, n, 1.0, x0d, 0.0, nullptr, op->T1, op->stream);
     else splitmix_fill(op->prec, n, seed, op->T1, op->stream);
     // x <- x0 / ||x0||
@@ -618,7 +624,7 @@ int ad_apply(ad_operator* op, const void* u, void* Au) {
   g_err.clear();
   if (!op || !u || !Au) return fail(AD_ERR_INVALID, "NULL argument");
   const void* ud;
-  AD_TRY(stage_in(op, u, op->T3, &ud, true));
+  AD_TRY(stage_in(op, u, 2, &ud, true));
   void* od = is_device_ptr(Au) ? Au : nullptr;
   if (!od) { AD_TRY(ensure_staging(op)); od = op->S1; }
   Sources none{};
@@ -639,7 +645,7 @@ int ad_leja_phi1(ad_operator* op, const void* v, void* out, double dt, double to
   st.alpha = op->alpha;
   const long long l0 = launch_counter();
   const void* vd;
-  AD_TRY(stage_in(op, v, op->S0, &vd, true));
+  AD_TRY(stage_in(op, v, 0, &vd, true));
   void* od = is_device_ptr(out) ? out : nullptr;
   if (!od) { AD_TRY(ensure_staging(op)); od = op->S1; }
   int r = phi1_device(op, vd, od, dt, tol, force_iters < 0 ? -1 : force_iters, &st);
@@ -667,7 +673,7 @@ int ad_expquad_step(ad_operator* op, void* u, double t, double dt, int s, const 
   st.alpha = op->alpha;
   const long long l0 = launch_counter();
   const void* ud_c;
-  AD_TRY(stage_in(op, u, op->S0, &ud_c, true));
+  AD_TRY(stage_in(op, u, 0, &ud_c, true));
   void* ud = const_cast<void*>(ud_c);
   const long long n = op->g.n;
   const int force = force_iters < 0 ? -1 : force_iters;
@@ -761,7 +767,7 @@ int ad_cn_step(ad_operator* op, void* u, double t, double dt, const ad_source* s
   st.alpha = op->alpha;
   const long long l0 = launch_counter();
   const void* ud_c;
-  AD_TRY(stage_in(op, u, op->S0, &ud_c, true));
+  AD_TRY(stage_in(op, u, 0, &ud_c, true));
   double* x = (double*)const_cast<void*>(ud_c);
   double* b = (double*)op->T1;
   double* w = (double*)op->T2;
