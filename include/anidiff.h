@@ -176,6 +176,31 @@ AD_API int ad_cn_step(ad_operator* op, void* u, double t, double dt, const ad_so
  * unaffected.  1 <= reps <= 500. */
 AD_API int ad_profile_leja_iteration(ad_operator* op, int aug, int reps, double* ms_per_launch);
 
+/* out = phi_1(dt A) v without allocating any device memory.  The paper has
+ * no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (code inside a host framework that owns the device heap, code
+ * under a no-allocation-after-start-up rule, or paths where an allocation's
+ * implicit synchronisation is not acceptable) and therefore cannot create an
+ * operator.  It runs the same kernels as ad_create_operator + ad_leja_phi1,
+ * with all scratch (packed weights, Newton vectors, partial sum, Leja
+ * scalars, control block, norm partials) in one fixed file-scope device array
+ * of about 6.4 MB that every GPU loading the library holds until exit.
+ *   grid, Dxx, Dxy, Dyy : as in ad_create_operator (device fields, FP64);
+ *   ax_c, ay_c          : constant advection;
+ *   alpha               : spectral bound (< 0), or 0 to compute it by Gershgorin;
+ *   v, out              : float64 DEVICE vectors [ny][nx] (may alias);
+ *   dt, tol, force_iters: as in ad_leja_phi1; one substep only.
+ * Limits: at most 65536 cells and gamma*dt <= 200 (AD_ERR_INVALID with a
+ * message otherwise).  Every call shares the scratch and it keeps the last
+ * call's contents; calls that overlap on the GPU race and must be serialised
+ * by the caller.  The first call on a device looks up the scratch address
+ * (once per device); make it before any stream capture.  Synchronises the
+ * stream before returning. */
+AD_API int ad_leja_phi1_noalloc(const ad_grid* grid, const double* Dxx, const double* Dxy,
+                                const double* Dyy, double ax_c, double ay_c, double alpha,
+                                const double* v, double* out, double dt, double tol,
+                                int force_iters, void* cuda_stream, ad_stats* stats);
+
 /* Thread-local message for the last error of this thread ("" if none). */
 AD_API const char* ad_last_error(void);
 

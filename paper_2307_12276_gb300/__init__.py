@@ -64,6 +64,8 @@ _sig = {
                              C.POINTER(Stats)]),
     "ad_cn_step": (_i, [_vp, _vp, _d, _d, C.POINTER(_Source), _d, _i, _i, C.POINTER(Stats)]),
     "ad_profile_leja_iteration": (_i, [_vp, _i, _i, C.POINTER(_d)]),
+    "ad_leja_phi1_noalloc": (_i, [C.POINTER(_Grid), _vp, _vp, _vp, _d, _d, _d, _vp, _vp, _d, _d,
+                                  _i, _vp, C.POINTER(Stats)]),
     "ad_last_error": (C.c_char_p, []),
     "ad_version": (_i, []),
 }
@@ -281,3 +283,22 @@ def profile_leja_iteration(op: Operator, aug: int = 0, reps: int = 200) -> float
     ms = _d()
     _check(_lib.ad_profile_leja_iteration(op.handle, aug, reps, C.byref(ms)))
     return ms.value
+
+
+NOALLOC_MAX_CELLS = 1 << 16
+
+
+def leja_phi1_noalloc(nx: int, ny: int, bc: int, Dxx, Dxy, Dyy, v, out, dt: float,
+                      ax: float = 0.0, ay: float = 0.0, alpha: float = 0.0, tol: float = 1e-10,
+                      force_iters: int = -1, stream=None, x0=-1.0, x1=1.0, y0=-1.0,
+                      y1=1.0) -> dict:
+    """ad_leja_phi1_noalloc: phi_1(dt A) v with no device allocation (fields,
+    v and out are float64 device tensors; see include/anidiff.h for limits)."""
+    g = _Grid(nx, ny, x0, x1, y0, y1, bc)
+    n = nx * ny
+    ptr = lambda x, w: _ptr(x, "float64", n, w)
+    st = Stats()
+    _check(_lib.ad_leja_phi1_noalloc(C.byref(g), ptr(Dxx, "Dxx"), ptr(Dxy, "Dxy"), ptr(Dyy, "Dyy"),
+                                     float(ax), float(ay), alpha, ptr(v, "v"), ptr(out, "out"),
+                                     dt, tol, force_iters, _stream_ptr(stream), C.byref(st)), st)
+    return st.as_dict()

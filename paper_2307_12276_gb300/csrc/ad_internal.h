@@ -132,6 +132,9 @@ void multi_axpy_add(long long n, const double* V, long long ldv, int k, const do
 
 int stream_blocks(long long n);   // grid size of the streaming kernels
 
+// Set the thread-local message returned by ad_last_error().
+void set_error_message(const char* msg);
+
 // Kernels enqueued from the host by this thread (every launcher adds one);
 // kernels run inside graph loops are counted by the caller.
 long long& launch_counter();

@@ -66,6 +66,10 @@ bool is_device_ptr(const void* p) {
 
 }  // namespace
 
+namespace ad {
+void set_error_message(const char* msg) { g_err = msg; }
+}  // namespace ad
+
 struct SeriesGraph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
