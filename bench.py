@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--form-steps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -193,6 +195,53 @@ def traffic_per_launch(kernel_file: str):
 
 
 # --------------------------------------------------------------------------- ours
+def measure_fp32_form(ad, dev, stream, flush, steps):
+    """The FP32-storage form on the 4096^2 stream-function workload
+    (exponential midpoint, tol 1e-6): throughput, Leja iterations and the
+    fused FP32 kernel's algorithmic HBM bandwidth against the copy peak."""
+    import numpy as np
+    import torch
+    from workloads import config2
+    p = config2(nx=4096)
+    g = p.grid
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(), device=dev)
+    op = ad.create_operator(g.nx, g.ny, g.bc, T(p.Dxx), T(p.Dxy), T(p.Dyy), 0.0, 0.0,
+                            ad.FP32_STORAGE, stream=stream)
+    src = ad.Source([T(p.source.g[0]).float()], None)
+    u = T(p.u0).float()
+    t = 0.0
+    for _ in range(2):
+        ad.expquad_step(op, u, t, p.dt, 1, (0.5,), src, tol=p.tol)
+        t += p.dt
+    torch.cuda.synchronize()
+    ms, iters = 0.0, []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = ad.expquad_step(op, u, t, p.dt, 1, (0.5,), src, tol=p.tol)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        iters.append(st["iters"])
+        t += p.dt
+    ms_launch = ad.profile_leja_iteration(op, aug=0, reps=100)
+    alg_bytes = 28.0 * g.n      # 3 fields + y + p r/w + y_next, 4 B each
+    gbs = alg_bytes / (ms_launch * 1e-3) / 1e9
+    op.close()
+    del u, src
+    torch.cuda.empty_cache()
+    return {"workload": "c2-4096sq-dirichlet-stream-midpoint-fp32", "cells": g.n,
+            "value": round(g.n * steps / (ms * 1e-3) / 1e6, 2), "unit": "Mcell-steps/s",
+            "ms_per_step": round(ms / steps, 4), "leja_iters_per_step": statistics.mean(iters),
+            "tol": p.tol, "dtype": "f32 storage/arithmetic, f64 Leja scalars and norm sums",
+            "roofline": {"bound": "hbm", "kernel": "leja_iter_f32_k", "ms_per_launch":
+                         round(ms_launch, 5), "achieved": round(gbs, 1), "peak": 6750.4,
+                         "unit": "GB/s", "frac": round(gbs / 6750.4, 4),
+                         "alg_bytes_per_launch": alg_bytes}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -292,6 +341,10 @@ def run_ours(args):
             "alg_GBps": round(bytes_alg / (ms_launch * 1e-3) / 1e9, 1),
             "peak_note": "FP64: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived)"}
 
+    forms = {}
+    if not args.no_forms:
+        forms["fp32_4096sq"] = measure_fp32_form(ad, dev, stream, flush, args.form_steps)
+
     if rank == 0:
         line = {
             "metric": "Mcell-steps/s", "value": round(value, 4), "unit": "Mcell-steps/s",
@@ -310,6 +363,8 @@ def run_ours(args):
             "roofline": roof,
             "clocks": clk.summary(),
         }
+        if forms:
+            line["forms"] = forms
         if cpu is not None:
             line["cpu_baseline"] = {"value": round(cpu["value"], 6), "unit": "Mcell-steps/s",
                                     "cores": 1, "kind": "oracle",

@@ -31,7 +31,8 @@ struct Ctrl {
   int status;     // 0 ok, 3 not converged
   int force;      // > 0: exact iteration count, no stopping test
   int max_iters;
-  int pad0, pad1;
+  unsigned int ticket;  // blocks of the running iteration that have finished
+  int pad1;
   double tol;
   double err_est;
   double ynorm2;  // last ||y_{m+1}||^2
@@ -94,15 +95,19 @@ struct SeriesArgs {
   int aug;
   int adv;                  // fp32 advection mode (see pack_fields_f32)
   float abx, aby;
+  unsigned long long handle;  // CUDA graph conditional of the WHILE loop
+  int has_handle;             // 1 when run inside the graph loop
 };
 // y[0] = src (or 0 if src == null), p = d0 * y[0]; resets ctrl.
 void series_init(const SeriesArgs& a, const void* src, double d0, int force, int max_iters,
                  double tol, cudaStream_t s);
+// One fused Leja iteration over the grid (a.nblocks blocks).  The last block to
+// finish reduces the norm partials in a fixed order, applies the stopping rule,
+// advances ctrl->m and, with a.has_handle, sets the graph loop condition.
 void series_iteration(const SeriesArgs& a, cudaStream_t s);
-// control kernel: reduce partials, apply stopping rule, advance m; when
-// has_handle, set the graph conditional to "continue".
-void series_control(const SeriesArgs& a, unsigned long long handle, int has_handle,
-                    cudaStream_t s);
+// grid size of the fused iteration kernel (FP64: by cell count; FP32: by tile count)
+int series_blocks(int prec, long long n);
+int series_blocks_grid(int prec, int nx, int ny);
 
 // ---------------------------------------------------------------- vector helpers
 // z = a*x + b*y (x or y may be null = 0), elementwise, storage type prec.

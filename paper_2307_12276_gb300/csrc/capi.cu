@@ -7,9 +7,9 @@
 // vec_kernels.cu.
 //
 // Each Newton series (Section 2) runs as one CUDA graph launch: a
-// conditional WHILE node whose body is [fused Leja iteration, one-block
-// control kernel].  The control kernel evaluates the stopping rule on the
-// device and sets the loop condition, so the host neither polls nor syncs per
+// conditional WHILE node whose body is the fused Leja iteration kernel.  The
+// last block of each launch evaluates the stopping rule on the device and
+// sets the loop condition, so the host neither polls nor syncs per
 // iteration; the loop is bounded by the iteration cap (<= 500).
 #include <cuda_runtime.h>
 
@@ -28,6 +28,8 @@
 using namespace ad;
 
 namespace {
+
+constexpr int kGraphUnroll = 4;   // iteration kernels per body of the graph loop
 
 thread_local std::string g_err;
 
@@ -137,7 +139,7 @@ SeriesArgs series_args(ad_operator* op, int aug) {
   a.lc = op->lc;
   a.ctrl = op->ctrl;
   a.partials = op->partials;
-  a.nblocks = op->nblocks;
+  a.nblocks = series_blocks_grid(op->prec, op->g.nx, op->g.ny);
   a.aug = aug;
   a.adv = op->adv;
   a.abx = op->abx;
@@ -190,9 +192,14 @@ bool build_graph(ad_operator* op, int aug) {
     cudaGraphDestroy(graph);
     return false;
   }
+  // The loop body holds kGraphUnroll iteration kernels: each body execution of a
+  // conditional node costs a few microseconds of scheduling on this driver, so
+  // it is amortised over several iterations.  Kernels after the one that stops
+  // the series return at once (they see ctrl->stop).
   SeriesArgs a = series_args(op, aug);
-  series_iteration(a, op->cap_stream);
-  series_control(a, (unsigned long long)handle, 1, op->cap_stream);
+  a.handle = (unsigned long long)handle;
+  a.has_handle = 1;
+  for (int u = 0; u < kGraphUnroll; ++u) series_iteration(a, op->cap_stream);
   cudaGraph_t captured = nullptr;
   if (cudaStreamEndCapture(op->cap_stream, &captured) != cudaSuccess) {
     cudaGetLastError();
@@ -329,10 +336,7 @@ int run_series(ad_operator* op, int aug, const void* src, double d0, int force, 
       int launched = 0;
       for (;;) {
         const int chunk = 16;
-        for (int k = 0; k < chunk; ++k) {
-          series_iteration(a, op->stream);
-          series_control(a, 0ULL, 0, op->stream);
-        }
+        for (int k = 0; k < chunk; ++k) series_iteration(a, op->stream);
         launched += chunk;
         CUDA_TRY(cudaGetLastError());
         CUDA_TRY(cudaMemcpyAsync(op->h_ctrl, op->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, op->stream));
@@ -345,9 +349,14 @@ int run_series(ad_operator* op, int aug, const void* src, double d0, int force, 
     CUDA_TRY(cudaStreamSynchronize(op->stream));
     iters = op->h_ctrl->iters;
     if (!op->h_ctrl->stop) return fail(AD_ERR_TIMEOUT, "Leja series did not reach its stop state");
-    // graph bodies: fused iteration + control kernel per iteration (host launches
+    {  // the device stores |d_{m+1}| and the squared norms; form the estimate here
+      const Ctrl& h = *op->h_ctrl;
+      op->h_ctrl->err_est = h.pnorm2 > 0.0 ? h.err_est * std::sqrt(h.ynorm2 / h.pnorm2)
+                                           : (h.ynorm2 > 0.0 ? INFINITY : 0.0);
+    }
+    // graph bodies: one fused iteration kernel per iteration (host launches
     // are counted by the launchers themselves)
-    if (st && graph_used) st->kernel_launches += 2 * iters;
+    if (st && graph_used) st->kernel_launches += iters;
   }
   if (st) {
     st->iters += iters;
@@ -905,7 +914,6 @@ int ad_profile_leja_iteration(ad_operator* op, int aug, int reps, double* ms_per
     CUDA_TRY(cudaEventRecord(ev[2 * r], op->stream));
     series_iteration(a, op->stream);
     CUDA_TRY(cudaEventRecord(ev[2 * r + 1], op->stream));
-    series_control(a, 0ULL, 0, op->stream);
   }
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(op->stream));

@@ -173,17 +173,14 @@ extern "C" int ad_leja_phi1_noalloc(const ad_grid* grid, const double* Dxx, cons
   a.lc = S->lc;
   a.ctrl = &S->ctrl;
   a.partials = S->partials;
-  a.nblocks = nb;
+  a.nblocks = series_blocks(0, n);
   const int force = force_iters < 0 ? -1 : force_iters;
   series_init(a, v, d[0], force, kMaxIters, tol, s);
   Ctrl hc{};
   if (force != 0) {
     int launched = 0;
     for (;;) {   // host-driven: chunks of iterations, then poll the stop flag
-      for (int k = 0; k < 16; ++k) {
-        series_iteration(a, s);
-        series_control(a, 0ULL, 0, s);
-      }
+      for (int k = 0; k < 16; ++k) series_iteration(a, s);
       launched += 16;
       NA_CUDA(cudaGetLastError());
       NA_CUDA(cudaMemcpyAsync(&hc, &S->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
@@ -191,6 +188,8 @@ extern "C" int ad_leja_phi1_noalloc(const ad_grid* grid, const double* Dxx, cons
       if (hc.stop || launched >= kMaxIters + 16) break;
     }
     if (!hc.stop) return nfail(AD_ERR_TIMEOUT, "Leja series did not reach its stop state");
+    hc.err_est = hc.pnorm2 > 0.0 ? hc.err_est * std::sqrt(hc.ynorm2 / hc.pnorm2)
+                                 : (hc.ynorm2 > 0.0 ? INFINITY : 0.0);
   }
   axpby(0, n, 1.0, S->p, 0.0, nullptr, out, s);
   NA_CUDA(cudaGetLastError());

@@ -28,20 +28,81 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Deterministic block sum of two values; result valid in thread 0.
+// Deterministic block sum of two values; result valid in thread 0.  Lanes of
+// warp 0 add eight values each, then one butterfly: far fewer FP64 additions
+// than a butterfly in every warp (FP64 is the scarce pipe on this GPU).
 __device__ __forceinline__ void block_sum2(double& a, double& b) {
-  __shared__ double sa[32], sb[32];
-  a = warp_sum(a);
-  b = warp_sum(b);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) { sa[wid] = a; sb[wid] = b; }
+  __shared__ double sa[kThreads], sb[kThreads];
+  const int t = threadIdx.x;
   __syncthreads();
-  if (wid == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    a = lane < nw ? sa[lane] : 0.0;
-    b = lane < nw ? sb[lane] : 0.0;
-    a = warp_sum(a);
-    b = warp_sum(b);
+  sa[t] = a;
+  sb[t] = b;
+  __syncthreads();
+  if (t < 32) {
+    double x = 0.0, y = 0.0;
+    for (int k = t; k < (int)blockDim.x; k += 32) {
+      x += sa[k];
+      y += sb[k];
+    }
+    a = warp_sum(x);
+    b = warp_sum(y);
+  }
+}
+
+// Per-iteration epilogue of the Newton series (Section 2): publish the block's
+// norm partials; the last block of the launch (ticket, no waiting) reduces all
+// partials in block order, applies the stopping rule
+//   |d_{m+1}| ||y_{m+1}|| <= tol ||p_{m+1}||  (m+1 >= 2), or the forced count,
+// advances m and sets the graph loop condition.  The series always ends: m
+// grows by one per launch and the rule stops at max_iters <= kMaxIters.
+__device__ void series_finish(const SeriesArgs& a, double sy, double sp) {
+  __shared__ unsigned int s_last;
+  block_sum2(sy, sp);
+  Ctrl* ctrl = a.ctrl;
+  if (threadIdx.x == 0) {
+    a.partials[2 * blockIdx.x] = sy;
+    a.partials[2 * blockIdx.x + 1] = sp;
+    __threadfence();
+    const unsigned int t = atomicAdd(&ctrl->ticket, 1u);
+    s_last = (t == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double ty = 0.0, tp = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    ty += __ldcg(&a.partials[2 * b]);
+    tp += __ldcg(&a.partials[2 * b + 1]);
+  }
+  block_sum2(ty, tp);
+  if (threadIdx.x == 0) {
+    const int m = ctrl->m;
+    const int terms = m + 1;
+    const double absd = a.lc[m].absd;
+    ctrl->ynorm2 = ty;
+    ctrl->pnorm2 = tp;
+    ctrl->iters = terms;
+    ctrl->err_est = absd;           // the host forms |d| ||y|| / ||p|| from the squares
+    const double tol = ctrl->tol;
+    int stop = 0;
+    if (ctrl->force > 0) {
+      stop = terms >= ctrl->force;
+    } else if (!(ty == ty) || !(tp == tp)) {       // NaN: give up
+      stop = 1;
+      ctrl->status = 3;
+    } else if (terms >= 2 && (absd * absd) * ty <= (tol * tol) * tp) {   // squared test
+      stop = 1;
+    } else if (terms >= ctrl->max_iters) {
+      stop = 1;
+      ctrl->status = 3;
+    }
+    if (terms >= kMaxIters) stop = 1;               // hard cap, independent of the settings
+    ctrl->ticket = 0u;
+    ctrl->stop = stop;
+    ctrl->m = m + 1;
+    __threadfence();
+    if (a.has_handle)
+      cudaGraphSetConditional((cudaGraphConditionalHandle)a.handle, stop ? 0u : 1u);
   }
 }
 
@@ -55,42 +116,38 @@ struct RowTiles {
 };
 
 // --------------------------------------------------------------------------
-// FP64: folded 9-weight stencil.
+// FP64: folded 9-weight stencil, branch-free.  Periodic: neighbour indices
+// wrap.  Dirichlet: the ghosts are folded into the interior slots, so every
+// out-of-domain slot has weight exactly 0; its index is clamped into the
+// domain (any finite value times 0 adds nothing), which keeps all nine loads
+// unconditional and independent.
 __device__ __forceinline__ double stencil9(const double* __restrict__ W, long long n,
                                            const double* __restrict__ u, int i, int j, int nx,
                                            int ny, int bc, long long idx) {
-  const double* r0 = u + (long long)j * nx;
-  double acc = W[4 * n + idx] * r0[i];
-  if (bc == 0) {  // periodic: wrap
-    const int im = i ? i - 1 : nx - 1, ip = (i + 1 < nx) ? i + 1 : 0;
-    const int jm = j ? j - 1 : ny - 1, jp = (j + 1 < ny) ? j + 1 : 0;
-    const double* rm = u + (long long)jm * nx;
-    const double* rp = u + (long long)jp * nx;
-    acc = fma(W[0 * n + idx], rm[im], acc);
-    acc = fma(W[1 * n + idx], rm[i], acc);
-    acc = fma(W[2 * n + idx], rm[ip], acc);
-    acc = fma(W[3 * n + idx], r0[im], acc);
-    acc = fma(W[5 * n + idx], r0[ip], acc);
-    acc = fma(W[6 * n + idx], rp[im], acc);
-    acc = fma(W[7 * n + idx], rp[i], acc);
-    acc = fma(W[8 * n + idx], rp[ip], acc);
-  } else {        // Dirichlet: ghosts are folded, out-of-domain slots are 0
-    const bool hm = i > 0, hp = i + 1 < nx;
-    if (j > 0) {
-      const double* rm = r0 - nx;
-      if (hm) acc = fma(W[0 * n + idx], rm[i - 1], acc);
-      acc = fma(W[1 * n + idx], rm[i], acc);
-      if (hp) acc = fma(W[2 * n + idx], rm[i + 1], acc);
-    }
-    if (hm) acc = fma(W[3 * n + idx], r0[i - 1], acc);
-    if (hp) acc = fma(W[5 * n + idx], r0[i + 1], acc);
-    if (j + 1 < ny) {
-      const double* rp = r0 + nx;
-      if (hm) acc = fma(W[6 * n + idx], rp[i - 1], acc);
-      acc = fma(W[7 * n + idx], rp[i], acc);
-      if (hp) acc = fma(W[8 * n + idx], rp[i + 1], acc);
-    }
+  int im, ip, jm, jp;
+  if (bc == 0) {
+    im = i ? i - 1 : nx - 1;
+    ip = (i + 1 < nx) ? i + 1 : 0;
+    jm = j ? j - 1 : ny - 1;
+    jp = (j + 1 < ny) ? j + 1 : 0;
+  } else {
+    im = i ? i - 1 : 0;
+    ip = (i + 1 < nx) ? i + 1 : i;
+    jm = j ? j - 1 : 0;
+    jp = (j + 1 < ny) ? j + 1 : j;
   }
+  const double* rm = u + (long long)jm * nx;
+  const double* r0 = u + (long long)j * nx;
+  const double* rp = u + (long long)jp * nx;
+  double acc = W[4 * n + idx] * r0[i];
+  acc = fma(W[0 * n + idx], rm[im], acc);
+  acc = fma(W[1 * n + idx], rm[i], acc);
+  acc = fma(W[2 * n + idx], rm[ip], acc);
+  acc = fma(W[3 * n + idx], r0[im], acc);
+  acc = fma(W[5 * n + idx], r0[ip], acc);
+  acc = fma(W[6 * n + idx], rp[im], acc);
+  acc = fma(W[7 * n + idx], rp[i], acc);
+  acc = fma(W[8 * n + idx], rp[ip], acc);
   return acc;
 }
 
@@ -238,12 +295,13 @@ __global__ void apply_f64_k(GridDev g, const double* __restrict__ W, const doubl
 }
 
 // Fused Leja iteration m: y_{m+1} = Ws y_m - xi_m y_m [+ e1 w2 + e2 w1],
-// p += d_{m+1} y_{m+1}, block partials of ||y_{m+1}||^2, ||p||^2.
+// p += d_{m+1} y_{m+1}, norm partials; each block owns a contiguous chunk of
+// cells (equal FP64 work per block: the kernel is FP64-pipe bound).
 template <bool AUG>
 __global__ void __launch_bounds__(kThreads) leja_iter_f64_k(SeriesArgs a) {
-  const Ctrl* ctrl = a.ctrl;
-  if (ctrl->stop) return;
-  const int m = ctrl->m;
+  const volatile Ctrl* vc = a.ctrl;
+  if (vc->stop) return;
+  const int m = vc->m;
   const LejaCoef lc = a.lc[m];
   const double* __restrict__ yin = static_cast<const double*>(a.y[m & 1]);
   double* __restrict__ yout = static_cast<double*>(a.y[(m + 1) & 1]);
@@ -252,29 +310,46 @@ __global__ void __launch_bounds__(kThreads) leja_iter_f64_k(SeriesArgs a) {
   const double* __restrict__ w1 = static_cast<const double*>(a.w1);
   const double* __restrict__ w2 = static_cast<const double*>(a.w2);
   const GridDev g = a.g;
-  const RowTiles rt(g.nx, g.ny);
+  const unsigned int n = (unsigned int)g.n, nx = (unsigned int)g.nx;
+  const unsigned int chunk = (n + gridDim.x - 1) / gridDim.x;
+  const unsigned int c0 = blockIdx.x * chunk;
+  const unsigned int c1 = min(n, c0 + chunk);
+  const bool use_w2 = AUG && lc.e1 != 0.0, use_w1 = AUG && lc.e2 != 0.0;
   double sy = 0.0, sp = 0.0;
-  for (int t = blockIdx.x; t < rt.ntiles; t += gridDim.x) {
-    const int j = t / rt.tiles_x, i = (t % rt.tiles_x) * kThreads + threadIdx.x;
-    if (i >= g.nx) continue;
-    const long long idx = (long long)j * g.nx + i;
-    double z = stencil9(Ws, g.n, yin, i, j, g.nx, g.ny, g.bc, idx);
-    z = fma(-lc.xi, yin[idx], z);
-    if (AUG) {
-      if (lc.e1 != 0.0) z = fma(lc.e1, w2[idx], z);
-      if (lc.e2 != 0.0) z = fma(lc.e2, w1[idx], z);
+  // two cells per thread and loop trip, computed side by side (independent
+  // FP64 chains and loads in flight)
+  for (unsigned int base = c0 + threadIdx.x; base < c1; base += 2 * blockDim.x) {
+    unsigned int id[2];
+    bool ok[2];
+    double z[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const unsigned int idx = base + q * blockDim.x;
+      ok[q] = idx < c1;
+      id[q] = ok[q] ? idx : base;
     }
-    yout[idx] = z;
-    const double pn = fma(lc.d, z, p[idx]);
-    p[idx] = pn;
-    sy = fma(z, z, sy);
-    sp = fma(pn, pn, sp);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const unsigned int idx = id[q];
+      const int j = (int)(idx / nx), i = (int)(idx - (unsigned int)j * nx);
+      double zz = stencil9(Ws, g.n, yin, i, j, g.nx, g.ny, g.bc, idx);
+      zz = fma(-lc.xi, yin[idx], zz);
+      if (use_w2) zz = fma(lc.e1, w2[idx], zz);
+      if (use_w1) zz = fma(lc.e2, w1[idx], zz);
+      z[q] = zz;
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (!ok[q]) continue;
+      const unsigned int idx = id[q];
+      yout[idx] = z[q];
+      const double pn = fma(lc.d, z[q], p[idx]);
+      p[idx] = pn;
+      sy = fma(z[q], z[q], sy);
+      sp = fma(pn, pn, sp);
+    }
   }
-  block_sum2(sy, sp);
-  if (threadIdx.x == 0) {
-    a.partials[2 * blockIdx.x] = sy;
-    a.partials[2 * blockIdx.x + 1] = sp;
-  }
+  series_finish(a, sy, sp);
 }
 
 // --------------------------------------------------------------------------
@@ -476,50 +551,246 @@ __global__ void apply_f32_k(GridDev g, const float* __restrict__ F, int adv, flo
 
 // FP32 fused Leja iteration; Leja scalars arrive in FP64 and are rounded once
 // per iteration; per-thread square sums in FP32, block sums in FP64.
-template <bool AUG>
+// ---- FP32 fused iteration: tiles of 256 columns x kTileRows rows, marching in y.
+// Each thread owns one column of the tile; rows j-1, j, j+1 of y and the rows
+// of Dxx/Dxy that need x-neighbours live in shared-memory rings, the next row
+// is prefetched into registers while the current row is computed.  Steady
+// state global traffic per cell: y, Dxx, Dxy, Dyy, p read, y', p written
+// (28 B), + w2 (augmented) + ax, ay (advection fields).
+constexpr int kTileRows = 32;
+constexpr int kTileCols = kThreads;
+
+struct RowMap {
+  long long off;   // mapped row offset j' * nx
+  float sg;        // ghost sign for values (Dirichlet odd reflection)
+};
+
+__device__ __forceinline__ RowMap map_row(int j, int nx, int ny, int bc) {
+  RowMap r;
+  float sg = 1.0f;
+  if (bc == 0) j = (j < 0) ? j + ny : (j >= ny ? j - ny : j);
+  else if (j < 0) { j = -1 - j; sg = -1.0f; }
+  else if (j >= ny) { j = 2 * ny - 1 - j; sg = -1.0f; }
+  r.off = (long long)j * nx;
+  r.sg = sg;
+  return r;
+}
+
+__device__ __forceinline__ int map_col(int i, int nx, int bc, float& sg) {
+  sg = 1.0f;
+  if (bc == 0) return (i < 0) ? i + nx : (i >= nx ? i - nx : i);
+  if (i < 0) { sg = -1.0f; return -1 - i; }
+  if (i >= nx) { sg = -1.0f; return 2 * nx - 1 - i; }
+  return i;
+}
+
+// Values needed from row r (for y, Dxy, Dxx rows with x-halo): this thread's
+// column and, for thread 0, the two halo columns.
+struct RowVals {
+  float c, l, r;
+};
+
+__device__ __forceinline__ RowVals load_row(const float* __restrict__ f, const RowMap& rm,
+                                            bool values, int ci, float csg, bool cvalid,
+                                            int li, float lsg, int ri, float rsg, bool halo) {
+  RowVals v;
+  const float s = values ? rm.sg : 1.0f;
+  v.c = cvalid ? f[rm.off + ci] * (values ? s * csg : 1.0f) : 0.0f;
+  v.l = v.r = 0.0f;
+  if (halo) {
+    v.l = f[rm.off + li] * (values ? s * lsg : 1.0f);
+    v.r = f[rm.off + ri] * (values ? s * rsg : 1.0f);
+  }
+  return v;
+}
+
+template <bool AUG, int ADV>
+__device__ __forceinline__ void tile_f32(const SeriesArgs& a, const LejaCoef& lc, int tx, int ty,
+                                         const float* __restrict__ yin, float* __restrict__ yout,
+                                         float* __restrict__ p, float ig, float sh, float d,
+                                         float e1, float e2, float (*sy)[kTileCols + 2],
+                                         float* sxx, float (*sxy)[kTileCols + 2], float* sax,
+                                         double& accy, double& accp) {
+  const GridDev g = a.g;
+  const int nx = g.nx, ny = g.ny, bc = g.bc;
+  const long long n = g.n;
+  const float* __restrict__ F = static_cast<const float*>(a.coef);
+  const float* Fxx = F;
+  const float* Fyy = F + n;
+  const float* Fxy = F + 2 * n;
+  const float* Fax = F + 3 * n;
+  const float* Fay = F + 4 * n;
+  const float* __restrict__ w1 = static_cast<const float*>(a.w1);
+  const float* __restrict__ w2 = static_cast<const float*>(a.w2);
+  const int t = threadIdx.x;
+  const int x0 = tx * kTileCols, y0 = ty * kTileRows;
+  const int y1 = min(ny, y0 + kTileRows);
+  const int i = x0 + t;
+  const bool compute = i < nx;
+  const bool cvalid = i <= nx;            // column nx is the right ghost
+  float csg, lsg, rsg;
+  const int ci = cvalid ? map_col(i, nx, bc, csg) : 0;
+  const int li = map_col(x0 - 1, nx, bc, lsg);
+  const int ri = map_col(min(x0 + kTileCols, nx), nx, bc, rsg);
+  const bool halo = (t == 0);
+  const int rslot = min(kTileCols, nx - x0) + 1;  // smem index of the right halo
+  __syncthreads();   // the previous tile's last row may still be read
+  // prologue: rows y0-1 and y0 of y, row y0 of Dxy (with halos), Dyy/Dxy/ay columns
+  {
+    const RowMap rm = map_row(y0 - 1, nx, ny, bc), r0 = map_row(y0, nx, ny, bc);
+    RowVals v = load_row(yin, rm, true, ci, csg, cvalid, li, lsg, ri, rsg, halo);
+    sy[(y0 + 2) % 3][t + 1] = v.c;
+    if (halo) { sy[(y0 + 2) % 3][0] = v.l; sy[(y0 + 2) % 3][rslot] = v.r; }
+    v = load_row(yin, r0, true, ci, csg, cvalid, li, lsg, ri, rsg, halo);
+    sy[y0 % 3][t + 1] = v.c;
+    if (halo) { sy[y0 % 3][0] = v.l; sy[y0 % 3][rslot] = v.r; }
+    v = load_row(Fxy, r0, false, ci, csg, cvalid, li, lsg, ri, rsg, halo);
+    sxy[y0 & 1][t + 1] = v.c;
+    if (halo) { sxy[y0 & 1][0] = v.l; sxy[y0 & 1][rslot] = v.r; }
+  }
+  float dyy_s = 0.f, dyy_c = 0.f, dxy_s = 0.f, ay_s = 0.f, ay_c = 0.f;
+  {
+    const RowMap rm = map_row(y0 - 1, nx, ny, bc), r0 = map_row(y0, nx, ny, bc);
+    if (cvalid) {
+      dyy_s = Fyy[rm.off + ci];
+      dyy_c = Fyy[r0.off + ci];
+      dxy_s = Fxy[rm.off + ci];
+      if (ADV == 2) { ay_s = Fay[rm.off + ci]; ay_c = Fay[r0.off + ci]; }
+    }
+  }
+  // prefetch for the first row
+  RowVals ynext, xynext, xxcur, axcur;
+  float dyy_n = 0.f, ay_n = 0.f, pc = 0.f, w2c = 0.f, w1c = 0.f;
+  auto prefetch = [&](int j) {
+    const RowMap rn = map_row(j + 1, nx, ny, bc), rc = map_row(j, nx, ny, bc);
+    ynext = load_row(yin, rn, true, ci, csg, cvalid, li, lsg, ri, rsg, halo);
+    xynext = load_row(Fxy, rn, false, ci, csg, cvalid, li, lsg, ri, rsg, halo);
+    xxcur = load_row(Fxx, rc, false, ci, csg, cvalid, li, lsg, ri, rsg, halo);
+    if (ADV == 2) axcur = load_row(Fax, rc, false, ci, csg, cvalid, li, lsg, ri, rsg, halo);
+    if (cvalid) {
+      dyy_n = Fyy[rn.off + ci];
+      if (ADV == 2) ay_n = Fay[rn.off + ci];
+    }
+    if (compute) {
+      const long long idx = (long long)j * nx + i;
+      pc = p[idx];
+      if (AUG) {
+        if (e1 != 0.0f) w2c = w2[idx];
+        if (e2 != 0.0f) w1c = w1[idx];
+      }
+    }
+  };
+  prefetch(y0);
+  float ly = 0.f, lp = 0.f;
+  for (int j = y0; j < y1; ++j) {
+    __syncthreads();                       // previous row's readers are done
+    const int sn = (j + 1) % 3, sc = j % 3, ss = (j + 2) % 3;
+    sy[sn][t + 1] = ynext.c;
+    sxy[(j + 1) & 1][t + 1] = xynext.c;
+    sxx[t + 1] = xxcur.c;
+    if (ADV == 2) sax[t + 1] = axcur.c;
+    if (halo) {
+      sy[sn][0] = ynext.l; sy[sn][rslot] = ynext.r;
+      sxy[(j + 1) & 1][0] = xynext.l; sxy[(j + 1) & 1][rslot] = xynext.r;
+      sxx[0] = xxcur.l; sxx[rslot] = xxcur.r;
+      if (ADV == 2) { sax[0] = axcur.l; sax[rslot] = axcur.r; }
+    }
+    const float dyyn = dyy_n, ayn = ay_n, pcur = pc, w2cur = w2c, w1cur = w1c;
+    __syncthreads();
+    if (j + 1 < y1) prefetch(j + 1);       // overlap the next row's loads with this row
+    if (compute) {
+      const float uC = sy[sc][t + 1], uE = sy[sc][t + 2], uW = sy[sc][t];
+      const float uN = sy[sn][t + 1], uNE = sy[sn][t + 2], uNW = sy[sn][t];
+      const float uS = sy[ss][t + 1], uSE = sy[ss][t + 2], uSW = sy[ss][t];
+      const float dxy_c = sxy[j & 1][t + 1];
+      const float axe = sxx[t + 1] + sxx[t + 2], axw = sxx[t] + sxx[t + 1];
+      const float qe = dxy_c + sxy[j & 1][t + 2], qw = sxy[j & 1][t] + dxy_c;
+      const float qn = dxy_c + sxy[(j + 1) & 1][t + 1], qs = dxy_s + dxy_c;
+      const float ayn_ = dyy_c + dyyn, ays = dyy_s + dyy_c;
+      float fe = axe * (uE - uC) + qe * ((uNE + uN) - (uSE + uS));
+      float fw = axw * (uC - uW) + qw * ((uN + uNW) - (uS + uSW));
+      float fn = ayn_ * (uN - uC) + qn * ((uNE + uE) - (uNW + uW));
+      float fs = ays * (uC - uS) + qs * ((uE + uSE) - (uW + uSW));
+      if (ADV == 1) {
+        fe = fmaf(a.abx, uC + uE, fe);
+        fw = fmaf(a.abx, uW + uC, fw);
+        fn = fmaf(a.aby, uC + uN, fn);
+        fs = fmaf(a.aby, uS + uC, fs);
+      } else if (ADV == 2) {
+        fe = fmaf(sax[t + 1] + sax[t + 2], uC + uE, fe);
+        fw = fmaf(sax[t] + sax[t + 1], uW + uC, fw);
+        fn = fmaf(ay_c + ayn, uC + uN, fn);
+        fs = fmaf(ay_s + ay_c, uS + uC, fs);
+      }
+      const float au = (fe - fw) + (fn - fs);
+      float z = fmaf(au, ig, -sh * uC);
+      if (AUG) {
+        if (e1 != 0.0f) z = fmaf(e1, w2cur, z);
+        if (e2 != 0.0f) z = fmaf(e2, w1cur, z);
+      }
+      const long long idx = (long long)j * nx + i;
+      yout[idx] = z;
+      const float pn = fmaf(d, z, pcur);
+      p[idx] = pn;
+      ly = fmaf(z, z, ly);
+      lp = fmaf(pn, pn, lp);
+    }
+    // roll the column registers
+    dxy_s = sxy[j & 1][t + 1];
+    dyy_s = dyy_c;
+    dyy_c = dyyn;
+    if (ADV == 2) { ay_s = ay_c; ay_c = ayn; }
+  }
+  accy += (double)ly;
+  accp += (double)lp;
+}
+
+template <bool AUG, int ADV>
 __global__ void __launch_bounds__(kThreads) leja_iter_f32_k(SeriesArgs a) {
-  const Ctrl* ctrl = a.ctrl;
-  if (ctrl->stop) return;
-  const int m = ctrl->m;
+  __shared__ float sy[3][kTileCols + 2];
+  __shared__ float sxy[2][kTileCols + 2];
+  __shared__ float sxx[kTileCols + 2];
+  __shared__ float sax[kTileCols + 2];
+  const volatile Ctrl* vc = a.ctrl;
+  if (vc->stop) return;
+  const int m = vc->m;
   const LejaCoef lc = a.lc[m];
   const float* __restrict__ yin = static_cast<const float*>(a.y[m & 1]);
   float* __restrict__ yout = static_cast<float*>(a.y[(m + 1) & 1]);
   float* __restrict__ p = static_cast<float*>(a.p);
-  const float* __restrict__ F = static_cast<const float*>(a.coef);
-  const float* __restrict__ w1 = static_cast<const float*>(a.w1);
-  const float* __restrict__ w2 = static_cast<const float*>(a.w2);
-  const GridDev g = a.g;
   const float ig = (float)(1.0 / a.gamma);
   const float sh = (float)(a.c / a.gamma + lc.xi);
   const float d = (float)lc.d, e1 = (float)lc.e1, e2 = (float)lc.e2;
-  const RowTiles rt(g.nx, g.ny);
-  double sy = 0.0, sp = 0.0;
-  for (int t = blockIdx.x; t < rt.ntiles; t += gridDim.x) {
-    const int j = t / rt.tiles_x, i = (t % rt.tiles_x) * kThreads + threadIdx.x;
-    if (i >= g.nx) continue;
-    const long long idx = (long long)j * g.nx + i;
-    const bool interior = i > 0 && j > 0 && i + 1 < g.nx && j + 1 < g.ny;
-    const float au =
-        flux_apply_f32(F, g.n, yin, i, j, g.nx, g.ny, g.bc, interior, a.adv, a.abx, a.aby);
-    float z = fmaf(au, ig, -sh * yin[idx]);
-    if (AUG) {
-      if (e1 != 0.0f) z = fmaf(e1, w2[idx], z);
-      if (e2 != 0.0f) z = fmaf(e2, w1[idx], z);
-    }
-    yout[idx] = z;
-    const float pn = fmaf(d, z, p[idx]);
-    p[idx] = pn;
-    sy += (double)(z * z);
-    sp += (double)(pn * pn);
-  }
-  block_sum2(sy, sp);
-  if (threadIdx.x == 0) {
-    a.partials[2 * blockIdx.x] = sy;
-    a.partials[2 * blockIdx.x + 1] = sp;
-  }
+  const int tiles_x = (a.g.nx + kTileCols - 1) / kTileCols;
+  const int tiles_y = (a.g.ny + kTileRows - 1) / kTileRows;
+  double accy = 0.0, accp = 0.0;
+  for (int tile = blockIdx.x; tile < tiles_x * tiles_y; tile += gridDim.x)
+    tile_f32<AUG, ADV>(a, lc, tile % tiles_x, tile / tiles_x, yin, yout, p, ig, sh, d, e1, e2,
+                       sy, sxx, sxy, sax, accy, accp);
+  series_finish(a, accy, accp);
 }
 
 }  // namespace
+
+int series_blocks(int prec, long long n) {
+  // FP64: 4 blocks per SM (two cells per thread per trip keep the FP64 pipe
+  // fed; fewer blocks keep the block reductions cheap); FP32: 8 blocks per SM
+  // for memory parallelism.
+  if (prec == 0) {
+    const long long want = (n + kThreads - 1) / kThreads;
+    const long long cap = 152LL * 4;
+    return (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+  }
+  return -1;  // FP32: depends on the tile count, see series_blocks_grid
+}
+
+int series_blocks_grid(int prec, int nx, int ny) {
+  if (prec == 0) return series_blocks(0, (long long)nx * ny);
+  const long long tiles = (long long)((nx + kTileCols - 1) / kTileCols) *
+                          ((ny + kTileRows - 1) / kTileRows);
+  const long long cap = 152LL * 4;   // resident blocks of 256 threads at 64-80 registers
+  return (int)(tiles < cap ? tiles : cap);
+}
 
 int stream_blocks(long long n) {
   // 152 SMs x 8 resident blocks of 256 threads, or fewer for small grids
@@ -586,14 +857,18 @@ void series_iteration(const SeriesArgs& a, cudaStream_t s) {
       leja_iter_f64_k<false><<<a.nblocks, kThreads, 0, s>>>(a);
     }
   } else {
+    ++launch_counter();
+#define AD_F32_LAUNCH(AUGV, ADVV) leja_iter_f32_k<AUGV, ADVV><<<a.nblocks, kThreads, 0, s>>>(a)
     if (a.aug) {
-      ++launch_counter();
-      leja_iter_f32_k<true><<<a.nblocks, kThreads, 0, s>>>(a);
+      if (a.adv == 0) AD_F32_LAUNCH(true, 0);
+      else if (a.adv == 1) AD_F32_LAUNCH(true, 1);
+      else AD_F32_LAUNCH(true, 2);
+    } else {
+      if (a.adv == 0) AD_F32_LAUNCH(false, 0);
+      else if (a.adv == 1) AD_F32_LAUNCH(false, 1);
+      else AD_F32_LAUNCH(false, 2);
     }
-    else {
-      ++launch_counter();
-      leja_iter_f32_k<false><<<a.nblocks, kThreads, 0, s>>>(a);
-    }
+#undef AD_F32_LAUNCH
   }
 }
 

@@ -45,7 +45,7 @@ __global__ void series_init_k(SeriesArgs a, const T* src, double d0, int force, 
        i += (long long)gridDim.x * blockDim.x) {
     const T v = src ? src[i] : T(0);
     y[i] = v;
-    p[i] = (T)(d0 * (double)v);
+    p[i] = (T)d0 * v;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     Ctrl* c = a.ctrl;
@@ -55,6 +55,7 @@ __global__ void series_init_k(SeriesArgs a, const T* src, double d0, int force, 
     c->status = 0;
     c->force = force;
     c->max_iters = max_iters;
+    c->ticket = 0u;
     c->tol = tol;
     c->err_est = 0.0;
     c->ynorm2 = 0.0;
@@ -62,62 +63,16 @@ __global__ void series_init_k(SeriesArgs a, const T* src, double d0, int force, 
   }
 }
 
-// One block: reduce the iteration's block partials in a fixed order, apply
-// the stopping rule |d_{m+1}| ||y_{m+1}|| <= tol ||p_{m+1}|| (m+1 >= 2) or the
-// forced count, advance m.  The loop always ends: m grows by one per call and
-// the series stops once m+1 reaches max_iters (<= kMaxIters).
-__global__ void series_control_k(Ctrl* ctrl, const LejaCoef* lc, const double* partials, int nb,
-                                 unsigned long long handle, int has_handle) {
-  if (ctrl->stop) {
-    if (has_handle && threadIdx.x == 0)
-      cudaGraphSetConditional((cudaGraphConditionalHandle)handle, 0u);
-    return;
-  }
-  double sy = 0.0, sp = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    sy += partials[2 * b];
-    sp += partials[2 * b + 1];
-  }
-  sy = block_sum(sy);
-  sp = block_sum(sp);
-  if (threadIdx.x == 0) {
-    const int m = ctrl->m;
-    const int terms = m + 1;
-    const double ny = sqrt(sy), np = sqrt(sp);
-    const double absd = lc[m].absd;
-    ctrl->ynorm2 = sy;
-    ctrl->pnorm2 = sp;
-    ctrl->iters = terms;
-    ctrl->err_est = np > 0.0 ? absd * ny / np : (ny > 0.0 ? INFINITY : 0.0);
-    int stop = 0;
-    if (ctrl->force > 0) {
-      stop = terms >= ctrl->force;
-    } else {
-      if (!(sy == sy) || !(sp == sp)) {            // NaN: give up
-        stop = 1;
-        ctrl->status = 3;
-      } else if (terms >= 2 && absd * ny <= ctrl->tol * np) {
-        stop = 1;
-      } else if (terms >= ctrl->max_iters) {
-        stop = 1;
-        ctrl->status = 3;
-      }
-    }
-    if (terms >= kMaxIters) stop = 1;              // hard cap, independent of the settings
-    ctrl->stop = stop;
-    ctrl->m = m + 1;
-    if (has_handle) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, stop ? 0u : 1u);
-  }
-}
-
+// z = a x + b y in the storage type's own arithmetic (no FP64 for float data:
+// FP64 is the scarce pipe on this GPU).
 template <typename T>
-__global__ void axpby_k(long long n, double a, const T* x, double b, const T* y, T* z) {
+__global__ void axpby_k(long long n, T a, const T* x, T b, const T* y, T* z) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    double r = 0.0;
-    if (x) r = a * (double)x[i];
-    if (y) r = fma(b, (double)y[i], r);
-    z[i] = (T)r;
+    T r = T(0);
+    if (x) r = a * x[i];
+    if (y) r = fma(b, y[i], r);
+    z[i] = r;
   }
 }
 
@@ -257,12 +212,6 @@ void series_init(const SeriesArgs& a, const void* src, double d0, int force, int
                                                  max_iters, tol);
 }
 
-void series_control(const SeriesArgs& a, unsigned long long handle, int has_handle,
-                    cudaStream_t s) {
-  ++launch_counter();
-  series_control_k<<<1, kThreads, 0, s>>>(a.ctrl, a.lc, a.partials, a.nblocks, handle, has_handle);
-}
-
 void axpby(int prec, long long n, double a, const void* x, double b, const void* y, void* z,
            cudaStream_t s) {
   const int nb = stream_blocks(n);
@@ -271,7 +220,7 @@ void axpby(int prec, long long n, double a, const void* x, double b, const void*
     axpby_k<double><<<nb, kThreads, 0, s>>>(n, a, static_cast<const double*>(x), b,
                                             static_cast<const double*>(y), static_cast<double*>(z));
   else
-    axpby_k<float><<<nb, kThreads, 0, s>>>(n, a, static_cast<const float*>(x), b,
+    axpby_k<float><<<nb, kThreads, 0, s>>>(n, (float)a, static_cast<const float*>(x), (float)b,
                                            static_cast<const float*>(y), static_cast<float*>(z));
 }
 

@@ -190,6 +190,47 @@ def test_cn_step(bc):
     assert rel(u2.cpu().numpy(), ref2) <= 1e-10
 
 
+FP32_CASES = CASES + [
+    (300, 70, BC_PERIODIC, "random", (0.4, -0.2), True),      # ragged tiles, advection field
+    (513, 33, BC_DIRICHLET0, "circular", (0.2, 0.1), False),  # 3 column tiles, 2 row tiles
+    (1, 40, BC_DIRICHLET0, "random", (0.0, 0.3), False),      # one column
+    (257, 1, BC_PERIODIC, "random", (0.1, 0.0), False),       # one row, halo at a tile seam
+]
+
+
+@pytest.mark.parametrize("case", FP32_CASES)
+@pytest.mark.parametrize("s", [1, 2])
+def test_fp32_forced_step_matches_oracle(case, s):
+    """FP32 storage and stencil arithmetic: same iteration count as the oracle,
+    agreement to the FP32 bar (1e-5 relative L2)."""
+    nx, ny, bc, kind, adv, advf = case
+    c = (0.5,) if s == 1 else (1 / 3, 2 / 3)
+    p = small_problem(nx, ny, bc, kind, adv=adv, adv_field=advf, dt_factor=60, s=s, c=c)
+    A, alpha = oracle_operator(p)
+    op = gpu_operator(p, precision=1)
+    ad().set_spectral_bound(op, alpha)
+    S = lambda t: p.source_at(t).ravel()
+    ref, ost = integrators.expquad_step(A, p.u0.ravel(), 0.1, p.dt, s, c, S, alpha, force_iters=20)
+    u = devT(p.u0, 1)
+    st = ad().expquad_step(op, u, 0.1, p.dt, s, c, gpu_source(p, 1), force_iters=20)
+    assert st["matvecs"] == ost.matvecs
+    assert rel(u.cpu().numpy(), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("case", FP32_CASES[:6])
+def test_fp32_phi1_forced_matches_oracle(case):
+    nx, ny, bc, kind, adv, advf = case
+    p = small_problem(nx, ny, bc, kind, adv=adv, adv_field=advf, dt_factor=150)
+    A, alpha = oracle_operator(p)
+    op = gpu_operator(p, precision=1)
+    ad().set_spectral_bound(op, alpha)
+    v = np.random.default_rng(11).standard_normal(p.grid.n)
+    ref, _ = leja.leja_phi1(A, v, p.dt, alpha, force_iters=30)
+    out = torch.empty(p.grid.n, dtype=torch.float32, device=DEV)
+    ad().leja_phi1(op, devT(v, 1), out, p.dt, force_iters=30)
+    assert rel(out.cpu().numpy(), ref) <= 1e-5
+
+
 def test_fp32_storage_step_against_fp64_oracle():
     p = small_problem(200, 180, BC_DIRICHLET0, "stream", dt_factor=100)
     A, alpha = oracle_operator(p)
