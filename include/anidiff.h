@@ -167,6 +167,39 @@ AD_API int ad_expquad_step(ad_operator* op, void* u, double t, double dt, int s,
 AD_API int ad_cn_step(ad_operator* op, void* u, double t, double dt, const ad_source* src,
                double gmres_tol, int restart, int force_iters, ad_stats* stats);
 
+/* ---------------------------------------------------------------- batched form
+ * Many independent problems of uneven size (for example the momentum slices
+ * of a cosmic-ray grid: with the momentum terms of the full transport
+ * equation dropped, each momentum only sets its own coefficients) advanced by
+ * one exponential-midpoint step each (Eq. exp_midpoint) in ONE CUDA graph
+ * launch.  Each slice keeps its own spectral bound, Leja scalars and stopping
+ * rule; the fused iteration kernel strides over one flat list of 256 x TY
+ * tiles of every active slice, and slices that have converged drop out. */
+typedef struct ad_batch ad_batch;
+
+/* Group nslices AD_FP32_STORAGE operators (same advection mode, same stream;
+ * sizes may differ).  The operators must outlive the batch and their
+ * workspaces are used by it.  autotune != 0: time tile heights {8,16,32,64} x
+ * {2,3,4} resident blocks per SM on this batch and keep the fastest; the
+ * choice is cached in a JSON file (AD_AUTOTUNE_CACHE, default
+ * autotune_cache.json beside the library) keyed by the slice-size mix. */
+AD_API int ad_create_batch(ad_operator* const* ops, int nslices, int autotune, ad_batch** out);
+AD_API int ad_destroy_batch(ad_batch* b);
+
+/* One exponential-midpoint step of every slice, in place on u[s] (float32
+ * device vectors).  src: NULL or an array of nslices sources (at most 4 terms
+ * each, evaluated at t + dt/2).  Every slice needs gamma_s dt <= rho_max (one
+ * substep).  force_iters > 0 runs exactly that many iterations per slice.
+ * per_slice: NULL or nslices stats (kernel_launches holds the whole step's
+ * count in every entry).  AD_ERR_NOT_CONVERGED if any slice hit max_iters. */
+AD_API int ad_batch_midpoint_step(ad_batch* b, void* const* u, double t, double dt,
+                                  const ad_source* src, double tol, int force_iters,
+                                  ad_stats* per_slice);
+
+/* Chosen tile height, launch blocks, tile count and the autotuned kernel time. */
+AD_API int ad_batch_info(const ad_batch* b, int* tile_rows, int* blocks, int* ntiles,
+                         double* tuned_ms);
+
 /* Measurement helper (no counterpart in the paper): time the fused Leja
  * iteration kernel alone.  Runs `reps` iterations of the series kernel
  * (aug = 0: phi_1 form, 1: augmented form) on the operator's stream with a

@@ -66,6 +66,10 @@ _sig = {
     "ad_profile_leja_iteration": (_i, [_vp, _i, _i, C.POINTER(_d)]),
     "ad_leja_phi1_noalloc": (_i, [C.POINTER(_Grid), _vp, _vp, _vp, _d, _d, _d, _vp, _vp, _d, _d,
                                   _i, _vp, C.POINTER(Stats)]),
+    "ad_create_batch": (_i, [C.POINTER(_vp), _i, _i, C.POINTER(_vp)]),
+    "ad_destroy_batch": (_i, [_vp]),
+    "ad_batch_midpoint_step": (_i, [_vp, C.POINTER(_vp), _d, _d, _vp, _d, _i, C.POINTER(Stats)]),
+    "ad_batch_info": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_d)]),
     "ad_last_error": (C.c_char_p, []),
     "ad_version": (_i, []),
 }
@@ -302,3 +306,67 @@ def leja_phi1_noalloc(nx: int, ny: int, bc: int, Dxx, Dxy, Dyy, v, out, dt: floa
                                      float(ax), float(ay), alpha, ptr(v, "v"), ptr(out, "out"),
                                      dt, tol, force_iters, _stream_ptr(stream), C.byref(st)), st)
     return st.as_dict()
+
+
+class Batch:
+    """Handle of an ad_batch: FP32-storage operators advanced together."""
+
+    def __init__(self, handle, ops):
+        self.handle = handle
+        self.ops = list(ops)          # keep the operators alive
+
+    def close(self):
+        if self.handle:
+            _lib.ad_destroy_batch(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def create_batch(ops, autotune: bool = True) -> Batch:
+    """ad_create_batch over a list of FP32_STORAGE operators."""
+    arr = (_vp * len(ops))(*[o.handle for o in ops])
+    h = _vp()
+    _check(_lib.ad_create_batch(arr, len(ops), 1 if autotune else 0, C.byref(h)))
+    return Batch(h.value, ops)
+
+
+def destroy_batch(b: Batch):
+    b.close()
+
+
+def batch_info(b: Batch) -> dict:
+    ty, nb, nt, ms = _i(), _i(), _i(), _d()
+    _check(_lib.ad_batch_info(b.handle, C.byref(ty), C.byref(nb), C.byref(nt), C.byref(ms)))
+    return {"tile_rows": ty.value, "blocks": nb.value, "tiles": nt.value, "tuned_ms": ms.value}
+
+
+def batch_midpoint_step(b: Batch, us, t: float, dt: float, sources=None, tol: float = 1e-6,
+                        force_iters: int = -1):
+    """ad_batch_midpoint_step: us = list of float32 device tensors (one per slice),
+    sources = None or a list of Source (at most 4 terms each).  Returns the
+    per-slice stats."""
+    S = len(b.ops)
+    if len(us) != S:
+        raise ValueError("one state vector per slice")
+    uptr = (_vp * S)(*[b.ops[s].vec(us[s], f"u[{s}]") for s in range(S)])
+    keep = []
+    srcp = None
+    if sources is not None:
+        arr = (_Source * S)()
+        for s, src in enumerate(sources):
+            st_, k = _source_struct(b.ops[s], src)
+            keep.append(k)
+            if st_ is not None:
+                arr[s] = st_
+        srcp = C.cast(arr, _vp)
+        keep.append(arr)
+    stats = (Stats * S)()
+    _check(_lib.ad_batch_midpoint_step(b.handle, uptr, t, dt, srcp, tol, force_iters, stats),
+           stats[0])
+    del keep
+    return [stats[s].as_dict() for s in range(S)]

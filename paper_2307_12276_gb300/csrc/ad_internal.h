@@ -32,7 +32,7 @@ struct Ctrl {
   int force;      // > 0: exact iteration count, no stopping test
   int max_iters;
   unsigned int ticket;  // blocks of the running iteration that have finished
-  int pad1;
+  unsigned int gen;     // grid-barrier generation of the persistent series kernel
   double tol;
   double err_est;
   double ynorm2;  // last ||y_{m+1}||^2
@@ -105,6 +105,12 @@ void series_init(const SeriesArgs& a, const void* src, double d0, int force, int
 // finish reduces the norm partials in a fixed order, applies the stopping rule,
 // advances ctrl->m and, with a.has_handle, sets the graph loop condition.
 void series_iteration(const SeriesArgs& a, cudaStream_t s);
+// Whole Newton series in one cooperative launch (FP64, n <= kPersistMaxCells).
+// gen: device barrier generation counter (persists across calls).  Returns
+// false if not applicable or refused; nothing was launched then.
+constexpr long long kPersistMaxCells = 152LL * 2048;
+bool series_run_persistent(const SeriesArgs& a, unsigned int* gen, cudaStream_t s);
+
 // grid size of the fused iteration kernel (FP64: by cell count; FP32: by tile count)
 int series_blocks(int prec, long long n);
 int series_blocks_grid(int prec, int nx, int ny);
@@ -136,6 +142,23 @@ void multi_axpy_add(long long n, const double* V, long long ldv, int k, const do
                     cudaStream_t s);
 
 int stream_blocks(long long n);   // grid size of the streaming kernels
+
+// Read-only view of an operator's buffers and spectral state (capi.cu).
+struct OperatorView {
+  GridDev g;
+  int prec;
+  const void* coef;
+  void *y0, *y1, *p, *w1, *w2;
+  double alpha, c, gamma, rho_max;
+  int max_iters;
+  int adv;
+  float abx, aby;
+  cudaStream_t stream;
+};
+}  // namespace ad
+struct ad_operator;
+namespace ad {
+bool operator_view(const ad_operator* op, OperatorView* v);
 
 // Set the thread-local message returned by ad_last_error().
 void set_error_message(const char* msg);

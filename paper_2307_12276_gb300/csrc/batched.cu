@@ -1,0 +1,708 @@
+// Batched exponential-midpoint step over many independent problems of uneven
+// size (the momentum slices of a cosmic-ray transport grid: the momentum
+// terms of the full transport equation are dropped, so each momentum p only
+// sets its own diffusion coefficients).  Every slice is an FP32-storage
+// operator; one step of Eq. exp_midpoint,
+//     u_s += dt phi_1(dt A_s)(A_s u_s + S_s(t + dt/2)),
+// runs for all slices as ONE CUDA graph launch:
+//   apply (v_s = A_s u_s + S_s)  ->  init (y_0 = v_s, p = d_0 v_s)
+//   -> WHILE { 4 x fused Leja iteration over every active slice's tiles }
+//   -> update (u_s += dt p_s).
+// The iteration kernel is persistent: its blocks stride over one flat list of
+// 256 x TY tiles of all slices.  Each slice keeps its own Leja scalars,
+// control block and stopping decision: the last tile of a slice to finish
+// reduces that slice's tile partials (fixed order) and applies the stopping
+// rule; slices that stopped are skipped; the last block of a launch keeps the
+// loop running while any slice is active.  The tile height TY and the number
+// of resident blocks are chosen per batch by a small autotuner whose choice is
+// cached in a JSON file.
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "ad_internal.h"
+#include "anidiff.h"
+#include "leja_host.h"
+#include "tile_f32.cuh"
+
+namespace ad {
+namespace {
+
+constexpr int kBatchSources = 4;
+constexpr int kBatchUnroll = 4;
+
+struct BatchSlice {
+  SeriesArgs a;                     // operator buffers, batch-owned lc/ctrl
+  float* u;                         // the slice's state (caller memory)
+  const float* src_g[kBatchSources];
+  float src_c[kBatchSources];       // h_k(t + dt/2)
+  int nsrc;
+  float dt;
+  double d0;
+  int tile_off, ntiles, tiles_x;
+};
+
+// Stopping rule of the Newton series (same reading as the single-operator
+// kernels): squared form of |d_{m+1}| ||y|| <= tol ||p|| for m+1 >= 2.
+__device__ int decide(Ctrl* ctrl, const LejaCoef& lc, int m, double ty, double tp) {
+  const int terms = m + 1;
+  ctrl->ynorm2 = ty;
+  ctrl->pnorm2 = tp;
+  ctrl->iters = terms;
+  ctrl->err_est = lc.absd;
+  const double tol = ctrl->tol;
+  int stop = 0;
+  if (ctrl->force > 0) {
+    stop = terms >= ctrl->force;
+  } else if (!(ty == ty) || !(tp == tp)) {
+    stop = 1;
+    ctrl->status = 3;
+  } else if (terms >= 2 && (lc.absd * lc.absd) * ty <= (tol * tol) * tp) {
+    stop = 1;
+  } else if (terms >= ctrl->max_iters) {
+    stop = 1;
+    ctrl->status = 3;
+  }
+  if (terms >= kMaxIters) stop = 1;
+  return stop;
+}
+
+// ---------------------------------------------------------------- kernels
+template <int ADV>
+__global__ void __launch_bounds__(kThreads) batch_apply_k(const BatchSlice* slices,
+                                                         const int* tile_slice, int ntiles, int TY) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const BatchSlice& S = slices[tile_slice[t]];
+    const GridDev g = S.a.g;
+    const int local = t - S.tile_off;
+    const int x0 = (local % S.tiles_x) * kTileCols, y0 = (local / S.tiles_x) * TY;
+    const int i = x0 + threadIdx.x;
+    if (i >= g.nx) continue;
+    const float* F = static_cast<const float*>(S.a.coef);
+    float* v = static_cast<float*>(const_cast<void*>(S.a.w1));
+    for (int j = y0; j < min(g.ny, y0 + TY); ++j) {
+      const long long idx = (long long)j * g.nx + i;
+      const bool interior = i > 0 && j > 0 && i + 1 < g.nx && j + 1 < g.ny;
+      float r = flux_apply_f32(F, g.n, S.u, i, j, g.nx, g.ny, g.bc, interior, ADV, S.a.abx, S.a.aby);
+      for (int k = 0; k < S.nsrc; ++k) r = fmaf(S.src_c[k], S.src_g[k][idx], r);
+      v[idx] = r;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) batch_init_k(const BatchSlice* slices,
+                                                        const int* tile_slice, int ntiles, int TY,
+                                                        int nslices, int force, int max_iters,
+                                                        double tol, unsigned int* bticket) {
+  if (blockIdx.x == 0) {
+    for (int s = threadIdx.x; s < nslices; s += blockDim.x) {
+      Ctrl* c = slices[s].a.ctrl;
+      c->m = 0;
+      c->stop = 0;
+      c->iters = 0;
+      c->status = 0;
+      c->force = force;
+      c->max_iters = max_iters;
+      c->ticket = 0u;
+      c->tol = tol;
+      c->err_est = 0.0;
+      c->ynorm2 = 0.0;
+      c->pnorm2 = 0.0;
+    }
+    if (threadIdx.x == 0) *bticket = 0u;
+  }
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const BatchSlice& S = slices[tile_slice[t]];
+    const GridDev g = S.a.g;
+    const int local = t - S.tile_off;
+    const int x0 = (local % S.tiles_x) * kTileCols, y0 = (local / S.tiles_x) * TY;
+    const int i = x0 + threadIdx.x;
+    if (i >= g.nx) continue;
+    const float* v = static_cast<const float*>(S.a.w1);
+    float* y = static_cast<float*>(S.a.y[0]);
+    float* p = static_cast<float*>(S.a.p);
+    const float d0 = (float)S.d0;
+    for (int j = y0; j < min(g.ny, y0 + TY); ++j) {
+      const long long idx = (long long)j * g.nx + i;
+      const float x = v[idx];
+      y[idx] = x;
+      p[idx] = d0 * x;
+    }
+  }
+}
+
+template <int ADV, int TY>
+__global__ void __launch_bounds__(kThreads) batch_iter_k(const BatchSlice* slices,
+                                                        const int* tile_slice, int ntiles,
+                                                        int nslices, double* tile_partials,
+                                                        unsigned int* bticket,
+                                                        unsigned long long handle, int has_handle) {
+  __shared__ float sy[3][kTileCols + 2];
+  __shared__ float sxy[2][kTileCols + 2];
+  __shared__ float sxx[kTileCols + 2];
+  __shared__ float sax[kTileCols + 2];
+  __shared__ int s_last;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int s = tile_slice[t];
+    const BatchSlice& S = slices[s];
+    const volatile Ctrl* vc = S.a.ctrl;
+    if (vc->stop) continue;                    // uniform over the block
+    const int m = vc->m;
+    const LejaCoef lc = S.a.lc[m];
+    const float* yin = static_cast<const float*>(S.a.y[m & 1]);
+    float* yout = static_cast<float*>(S.a.y[(m + 1) & 1]);
+    float* p = static_cast<float*>(S.a.p);
+    const float ig = (float)(1.0 / S.a.gamma);
+    const float sh = (float)(S.a.c / S.a.gamma + lc.xi);
+    const int local = t - S.tile_off;
+    double ty = 0.0, tp = 0.0;
+    tile_f32<false, ADV, TY>(S.a, lc, local % S.tiles_x, local / S.tiles_x, yin, yout, p, ig, sh,
+                             (float)lc.d, 0.0f, 0.0f, sy, sxx, sxy, sax, ty, tp);
+    block_sum2(ty, tp);
+    if (threadIdx.x == 0) {
+      tile_partials[2 * t] = ty;
+      tile_partials[2 * t + 1] = tp;
+      __threadfence();
+      const unsigned int k = atomicAdd(&S.a.ctrl->ticket, 1u);
+      s_last = (k == (unsigned int)S.ntiles - 1u) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last) {                              // this slice's last tile: decide for it
+      __threadfence();
+      double ay = 0.0, ap = 0.0;
+      for (int q = threadIdx.x; q < S.ntiles; q += blockDim.x) {
+        ay += __ldcg(&tile_partials[2 * (S.tile_off + q)]);
+        ap += __ldcg(&tile_partials[2 * (S.tile_off + q) + 1]);
+      }
+      block_sum2(ay, ap);
+      if (threadIdx.x == 0) {
+        Ctrl* ctrl = S.a.ctrl;
+        const int stop = decide(ctrl, lc, m, ay, ap);
+        ctrl->ticket = 0u;
+        ctrl->stop = stop;
+        ctrl->m = m + 1;
+        __threadfence();
+      }
+    }
+  }
+  // the launch's last block keeps the loop running while any slice is active
+  __syncthreads();                             // every warp has read s_last
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int k = atomicAdd(bticket, 1u);
+    s_last = (k == gridDim.x - 1u) ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    int active = 0;
+    for (int s = 0; s < nslices; ++s) active |= !*(volatile int*)&slices[s].a.ctrl->stop;
+    *bticket = 0u;
+    __threadfence();
+    if (has_handle) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, active ? 1u : 0u);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) batch_update_k(const BatchSlice* slices,
+                                                          const int* tile_slice, int ntiles,
+                                                          int TY) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const BatchSlice& S = slices[tile_slice[t]];
+    const GridDev g = S.a.g;
+    const int local = t - S.tile_off;
+    const int x0 = (local % S.tiles_x) * kTileCols, y0 = (local / S.tiles_x) * TY;
+    const int i = x0 + threadIdx.x;
+    if (i >= g.nx) continue;
+    const float* p = static_cast<const float*>(S.a.p);
+    for (int j = y0; j < min(g.ny, y0 + TY); ++j) {
+      const long long idx = (long long)j * g.nx + i;
+      S.u[idx] = fmaf(S.dt, p[idx], S.u[idx]);
+    }
+  }
+}
+
+using IterFn = void (*)(const BatchSlice*, const int*, int, int, double*, unsigned int*,
+                        unsigned long long, int);
+
+template <int ADV>
+IterFn iter_fn(int TY) {
+  switch (TY) {
+    case 8: return batch_iter_k<ADV, 8>;
+    case 16: return batch_iter_k<ADV, 16>;
+    case 32: return batch_iter_k<ADV, 32>;
+    default: return batch_iter_k<ADV, 64>;
+  }
+}
+
+IterFn pick_iter(int adv, int TY) {
+  return adv == 0 ? iter_fn<0>(TY) : (adv == 1 ? iter_fn<1>(TY) : iter_fn<2>(TY));
+}
+
+void* pick_apply(int adv) {
+  return adv == 0 ? (void*)batch_apply_k<0> : (adv == 1 ? (void*)batch_apply_k<1> : (void*)batch_apply_k<2>);
+}
+
+}  // namespace
+}  // namespace ad
+
+using namespace ad;
+
+struct ad_batch {
+  std::vector<ad_operator*> ops;
+  int S = 0;
+  int adv = 0;
+  cudaStream_t stream = nullptr;
+  int TY = 32;
+  int nblocks = 608;
+  double tuned_ms = 0.0;
+  std::vector<BatchSlice> hs;
+  BatchSlice* d_slices = nullptr;
+  int* d_tile_slice = nullptr;
+  int ntiles = 0;
+  double* d_partials = nullptr;
+  LejaCoef* d_lc = nullptr;
+  Ctrl* d_ctrl = nullptr;
+  unsigned int* d_bticket = nullptr;
+  std::vector<LejaCoef> h_lc;
+  std::vector<double> lc_dt, lc_alpha;
+  std::vector<Ctrl> h_ctrl;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int graph_force = -2;
+  double graph_tol = -1.0;
+};
+
+namespace {
+
+int bfail(int code, const std::string& m) {
+  set_error_message(m.c_str());
+  return code;
+}
+
+#define B_CUDA(expr)                                                                     \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      cudaGetLastError();                                                                \
+      return bfail(AD_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));     \
+    }                                                                                    \
+  } while (0)
+
+// Tile table for tile height TY: slice s owns tiles [off_s, off_s + n_s).
+void build_tiles(ad_batch* b, int TY, std::vector<int>& tile_slice) {
+  tile_slice.clear();
+  for (int s = 0; s < b->S; ++s) {
+    BatchSlice& hs = b->hs[s];
+    const int tx = (hs.a.g.nx + kTileCols - 1) / kTileCols;
+    const int ty = (hs.a.g.ny + TY - 1) / TY;
+    hs.tiles_x = tx;
+    hs.ntiles = tx * ty;
+    hs.tile_off = (int)tile_slice.size();
+    for (int k = 0; k < hs.ntiles; ++k) tile_slice.push_back(s);
+  }
+}
+
+int upload_tiles(ad_batch* b, int TY) {
+  std::vector<int> ts;
+  build_tiles(b, TY, ts);
+  if ((int)ts.size() > b->ntiles) {
+    if (b->d_tile_slice) cudaFree(b->d_tile_slice);
+    if (b->d_partials) cudaFree(b->d_partials);
+    b->d_tile_slice = nullptr;
+    b->d_partials = nullptr;
+    B_CUDA(cudaMalloc(&b->d_tile_slice, sizeof(int) * ts.size()));
+    B_CUDA(cudaMalloc(&b->d_partials, sizeof(double) * 2 * ts.size()));
+  }
+  b->ntiles = (int)ts.size();
+  b->TY = TY;
+  B_CUDA(cudaMemcpyAsync(b->d_tile_slice, ts.data(), sizeof(int) * ts.size(),
+                         cudaMemcpyHostToDevice, b->stream));
+  B_CUDA(cudaMemcpyAsync(b->d_slices, b->hs.data(), sizeof(BatchSlice) * b->S,
+                         cudaMemcpyHostToDevice, b->stream));
+  B_CUDA(cudaStreamSynchronize(b->stream));
+  return AD_OK;
+}
+
+void destroy_batch_graph(ad_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+int build_batch_graph(ad_batch* b, int force, double tol) {
+  destroy_batch_graph(b);
+  cudaGraph_t g;
+  B_CUDA(cudaGraphCreate(&g, 0));
+  b->graph = g;
+  cudaGraphConditionalHandle h;
+  B_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  int TY = b->TY, nt = b->ntiles, S = b->S, maxit = kMaxIters;
+  const BatchSlice* sl = b->d_slices;
+  const int* ts = b->d_tile_slice;
+  unsigned int* bt = b->d_bticket;
+  double* parts = b->d_partials;
+  unsigned long long hv = (unsigned long long)h;
+  int one = 1;
+  const int grid = std::min(nt, b->nblocks);
+  cudaKernelNodeParams kp = {};
+  kp.blockDim = dim3(kThreads);
+  kp.gridDim = dim3(grid);
+  cudaGraphNode_t n_apply, n_init, n_cond, n_upd;
+  {
+    void* args[] = {&sl, &ts, &nt, &TY};
+    kp.func = pick_apply(b->adv);
+    kp.kernelParams = args;
+    B_CUDA(cudaGraphAddKernelNode(&n_apply, g, nullptr, 0, &kp));
+  }
+  {
+    void* args[] = {&sl, &ts, &nt, &TY, &S, &force, &maxit, &tol, &bt};
+    kp.func = (void*)batch_init_k;
+    kp.kernelParams = args;
+    B_CUDA(cudaGraphAddKernelNode(&n_init, g, &n_apply, 1, &kp));
+  }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  B_CUDA(cudaGraphAddNode(&n_cond, g, &n_init, nullptr, 1, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  {
+    void* args[] = {&sl, &ts, &nt, &S, &parts, &bt, &hv, &one};
+    kp.func = (void*)pick_iter(b->adv, TY);
+    kp.kernelParams = args;
+    cudaGraphNode_t prev = nullptr;
+    for (int u = 0; u < kBatchUnroll; ++u) {
+      cudaGraphNode_t nn;
+      B_CUDA(cudaGraphAddKernelNode(&nn, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+      prev = nn;
+    }
+  }
+  {
+    void* args[] = {&sl, &ts, &nt, &TY};
+    kp.func = (void*)batch_update_k;
+    kp.kernelParams = args;
+    B_CUDA(cudaGraphAddKernelNode(&n_upd, g, &n_cond, 1, &kp));
+  }
+  B_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
+  b->graph_force = force;
+  b->graph_tol = tol;
+  return AD_OK;
+}
+
+// --------------------------------------------------------------- autotune cache
+std::string cache_path() {
+  if (const char* e = getenv("AD_AUTOTUNE_CACHE")) return e;
+  Dl_info info;
+  if (dladdr((void*)&cache_path, &info) && info.dli_fname) {
+    std::string f = info.dli_fname;
+    const size_t k = f.rfind('/');
+    return (k == std::string::npos ? std::string(".") : f.substr(0, k)) + "/autotune_cache.json";
+  }
+  return "autotune_cache.json";
+}
+
+struct TuneEntry {
+  int ty, bps;
+  double ms;
+};
+
+// The cache is a JSON object with one entry per line:
+//   "key": {"ty": 16, "bps": 4, "ms": 0.1234},
+std::map<std::string, TuneEntry> read_cache() {
+  std::map<std::string, TuneEntry> m;
+  FILE* f = fopen(cache_path().c_str(), "r");
+  if (!f) return m;
+  char line[1024];
+  while (fgets(line, sizeof line, f)) {
+    char key[512];
+    TuneEntry e{};
+    if (sscanf(line, " \"%511[^\"]\": {\"ty\": %d, \"bps\": %d, \"ms\": %lf", key, &e.ty, &e.bps,
+               &e.ms) == 4)
+      m[key] = e;
+  }
+  fclose(f);
+  return m;
+}
+
+void write_cache(const std::map<std::string, TuneEntry>& m) {
+  const std::string path = cache_path();
+  const std::string tmp = path + ".tmp";
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) return;
+  fprintf(f, "{\n");
+  size_t k = 0;
+  for (const auto& kv : m) {
+    fprintf(f, "  \"%s\": {\"ty\": %d, \"bps\": %d, \"ms\": %.6f}%s\n", kv.first.c_str(), kv.second.ty,
+            kv.second.bps, kv.second.ms, (++k < m.size()) ? "," : "");
+  }
+  fprintf(f, "}\n");
+  fclose(f);
+  rename(tmp.c_str(), path.c_str());
+}
+
+std::string tune_key(const ad_batch* b) {
+  std::map<std::pair<int, int>, int> sizes;
+  for (const auto& s : b->hs) sizes[{s.a.g.nx, s.a.g.ny}]++;
+  std::string k = "f32-adv" + std::to_string(b->adv) + "-S" + std::to_string(b->S);
+  for (const auto& kv : sizes)
+    k += "-" + std::to_string(kv.first.first) + "x" + std::to_string(kv.first.second) + "*" +
+         std::to_string(kv.second);
+  return k;
+}
+
+// Time `reps` forced iterations of the batched kernel for one (TY, blocks).
+int time_config(ad_batch* b, int TY, int nblocks, int reps, double* ms_out) {
+  {
+    const int r = upload_tiles(b, TY);
+    if (r != AD_OK) return r;
+  }
+  const int grid = std::min(b->ntiles, nblocks);
+  int force = reps, maxit = kMaxIters;
+  double tol = 0.0;
+  batch_init_k<<<grid, kThreads, 0, b->stream>>>(b->d_slices, b->d_tile_slice, b->ntiles, TY, b->S,
+                                                 force, maxit, tol, b->d_bticket);
+  IterFn fn = pick_iter(b->adv, TY);
+  cudaEvent_t e0, e1;
+  B_CUDA(cudaEventCreate(&e0));
+  B_CUDA(cudaEventCreate(&e1));
+  B_CUDA(cudaEventRecord(e0, b->stream));
+  for (int r = 0; r < reps; ++r)
+    fn<<<grid, kThreads, 0, b->stream>>>(b->d_slices, b->d_tile_slice, b->ntiles, b->S,
+                                         b->d_partials, b->d_bticket, 0ULL, 0);
+  B_CUDA(cudaEventRecord(e1, b->stream));
+  B_CUDA(cudaStreamSynchronize(b->stream));
+  float ms = 0.f;
+  B_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = ms / reps;
+  return AD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ad_create_batch(ad_operator* const* ops, int nslices, int autotune, ad_batch** out) {
+  set_error_message("");
+  if (!out || !ops || nslices < 1) return bfail(AD_ERR_INVALID, "ops/out NULL or nslices < 1");
+  *out = nullptr;
+  ad_batch* b = new ad_batch();
+  b->S = nslices;
+  b->hs.resize(nslices);
+  for (int s = 0; s < nslices; ++s) {
+    OperatorView v;
+    if (!ops[s] || !operator_view(ops[s], &v)) {
+      delete b;
+      return bfail(AD_ERR_INVALID, "NULL operator in the batch");
+    }
+    if (v.prec != 1) {
+      delete b;
+      return bfail(AD_ERR_INVALID, "batched steps need AD_FP32_STORAGE operators");
+    }
+    if (s == 0) {
+      b->adv = v.adv;
+      b->stream = v.stream;
+    } else if (v.adv != b->adv || v.stream != b->stream) {
+      delete b;
+      return bfail(AD_ERR_INVALID, "batch slices must share the advection mode and the stream");
+    }
+    b->ops.push_back(ops[s]);
+    BatchSlice& hs = b->hs[s];
+    hs = BatchSlice{};
+    hs.a.g = v.g;
+    hs.a.prec = 1;
+    hs.a.coef = v.coef;
+    hs.a.y[0] = v.y0;
+    hs.a.y[1] = v.y1;
+    hs.a.p = v.p;
+    hs.a.w1 = v.w1;
+    hs.a.adv = v.adv;
+    hs.a.abx = v.abx;
+    hs.a.aby = v.aby;
+    hs.a.c = v.c;
+    hs.a.gamma = v.gamma;
+    // the autotuner iterates on whatever the workspace holds: start from zeros
+    cudaMemsetAsync(v.w1, 0, sizeof(float) * (size_t)v.g.n, v.stream);
+  }
+  bool ok = cudaMalloc(&b->d_slices, sizeof(BatchSlice) * nslices) == cudaSuccess &&
+            cudaMalloc(&b->d_lc, sizeof(LejaCoef) * kMaxIters * nslices) == cudaSuccess &&
+            cudaMalloc(&b->d_ctrl, sizeof(Ctrl) * nslices) == cudaSuccess &&
+            cudaMalloc(&b->d_bticket, sizeof(unsigned int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    ad_destroy_batch(b);
+    return bfail(AD_ERR_NOMEM, "batch allocation failed");
+  }
+  cudaMemsetAsync(b->d_ctrl, 0, sizeof(Ctrl) * nslices, b->stream);
+  cudaMemsetAsync(b->d_bticket, 0, sizeof(unsigned int), b->stream);
+  for (int s = 0; s < nslices; ++s) {
+    b->hs[s].a.lc = b->d_lc + (size_t)s * kMaxIters;
+    b->hs[s].a.ctrl = b->d_ctrl + s;
+  }
+  b->h_lc.resize((size_t)kMaxIters * nslices);
+  b->lc_dt.assign(nslices, -1.0);
+  b->lc_alpha.assign(nslices, 0.0);
+  b->h_ctrl.resize(nslices);
+  // tile shape: cached autotune result, a fresh autotune, or the default
+  int TY = 32, bps = 4;
+  double tuned = 0.0;
+  const std::string key = tune_key(b);
+  auto cache = read_cache();
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    TY = it->second.ty;
+    bps = it->second.bps;
+    tuned = it->second.ms;
+  } else if (autotune) {
+    double best = 1e30;
+    for (int ty : {8, 16, 32, 64})
+      for (int bp : {2, 3, 4}) {
+        double ms = 0.0;
+        const int r = time_config(b, ty, 152 * bp, 6, &ms);
+        if (r != AD_OK) {
+          std::string msg = ad_last_error();
+          ad_destroy_batch(b);
+          return bfail(r, msg);
+        }
+        if (ms < best) { best = ms; TY = ty; bps = bp; }
+      }
+    tuned = best;
+    cache[key] = TuneEntry{TY, bps, best};
+    write_cache(cache);
+  }
+  b->nblocks = 152 * bps;
+  b->tuned_ms = tuned;
+  const int r = upload_tiles(b, TY);
+  if (r != AD_OK) {
+    std::string msg = ad_last_error();
+    ad_destroy_batch(b);
+    return bfail(r, msg);
+  }
+  *out = b;
+  return AD_OK;
+}
+
+int ad_destroy_batch(ad_batch* b) {
+  if (!b) return AD_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  destroy_batch_graph(b);
+  for (void* p : {(void*)b->d_slices, (void*)b->d_tile_slice, (void*)b->d_partials, (void*)b->d_lc,
+                  (void*)b->d_ctrl, (void*)b->d_bticket})
+    if (p) cudaFree(p);
+  delete b;
+  return AD_OK;
+}
+
+int ad_batch_info(const ad_batch* b, int* tile_rows, int* blocks, int* ntiles, double* tuned_ms) {
+  if (!b) return bfail(AD_ERR_INVALID, "NULL batch");
+  if (tile_rows) *tile_rows = b->TY;
+  if (blocks) *blocks = std::min(b->ntiles, b->nblocks);
+  if (ntiles) *ntiles = b->ntiles;
+  if (tuned_ms) *tuned_ms = b->tuned_ms;
+  return AD_OK;
+}
+
+int ad_batch_midpoint_step(ad_batch* b, void* const* u, double t, double dt,
+                           const ad_source* src, double tol, int force_iters,
+                           ad_stats* per_slice) {
+  set_error_message("");
+  if (!b || !u) return bfail(AD_ERR_INVALID, "NULL argument");
+  if (!(dt > 0) || !std::isfinite(dt) || !std::isfinite(t)) return bfail(AD_ERR_INVALID, "bad t or dt");
+  if (force_iters < 0 && !(tol > 0)) return bfail(AD_ERR_INVALID, "tol must be positive");
+  if (force_iters > kMaxIters) return bfail(AD_ERR_INVALID, "force_iters > 500");
+  const std::vector<double>& xi = leja_points();
+  const long long l0 = launch_counter();
+  bool lc_dirty = false;
+  for (int s = 0; s < b->S; ++s) {
+    OperatorView v;
+    operator_view(b->ops[s], &v);
+    BatchSlice& hs = b->hs[s];
+    if (!u[s]) return bfail(AD_ERR_INVALID, "u[s] is NULL");
+    hs.u = static_cast<float*>(u[s]);
+    hs.a.c = v.c;
+    hs.a.gamma = v.gamma;
+    hs.dt = (float)dt;
+    if (v.gamma * dt > v.rho_max)
+      return bfail(AD_ERR_INVALID, "batched steps need gamma*dt <= rho_max for every slice "
+                                   "(one substep); reduce dt or raise rho_max");
+    hs.nsrc = 0;
+    if (src) {
+      const ad_source& q = src[s];
+      if (q.nterms < 0 || q.nterms > kBatchSources)
+        return bfail(AD_ERR_INVALID, "batched sources: at most 4 terms per slice");
+      hs.nsrc = q.nterms;
+      for (int k = 0; k < q.nterms; ++k) {
+        hs.src_g[k] = static_cast<const float*>(q.g[k]);
+        hs.src_c[k] = (float)(q.h ? q.h(k, t + 0.5 * dt, q.ctx) : 1.0);
+      }
+    }
+    if (b->lc_dt[s] != dt || b->lc_alpha[s] != v.alpha) {
+      double f[kMaxIters + 1], d[kMaxIters + 1];
+      for (int m = 0; m <= kMaxIters; ++m) f[m] = phi1((v.c + v.gamma * xi[m]) * dt);
+      divided_differences(xi.data(), f, kMaxIters + 1, d);
+      for (int m = 0; m < kMaxIters; ++m)
+        b->h_lc[(size_t)s * kMaxIters + m] =
+            LejaCoef{xi[m], d[m + 1], std::fabs(d[m + 1]), 0.0, 0.0, {0.0, 0.0, 0.0}};
+      hs.d0 = d[0];
+      b->lc_dt[s] = dt;
+      b->lc_alpha[s] = v.alpha;
+      lc_dirty = true;
+    }
+  }
+  if (lc_dirty)
+    B_CUDA(cudaMemcpyAsync(b->d_lc, b->h_lc.data(), sizeof(LejaCoef) * b->h_lc.size(),
+                           cudaMemcpyHostToDevice, b->stream));
+  B_CUDA(cudaMemcpyAsync(b->d_slices, b->hs.data(), sizeof(BatchSlice) * b->S,
+                         cudaMemcpyHostToDevice, b->stream));
+  const int force = force_iters < 0 ? -1 : force_iters;
+  if (!b->exec || b->graph_force != force || b->graph_tol != tol) {
+    const int r = build_batch_graph(b, force, tol);
+    if (r != AD_OK) return r;
+  }
+  if (force == 0) return bfail(AD_ERR_INVALID, "force_iters == 0 is not supported in batches");
+  B_CUDA(cudaGraphLaunch(b->exec, b->stream));
+  B_CUDA(cudaMemcpyAsync(b->h_ctrl.data(), b->d_ctrl, sizeof(Ctrl) * b->S, cudaMemcpyDeviceToHost,
+                         b->stream));
+  B_CUDA(cudaStreamSynchronize(b->stream));
+  int status = AD_OK;
+  int total_iters = 0;
+  for (int s = 0; s < b->S; ++s) {
+    const Ctrl& c = b->h_ctrl[s];
+    total_iters += c.iters;
+    if (c.status != 0) status = AD_ERR_NOT_CONVERGED;
+    if (per_slice) {
+      ad_stats& st = per_slice[s];
+      st = ad_stats{};
+      st.iters = c.iters;
+      st.matvecs = c.iters + 1;
+      st.substeps = 1;
+      st.converged = c.status == 0;
+      st.err_est = c.pnorm2 > 0.0 ? c.err_est * std::sqrt(c.ynorm2 / c.pnorm2) : 0.0;
+      st.alpha = b->lc_alpha[s];
+    }
+  }
+  if (per_slice) {
+    // kernels of the whole batched step: apply, init, update and every kernel of
+    // every loop-body run (kBatchUnroll per run, enough runs for the slowest slice)
+    int max_it = 0;
+    for (int s = 0; s < b->S; ++s) max_it = std::max(max_it, b->h_ctrl[s].iters);
+    const int launches = (int)(launch_counter() - l0) + 3 +
+                         kBatchUnroll * ((max_it + kBatchUnroll - 1) / kBatchUnroll);
+    for (int s = 0; s < b->S; ++s) per_slice[s].kernel_launches = launches;
+  }
+  if (status != AD_OK) return bfail(status, "a slice's Leja series reached max_iters");
+  return AD_OK;
+}
+
+}  // extern "C"

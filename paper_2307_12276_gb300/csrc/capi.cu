@@ -122,6 +122,30 @@ struct ad_operator {
   std::vector<double> d_host;                  // divided differences of the current series
 };
 
+namespace ad {
+bool operator_view(const ad_operator* op, OperatorView* v) {
+  if (!op || !v) return false;
+  v->g = op->g;
+  v->prec = op->prec;
+  v->coef = op->prec == 0 ? (const void*)op->Ws : (const void*)op->F;
+  v->y0 = op->Y0;
+  v->y1 = op->Y1;
+  v->p = op->P;
+  v->w1 = op->W1;
+  v->w2 = op->W2;
+  v->alpha = op->alpha;
+  v->c = op->c;
+  v->gamma = op->gamma;
+  v->rho_max = op->rho_max;
+  v->max_iters = op->max_iters;
+  v->adv = op->adv;
+  v->abx = op->abx;
+  v->aby = op->aby;
+  v->stream = op->stream;
+  return true;
+}
+}  // namespace ad
+
 namespace {
 
 SeriesArgs series_args(ad_operator* op, int aug) {
@@ -328,8 +352,13 @@ int run_series(ad_operator* op, int aug, const void* src, double d0, int force, 
     op->h_ctrl->err_est = 0.0;
   } else {
     SeriesGraph& sg = op->graphs[aug];
-    if (!sg.tried) build_graph(op, aug);
-    if (sg.ok) {
+    // small and medium FP64 grids: the whole series in one cooperative launch
+    const bool persist = !getenv("AD_NO_PERSIST") &&
+                         series_run_persistent(a, &op->ctrl->gen, op->stream);
+    if (!persist && !sg.tried) build_graph(op, aug);
+    if (persist) {
+      // launched; the kernel counted itself
+    } else if (sg.ok) {
       CUDA_TRY(cudaGraphLaunch(sg.exec, op->stream));
       graph_used = true;
     } else {  // host-driven fallback: chunks of iterations, poll the stop flag
@@ -357,6 +386,7 @@ int run_series(ad_operator* op, int aug, const void* src, double d0, int force, 
     // graph bodies: one fused iteration kernel per iteration (host launches
     // are counted by the launchers themselves)
     if (st && graph_used) st->kernel_launches += iters;
+    if (op->h_ctrl->status == 4) return fail(AD_ERR_TIMEOUT, "a grid barrier wait gave up");
   }
   if (st) {
     st->iters += iters;
@@ -908,6 +938,26 @@ int ad_profile_leja_iteration(ad_operator* op, int aug, int reps, double* ms_per
   splitmix_fill(op->prec, op->g.n, 8ULL, op->W2, op->stream);
   SeriesArgs a = series_args(op, aug);
   series_init(a, op->W1, d0, reps, op->max_iters, 0.0, op->stream);
+  if (!getenv("AD_NO_PERSIST") && op->prec == 0 && op->g.n <= kPersistMaxCells) {
+    // the persistent kernel runs the whole series: one launch of `reps` iterations
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    CUDA_TRY(cudaEventRecord(e0, op->stream));
+    const bool ok = series_run_persistent(a, &op->ctrl->gen, op->stream);
+    CUDA_TRY(cudaEventRecord(e1, op->stream));
+    CUDA_TRY(cudaStreamSynchronize(op->stream));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ok) {
+      op->cache_kind = -1;
+      *ms_per_launch = ms / reps;
+      return AD_OK;
+    }
+    series_init(a, op->W1, d0, reps, op->max_iters, 0.0, op->stream);
+  }
   std::vector<cudaEvent_t> ev(2 * reps);
   for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
   for (int r = 0; r < reps; ++r) {

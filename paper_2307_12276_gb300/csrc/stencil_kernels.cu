@@ -18,36 +18,13 @@
 // face means and fluxes are formed on the fly (fewest bytes).
 #include "ad_internal.h"
 
+#include <algorithm>
+
+#include "tile_f32.cuh"
+
 namespace ad {
 
 namespace {
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Deterministic block sum of two values; result valid in thread 0.  Lanes of
-// warp 0 add eight values each, then one butterfly: far fewer FP64 additions
-// than a butterfly in every warp (FP64 is the scarce pipe on this GPU).
-__device__ __forceinline__ void block_sum2(double& a, double& b) {
-  __shared__ double sa[kThreads], sb[kThreads];
-  const int t = threadIdx.x;
-  __syncthreads();
-  sa[t] = a;
-  sb[t] = b;
-  __syncthreads();
-  if (t < 32) {
-    double x = 0.0, y = 0.0;
-    for (int k = t; k < (int)blockDim.x; k += 32) {
-      x += sa[k];
-      y += sb[k];
-    }
-    a = warp_sum(x);
-    b = warp_sum(y);
-  }
-}
 
 // Per-iteration epilogue of the Newton series (Section 2): publish the block's
 // norm partials; the last block of the launch (ticket, no waiting) reduces all
@@ -353,6 +330,205 @@ __global__ void __launch_bounds__(kThreads) leja_iter_f64_k(SeriesArgs a) {
 }
 
 // --------------------------------------------------------------------------
+// Persistent FP64 series for grids up to kPersistMaxCells: one cooperative
+// launch runs every iteration of a Newton series.  Block b owns a contiguous
+// chunk of cells; its 9 scaled weights, p and w2 stay in shared memory for the
+// whole series (loaded once, 88 B/cell), y ping-pongs through global memory.
+// One grid barrier per iteration: the last block to arrive reduces the norm
+// partials in block order, applies the stopping rule and publishes it; the
+// others wait for the barrier generation to change.  Every wait is bounded
+// (kBarrierTimeoutNs of global time), after which the block records a timeout
+// status and leaves, so the kernel cannot hang.
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ULL;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Tree sum of two values over the block (FP64; result in every thread).  The
+// active threads of each level are contiguous, so levels above 32 run whole
+// warps only: about 2*(nt/32 + 5) warp-level FP64 additions per block, which
+// matters on a GPU whose FP64 pipe runs one warp instruction per 16 cycles.
+__device__ __forceinline__ void block_tree_sum2(double& a, double& b, double* sa, double* sb) {
+  const int t = threadIdx.x, nt = blockDim.x;  // nt is a power of two
+  __syncthreads();
+  sa[t] = a;
+  sb[t] = b;
+  __syncthreads();
+  for (int s = nt >> 1; s >= 32; s >>= 1) {
+    if (t < s) {
+      sa[t] += sa[t + s];
+      sb[t] += sb[t + s];
+    }
+    __syncthreads();
+  }
+  if (t < 32) {
+    double x = sa[t], y = sb[t];
+    if (nt < 32) {                 // tiny blocks: lanes beyond the block hold nothing
+      x = t < nt ? x : 0.0;
+      y = t < nt ? y : 0.0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_down_sync(0xffffffffu, x, o);
+      y += __shfl_down_sync(0xffffffffu, y, o);
+    }
+    if (t == 0) {
+      sa[0] = x;
+      sb[0] = y;
+    }
+  }
+  __syncthreads();
+  a = sa[0];
+  b = sb[0];
+}
+
+template <bool AUG>
+__global__ void __launch_bounds__(1024) leja_persistent_f64_k(SeriesArgs a, unsigned int cpb,
+                                                             unsigned int* gen) {
+  extern __shared__ double smem[];
+  __shared__ double ra[1024], rb[1024];
+  __shared__ int s_flag;
+  const GridDev g = a.g;
+  const unsigned int n = (unsigned int)g.n, nx = (unsigned int)g.nx;
+  const unsigned int c0 = blockIdx.x * cpb;
+  const unsigned int c1 = min(n, c0 + cpb);
+  const unsigned int nc = c1 > c0 ? c1 - c0 : 0u;
+  double* sW = smem;                 // [9][cpb]
+  double* sP = smem + 9 * cpb;       // [cpb]
+  double* sW2 = sP + cpb;            // [cpb] (augmented)
+  const double* __restrict__ Ws = static_cast<const double*>(a.coef);
+  double* __restrict__ p = static_cast<double*>(a.p);
+  const double* __restrict__ w1 = static_cast<const double*>(a.w1);
+  const double* __restrict__ w2 = static_cast<const double*>(a.w2);
+  Ctrl* ctrl = a.ctrl;
+  for (unsigned int k = threadIdx.x; k < nc; k += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) sW[q * cpb + k] = Ws[(long long)q * n + c0 + k];
+    sP[k] = p[c0 + k];
+    if (AUG) sW2[k] = w2[c0 + k];
+  }
+  unsigned int my_gen = 0;
+  if (threadIdx.x == 0) my_gen = *(volatile unsigned int*)gen;
+  int m = 0;
+  for (;;) {
+    const LejaCoef lc = a.lc[m];
+    const double* __restrict__ yin = static_cast<const double*>(a.y[m & 1]);
+    double* __restrict__ yout = static_cast<double*>(a.y[(m + 1) & 1]);
+    __syncthreads();                 // shared weights/p ready; previous iteration done
+    double sy = 0.0, sp = 0.0;
+    for (unsigned int k = threadIdx.x; k < nc; k += blockDim.x) {
+      const unsigned int idx = c0 + k;
+      const int j = (int)(idx / nx), i = (int)(idx - (unsigned int)j * nx);
+      int im, ip, jm, jp;
+      if (g.bc == 0) {
+        im = i ? i - 1 : g.nx - 1;
+        ip = (i + 1 < g.nx) ? i + 1 : 0;
+        jm = j ? j - 1 : g.ny - 1;
+        jp = (j + 1 < g.ny) ? j + 1 : 0;
+      } else {
+        im = i ? i - 1 : 0;
+        ip = (i + 1 < g.nx) ? i + 1 : i;
+        jm = j ? j - 1 : 0;
+        jp = (j + 1 < g.ny) ? j + 1 : j;
+      }
+      const double* rm = yin + (long long)jm * g.nx;
+      const double* r0 = yin + (long long)j * g.nx;
+      const double* rp = yin + (long long)jp * g.nx;
+      const double yc = r0[i];
+      double z = sW[4 * cpb + k] * yc;
+      z = fma(sW[0 * cpb + k], rm[im], z);
+      z = fma(sW[1 * cpb + k], rm[i], z);
+      z = fma(sW[2 * cpb + k], rm[ip], z);
+      z = fma(sW[3 * cpb + k], r0[im], z);
+      z = fma(sW[5 * cpb + k], r0[ip], z);
+      z = fma(sW[6 * cpb + k], rp[im], z);
+      z = fma(sW[7 * cpb + k], rp[i], z);
+      z = fma(sW[8 * cpb + k], rp[ip], z);
+      z = fma(-lc.xi, yc, z);
+      if (AUG) {
+        if (lc.e1 != 0.0) z = fma(lc.e1, sW2[k], z);
+        if (lc.e2 != 0.0) z = fma(lc.e2, w1[idx], z);
+      }
+      yout[idx] = z;
+      const double pn = fma(lc.d, z, sP[k]);
+      sP[k] = pn;
+      sy = fma(z, z, sy);
+      sp = fma(pn, pn, sp);
+    }
+    block_tree_sum2(sy, sp, ra, rb);
+    // grid barrier; the last arriver decides
+    if (threadIdx.x == 0) {
+      a.partials[2 * blockIdx.x] = sy;
+      a.partials[2 * blockIdx.x + 1] = sp;
+      __threadfence();
+      const unsigned int t = atomicAdd(&ctrl->ticket, 1u);
+      s_flag = (t == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_flag) {
+      __threadfence();
+      double ty = 0.0, tp = 0.0;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        ty += __ldcg(&a.partials[2 * b]);
+        tp += __ldcg(&a.partials[2 * b + 1]);
+      }
+      block_tree_sum2(ty, tp, ra, rb);
+      if (threadIdx.x == 0) {
+        const int terms = m + 1;
+        const double absd = lc.absd, tol = ctrl->tol;
+        ctrl->ynorm2 = ty;
+        ctrl->pnorm2 = tp;
+        ctrl->iters = terms;
+        ctrl->err_est = absd;
+        int stop = 0;
+        if (ctrl->force > 0) {
+          stop = terms >= ctrl->force;
+        } else if (!(ty == ty) || !(tp == tp)) {
+          stop = 1;
+          ctrl->status = 3;
+        } else if (terms >= 2 && (absd * absd) * ty <= (tol * tol) * tp) {
+          stop = 1;
+        } else if (terms >= ctrl->max_iters) {
+          stop = 1;
+          ctrl->status = 3;
+        }
+        if (terms >= kMaxIters) stop = 1;
+        ctrl->stop = stop;
+        ctrl->m = m + 1;
+        ctrl->ticket = 0u;
+        __threadfence();
+        atomicAdd(gen, 1u);           // release the waiting blocks
+        my_gen += 1u;
+        s_flag = stop ? 2 : 0;
+      }
+    } else if (threadIdx.x == 0) {
+      const unsigned long long t0 = global_ns();
+      int state = 0;
+      while (*(volatile unsigned int*)gen == my_gen) {
+        if (global_ns() - t0 > kBarrierTimeoutNs) { state = 3; break; }
+        __nanosleep(64);
+      }
+      if (state == 3) {
+        ctrl->status = 4;              // a wait gave up: AD_ERR_TIMEOUT
+        s_flag = 3;
+      } else {
+        __threadfence();
+        my_gen += 1u;
+        s_flag = (*(volatile int*)&ctrl->stop) ? 2 : 0;
+      }
+    }
+    __syncthreads();
+    if (s_flag != 0) break;
+    ++m;
+  }
+  __syncthreads();
+  for (unsigned int k = threadIdx.x; k < nc; k += blockDim.x) p[c0 + k] = sP[k];
+}
+
+// --------------------------------------------------------------------------
 // FP32 storage: fields F[5][n] = Dxx/(2dx^2), Dyy/(2dy^2), Dxy/(8dxdy), ax/(4dx), ay/(4dy).
 __global__ void pack_fields_f32_k(GridDev g, double dx, double dy, const double* Dxx,
                                   const double* Dxy, const double* Dyy, const double* ax,
@@ -370,98 +546,6 @@ __global__ void pack_fields_f32_k(GridDev g, double dx, double dy, const double*
   }
 }
 
-// Neighbourhood of cell (i, j) with ghost values (sign) and ghost coefficients (mirror).
-struct Nbr32 {
-  float u[3][3];      // u[dj+1][di+1]
-  float fxx[3], fyy[3], fxy[5], fax[3], fay[3];  // centre, -, + along the axis; fxy: C,W,E,S,N
-};
-
-__device__ __forceinline__ void map_idx(int& ti, int& tj, float& sg, int nx, int ny, int bc) {
-  if (bc == 0) {
-    ti = (ti < 0) ? ti + nx : (ti >= nx ? ti - nx : ti);
-    tj = (tj < 0) ? tj + ny : (tj >= ny ? tj - ny : tj);
-  } else {
-    if (ti < 0) { ti = -1 - ti; sg = -sg; } else if (ti >= nx) { ti = 2 * nx - 1 - ti; sg = -sg; }
-    if (tj < 0) { tj = -1 - tj; sg = -sg; } else if (tj >= ny) { tj = 2 * ny - 1 - tj; sg = -sg; }
-  }
-}
-
-// A u at one cell from the flux form (FP32 arithmetic).
-// adv: 0 none, 1 constant (be = bw = abx, bn = bs = aby), 2 fields F[3], F[4].
-__device__ __forceinline__ float flux_apply_f32(const float* __restrict__ F, long long n,
-                                                const float* __restrict__ u, int i, int j, int nx,
-                                                int ny, int bc, bool interior, int adv, float abx,
-                                                float aby) {
-  float U[3][3];
-  float cxx[3], cyy[3], cxyx[3], cxyy[3], cax[3], cay[3];
-  if (interior) {
-    const long long idx = (long long)j * nx + i;
-#pragma unroll
-    for (int dj = -1; dj <= 1; ++dj)
-#pragma unroll
-      for (int di = -1; di <= 1; ++di) U[dj + 1][di + 1] = u[idx + (long long)dj * nx + di];
-#pragma unroll
-    for (int d = -1; d <= 1; ++d) {
-      cxx[d + 1] = F[0 * n + idx + d];
-      cxyx[d + 1] = F[2 * n + idx + d];
-      cyy[d + 1] = F[1 * n + idx + (long long)d * nx];
-      cxyy[d + 1] = F[2 * n + idx + (long long)d * nx];
-      if (adv == 2) {
-        cax[d + 1] = F[3 * n + idx + d];
-        cay[d + 1] = F[4 * n + idx + (long long)d * nx];
-      }
-    }
-  } else {
-#pragma unroll
-    for (int dj = -1; dj <= 1; ++dj)
-#pragma unroll
-      for (int di = -1; di <= 1; ++di) {
-        int ti = i + di, tj = j + dj;
-        float sg = 1.0f;
-        map_idx(ti, tj, sg, nx, ny, bc);
-        U[dj + 1][di + 1] = sg * u[(long long)tj * nx + ti];
-      }
-#pragma unroll
-    for (int d = -1; d <= 1; ++d) {
-      int ti = i + d, tj = j;
-      float sg = 1.0f;
-      map_idx(ti, tj, sg, nx, ny, bc);
-      long long q = (long long)tj * nx + ti;
-      cxx[d + 1] = F[0 * n + q];
-      cxyx[d + 1] = F[2 * n + q];
-      if (adv == 2) cax[d + 1] = F[3 * n + q];
-      ti = i; tj = j + d; sg = 1.0f;
-      map_idx(ti, tj, sg, nx, ny, bc);
-      q = (long long)tj * nx + ti;
-      cyy[d + 1] = F[1 * n + q];
-      cxyy[d + 1] = F[2 * n + q];
-      if (adv == 2) cay[d + 1] = F[4 * n + q];
-    }
-  }
-  // face coefficients (factors 1/2 and the grid scalings are folded into F)
-  const float axe = cxx[1] + cxx[2], axw = cxx[0] + cxx[1];
-  const float ayn = cyy[1] + cyy[2], ays = cyy[0] + cyy[1];
-  const float qe = cxyx[1] + cxyx[2], qw = cxyx[0] + cxyx[1];
-  const float qn = cxyy[1] + cxyy[2], qs = cxyy[0] + cxyy[1];
-  float be = abx, bw = abx, bn = aby, bs = aby;
-  if (adv == 2) {
-    be = cax[1] + cax[2]; bw = cax[0] + cax[1];
-    bn = cay[1] + cay[2]; bs = cay[0] + cay[1];
-  }
-  const float uC = U[1][1], uE = U[1][2], uW = U[1][0], uN = U[2][1], uS = U[0][1];
-  const float uNE = U[2][2], uNW = U[2][0], uSE = U[0][2], uSW = U[0][0];
-  float fe = axe * (uE - uC) + qe * ((uNE + uN) - (uSE + uS));
-  float fw = axw * (uC - uW) + qw * ((uN + uNW) - (uS + uSW));
-  float fn = ayn * (uN - uC) + qn * ((uNE + uE) - (uNW + uW));
-  float fs = ays * (uC - uS) + qs * ((uE + uSE) - (uW + uSW));
-  if (adv != 0) {
-    fe = fmaf(be, uC + uE, fe);
-    fw = fmaf(bw, uW + uC, fw);
-    fn = fmaf(bn, uC + uN, fn);
-    fs = fmaf(bs, uS + uC, fs);
-  }
-  return (fe - fw) + (fn - fs);
-}
 
 __global__ void gershgorin_f32_k(GridDev g, const float* F, int adv, double abx, double aby,
                                  double* partials) {
@@ -551,200 +635,6 @@ __global__ void apply_f32_k(GridDev g, const float* __restrict__ F, int adv, flo
 
 // FP32 fused Leja iteration; Leja scalars arrive in FP64 and are rounded once
 // per iteration; per-thread square sums in FP32, block sums in FP64.
-// ---- FP32 fused iteration: tiles of 256 columns x kTileRows rows, marching in y.
-// Each thread owns one column of the tile; rows j-1, j, j+1 of y and the rows
-// of Dxx/Dxy that need x-neighbours live in shared-memory rings, the next row
-// is prefetched into registers while the current row is computed.  Steady
-// state global traffic per cell: y, Dxx, Dxy, Dyy, p read, y', p written
-// (28 B), + w2 (augmented) + ax, ay (advection fields).
-constexpr int kTileRows = 32;
-constexpr int kTileCols = kThreads;
-
-struct RowMap {
-  long long off;   // mapped row offset j' * nx
-  float sg;        // ghost sign for values (Dirichlet odd reflection)
-};
-
-__device__ __forceinline__ RowMap map_row(int j, int nx, int ny, int bc) {
-  RowMap r;
-  float sg = 1.0f;
-  if (bc == 0) j = (j < 0) ? j + ny : (j >= ny ? j - ny : j);
-  else if (j < 0) { j = -1 - j; sg = -1.0f; }
-  else if (j >= ny) { j = 2 * ny - 1 - j; sg = -1.0f; }
-  r.off = (long long)j * nx;
-  r.sg = sg;
-  return r;
-}
-
-__device__ __forceinline__ int map_col(int i, int nx, int bc, float& sg) {
-  sg = 1.0f;
-  if (bc == 0) return (i < 0) ? i + nx : (i >= nx ? i - nx : i);
-  if (i < 0) { sg = -1.0f; return -1 - i; }
-  if (i >= nx) { sg = -1.0f; return 2 * nx - 1 - i; }
-  return i;
-}
-
-// Values needed from row r (for y, Dxy, Dxx rows with x-halo): this thread's
-// column and, for thread 0, the two halo columns.
-struct RowVals {
-  float c, l, r;
-};
-
-__device__ __forceinline__ RowVals load_row(const float* __restrict__ f, const RowMap& rm,
-                                            bool values, int ci, float csg, bool cvalid,
-                                            int li, float lsg, int ri, float rsg, bool halo) {
-  RowVals v;
-  const float s = values ? rm.sg : 1.0f;
-  v.c = cvalid ? f[rm.off + ci] * (values ? s * csg : 1.0f) : 0.0f;
-  v.l = v.r = 0.0f;
-  if (halo) {
-    v.l = f[rm.off + li] * (values ? s * lsg : 1.0f);
-    v.r = f[rm.off + ri] * (values ? s * rsg : 1.0f);
-  }
-  return v;
-}
-
-template <bool AUG, int ADV>
-__device__ __forceinline__ void tile_f32(const SeriesArgs& a, const LejaCoef& lc, int tx, int ty,
-                                         const float* __restrict__ yin, float* __restrict__ yout,
-                                         float* __restrict__ p, float ig, float sh, float d,
-                                         float e1, float e2, float (*sy)[kTileCols + 2],
-                                         float* sxx, float (*sxy)[kTileCols + 2], float* sax,
-                                         double& accy, double& accp) {
-  const GridDev g = a.g;
-  const int nx = g.nx, ny = g.ny, bc = g.bc;
-  const long long n = g.n;
-  const float* __restrict__ F = static_cast<const float*>(a.coef);
-  const float* Fxx = F;
-  const float* Fyy = F + n;
-  const float* Fxy = F + 2 * n;
-  const float* Fax = F + 3 * n;
-  const float* Fay = F + 4 * n;
-  const float* __restrict__ w1 = static_cast<const float*>(a.w1);
-  const float* __restrict__ w2 = static_cast<const float*>(a.w2);
-  const int t = threadIdx.x;
-  const int x0 = tx * kTileCols, y0 = ty * kTileRows;
-  const int y1 = min(ny, y0 + kTileRows);
-  const int i = x0 + t;
-  const bool compute = i < nx;
-  const bool cvalid = i <= nx;            // column nx is the right ghost
-  float csg, lsg, rsg;
-  const int ci = cvalid ? map_col(i, nx, bc, csg) : 0;
-  const int li = map_col(x0 - 1, nx, bc, lsg);
-  const int ri = map_col(min(x0 + kTileCols, nx), nx, bc, rsg);
-  const bool halo = (t == 0);
-  const int rslot = min(kTileCols, nx - x0) + 1;  // smem index of the right halo
-  __syncthreads();   // the previous tile's last row may still be read
-  // prologue: rows y0-1 and y0 of y, row y0 of Dxy (with halos), Dyy/Dxy/ay columns
-  {
-    const RowMap rm = map_row(y0 - 1, nx, ny, bc), r0 = map_row(y0, nx, ny, bc);
-    RowVals v = load_row(yin, rm, true, ci, csg, cvalid, li, lsg, ri, rsg, halo);
-    sy[(y0 + 2) % 3][t + 1] = v.c;
-    if (halo) { sy[(y0 + 2) % 3][0] = v.l; sy[(y0 + 2) % 3][rslot] = v.r; }
-    v = load_row(yin, r0, true, ci, csg, cvalid, li, lsg, ri, rsg, halo);
-    sy[y0 % 3][t + 1] = v.c;
-    if (halo) { sy[y0 % 3][0] = v.l; sy[y0 % 3][rslot] = v.r; }
-    v = load_row(Fxy, r0, false, ci, csg, cvalid, li, lsg, ri, rsg, halo);
-    sxy[y0 & 1][t + 1] = v.c;
-    if (halo) { sxy[y0 & 1][0] = v.l; sxy[y0 & 1][rslot] = v.r; }
-  }
-  float dyy_s = 0.f, dyy_c = 0.f, dxy_s = 0.f, ay_s = 0.f, ay_c = 0.f;
-  {
-    const RowMap rm = map_row(y0 - 1, nx, ny, bc), r0 = map_row(y0, nx, ny, bc);
-    if (cvalid) {
-      dyy_s = Fyy[rm.off + ci];
-      dyy_c = Fyy[r0.off + ci];
-      dxy_s = Fxy[rm.off + ci];
-      if (ADV == 2) { ay_s = Fay[rm.off + ci]; ay_c = Fay[r0.off + ci]; }
-    }
-  }
-  // prefetch for the first row
-  RowVals ynext, xynext, xxcur, axcur;
-  float dyy_n = 0.f, ay_n = 0.f, pc = 0.f, w2c = 0.f, w1c = 0.f;
-  auto prefetch = [&](int j) {
-    const RowMap rn = map_row(j + 1, nx, ny, bc), rc = map_row(j, nx, ny, bc);
-    ynext = load_row(yin, rn, true, ci, csg, cvalid, li, lsg, ri, rsg, halo);
-    xynext = load_row(Fxy, rn, false, ci, csg, cvalid, li, lsg, ri, rsg, halo);
-    xxcur = load_row(Fxx, rc, false, ci, csg, cvalid, li, lsg, ri, rsg, halo);
-    if (ADV == 2) axcur = load_row(Fax, rc, false, ci, csg, cvalid, li, lsg, ri, rsg, halo);
-    if (cvalid) {
-      dyy_n = Fyy[rn.off + ci];
-      if (ADV == 2) ay_n = Fay[rn.off + ci];
-    }
-    if (compute) {
-      const long long idx = (long long)j * nx + i;
-      pc = p[idx];
-      if (AUG) {
-        if (e1 != 0.0f) w2c = w2[idx];
-        if (e2 != 0.0f) w1c = w1[idx];
-      }
-    }
-  };
-  prefetch(y0);
-  float ly = 0.f, lp = 0.f;
-  for (int j = y0; j < y1; ++j) {
-    __syncthreads();                       // previous row's readers are done
-    const int sn = (j + 1) % 3, sc = j % 3, ss = (j + 2) % 3;
-    sy[sn][t + 1] = ynext.c;
-    sxy[(j + 1) & 1][t + 1] = xynext.c;
-    sxx[t + 1] = xxcur.c;
-    if (ADV == 2) sax[t + 1] = axcur.c;
-    if (halo) {
-      sy[sn][0] = ynext.l; sy[sn][rslot] = ynext.r;
-      sxy[(j + 1) & 1][0] = xynext.l; sxy[(j + 1) & 1][rslot] = xynext.r;
-      sxx[0] = xxcur.l; sxx[rslot] = xxcur.r;
-      if (ADV == 2) { sax[0] = axcur.l; sax[rslot] = axcur.r; }
-    }
-    const float dyyn = dyy_n, ayn = ay_n, pcur = pc, w2cur = w2c, w1cur = w1c;
-    __syncthreads();
-    if (j + 1 < y1) prefetch(j + 1);       // overlap the next row's loads with this row
-    if (compute) {
-      const float uC = sy[sc][t + 1], uE = sy[sc][t + 2], uW = sy[sc][t];
-      const float uN = sy[sn][t + 1], uNE = sy[sn][t + 2], uNW = sy[sn][t];
-      const float uS = sy[ss][t + 1], uSE = sy[ss][t + 2], uSW = sy[ss][t];
-      const float dxy_c = sxy[j & 1][t + 1];
-      const float axe = sxx[t + 1] + sxx[t + 2], axw = sxx[t] + sxx[t + 1];
-      const float qe = dxy_c + sxy[j & 1][t + 2], qw = sxy[j & 1][t] + dxy_c;
-      const float qn = dxy_c + sxy[(j + 1) & 1][t + 1], qs = dxy_s + dxy_c;
-      const float ayn_ = dyy_c + dyyn, ays = dyy_s + dyy_c;
-      float fe = axe * (uE - uC) + qe * ((uNE + uN) - (uSE + uS));
-      float fw = axw * (uC - uW) + qw * ((uN + uNW) - (uS + uSW));
-      float fn = ayn_ * (uN - uC) + qn * ((uNE + uE) - (uNW + uW));
-      float fs = ays * (uC - uS) + qs * ((uE + uSE) - (uW + uSW));
-      if (ADV == 1) {
-        fe = fmaf(a.abx, uC + uE, fe);
-        fw = fmaf(a.abx, uW + uC, fw);
-        fn = fmaf(a.aby, uC + uN, fn);
-        fs = fmaf(a.aby, uS + uC, fs);
-      } else if (ADV == 2) {
-        fe = fmaf(sax[t + 1] + sax[t + 2], uC + uE, fe);
-        fw = fmaf(sax[t] + sax[t + 1], uW + uC, fw);
-        fn = fmaf(ay_c + ayn, uC + uN, fn);
-        fs = fmaf(ay_s + ay_c, uS + uC, fs);
-      }
-      const float au = (fe - fw) + (fn - fs);
-      float z = fmaf(au, ig, -sh * uC);
-      if (AUG) {
-        if (e1 != 0.0f) z = fmaf(e1, w2cur, z);
-        if (e2 != 0.0f) z = fmaf(e2, w1cur, z);
-      }
-      const long long idx = (long long)j * nx + i;
-      yout[idx] = z;
-      const float pn = fmaf(d, z, pcur);
-      p[idx] = pn;
-      ly = fmaf(z, z, ly);
-      lp = fmaf(pn, pn, lp);
-    }
-    // roll the column registers
-    dxy_s = sxy[j & 1][t + 1];
-    dyy_s = dyy_c;
-    dyy_c = dyyn;
-    if (ADV == 2) { ay_s = ay_c; ay_c = ayn; }
-  }
-  accy += (double)ly;
-  accp += (double)lp;
-}
-
 template <bool AUG, int ADV>
 __global__ void __launch_bounds__(kThreads) leja_iter_f32_k(SeriesArgs a) {
   __shared__ float sy[3][kTileCols + 2];
@@ -771,6 +661,43 @@ __global__ void __launch_bounds__(kThreads) leja_iter_f32_k(SeriesArgs a) {
 }
 
 }  // namespace
+
+// Cooperative persistent series (FP64).  Returns false when the grid is too
+// large or the launch is refused (the caller then uses the per-iteration path).
+bool series_run_persistent(const SeriesArgs& a, unsigned int* gen, cudaStream_t s) {
+  if (a.prec != 0 || a.g.n > kPersistMaxCells) return false;
+  const long long n = a.g.n;
+  const int G = (int)std::min<long long>(152, (n + 31) / 32);
+  const unsigned int cpb = (unsigned int)((n + G - 1) / G);
+  int T = 32;
+  while (T < (int)cpb && T < 1024) T <<= 1;
+  const size_t smem = (size_t)cpb * (a.aug ? 11 : 10) * sizeof(double);
+  void* fn = a.aug ? (void*)leja_persistent_f64_k<true> : (void*)leja_persistent_f64_k<false>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, T, smem) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if ((long long)per_sm * sms < G) return false;
+  SeriesArgs args = a;
+  args.nblocks = G;
+  unsigned int cpb_arg = cpb;
+  void* params[] = {&args, &cpb_arg, &gen};
+  ++launch_counter();
+  if (cudaLaunchCooperativeKernel(fn, dim3(G), dim3(T), params, smem, s) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
 
 int series_blocks(int prec, long long n) {
   // FP64: 4 blocks per SM (two cells per thread per trip keep the FP64 pipe

@@ -1,0 +1,109 @@
+"""Batched exponential-midpoint step (one graph launch for many slices of
+uneven size) against the FP64 oracle, slice by slice.
+
+Each slice is an FP32-storage operator; the bar is the FP32 one (1e-5
+relative L2).  Forced iteration counts make the comparison exact in method;
+the adaptive case checks each slice's own stopping decision against the
+oracle's.  The autotuner's JSON cache is checked for a round trip.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from gpu_util import DEV, ad, devT, dev64, need_gpu, rel, torch
+from oracle import integrators
+from oracle import operator as oop
+from oracle import spectral
+from workloads import Grid, cell_centres, gaussian, tensor_from_b, b_circular
+from workloads.fields import BC_DIRICHLET0, SeparableSource
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(40, 33), (64, 64), (300, 70), (17, 23), (256, 256), (513, 40)]
+
+
+def _slice(nx, ny, dpar):
+    g = Grid(nx, ny, BC_DIRICHLET0)
+    X, Y = cell_centres(g)
+    bx, by, w = b_circular(X, Y, 0.05)
+    Dxx, Dxy, Dyy = tensor_from_b(bx, by, dpar, 1e-3 * dpar, w)
+    src = gaussian(X, Y, 0.0, 0.0, 0.1)
+    u0 = gaussian(X, Y, 0.1, -0.1, 0.2)
+    return g, Dxx, Dxy, Dyy, src, u0
+
+
+def _build(autotune=False):
+    slices, ops = [], []
+    for k, (nx, ny) in enumerate(SIZES):
+        g, Dxx, Dxy, Dyy, src, u0 = _slice(nx, ny, 1.0 + 3.0 * k)
+        A = oop.assemble(g, Dxx, Dxy, Dyy, 0.05, 0.0)
+        alpha = spectral.gershgorin(A)
+        op = ad().create_operator(nx, ny, g.bc, dev64(Dxx), dev64(Dxy), dev64(Dyy), 0.05, 0.0,
+                                  ad().FP32_STORAGE)
+        ad().set_spectral_bound(op, alpha)
+        slices.append((g, A, alpha, src, u0))
+        ops.append(op)
+    return slices, ops, ad().create_batch(ops, autotune=autotune)
+
+
+def _dt(slices):
+    # largest dt keeping every slice at gamma dt <= 150 (one substep)
+    return min(150.0 / (-alpha / 4.0) for (_, _, alpha, _, _) in slices)
+
+
+@pytest.mark.parametrize("force", [1, 20])
+def test_batched_forced_matches_oracle(force):
+    need_gpu()
+    slices, ops, batch = _build()
+    dt = _dt(slices)
+    us = [devT(s[4], 1) for s in slices]
+    srcs = [ad().Source([devT(s[3], 1)], None) for s in slices]
+    st = ad().batch_midpoint_step(batch, us, 0.0, dt, srcs, force_iters=force)
+    for k, (g, A, alpha, src, u0) in enumerate(slices):
+        ref, ost = integrators.expquad_step(A, u0.ravel(), 0.0, dt, 1, (0.5,),
+                                            lambda t, src=src: src.ravel(), alpha,
+                                            force_iters=force)
+        assert st[k]["iters"] == force
+        assert rel(us[k].cpu().numpy(), ref) <= 1e-5, (k, SIZES[k])
+
+
+def test_batched_adaptive_matches_oracle_per_slice():
+    need_gpu()
+    slices, ops, batch = _build()
+    dt = _dt(slices)
+    us = [devT(s[4], 1) for s in slices]
+    srcs = [ad().Source([devT(s[3], 1)], None) for s in slices]
+    st = ad().batch_midpoint_step(batch, us, 0.0, dt, srcs, tol=1e-6)
+    iters = [s["iters"] for s in st]
+    assert len(set(iters)) > 1                  # slices really stop at different counts
+    for k, (g, A, alpha, src, u0) in enumerate(slices):
+        ref, ost = integrators.expquad_step(A, u0.ravel(), 0.0, dt, 1, (0.5,),
+                                            lambda t, src=src: src.ravel(), alpha, tol=1e-10)
+        _, ost6 = integrators.expquad_step(A, u0.ravel(), 0.0, dt, 1, (0.5,),
+                                           lambda t, src=src: src.ravel(), alpha, tol=1e-6)
+        assert abs(st[k]["iters"] - ost6.iters) <= 2, (k, st[k]["iters"], ost6.iters)
+        assert rel(us[k].cpu().numpy(), ref) <= 1e-5, (k, SIZES[k])
+    # a second step from the new state still matches (state reuse, cached scalars)
+    u1 = [u.clone() for u in us]
+    ad().batch_midpoint_step(batch, u1, dt, dt, srcs, tol=1e-6)
+    for k, (g, A, alpha, src, u0) in enumerate(slices):
+        ref, _ = integrators.expquad_step(A, us[k].cpu().numpy().astype(np.float64), dt, dt, 1,
+                                          (0.5,), lambda t, src=src: src.ravel(), alpha, tol=1e-10)
+        assert rel(u1[k].cpu().numpy(), ref) <= 1e-5
+
+
+def test_autotune_cache_round_trip(tmp_path, monkeypatch):
+    need_gpu()
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("AD_AUTOTUNE_CACHE", str(cache))
+    _, _, b1 = _build(autotune=True)
+    info1 = ad().batch_info(b1)
+    data = json.loads(cache.read_text())
+    assert len(data) == 1
+    entry = next(iter(data.values()))
+    assert entry["ty"] == info1["tile_rows"] and entry["ty"] in (8, 16, 32, 64)
+    _, _, b2 = _build(autotune=True)            # served from the cache
+    assert ad().batch_info(b2)["tile_rows"] == info1["tile_rows"]
+    assert abs(ad().batch_info(b2)["tuned_ms"] - entry["ms"]) < 1e-6
