@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--form-steps", type=int, default=5)
+    ap.add_argument("--learned-fields", type=int, default=1000)
+    ap.add_argument("--forms", default="fp32,cn,batched,learned",
+                    help="comma list of extra forms to measure: fp32, cn, batched, learned")
     return ap.parse_args()
 
 
@@ -180,18 +183,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_per_launch(kernel_file: str):
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
-    or None when the kernel source changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "leja_iter_traffic.json")
+def traffic_per_launch(kernel_file: str, summary: str):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu summary
+    (lines "source_sha256: ..." and "dram_bytes_per_launch: ..."), or None when
+    the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", summary)
     try:
-        d = json.load(open(path))
-    except (FileNotFoundError, ValueError):
+        text = open(path).read()
+    except FileNotFoundError:
         return None
+    fields = {}
+    for line in text.splitlines():
+        line = line.strip().lstrip("-* ").replace("`", "")
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip()
     sha = hashlib.sha256(open(kernel_file, "rb").read()).hexdigest()
-    if d.get("source_sha256") != sha:
+    if fields.get("source_sha256") != sha:
         return None
-    return d.get("dram_bytes_per_launch_full_size")
+    try:
+        return float(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 # --------------------------------------------------------------------------- ours
@@ -240,6 +253,211 @@ def measure_fp32_form(ad, dev, stream, flush, steps):
                          round(ms_launch, 5), "achieved": round(gbs, 1), "peak": 6750.4,
                          "unit": "GB/s", "frac": round(gbs / 6750.4, 4),
                          "alg_bytes_per_launch": alg_bytes}}
+
+
+def measure_cn_vs_exp(ad, dev, stream, T_cfl=1000.0):
+    """Crank-Nicolson (GMRES) against two-stage exponential quadrature on the
+    512^2 workload, to T = T_cfl Delta t_CFL: the exponential method at 200
+    Delta t_CFL, CN at the largest step (halving from 200) whose error matches
+    it.  Reference: the FP64 GPU path, Gauss nodes, step 12.5 Delta t_CFL,
+    tol 1e-12 (its per-step parity with the oracle is pinned by the GPU tests)."""
+    import numpy as np
+    import torch
+    from workloads import config1
+    p = config1(nx=512, dt_factor=200.0)
+    g = p.grid
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(), device=dev)
+    op = ad.create_operator(g.nx, g.ny, g.bc, T(p.Dxx), T(p.Dxy), T(p.Dyy), p.ax, p.ay, ad.FP64,
+                            stream=stream)
+    src = ad.Source([T(gk) for gk in p.source.g], list(p.source.h))
+    t_end = T_cfl * p.cfl
+    gauss = (0.5 - 0.5 / 3 ** 0.5, 0.5 + 0.5 / 3 ** 0.5)
+
+    def run(method, factor, tol=1e-10):
+        n = int(round(T_cfl / factor))
+        dt = t_end / n
+        u = T(p.u0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it = 0
+        for k in range(n):
+            if method == "cn":
+                st = ad.cn_step(op, u, k * dt, dt, src, gmres_tol=1e-10, restart=50)
+            elif method == "gauss":
+                st = ad.expquad_step(op, u, k * dt, dt, 2, gauss, src, tol=tol)
+            else:
+                st = ad.expquad_step(op, u, k * dt, dt, 2, p.c, src, tol=tol)
+            it += st["matvecs"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return u, e0.elapsed_time(e1), it, n
+
+    ref, _, _, _ = run("gauss", 12.5, tol=1e-12)
+    nref = float(torch.linalg.norm(ref))
+    ue, ms_e, mv_e, n_e = run("exp", 200.0)
+    err_e = float(torch.linalg.norm(ue - ref)) / nref
+    tried = []
+    factor = 200.0
+    while factor >= 3.125:
+        uc, ms_c, mv_c, n_c = run("cn", factor)
+        err_c = float(torch.linalg.norm(uc - ref)) / nref
+        tried.append({"dt_over_cfl": factor, "err": err_c, "ms": round(ms_c, 3), "matvecs": mv_c})
+        if err_c <= err_e:
+            break
+        factor /= 2.0
+    op.close()
+    best = tried[-1]
+    return {"workload": "c1-512sq-dirichlet-circular", "T_over_cfl": T_cfl,
+            "exp": {"dt_over_cfl": 200.0, "steps": n_e, "err": err_e, "ms": round(ms_e, 3),
+                    "matvecs": mv_e},
+            "cn_tried": tried, "cn_matched": best["err"] <= err_e,
+            "speedup_exp_over_cn": round(best["ms"] / ms_e, 2),
+            "matvec_ratio_cn_over_exp": round(best["matvecs"] / mv_e, 2)}
+
+
+def _slice_operators(ad, dev, stream, nslices, sides):
+    """The momentum-slice batch: per slice a side drawn from ``sides`` (seed 3),
+    D_par = p^0.5 for p log-spaced in [1, 1e4], D_perp = 1e-3 D_par, circular
+    b, a = (0.05, 0), constant Gaussian source, Gaussian initial field."""
+    import numpy as np
+    import torch
+    from workloads import config3_slices, slice_problem
+    specs = config3_slices(nslices, sides=sides)
+    ops, us, srcs, probs = [], [], [], []
+    for side, dpar, dperp in specs:
+        p = slice_problem(side, dpar, dperp, dt=1.0)
+        T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(), device=dev)
+        op = ad.create_operator(side, side, p.grid.bc, T(p.Dxx), T(p.Dxy), T(p.Dyy), 0.05, 0.0,
+                                ad.FP32_STORAGE, stream=stream)
+        ops.append(op)
+        us.append(T(p.u0).float())
+        srcs.append(ad.Source([T(p.source.g[0]).float()], None))
+        probs.append(p)
+    return ops, us, srcs, probs
+
+
+def measure_batched_form(ad, dev, stream, steps, nslices=128, sides=(256, 512, 1024, 2048),
+                         learned_fields=0):
+    """The 128-slice batch (FP32 storage, tol 1e-6): one graph launch per step
+    against the same slices stepped one operator call at a time; optionally the
+    learned spectral bound against power iteration."""
+    import numpy as np
+    import torch
+    t_setup = time.perf_counter()
+    ops, us, srcs, probs = _slice_operators(ad, dev, stream, nslices, sides)
+    setup_s = time.perf_counter() - t_setup
+    # bounds: power iteration per slice (timed), dt = 100 Delta t_CFL of the stiffest slice
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k, op in enumerate(ops):
+        ad.spectral_bound(op, ad.BOUND_POWER, seed=k + 1, power_iters=30, safety=1.1)
+    torch.cuda.synchronize()
+    power_s = time.perf_counter() - t0
+    dt = 100.0 * min(p.cfl for p in probs)
+    cells = sum(p.grid.n for p in probs)
+    batch = ad.create_batch(ops, autotune=True)
+    info = ad.batch_info(batch)
+    u_start = [u.clone() for u in us]
+    ad.batch_midpoint_step(batch, us, 0.0, dt, srcs, tol=1e-6)      # warm-up
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters = []
+    ev0.record(stream)
+    for k in range(steps):
+        st = ad.batch_midpoint_step(batch, us, (k + 1) * dt, dt, srcs, tol=1e-6)
+        iters.append(sum(s["iters"] for s in st))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = ev0.elapsed_time(ev1) / steps
+    # the same slices, one operator call each
+    u2 = [u.clone() for u in u_start]
+    for op, u, src in zip(ops, u2, srcs):
+        ad.expquad_step(op, u, 0.0, dt, 1, (0.5,), src, tol=1e-6)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for k in range(steps):
+        for op, u, src in zip(ops, u2, srcs):
+            ad.expquad_step(op, u, (k + 1) * dt, dt, 1, (0.5,), src, tol=1e-6)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = ev0.elapsed_time(ev1) / steps
+    # algorithmic HBM bytes of the iteration passes: 28 B per cell and iteration
+    per_slice_iters = [s["iters"] for s in st]
+    alg_bytes = sum(28.0 * p.grid.n * it for p, it in zip(probs, per_slice_iters))
+    out = {"workload": f"c3-{nslices}-slices-sides{'-'.join(map(str, sides))}-fp32-midpoint",
+           "cells": cells, "value": round(cells / (ms_batch * 1e-3) / 1e6, 2),
+           "unit": "Mcell-steps/s", "ms_per_step": round(ms_batch, 4),
+           "sequential_ms_per_step": round(ms_seq, 4),
+           "speedup_vs_one_call_per_slice": round(ms_seq / ms_batch, 3),
+           "leja_iters_per_slice": {"min": int(min(per_slice_iters)), "max": int(max(per_slice_iters)),
+                                    "mean": round(float(np.mean(per_slice_iters)), 1)},
+           "alg_GBps_whole_step": round(alg_bytes / (ms_batch * 1e-3) / 1e9, 1),
+           "autotune": info, "power_iteration_bounds_s": round(power_s, 4),
+           "setup_s": round(setup_s, 1), "tol": 1e-6}
+    if learned_fields:
+        out["learned"] = measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, dt, batch,
+                                         steps, ms_batch, power_s, learned_fields)
+    for op in ops:
+        op.close()
+    return out
+
+
+def measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, dt, batch, steps, ms_batch,
+                    power_s, nfields):
+    """Train the bound network on generated fields (labels: power-iteration
+    spectra), predict every slice's bound, run the batch with fallback."""
+    import numpy as np
+    import torch
+    from paper_2307_12276_gb300 import learned
+    t0 = time.perf_counter()
+    X, Y, _ = learned.build_dataset(nfields + nfields // 10, seed=4, device=dev)
+    label_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    model = learned.train_bound_model(X[:nfields], Y[:nfields], dev, epochs=3000, lr=3e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    hold = model.predict(torch.as_tensor(X[nfields:], device=dev)).cpu().numpy()
+    alpha_err = np.abs(np.exp(hold[:, 0] - Y[nfields:, 0]) - 1.0)
+    # bounds for the slices from features + one batched inference
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    feats = []
+    for p in probs:
+        T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(), device=dev)
+        feats.append(ad.field_features(p.grid.nx, p.grid.ny, p.grid.bc, T(p.Dxx), T(p.Dxy),
+                                       T(p.Dyy), 0.05, dt))
+    alpha, it_pred = learned.predict_bounds(model, np.stack(feats), [p.grid.dx for p in probs], dev,
+                                            margin=1.2)
+    torch.cuda.synchronize()
+    predict_s = time.perf_counter() - t0
+    power_alpha = [ad.get_spectral_bound(op) for op in ops]
+    for op, a in zip(ops, alpha):
+        ad.set_spectral_bound(op, float(a))
+    for s in range(len(us)):
+        us[s].copy_(u_start[s])
+    fallbacks = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    iters = []
+    for k in range(steps):
+        st, fb = learned.batched_step_with_fallback(batch, ops, us, k * dt, dt, srcs, tol=1e-6)
+        fallbacks += len(fb)
+        iters.append(sum(s["iters"] for s in st))
+    torch.cuda.synchronize()
+    ms_learned = (time.perf_counter() - t0) * 1e3 / steps
+    for op, a in zip(ops, power_alpha):
+        ad.set_spectral_bound(op, a)
+    plain_total = power_s + steps * ms_batch * 1e-3
+    learned_total = predict_s + steps * ms_learned * 1e-3
+    return {"training_fields": nfields, "label_s": round(label_s, 1), "train_s": round(train_s, 2),
+            "heldout_alpha_rel_err_median": round(float(np.median(alpha_err)), 4),
+            "heldout_alpha_rel_err_p90": round(float(np.quantile(alpha_err, 0.9)), 4),
+            "predict_s": round(predict_s, 4), "ms_per_step": round(ms_learned, 4),
+            "fallback_rate": round(fallbacks / (steps * len(ops)), 4),
+            "mean_pred_over_power_alpha": round(float(np.mean(np.asarray(alpha) / np.asarray(power_alpha))), 3),
+            "speedup_vs_power_iteration_bounds": round(plain_total / learned_total, 3),
+            "steps_in_comparison": steps}
 
 
 def run_ours(args):
@@ -332,18 +550,33 @@ def run_ours(args):
     bytes_alg = 112.0 * g.n   # 9 weights + y + w2 + p (r/w) + y_next, 8 B each
     achieved = flops / (ms_launch * 1e-3) / 1e12
     traffic = traffic_per_launch(os.path.join(ROOT, "paper_2307_12276_gb300", "csrc",
-                                              "stencil_kernels.cu"))
+                                              "stencil_kernels.cu"),
+                                 "leja_persistent_f64_512sq.md")
+    persistent = g.n <= 152 * 2048
     roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
             "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-            "traffic": traffic, "kernel": "leja_iter_f64_k<aug>",
-            "ms_per_launch": round(ms_launch, 5),
-            "alg_bytes_per_launch": bytes_alg,
+            "traffic": traffic,
+            "kernel": "leja_persistent_f64_k<aug>" if persistent else "leja_iter_f64_k<aug>",
+            "work_unit": ("one Leja iteration; the persistent kernel runs a whole Newton series "
+                          "per launch, timed with CUDA events around a 300-iteration launch"
+                          if persistent else "one launch = one Leja iteration"),
+            "ms_per_iteration": round(ms_launch, 5),
+            "alg_flops_per_iteration": flops,
+            "alg_bytes_per_iteration": bytes_alg,
             "alg_GBps": round(bytes_alg / (ms_launch * 1e-3) / 1e9, 1),
-            "peak_note": "FP64: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived)"}
+            "peak_note": "of derived FP64 peak: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz "
+                         "(probe measured 1.89 DFMA/clk/SM)"}
 
     forms = {}
-    if not args.no_forms:
+    wanted = set() if args.no_forms else set(args.forms.split(","))
+    if "fp32" in wanted:
         forms["fp32_4096sq"] = measure_fp32_form(ad, dev, stream, flush, args.form_steps)
+    if "cn" in wanted:
+        forms["cn_vs_exp"] = measure_cn_vs_exp(ad, dev, stream)
+    if "batched" in wanted:
+        forms["batched"] = measure_batched_form(
+            ad, dev, stream, args.form_steps,
+            learned_fields=args.learned_fields if "learned" in wanted else 0)
 
     if rank == 0:
         line = {

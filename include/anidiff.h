@@ -200,6 +200,42 @@ AD_API int ad_batch_midpoint_step(ad_batch* b, void* const* u, double t, double 
 AD_API int ad_batch_info(const ad_batch* b, int* tile_rows, int* blocks, int* ntiles,
                          double* tuned_ms);
 
+/* ---------------------------------------------------------------- learned bound
+ * A small network predicting, from per-field features, the spectral bound
+ * that Section 2 estimates with Gershgorin discs (here: the dimensionless
+ * log(|alpha| dx^2 / D_par)) and the Leja iteration count, trained on spectra
+ * the method itself computes.  h1 = tanh(x W1 + b1), h2 = tanh(h1 W2 + b2),
+ * y = h2 W3 + b3; inputs standardised, outputs de-standardised.  FP32
+ * training (forward, MSE backward, Adam), BF16 inference with FP32
+ * accumulation.  X: float32 DEVICE [B][n_in]; Y: float32 DEVICE [B][n_out]. */
+typedef struct ad_mlp ad_mlp;
+/* Glorot-uniform weights from SplitMix64(seed), zero biases, identity normalisation. */
+AD_API int ad_mlp_create(int n_in, int n_hidden, int n_out, unsigned long long seed,
+                         void* cuda_stream, ad_mlp** out);
+AD_API int ad_mlp_destroy(ad_mlp* m);
+AD_API int ad_mlp_num_params(const ad_mlp* m, int* n);
+/* set != 0: host -> model (resets Adam state); set == 0: model -> host.
+ * Flat order W1 [n_in][h], b1, W2 [h][h], b2, W3 [h][n_out], b3. */
+AD_API int ad_mlp_params(ad_mlp* m, float* host, int n, int set);
+AD_API int ad_mlp_normalization(ad_mlp* m, float* x_mean, float* x_std, float* y_mean,
+                                float* y_std, int set);
+/* Loss 1/(2B) sum (y - t)^2 on standardised data and its gradient (host, flat order). */
+AD_API int ad_mlp_loss_grad(ad_mlp* m, const float* X, const float* Y, int B, float* loss,
+                            float* host_grad);
+/* Full-batch Adam for `epochs` steps (fit_normalization: first compute the
+ * column statistics of X and Y on the GPU).  final_loss may be NULL. */
+AD_API int ad_mlp_train(ad_mlp* m, const float* X, const float* Y, int B, int epochs, float lr,
+                        int fit_normalization, float* final_loss);
+/* Y = model(X), de-standardised; bf16 != 0 runs the BF16 inference kernels. */
+AD_API int ad_mlp_predict(ad_mlp* m, const float* X, int B, int bf16, float* Y);
+/* The 21 input features of one field: log max lambda_1(D), log min lambda_2(D),
+ * log(max|a| + 1e-6), log min(dx, dy), log dt, and the anisotropy-weighted
+ * 16-bin histogram of the principal direction of D over (-pi/2, pi/2]
+ * (normalised).  Dxx, Dxy, Dyy: float64 device fields; out21: host. */
+AD_API int ad_field_features(const ad_grid* grid, const double* Dxx, const double* Dxy,
+                             const double* Dyy, double max_a, double dt, void* cuda_stream,
+                             float* out21);
+
 /* Measurement helper (no counterpart in the paper): time the fused Leja
  * iteration kernel alone.  Runs `reps` iterations of the series kernel
  * (aug = 0: phi_1 form, 1: augmented form) on the operator's stream with a
@@ -233,6 +269,13 @@ AD_API int ad_leja_phi1_noalloc(const ad_grid* grid, const double* Dxx, const do
                                 const double* Dyy, double ax_c, double ay_c, double alpha,
                                 const double* v, double* out, double dt, double tol,
                                 int force_iters, void* cuda_stream, ad_stats* stats);
+
+/* Failure-detection check (no counterpart in the paper): one block waits on a
+ * device barrier that nothing releases, with the library's bounded-wait
+ * machinery and a bound of timeout_ms (0 < timeout_ms <= 1000).  Returns
+ * AD_ERR_TIMEOUT when the wait gives up as designed; the CUDA context stays
+ * usable.  Any other status means the bounded-wait path is broken. */
+AD_API int ad_check_wait_timeout(double timeout_ms, void* cuda_stream);
 
 /* Thread-local message for the last error of this thread ("" if none). */
 AD_API const char* ad_last_error(void);

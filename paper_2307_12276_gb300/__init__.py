@@ -70,6 +70,16 @@ _sig = {
     "ad_destroy_batch": (_i, [_vp]),
     "ad_batch_midpoint_step": (_i, [_vp, C.POINTER(_vp), _d, _d, _vp, _d, _i, C.POINTER(Stats)]),
     "ad_batch_info": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_d)]),
+    "ad_mlp_create": (_i, [_i, _i, _i, C.c_ulonglong, _vp, C.POINTER(_vp)]),
+    "ad_mlp_destroy": (_i, [_vp]),
+    "ad_mlp_num_params": (_i, [_vp, C.POINTER(_i)]),
+    "ad_mlp_params": (_i, [_vp, _vp, _i, _i]),
+    "ad_mlp_normalization": (_i, [_vp, _vp, _vp, _vp, _vp, _i]),
+    "ad_mlp_loss_grad": (_i, [_vp, _vp, _vp, _i, C.POINTER(C.c_float), _vp]),
+    "ad_mlp_train": (_i, [_vp, _vp, _vp, _i, _i, C.c_float, _i, C.POINTER(C.c_float)]),
+    "ad_mlp_predict": (_i, [_vp, _vp, _i, _i, _vp]),
+    "ad_field_features": (_i, [C.POINTER(_Grid), _vp, _vp, _vp, _d, _d, _vp, _vp]),
+    "ad_check_wait_timeout": (_i, [_d, _vp]),
     "ad_last_error": (C.c_char_p, []),
     "ad_version": (_i, []),
 }
@@ -346,7 +356,7 @@ def batch_info(b: Batch) -> dict:
 
 
 def batch_midpoint_step(b: Batch, us, t: float, dt: float, sources=None, tol: float = 1e-6,
-                        force_iters: int = -1):
+                        force_iters: int = -1, raise_not_converged: bool = True):
     """ad_batch_midpoint_step: us = list of float32 device tensors (one per slice),
     sources = None or a list of Source (at most 4 terms each).  Returns the
     per-slice stats."""
@@ -366,7 +376,96 @@ def batch_midpoint_step(b: Batch, us, t: float, dt: float, sources=None, tol: fl
         srcp = C.cast(arr, _vp)
         keep.append(arr)
     stats = (Stats * S)()
-    _check(_lib.ad_batch_midpoint_step(b.handle, uptr, t, dt, srcp, tol, force_iters, stats),
-           stats[0])
+    status = _lib.ad_batch_midpoint_step(b.handle, uptr, t, dt, srcp, tol, force_iters, stats)
+    if not (status == AD_ERR_NOT_CONVERGED and not raise_not_converged):
+        _check(status, stats[0])
     del keep
     return [stats[s].as_dict() for s in range(S)]
+
+
+class MLP:
+    """Handle of an ad_mlp (the learned spectral-bound network)."""
+
+    def __init__(self, n_in=21, n_hidden=64, n_out=2, seed=0, stream=None):
+        h = _vp()
+        _check(_lib.ad_mlp_create(n_in, n_hidden, n_out, seed, _stream_ptr(stream), C.byref(h)))
+        self.handle = h.value
+        self.n_in, self.n_hidden, self.n_out = n_in, n_hidden, n_out
+        n = _i()
+        _check(_lib.ad_mlp_num_params(self.handle, C.byref(n)))
+        self.n_params = n.value
+
+    def close(self):
+        if self.handle:
+            _lib.ad_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _f32(self, x, cols, what):
+        return _ptr(x, "float32", x.numel() if hasattr(x, "numel") else x.size, what)
+
+    def get_params(self):
+        import numpy as np
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(_lib.ad_mlp_params(self.handle, out.ctypes.data, self.n_params, 0))
+        return out
+
+    def set_params(self, theta):
+        import numpy as np
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(_lib.ad_mlp_params(self.handle, t.ctypes.data, self.n_params, 1))
+
+    def normalization(self, x_mean=None, x_std=None, y_mean=None, y_std=None):
+        import numpy as np
+        if x_mean is None:
+            bufs = [np.empty(k, dtype=np.float32) for k in (self.n_in, self.n_in, self.n_out, self.n_out)]
+            _check(_lib.ad_mlp_normalization(self.handle, *[b.ctypes.data for b in bufs], 0))
+            return bufs
+        bufs = [np.ascontiguousarray(b, dtype=np.float32) for b in (x_mean, x_std, y_mean, y_std)]
+        _check(_lib.ad_mlp_normalization(self.handle, *[b.ctypes.data for b in bufs], 1))
+
+    def loss_grad(self, X, Y):
+        import numpy as np
+        B = X.shape[0]
+        g = np.empty(self.n_params, dtype=np.float32)
+        L = C.c_float()
+        _check(_lib.ad_mlp_loss_grad(self.handle, X.data_ptr(), Y.data_ptr(), B, C.byref(L),
+                                     g.ctypes.data))
+        return L.value, g
+
+    def train(self, X, Y, epochs=2000, lr=3e-3, fit_normalization=True):
+        B = X.shape[0]
+        L = C.c_float()
+        _check(_lib.ad_mlp_train(self.handle, X.data_ptr(), Y.data_ptr(), B, epochs, lr,
+                                 1 if fit_normalization else 0, C.byref(L)))
+        return L.value
+
+    def predict(self, X, bf16=True):
+        import torch
+        B = X.shape[0]
+        Y = torch.empty((B, self.n_out), dtype=torch.float32, device=X.device)
+        _check(_lib.ad_mlp_predict(self.handle, X.data_ptr(), B, 1 if bf16 else 0, Y.data_ptr()))
+        return Y
+
+
+def field_features(nx, ny, bc, Dxx, Dxy, Dyy, max_a, dt, stream=None, x0=-1.0, x1=1.0, y0=-1.0,
+                   y1=1.0):
+    """ad_field_features: the 21 network inputs of one field (numpy float32)."""
+    import numpy as np
+    g = _Grid(nx, ny, x0, x1, y0, y1, bc)
+    n = nx * ny
+    out = np.empty(21, dtype=np.float32)
+    _check(_lib.ad_field_features(C.byref(g), _ptr(Dxx, "float64", n, "Dxx"),
+                                  _ptr(Dxy, "float64", n, "Dxy"), _ptr(Dyy, "float64", n, "Dyy"),
+                                  float(max_a), float(dt), _stream_ptr(stream), out.ctypes.data))
+    return out
+
+
+def check_wait_timeout(timeout_ms: float = 50.0, stream=None) -> int:
+    """ad_check_wait_timeout: returns the status (AD_ERR_TIMEOUT expected)."""
+    return _lib.ad_check_wait_timeout(timeout_ms, _stream_ptr(stream))

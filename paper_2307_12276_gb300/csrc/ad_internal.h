@@ -97,6 +97,7 @@ struct SeriesArgs {
   float abx, aby;
   unsigned long long handle;  // CUDA graph conditional of the WHILE loop
   int has_handle;             // 1 when run inside the graph loop
+  int bulk;                   // FP32: warp-specialised bulk-copy kernel (nx % 4 == 0)
 };
 // y[0] = src (or 0 if src == null), p = d0 * y[0]; resets ctrl.
 void series_init(const SeriesArgs& a, const void* src, double d0, int force, int max_iters,
@@ -114,6 +115,7 @@ bool series_run_persistent(const SeriesArgs& a, unsigned int* gen, cudaStream_t 
 // grid size of the fused iteration kernel (FP64: by cell count; FP32: by tile count)
 int series_blocks(int prec, long long n);
 int series_blocks_grid(int prec, int nx, int ny);
+bool series_use_bulk(int prec, int nx);
 
 // ---------------------------------------------------------------- vector helpers
 // z = a*x + b*y (x or y may be null = 0), elementwise, storage type prec.
@@ -159,6 +161,9 @@ struct OperatorView {
 struct ad_operator;
 namespace ad {
 bool operator_view(const ad_operator* op, OperatorView* v);
+
+// One-block kernel whose bounded wait must run out (failure-detection test).
+int wait_timeout_probe(unsigned long long timeout_ns, int* status_dev, cudaStream_t s);
 
 // Set the thread-local message returned by ad_last_error().
 void set_error_message(const char* msg);

@@ -164,6 +164,7 @@ SeriesArgs series_args(ad_operator* op, int aug) {
   a.ctrl = op->ctrl;
   a.partials = op->partials;
   a.nblocks = series_blocks_grid(op->prec, op->g.nx, op->g.ny);
+  a.bulk = series_use_bulk(op->prec, op->g.nx) ? 1 : 0;
   a.aug = aug;
   a.adv = op->adv;
   a.abx = op->abx;
@@ -924,6 +925,25 @@ int ad_cn_step(ad_operator* op, void* u, double t, double dt, const ad_source* s
   if (stats) *stats = st;
   if (!st.converged) return fail(AD_ERR_NOT_CONVERGED, "GMRES reached its iteration cap");
   return AD_OK;
+}
+
+int ad_check_wait_timeout(double timeout_ms, void* cuda_stream) {
+  g_err.clear();
+  if (!(timeout_ms > 0) || timeout_ms > 1000.0) return fail(AD_ERR_INVALID, "timeout_ms in (0, 1000]");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int* d = nullptr;
+  CUDA_TRY(cudaMalloc(&d, sizeof(int)));
+  int h = -1;
+  const int r = wait_timeout_probe((unsigned long long)(timeout_ms * 1e6), d, s);
+  cudaError_t e1 = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  cudaFree(d);
+  if (r != 0 || e1 != cudaSuccess || e2 != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AD_ERR_CUDA, "wait probe launch failed");
+  }
+  if (h == 4) return fail(AD_ERR_TIMEOUT, "bounded device wait gave up (expected)");
+  return fail(AD_ERR_INVALID, "the wait completed although nothing released it");
 }
 
 int ad_profile_leja_iteration(ad_operator* op, int aug, int reps, double* ms_per_launch) {

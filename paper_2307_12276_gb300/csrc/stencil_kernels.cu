@@ -19,8 +19,10 @@
 #include "ad_internal.h"
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "tile_f32.cuh"
+#include "tile_f32_bulk.cuh"
 
 namespace ad {
 
@@ -74,6 +76,7 @@ __device__ void series_finish(const SeriesArgs& a, double sy, double sp) {
       ctrl->status = 3;
     }
     if (terms >= kMaxIters) stop = 1;               // hard cap, independent of the settings
+    if (ctrl->status == 4) stop = 1;                // a bounded wait gave up in this launch
     ctrl->ticket = 0u;
     ctrl->stop = stop;
     ctrl->m = m + 1;
@@ -469,13 +472,21 @@ __global__ void __launch_bounds__(1024) leja_persistent_f64_k(SeriesArgs a, unsi
     }
     __syncthreads();
     if (s_flag) {
-      __threadfence();
+      // one warp reduces the block partials (fixed order: lane-strided sums,
+      // then a shuffle tree); no block-wide barrier on the critical path
       double ty = 0.0, tp = 0.0;
-      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-        ty += __ldcg(&a.partials[2 * b]);
-        tp += __ldcg(&a.partials[2 * b + 1]);
+      if (threadIdx.x < 32) {
+        __threadfence();
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
+          ty += __ldcg(&a.partials[2 * b]);
+          tp += __ldcg(&a.partials[2 * b + 1]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          ty += __shfl_down_sync(0xffffffffu, ty, o);
+          tp += __shfl_down_sync(0xffffffffu, tp, o);
+        }
       }
-      block_tree_sum2(ty, tp, ra, rb);
       if (threadIdx.x == 0) {
         const int terms = m + 1;
         const double absd = lc.absd, tol = ctrl->tol;
@@ -635,6 +646,46 @@ __global__ void apply_f32_k(GridDev g, const float* __restrict__ F, int adv, flo
 
 // FP32 fused Leja iteration; Leja scalars arrive in FP64 and are rounded once
 // per iteration; per-thread square sums in FP32, block sums in FP64.
+// FP32 fused iteration, warp-specialised bulk-copy pipeline (tile_f32_bulk.cuh).
+template <bool AUG, int ADV>
+__global__ void __launch_bounds__(kBulkThreads) leja_iter_f32_bulk_k(SeriesArgs a) {
+  extern __shared__ __align__(16) float ring[];
+  __shared__ __align__(8) uint64_t full[kBulkStages], empty[kBulkStages];
+  __shared__ float rowsign[kBulkStages];
+  const volatile Ctrl* vc = a.ctrl;
+  if (vc->stop) return;
+  const int m = vc->m;
+  const LejaCoef lc = a.lc[m];
+  const float* __restrict__ yin = static_cast<const float*>(a.y[m & 1]);
+  float* __restrict__ yout = static_cast<float*>(a.y[(m + 1) & 1]);
+  float* __restrict__ p = static_cast<float*>(a.p);
+  const float ig = (float)(1.0 / a.gamma);
+  const float sh = (float)(a.c / a.gamma + lc.xi);
+  const float d = (float)lc.d, e1 = (float)lc.e1, e2 = (float)lc.e2;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kBulkStages; ++k) {
+      mbar_init(&full[k], 2u);               // producer's expect_tx arrive + cp.async arrive
+      mbar_init(&empty[k], kThreads / 32);   // one arrive per consumer warp
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  BulkItems it;
+  it.tiles_x = (a.g.nx + kTileCols - 1) / kTileCols;
+  it.ntiles = it.tiles_x * ((a.g.ny + kBulkTY - 1) / kBulkTY);
+  it.tile0 = blockIdx.x;
+  it.stride = gridDim.x;
+  double accy = 0.0, accp = 0.0;
+  int failed = 0;
+  if (threadIdx.x >= kThreads)
+    bulk_producer<AUG, ADV>(a, yin, it, ring, full, empty, rowsign, failed);
+  else
+    bulk_consumer<AUG, ADV>(a, lc, yout, p, it, ring, full, empty, rowsign, ig, sh, d, e1, e2,
+                            accy, accp, failed);
+  if (failed) a.ctrl->status = 4;            // AD_ERR_TIMEOUT; the series stops
+  series_finish(a, accy, accp);
+}
+
 template <bool AUG, int ADV>
 __global__ void __launch_bounds__(kThreads) leja_iter_f32_k(SeriesArgs a) {
   __shared__ float sy[3][kTileCols + 2];
@@ -699,6 +750,31 @@ bool series_run_persistent(const SeriesArgs& a, unsigned int* gen, cudaStream_t 
   return true;
 }
 
+// Failure-detection check of the bounded waits: one block waits on an
+// mbarrier whose phase never completes (two arrivals expected, one made) and
+// must give up after timeout_ns, recording 4 (timeout) in *status.
+__global__ void wait_timeout_probe_k(unsigned long long timeout_ns, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 2u);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_arrive(&bar);
+    const unsigned long long t0 = global_ns_();
+    int st = 0;
+    while (!mbar_try_wait(&bar, 0u)) {
+      if (global_ns_() - t0 > timeout_ns) { st = 4; break; }
+    }
+    *status = st;
+    mbar_arrive(&bar);   // complete the phase so the barrier is left consistent
+  }
+}
+
+int wait_timeout_probe(unsigned long long timeout_ns, int* status_dev, cudaStream_t s) {
+  ++launch_counter();
+  wait_timeout_probe_k<<<1, 32, 0, s>>>(timeout_ns, status_dev);
+  return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
 int series_blocks(int prec, long long n) {
   // FP64: 4 blocks per SM (two cells per thread per trip keep the FP64 pipe
   // fed; fewer blocks keep the block reductions cheap); FP32: 8 blocks per SM
@@ -711,8 +787,28 @@ int series_blocks(int prec, long long n) {
   return -1;  // FP32: depends on the tile count, see series_blocks_grid
 }
 
+bool series_use_bulk(int prec, int nx) {
+  static const bool off = getenv("AD_NO_BULK") != nullptr;
+  return prec == 1 && nx % 4 == 0 && !off;
+}
+
 int series_blocks_grid(int prec, int nx, int ny) {
   if (prec == 0) return series_blocks(0, (long long)nx * ny);
+  if (series_use_bulk(prec, nx)) {
+    static bool attr = false;
+    if (!attr) {   // the ring needs more than the default 48 KB of dynamic shared memory
+      const int smem = kBulkStages * kStageFloats * (int)sizeof(float);
+      for (void* f : {(void*)leja_iter_f32_bulk_k<false, 0>, (void*)leja_iter_f32_bulk_k<false, 1>,
+                      (void*)leja_iter_f32_bulk_k<false, 2>, (void*)leja_iter_f32_bulk_k<true, 0>,
+                      (void*)leja_iter_f32_bulk_k<true, 1>, (void*)leja_iter_f32_bulk_k<true, 2>})
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      attr = true;
+    }
+    const long long tiles = (long long)((nx + kTileCols - 1) / kTileCols) *
+                            ((ny + kBulkTY - 1) / kBulkTY);
+    const long long cap = 152LL * 3;   // 3 blocks of 288 threads and 66.5 KB per SM
+    return (int)(tiles < cap ? tiles : cap);
+  }
   const long long tiles = (long long)((nx + kTileCols - 1) / kTileCols) *
                           ((ny + kTileRows - 1) / kTileRows);
   const long long cap = 152LL * 4;   // resident blocks of 256 threads at 64-80 registers
@@ -783,6 +879,22 @@ void series_iteration(const SeriesArgs& a, cudaStream_t s) {
       ++launch_counter();
       leja_iter_f64_k<false><<<a.nblocks, kThreads, 0, s>>>(a);
     }
+  } else if (a.bulk) {
+    // bulk-copy pipeline
+    ++launch_counter();
+    const size_t smem = (size_t)kBulkStages * kStageFloats * sizeof(float);
+#define AD_F32B_LAUNCH(AUGV, ADVV) \
+    leja_iter_f32_bulk_k<AUGV, ADVV><<<a.nblocks, kBulkThreads, smem, s>>>(a)
+    if (a.aug) {
+      if (a.adv == 0) AD_F32B_LAUNCH(true, 0);
+      else if (a.adv == 1) AD_F32B_LAUNCH(true, 1);
+      else AD_F32B_LAUNCH(true, 2);
+    } else {
+      if (a.adv == 0) AD_F32B_LAUNCH(false, 0);
+      else if (a.adv == 1) AD_F32B_LAUNCH(false, 1);
+      else AD_F32B_LAUNCH(false, 2);
+    }
+#undef AD_F32B_LAUNCH
   } else {
     ++launch_counter();
 #define AD_F32_LAUNCH(AUGV, ADVV) leja_iter_f32_k<AUGV, ADVV><<<a.nblocks, kThreads, 0, s>>>(a)

@@ -18,7 +18,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // warp 0 add eight values each, then one butterfly: far fewer FP64 additions
 // than a butterfly in every warp (FP64 is the scarce pipe on this GPU).
 __device__ __forceinline__ void block_sum2(double& a, double& b) {
-  __shared__ double sa[kThreads], sb[kThreads];
+  __shared__ double sa[kThreads + 32], sb[kThreads + 32];   // up to 9 warps
   const int t = threadIdx.x;
   __syncthreads();
   sa[t] = a;
