@@ -40,6 +40,18 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "c1-512sq-dirichlet-circular-expquad2-dt200cfl"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz
+
+
+def _measured_hbm_gbs() -> float:
+    """Copy bandwidth from the measured peaks beside this file (falls back to 6.8 TB/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+HBM_PEAK_GBS = _measured_hbm_gbs()
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -183,10 +195,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_per_launch(kernel_file: str, summary: str):
+def source_digest(files) -> str:
+    """sha256 over the named source files (package csrc/), in order."""
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_2307_12276_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def traffic_per_launch(files, summary: str):
     """DRAM bytes per launch of the dominant kernel from a committed ncu summary
     (lines "source_sha256: ..." and "dram_bytes_per_launch: ..."), or None when
-    the kernel source changed since the counters were taken."""
+    the kernel's sources changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", summary)
     try:
         text = open(path).read()
@@ -198,13 +218,18 @@ def traffic_per_launch(kernel_file: str, summary: str):
         if ":" in line:
             k, v = line.split(":", 1)
             fields[k.strip()] = v.strip()
-    sha = hashlib.sha256(open(kernel_file, "rb").read()).hexdigest()
-    if fields.get("source_sha256") != sha:
+    if fields.get("source_sha256") != source_digest(files):
         return None
     try:
         return float(fields["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+# sources that define each profiled kernel (the digest in its summary covers these)
+F64_SERIES_SOURCES = ("persistent_f64.cu", "ad_internal.h")
+F32_ITER_SOURCES = ("stencil_kernels.cu", "tile_f32.cuh", "tile_f32_vec.cuh", "tile_f32_ring.cuh",
+                    "ad_internal.h")
 
 
 # --------------------------------------------------------------------------- ours
@@ -242,6 +267,11 @@ def measure_fp32_form(ad, dev, stream, flush, steps):
     ms_launch = ad.profile_leja_iteration(op, aug=0, reps=100)
     alg_bytes = 28.0 * g.n      # 3 fields + y + p r/w + y_next, 4 B each
     gbs = alg_bytes / (ms_launch * 1e-3) / 1e9
+    kind = os.environ.get("AD_F32_KERNEL", "ring")[:1]
+    kernel = {"b": "leja_iter_f32_bulk_k", "t": "leja_iter_f32_k",
+              "v": "leja_iter_f32_vec_k"}.get(kind, "leja_iter_f32_ring_k")
+    traffic = (traffic_per_launch(F32_ITER_SOURCES, "leja_iter_f32_ring_4096sq.md")
+               if kernel == "leja_iter_f32_ring_k" else None)
     op.close()
     del u, src
     torch.cuda.empty_cache()
@@ -249,10 +279,11 @@ def measure_fp32_form(ad, dev, stream, flush, steps):
             "value": round(g.n * steps / (ms * 1e-3) / 1e6, 2), "unit": "Mcell-steps/s",
             "ms_per_step": round(ms / steps, 4), "leja_iters_per_step": statistics.mean(iters),
             "tol": p.tol, "dtype": "f32 storage/arithmetic, f64 Leja scalars and norm sums",
-            "roofline": {"bound": "hbm", "kernel": "leja_iter_f32_k", "ms_per_launch":
-                         round(ms_launch, 5), "achieved": round(gbs, 1), "peak": 6750.4,
-                         "unit": "GB/s", "frac": round(gbs / 6750.4, 4),
-                         "alg_bytes_per_launch": alg_bytes}}
+            "roofline": {"bound": "hbm", "kernel": f"{kernel}<0,0>", "ms_per_launch":
+                         round(ms_launch, 5), "achieved": round(gbs, 1), "peak": HBM_PEAK_GBS,
+                         "unit": "GB/s", "frac": round(gbs / HBM_PEAK_GBS, 4),
+                         "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
+                         "peak_note": "of measured copy bandwidth"}}
 
 
 def measure_cn_vs_exp(ad, dev, stream, T_cfl=1000.0):
@@ -324,17 +355,18 @@ def _slice_operators(ad, dev, stream, nslices, sides):
     import torch
     from workloads import config3_slices, slice_problem
     specs = config3_slices(nslices, sides=sides)
-    ops, us, srcs, probs = [], [], [], []
+    ops, us, srcs, probs, fields = [], [], [], [], []
     for side, dpar, dperp in specs:
         p = slice_problem(side, dpar, dperp, dt=1.0)
         T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(), device=dev)
-        op = ad.create_operator(side, side, p.grid.bc, T(p.Dxx), T(p.Dxy), T(p.Dyy), 0.05, 0.0,
-                                ad.FP32_STORAGE, stream=stream)
+        D = (T(p.Dxx), T(p.Dxy), T(p.Dyy))
+        op = ad.create_operator(side, side, p.grid.bc, *D, 0.05, 0.0, ad.FP32_STORAGE, stream=stream)
         ops.append(op)
         us.append(T(p.u0).float())
         srcs.append(ad.Source([T(p.source.g[0]).float()], None))
         probs.append(p)
-    return ops, us, srcs, probs
+        fields.append(D)
+    return ops, us, srcs, probs, fields
 
 
 def measure_batched_form(ad, dev, stream, steps, nslices=128, sides=(256, 512, 1024, 2048),
@@ -345,7 +377,7 @@ def measure_batched_form(ad, dev, stream, steps, nslices=128, sides=(256, 512, 1
     import numpy as np
     import torch
     t_setup = time.perf_counter()
-    ops, us, srcs, probs = _slice_operators(ad, dev, stream, nslices, sides)
+    ops, us, srcs, probs, fields = _slice_operators(ad, dev, stream, nslices, sides)
     setup_s = time.perf_counter() - t_setup
     # bounds: power iteration per slice (timed), dt = 100 Delta t_CFL of the stiffest slice
     torch.cuda.synchronize()
@@ -396,17 +428,19 @@ def measure_batched_form(ad, dev, stream, steps, nslices=128, sides=(256, 512, 1
            "autotune": info, "power_iteration_bounds_s": round(power_s, 4),
            "setup_s": round(setup_s, 1), "tol": 1e-6}
     if learned_fields:
-        out["learned"] = measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, dt, batch,
-                                         steps, ms_batch, power_s, learned_fields)
+        out["learned"] = measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, fields,
+                                         dt, batch, steps, ms_batch, power_s, learned_fields)
     for op in ops:
         op.close()
     return out
 
 
-def measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, dt, batch, steps, ms_batch,
-                    power_s, nfields):
+def measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, fields, dt, batch, steps,
+                    ms_batch, power_s, nfields, margin=1.1):
     """Train the bound network on generated fields (labels: power-iteration
-    spectra), predict every slice's bound, run the batch with fallback."""
+    spectra), predict every slice's bound from its device-resident diffusion
+    tensor, run the batch with fallback.  The comparison with power-iteration
+    bounds counts bound time plus ``steps`` batched steps on both sides."""
     import numpy as np
     import torch
     from paper_2307_12276_gb300 import learned
@@ -419,16 +453,13 @@ def measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, dt, batch, s
     train_s = time.perf_counter() - t0
     hold = model.predict(torch.as_tensor(X[nfields:], device=dev)).cpu().numpy()
     alpha_err = np.abs(np.exp(hold[:, 0] - Y[nfields:, 0]) - 1.0)
-    # bounds for the slices from features + one batched inference
+    # bounds for the slices: features of the resident fields + one batched inference
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    feats = []
-    for p in probs:
-        T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(), device=dev)
-        feats.append(ad.field_features(p.grid.nx, p.grid.ny, p.grid.bc, T(p.Dxx), T(p.Dxy),
-                                       T(p.Dyy), 0.05, dt))
-    alpha, it_pred = learned.predict_bounds(model, np.stack(feats), [p.grid.dx for p in probs], dev,
-                                            margin=1.2)
+    feats = np.stack([ad.field_features(p.grid.nx, p.grid.ny, p.grid.bc, *D, 0.05, dt,
+                                        stream=stream) for p, D in zip(probs, fields)])
+    alpha, it_pred = learned.predict_bounds(model, feats, [p.grid.dx for p in probs], dev,
+                                            margin=margin)
     torch.cuda.synchronize()
     predict_s = time.perf_counter() - t0
     power_alpha = [ad.get_spectral_bound(op) for op in ops]
@@ -436,26 +467,36 @@ def measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, dt, batch, s
         ad.set_spectral_bound(op, float(a))
     for s in range(len(us)):
         us[s].copy_(u_start[s])
+    # warm-up step (the plain batch had one too), then the timed steps
+    learned.batched_step_with_fallback(batch, ops, us, 0.0, dt, srcs, tol=1e-6)
     fallbacks = 0
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
     iters = []
     for k in range(steps):
-        st, fb = learned.batched_step_with_fallback(batch, ops, us, k * dt, dt, srcs, tol=1e-6)
+        st, fb = learned.batched_step_with_fallback(batch, ops, us, (k + 1) * dt, dt, srcs,
+                                                    tol=1e-6)
         fallbacks += len(fb)
         iters.append(sum(s["iters"] for s in st))
+    ev1.record(stream)
     torch.cuda.synchronize()
-    ms_learned = (time.perf_counter() - t0) * 1e3 / steps
+    ms_learned = ev0.elapsed_time(ev1) / steps
     for op, a in zip(ops, power_alpha):
         ad.set_spectral_bound(op, a)
     plain_total = power_s + steps * ms_batch * 1e-3
     learned_total = predict_s + steps * ms_learned * 1e-3
+    ratio = np.asarray(alpha) / np.asarray(power_alpha)
     return {"training_fields": nfields, "label_s": round(label_s, 1), "train_s": round(train_s, 2),
             "heldout_alpha_rel_err_median": round(float(np.median(alpha_err)), 4),
             "heldout_alpha_rel_err_p90": round(float(np.quantile(alpha_err, 0.9)), 4),
-            "predict_s": round(predict_s, 4), "ms_per_step": round(ms_learned, 4),
+            "margin": margin, "bounds_s": round(predict_s, 4),
+            "power_iteration_bounds_s": round(power_s, 4),
+            "ms_per_step": round(ms_learned, 4), "power_bound_ms_per_step": round(ms_batch, 4),
             "fallback_rate": round(fallbacks / (steps * len(ops)), 4),
-            "mean_pred_over_power_alpha": round(float(np.mean(np.asarray(alpha) / np.asarray(power_alpha))), 3),
+            "pred_over_power_alpha": {"mean": round(float(ratio.mean()), 3),
+                                      "min": round(float(ratio.min()), 3),
+                                      "max": round(float(ratio.max()), 3)},
             "speedup_vs_power_iteration_bounds": round(plain_total / learned_total, 3),
             "steps_in_comparison": steps}
 
@@ -510,6 +551,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    ad.time_series(op)          # event pair around every series kernel launch in the timed steps
     with ClockSampler(local) as clk:
         for k in range(args.steps):
             flush.zero_()
@@ -520,6 +562,8 @@ def run_ours(args):
             iters.append(st["iters"])
             t += p.dt
         torch.cuda.synchronize()
+    series_t = ad.series_timing(op)
+    ad.time_series(op, False)
     if world > 1:
         dist.barrier()
     dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
@@ -544,26 +588,26 @@ def run_ours(args):
             te += el
     e2e_value = g.n * args.e2e_steps / te / 1e6
 
-    # roofline of the fused (augmented) Leja iteration kernel
-    ms_launch = ad.profile_leja_iteration(op, aug=1, reps=300)
+    # roofline of the series kernel, from the event pairs around its launches in the timed steps
     flops = 28.0 * g.n        # 14 FP64 FMA per cell: 9 stencil, shift, coupling, p, 2 norms
     bytes_alg = 112.0 * g.n   # 9 weights + y + w2 + p (r/w) + y_next, 8 B each
-    achieved = flops / (ms_launch * 1e-3) / 1e12
-    traffic = traffic_per_launch(os.path.join(ROOT, "paper_2307_12276_gb300", "csrc",
-                                              "stencil_kernels.cu"),
-                                 "leja_persistent_f64_512sq.md")
-    persistent = g.n <= 152 * 2048
+    ms_it = series_t["ms"] / max(series_t["iters"], 1)
+    achieved = flops * series_t["iters"] / (series_t["ms"] * 1e-3) / 1e12
+    ms_forced = ad.profile_leja_iteration(op, aug=1, reps=300)
+    kernel = series_t["kernel"]
+    traffic = None
+    if kernel == "leja_nsync_f64_k":
+        traffic = traffic_per_launch(F64_SERIES_SOURCES, "leja_nsync_f64_512sq.md")
     roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
             "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-            "traffic": traffic,
-            "kernel": "leja_persistent_f64_k<aug>" if persistent else "leja_iter_f64_k<aug>",
-            "work_unit": ("one Leja iteration; the persistent kernel runs a whole Newton series "
-                          "per launch, timed with CUDA events around a 300-iteration launch"
-                          if persistent else "one launch = one Leja iteration"),
-            "ms_per_iteration": round(ms_launch, 5),
+            "traffic": traffic, "kernel": f"{kernel}<aug>",
+            "work_unit": "one launch = one whole Newton series (all its Leja iterations)",
+            "launches_timed": series_t["series"], "iterations_timed": series_t["iters"],
+            "ms_per_launch": round(series_t["ms"] / max(series_t["series"], 1), 5),
+            "ms_per_iteration": round(ms_it, 5),
+            "ms_per_iteration_forced_300": round(ms_forced, 5),
             "alg_flops_per_iteration": flops,
             "alg_bytes_per_iteration": bytes_alg,
-            "alg_GBps": round(bytes_alg / (ms_launch * 1e-3) / 1e9, 1),
             "peak_note": "of derived FP64 peak: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz "
                          "(probe measured 1.89 DFMA/clk/SM)"}
 

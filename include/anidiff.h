@@ -191,7 +191,10 @@ AD_API int ad_destroy_batch(ad_batch* b);
  * each, evaluated at t + dt/2).  Every slice needs gamma_s dt <= rho_max (one
  * substep).  force_iters > 0 runs exactly that many iterations per slice.
  * per_slice: NULL or nslices stats (kernel_launches holds the whole step's
- * count in every entry).  AD_ERR_NOT_CONVERGED if any slice hit max_iters. */
+ * count in every entry).  AD_ERR_NOT_CONVERGED if any slice hit max_iters
+ * (or produced a non-finite norm); such a slice keeps its input state, so the
+ * caller can repeat it alone with a safer bound, while every converged slice
+ * has been advanced. */
 AD_API int ad_batch_midpoint_step(ad_batch* b, void* const* u, double t, double dt,
                                   const ad_source* src, double tol, int force_iters,
                                   ad_stats* per_slice);
@@ -237,13 +240,31 @@ AD_API int ad_field_features(const ad_grid* grid, const double* Dxx, const doubl
                              float* out21);
 
 /* Measurement helper (no counterpart in the paper): time the fused Leja
- * iteration kernel alone.  Runs `reps` iterations of the series kernel
- * (aug = 0: phi_1 form, 1: augmented form) on the operator's stream with a
- * CUDA event pair around each kernel launch (the control kernel between
- * them is not timed) and returns the mean kernel duration in *ms_per_launch.
- * Overwrites the operator's series workspace; results of earlier calls are
- * unaffected.  1 <= reps <= 500. */
+ * iteration kernel alone.  Runs a forced series of `reps` iterations (aug =
+ * 0: phi_1 form, 1: augmented form) on the operator's stream and returns the
+ * mean device time of one iteration in *ms_per_launch: on the persistent FP64
+ * path (one cooperative launch per series) the launch time / reps, otherwise
+ * the mean of CUDA event pairs around each iteration kernel.  Overwrites the
+ * operator's series workspace; results of earlier calls are unaffected.
+ * 1 <= reps <= 500. */
 AD_API int ad_profile_leja_iteration(ad_operator* op, int aug, int reps, double* ms_per_launch);
+
+/* Measurement helper (no counterpart in the paper): device time of the Newton
+ * series inside real calls.  enable != 0 resets the totals and from then on
+ * records a CUDA event pair on the operator's stream around the iteration
+ * kernels of every series the operator runs (the cooperative launch, the
+ * graph launch or the host-driven launches; substeps and both series of a
+ * step count separately); enable == 0 stops recording.  ad_series_timing
+ * returns the totals since the last enable: milliseconds, number of series
+ * and their total Leja iterations, and (kernel may be NULL) the path of the
+ * last timed series: 1 persistent kernel with a grid barrier per iteration,
+ * 2 persistent kernel with neighbour synchronisation, 3 graph loop of
+ * per-iteration kernels, 4 host-driven per-iteration launches, 0 none yet.
+ * Recording adds two event records and no synchronisation (each series
+ * already ends with one). */
+AD_API int ad_time_series(ad_operator* op, int enable);
+AD_API int ad_series_timing(const ad_operator* op, double* ms, int* series, long long* iters,
+                            int* kernel);
 
 /* out = phi_1(dt A) v without allocating any device memory.  The paper has
  * no counterpart: this entry point exists for callers that cannot call

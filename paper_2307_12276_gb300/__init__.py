@@ -79,6 +79,9 @@ _sig = {
     "ad_mlp_train": (_i, [_vp, _vp, _vp, _i, _i, C.c_float, _i, C.POINTER(C.c_float)]),
     "ad_mlp_predict": (_i, [_vp, _vp, _i, _i, _vp]),
     "ad_field_features": (_i, [C.POINTER(_Grid), _vp, _vp, _vp, _d, _d, _vp, _vp]),
+    "ad_time_series": (_i, [_vp, _i]),
+    "ad_series_timing": (_i, [_vp, C.POINTER(_d), C.POINTER(_i), C.POINTER(C.c_longlong),
+                              C.POINTER(_i)]),
     "ad_check_wait_timeout": (_i, [_d, _vp]),
     "ad_last_error": (C.c_char_p, []),
     "ad_version": (_i, []),
@@ -297,6 +300,25 @@ def profile_leja_iteration(op: Operator, aug: int = 0, reps: int = 200) -> float
     ms = _d()
     _check(_lib.ad_profile_leja_iteration(op.handle, aug, reps, C.byref(ms)))
     return ms.value
+
+
+def time_series(op: Operator, enable: bool = True) -> None:
+    """ad_time_series: start (and reset) or stop recording the device time of
+    every Newton series the operator runs."""
+    _check(_lib.ad_time_series(op.handle, 1 if enable else 0))
+
+
+SERIES_KERNELS = {0: None, 1: "leja_persistent_f64_k", 2: "leja_nsync_f64_k",
+                  3: "graph loop of per-iteration kernels", 4: "host-driven per-iteration kernels"}
+
+
+def series_timing(op: Operator) -> dict:
+    """ad_series_timing: {"ms", "series", "iters", "kernel"} since the last
+    enable ("kernel": the path of the last timed series)."""
+    ms, ns, it, k = _d(), _i(), C.c_longlong(), _i()
+    _check(_lib.ad_series_timing(op.handle, C.byref(ms), C.byref(ns), C.byref(it), C.byref(k)))
+    return {"ms": ms.value, "series": ns.value, "iters": it.value,
+            "kernel": SERIES_KERNELS.get(k.value)}
 
 
 NOALLOC_MAX_CELLS = 1 << 16

@@ -97,7 +97,8 @@ struct SeriesArgs {
   float abx, aby;
   unsigned long long handle;  // CUDA graph conditional of the WHILE loop
   int has_handle;             // 1 when run inside the graph loop
-  int bulk;                   // FP32: warp-specialised bulk-copy kernel (nx % 4 == 0)
+  int f32k;                   // FP32 iteration kernel: 0 tile, 1 bulk-copy pipeline, 2 register
+                            // marching, 3 register marching fed by cp.async rings
 };
 // y[0] = src (or 0 if src == null), p = d0 * y[0]; resets ctrl.
 void series_init(const SeriesArgs& a, const void* src, double d0, int force, int max_iters,
@@ -110,12 +111,26 @@ void series_iteration(const SeriesArgs& a, cudaStream_t s);
 // gen: device barrier generation counter (persists across calls).  Returns
 // false if not applicable or refused; nothing was launched then.
 constexpr long long kPersistMaxCells = 152LL * 2048;
-bool series_run_persistent(const SeriesArgs& a, unsigned int* gen, cudaStream_t s);
+// Device scratch of the neighbour-synchronised persistent kernel: write-once
+// norm slots [kMaxIters][nsync_max_blocks()][2] and one flag per block.
+struct NsyncScratch {
+  double* slots;
+  unsigned int* flags;
+};
+size_t nsync_slots_bytes();
+int nsync_max_blocks();
+// ns == nullptr selects the grid-barrier kernel.  Returns 2 (neighbour-
+// synchronised kernel launched), 1 (grid-barrier kernel launched) or 0.
+int series_run_persistent(const SeriesArgs& a, unsigned int* gen, const NsyncScratch* ns,
+                           cudaStream_t s);
 
 // grid size of the fused iteration kernel (FP64: by cell count; FP32: by tile count)
 int series_blocks(int prec, long long n);
 int series_blocks_grid(int prec, int nx, int ny);
-bool series_use_bulk(int prec, int nx);
+// FP32 iteration kernel for this grid: 3 cp.async-ring marching (default, nx % 4 == 0),
+// 2 register marching, 1 bulk-copy pipeline, 0 tile (any nx);
+// AD_F32_KERNEL=ring|vec|bulk|tile overrides.
+int series_f32_kernel(int prec, int nx);
 
 // ---------------------------------------------------------------- vector helpers
 // z = a*x + b*y (x or y may be null = 0), elementwise, storage type prec.

@@ -216,6 +216,7 @@ __global__ void __launch_bounds__(kThreads) batch_update_k(const BatchSlice* sli
                                                           int TY) {
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const BatchSlice& S = slices[tile_slice[t]];
+    if (S.a.ctrl->status != 0) continue;      // not converged: keep the input state
     const GridDev g = S.a.g;
     const int local = t - S.tile_off;
     const int x0 = (local % S.tiles_x) * kTileCols, y0 = (local / S.tiles_x) * TY;

@@ -105,7 +105,15 @@ struct ad_operator {
   double* partials = nullptr;                  // >= 2 * nblocks and >= kMaxGmres+1 rows for GMRES
   size_t partials_len = 0;
   double* dscal = nullptr;                     // device scalars [64]
+  NsyncScratch nsync{nullptr, nullptr};        // persistent-kernel scratch (FP64, small grids)
   int nblocks = 1;
+  // series timing (ad_time_series)
+  bool time_series = false;
+  cudaEvent_t tev[2] = {nullptr, nullptr};
+  double t_ms = 0.0;
+  int t_series = 0;
+  long long t_iters = 0;
+  int t_path = 0;
   // pinned host mirrors
   LejaCoef* h_lc = nullptr;
   Ctrl* h_ctrl = nullptr;
@@ -164,7 +172,7 @@ SeriesArgs series_args(ad_operator* op, int aug) {
   a.ctrl = op->ctrl;
   a.partials = op->partials;
   a.nblocks = series_blocks_grid(op->prec, op->g.nx, op->g.ny);
-  a.bulk = series_use_bulk(op->prec, op->g.nx) ? 1 : 0;
+  a.f32k = series_f32_kernel(op->prec, op->g.nx);
   a.aug = aug;
   a.adv = op->adv;
   a.abx = op->abx;
@@ -353,9 +361,11 @@ int run_series(ad_operator* op, int aug, const void* src, double d0, int force, 
     op->h_ctrl->err_est = 0.0;
   } else {
     SeriesGraph& sg = op->graphs[aug];
+    if (op->time_series) CUDA_TRY(cudaEventRecord(op->tev[0], op->stream));
     // small and medium FP64 grids: the whole series in one cooperative launch
-    const bool persist = !getenv("AD_NO_PERSIST") &&
-                         series_run_persistent(a, &op->ctrl->gen, op->stream);
+    const int pk = getenv("AD_NO_PERSIST") ? 0
+                   : series_run_persistent(a, &op->ctrl->gen, &op->nsync, op->stream);
+    const bool persist = pk != 0;
     if (!persist && !sg.tried) build_graph(op, aug);
     if (persist) {
       // launched; the kernel counted itself
@@ -375,9 +385,18 @@ int run_series(ad_operator* op, int aug, const void* src, double d0, int force, 
       }
     }
     CUDA_TRY(cudaGetLastError());
+    if (op->time_series) CUDA_TRY(cudaEventRecord(op->tev[1], op->stream));
     CUDA_TRY(cudaMemcpyAsync(op->h_ctrl, op->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, op->stream));
     CUDA_TRY(cudaStreamSynchronize(op->stream));
     iters = op->h_ctrl->iters;
+    if (op->time_series) {
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, op->tev[0], op->tev[1]));
+      op->t_ms += ms;
+      op->t_series += 1;
+      op->t_iters += iters;
+      op->t_path = persist ? pk : (graph_used ? 3 : 4);
+    }
     if (!op->h_ctrl->stop) return fail(AD_ERR_TIMEOUT, "Leja series did not reach its stop state");
     {  // the device stores |d_{m+1}| and the squared norms; form the estimate here
       const Ctrl& h = *op->h_ctrl;
@@ -554,6 +573,10 @@ int ad_create_operator(const ad_grid* grid, const double* Dxx, const double* Dxy
   ok = ok && alloc((void**)&op->lc, sizeof(LejaCoef) * kMaxIters);
   ok = ok && alloc((void**)&op->ctrl, sizeof(Ctrl));
   ok = ok && alloc((void**)&op->dscal, sizeof(double) * 4 * (kMaxGmres + 2));
+  if (precision == AD_FP64 && n <= kPersistMaxCells) {
+    ok = ok && alloc((void**)&op->nsync.slots, nsync_slots_bytes());
+    ok = ok && alloc((void**)&op->nsync.flags, sizeof(unsigned int) * nsync_max_blocks());
+  }
   if (ok) ok = cudaMallocHost((void**)&op->h_lc, sizeof(LejaCoef) * kMaxIters) == cudaSuccess;
   if (ok) ok = cudaMallocHost((void**)&op->h_ctrl, sizeof(Ctrl)) == cudaSuccess;
   if (ok) ok = cudaMallocHost((void**)&op->h_scal, sizeof(double) * 4 * (kMaxGmres + 2)) == cudaSuccess;
@@ -596,8 +619,11 @@ int ad_destroy_operator(ad_operator* op) {
   if (op->cap_stream) cudaStreamDestroy(op->cap_stream);
   for (void* p : {(void*)op->W, (void*)op->Ws, (void*)op->F, op->Y0, op->Y1, op->P, op->W1, op->W2,
                   op->T1, op->T2, op->T3, op->S0, op->S1, (void*)op->Vk, (void*)op->lc,
-                  (void*)op->ctrl, (void*)op->partials, (void*)op->dscal})
+                  (void*)op->ctrl, (void*)op->partials, (void*)op->dscal,
+                  (void*)op->nsync.slots, (void*)op->nsync.flags})
     if (p) cudaFree(p);
+  for (cudaEvent_t e : op->tev)
+    if (e) cudaEventDestroy(e);
   if (op->h_lc) cudaFreeHost(op->h_lc);
   if (op->h_ctrl) cudaFreeHost(op->h_ctrl);
   if (op->h_scal) cudaFreeHost(op->h_scal);
@@ -946,6 +972,32 @@ int ad_check_wait_timeout(double timeout_ms, void* cuda_stream) {
   return fail(AD_ERR_INVALID, "the wait completed although nothing released it");
 }
 
+int ad_time_series(ad_operator* op, int enable) {
+  g_err.clear();
+  if (!op) return fail(AD_ERR_INVALID, "op is NULL");
+  if (enable) {
+    for (cudaEvent_t& e : op->tev)
+      if (!e) CUDA_TRY(cudaEventCreate(&e));
+    op->t_ms = 0.0;
+    op->t_series = 0;
+    op->t_iters = 0;
+    op->t_path = 0;
+  }
+  op->time_series = enable != 0;
+  return AD_OK;
+}
+
+int ad_series_timing(const ad_operator* op, double* ms, int* series, long long* iters,
+                     int* kernel) {
+  g_err.clear();
+  if (!op || !ms || !series || !iters) return fail(AD_ERR_INVALID, "NULL argument");
+  *ms = op->t_ms;
+  *series = op->t_series;
+  *iters = op->t_iters;
+  if (kernel) *kernel = op->t_path;
+  return AD_OK;
+}
+
 int ad_profile_leja_iteration(ad_operator* op, int aug, int reps, double* ms_per_launch) {
   g_err.clear();
   if (!op || !ms_per_launch) return fail(AD_ERR_INVALID, "NULL argument");
@@ -964,7 +1016,7 @@ int ad_profile_leja_iteration(ad_operator* op, int aug, int reps, double* ms_per
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     CUDA_TRY(cudaEventRecord(e0, op->stream));
-    const bool ok = series_run_persistent(a, &op->ctrl->gen, op->stream);
+    const bool ok = series_run_persistent(a, &op->ctrl->gen, &op->nsync, op->stream) != 0;
     CUDA_TRY(cudaEventRecord(e1, op->stream));
     CUDA_TRY(cudaStreamSynchronize(op->stream));
     float ms = 0.f;

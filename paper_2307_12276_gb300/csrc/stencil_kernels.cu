@@ -23,6 +23,8 @@
 
 #include "tile_f32.cuh"
 #include "tile_f32_bulk.cuh"
+#include "tile_f32_vec.cuh"
+#include "tile_f32_ring.cuh"
 
 namespace ad {
 
@@ -333,213 +335,6 @@ __global__ void __launch_bounds__(kThreads) leja_iter_f64_k(SeriesArgs a) {
 }
 
 // --------------------------------------------------------------------------
-// Persistent FP64 series for grids up to kPersistMaxCells: one cooperative
-// launch runs every iteration of a Newton series.  Block b owns a contiguous
-// chunk of cells; its 9 scaled weights, p and w2 stay in shared memory for the
-// whole series (loaded once, 88 B/cell), y ping-pongs through global memory.
-// One grid barrier per iteration: the last block to arrive reduces the norm
-// partials in block order, applies the stopping rule and publishes it; the
-// others wait for the barrier generation to change.  Every wait is bounded
-// (kBarrierTimeoutNs of global time), after which the block records a timeout
-// status and leaves, so the kernel cannot hang.
-constexpr unsigned long long kBarrierTimeoutNs = 2000000000ULL;
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Tree sum of two values over the block (FP64; result in every thread).  The
-// active threads of each level are contiguous, so levels above 32 run whole
-// warps only: about 2*(nt/32 + 5) warp-level FP64 additions per block, which
-// matters on a GPU whose FP64 pipe runs one warp instruction per 16 cycles.
-__device__ __forceinline__ void block_tree_sum2(double& a, double& b, double* sa, double* sb) {
-  const int t = threadIdx.x, nt = blockDim.x;  // nt is a power of two
-  __syncthreads();
-  sa[t] = a;
-  sb[t] = b;
-  __syncthreads();
-  for (int s = nt >> 1; s >= 32; s >>= 1) {
-    if (t < s) {
-      sa[t] += sa[t + s];
-      sb[t] += sb[t + s];
-    }
-    __syncthreads();
-  }
-  if (t < 32) {
-    double x = sa[t], y = sb[t];
-    if (nt < 32) {                 // tiny blocks: lanes beyond the block hold nothing
-      x = t < nt ? x : 0.0;
-      y = t < nt ? y : 0.0;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      x += __shfl_down_sync(0xffffffffu, x, o);
-      y += __shfl_down_sync(0xffffffffu, y, o);
-    }
-    if (t == 0) {
-      sa[0] = x;
-      sb[0] = y;
-    }
-  }
-  __syncthreads();
-  a = sa[0];
-  b = sb[0];
-}
-
-template <bool AUG>
-__global__ void __launch_bounds__(1024) leja_persistent_f64_k(SeriesArgs a, unsigned int cpb,
-                                                             unsigned int* gen) {
-  extern __shared__ double smem[];
-  __shared__ double ra[1024], rb[1024];
-  __shared__ int s_flag;
-  const GridDev g = a.g;
-  const unsigned int n = (unsigned int)g.n, nx = (unsigned int)g.nx;
-  const unsigned int c0 = blockIdx.x * cpb;
-  const unsigned int c1 = min(n, c0 + cpb);
-  const unsigned int nc = c1 > c0 ? c1 - c0 : 0u;
-  double* sW = smem;                 // [9][cpb]
-  double* sP = smem + 9 * cpb;       // [cpb]
-  double* sW2 = sP + cpb;            // [cpb] (augmented)
-  const double* __restrict__ Ws = static_cast<const double*>(a.coef);
-  double* __restrict__ p = static_cast<double*>(a.p);
-  const double* __restrict__ w1 = static_cast<const double*>(a.w1);
-  const double* __restrict__ w2 = static_cast<const double*>(a.w2);
-  Ctrl* ctrl = a.ctrl;
-  for (unsigned int k = threadIdx.x; k < nc; k += blockDim.x) {
-#pragma unroll
-    for (int q = 0; q < 9; ++q) sW[q * cpb + k] = Ws[(long long)q * n + c0 + k];
-    sP[k] = p[c0 + k];
-    if (AUG) sW2[k] = w2[c0 + k];
-  }
-  unsigned int my_gen = 0;
-  if (threadIdx.x == 0) my_gen = *(volatile unsigned int*)gen;
-  int m = 0;
-  for (;;) {
-    const LejaCoef lc = a.lc[m];
-    const double* __restrict__ yin = static_cast<const double*>(a.y[m & 1]);
-    double* __restrict__ yout = static_cast<double*>(a.y[(m + 1) & 1]);
-    __syncthreads();                 // shared weights/p ready; previous iteration done
-    double sy = 0.0, sp = 0.0;
-    for (unsigned int k = threadIdx.x; k < nc; k += blockDim.x) {
-      const unsigned int idx = c0 + k;
-      const int j = (int)(idx / nx), i = (int)(idx - (unsigned int)j * nx);
-      int im, ip, jm, jp;
-      if (g.bc == 0) {
-        im = i ? i - 1 : g.nx - 1;
-        ip = (i + 1 < g.nx) ? i + 1 : 0;
-        jm = j ? j - 1 : g.ny - 1;
-        jp = (j + 1 < g.ny) ? j + 1 : 0;
-      } else {
-        im = i ? i - 1 : 0;
-        ip = (i + 1 < g.nx) ? i + 1 : i;
-        jm = j ? j - 1 : 0;
-        jp = (j + 1 < g.ny) ? j + 1 : j;
-      }
-      const double* rm = yin + (long long)jm * g.nx;
-      const double* r0 = yin + (long long)j * g.nx;
-      const double* rp = yin + (long long)jp * g.nx;
-      const double yc = r0[i];
-      double z = sW[4 * cpb + k] * yc;
-      z = fma(sW[0 * cpb + k], rm[im], z);
-      z = fma(sW[1 * cpb + k], rm[i], z);
-      z = fma(sW[2 * cpb + k], rm[ip], z);
-      z = fma(sW[3 * cpb + k], r0[im], z);
-      z = fma(sW[5 * cpb + k], r0[ip], z);
-      z = fma(sW[6 * cpb + k], rp[im], z);
-      z = fma(sW[7 * cpb + k], rp[i], z);
-      z = fma(sW[8 * cpb + k], rp[ip], z);
-      z = fma(-lc.xi, yc, z);
-      if (AUG) {
-        if (lc.e1 != 0.0) z = fma(lc.e1, sW2[k], z);
-        if (lc.e2 != 0.0) z = fma(lc.e2, w1[idx], z);
-      }
-      yout[idx] = z;
-      const double pn = fma(lc.d, z, sP[k]);
-      sP[k] = pn;
-      sy = fma(z, z, sy);
-      sp = fma(pn, pn, sp);
-    }
-    block_tree_sum2(sy, sp, ra, rb);
-    // grid barrier; the last arriver decides
-    if (threadIdx.x == 0) {
-      a.partials[2 * blockIdx.x] = sy;
-      a.partials[2 * blockIdx.x + 1] = sp;
-      __threadfence();
-      const unsigned int t = atomicAdd(&ctrl->ticket, 1u);
-      s_flag = (t == gridDim.x - 1) ? 1 : 0;
-    }
-    __syncthreads();
-    if (s_flag) {
-      // one warp reduces the block partials (fixed order: lane-strided sums,
-      // then a shuffle tree); no block-wide barrier on the critical path
-      double ty = 0.0, tp = 0.0;
-      if (threadIdx.x < 32) {
-        __threadfence();
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
-          ty += __ldcg(&a.partials[2 * b]);
-          tp += __ldcg(&a.partials[2 * b + 1]);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          ty += __shfl_down_sync(0xffffffffu, ty, o);
-          tp += __shfl_down_sync(0xffffffffu, tp, o);
-        }
-      }
-      if (threadIdx.x == 0) {
-        const int terms = m + 1;
-        const double absd = lc.absd, tol = ctrl->tol;
-        ctrl->ynorm2 = ty;
-        ctrl->pnorm2 = tp;
-        ctrl->iters = terms;
-        ctrl->err_est = absd;
-        int stop = 0;
-        if (ctrl->force > 0) {
-          stop = terms >= ctrl->force;
-        } else if (!(ty == ty) || !(tp == tp)) {
-          stop = 1;
-          ctrl->status = 3;
-        } else if (terms >= 2 && (absd * absd) * ty <= (tol * tol) * tp) {
-          stop = 1;
-        } else if (terms >= ctrl->max_iters) {
-          stop = 1;
-          ctrl->status = 3;
-        }
-        if (terms >= kMaxIters) stop = 1;
-        ctrl->stop = stop;
-        ctrl->m = m + 1;
-        ctrl->ticket = 0u;
-        __threadfence();
-        atomicAdd(gen, 1u);           // release the waiting blocks
-        my_gen += 1u;
-        s_flag = stop ? 2 : 0;
-      }
-    } else if (threadIdx.x == 0) {
-      const unsigned long long t0 = global_ns();
-      int state = 0;
-      while (*(volatile unsigned int*)gen == my_gen) {
-        if (global_ns() - t0 > kBarrierTimeoutNs) { state = 3; break; }
-        __nanosleep(64);
-      }
-      if (state == 3) {
-        ctrl->status = 4;              // a wait gave up: AD_ERR_TIMEOUT
-        s_flag = 3;
-      } else {
-        __threadfence();
-        my_gen += 1u;
-        s_flag = (*(volatile int*)&ctrl->stop) ? 2 : 0;
-      }
-    }
-    __syncthreads();
-    if (s_flag != 0) break;
-    ++m;
-  }
-  __syncthreads();
-  for (unsigned int k = threadIdx.x; k < nc; k += blockDim.x) p[c0 + k] = sP[k];
-}
-
-// --------------------------------------------------------------------------
 // FP32 storage: fields F[5][n] = Dxx/(2dx^2), Dyy/(2dy^2), Dxy/(8dxdy), ax/(4dx), ay/(4dy).
 __global__ void pack_fields_f32_k(GridDev g, double dx, double dy, const double* Dxx,
                                   const double* Dxy, const double* Dyy, const double* ax,
@@ -686,6 +481,94 @@ __global__ void __launch_bounds__(kBulkThreads) leja_iter_f32_bulk_k(SeriesArgs 
   series_finish(a, accy, accp);
 }
 
+// FP32 fused iteration by register marching (tile_f32_vec.cuh).
+template <bool AUG, int ADV>
+__global__ void __launch_bounds__(kVecThreads, 2) leja_iter_f32_vec_k(SeriesArgs a) {
+  const volatile Ctrl* vc = a.ctrl;
+  if (vc->stop) return;
+  const int m = vc->m;
+  const LejaCoef lc = a.lc[m];
+  const float* __restrict__ yin = static_cast<const float*>(a.y[m & 1]);
+  float* __restrict__ yout = static_cast<float*>(a.y[(m + 1) & 1]);
+  float* __restrict__ p = static_cast<float*>(a.p);
+  const float ig = (float)(1.0 / a.gamma);
+  const float sh = (float)(a.c / a.gamma + lc.xi);
+  const float d = (float)lc.d, e1 = (float)lc.e1, e2 = (float)lc.e2;
+  VGeo G;
+  G.nx = a.g.nx;
+  G.ny = a.g.ny;
+  G.bc = a.g.bc;
+  G.n = a.g.n;
+  G.lane = threadIdx.x & 31;
+  const long long strips = (G.nx + kVecCols - 1) / kVecCols;
+  const long long units = strips * G.ny;
+  const long long warps = (long long)gridDim.x * (kVecThreads / 32);
+  const long long w = (long long)blockIdx.x * (kVecThreads / 32) + (threadIdx.x >> 5);
+  long long u0, u1;
+  vec_range(units, warps, w, u0, u1);
+  float ly = 0.f, lp = 0.f;
+  for (long long u = u0; u < u1;) {
+    const int strip = (int)(u / G.ny);
+    const int r0 = (int)(u - (long long)strip * G.ny);
+    const long long rr = r0 + (u1 - u);
+    const int r1 = (int)(rr < G.ny ? rr : G.ny);
+    G.x = strip * kVecCols + 4 * G.lane;
+    G.active = G.x < G.nx;
+    vec_run<AUG, ADV>(a, G, r0, r1, yin, yout, p, ig, sh, d, e1, e2, ly, lp);
+    u += r1 - r0;
+  }
+  series_finish(a, (double)ly, (double)lp);
+}
+
+// FP32 fused iteration by register marching from per-warp cp.async rings
+// (tile_f32_ring.cuh); one block of 8 warps per SM.
+template <bool AUG, int ADV>
+__global__ void __launch_bounds__(kRingThreads, 1) leja_iter_f32_ring_k(SeriesArgs a) {
+  extern __shared__ __align__(16) float ring_smem[];
+  const volatile Ctrl* vc = a.ctrl;
+  if (vc->stop) return;
+  const int m = vc->m;
+  const LejaCoef lc = a.lc[m];
+  const float* __restrict__ yin = static_cast<const float*>(a.y[m & 1]);
+  float* __restrict__ yout = static_cast<float*>(a.y[(m + 1) & 1]);
+  float* __restrict__ p = static_cast<float*>(a.p);
+  const float ig = (float)(1.0 / a.gamma);
+  const float sh = (float)(a.c / a.gamma + lc.xi);
+  const float d = (float)lc.d, e1 = (float)lc.e1, e2 = (float)lc.e2;
+  using L = RingLayout<AUG, ADV>;
+  float* ring = ring_smem + (size_t)(threadIdx.x >> 5) * L::STAGES * L::SIZE;
+  VGeo G;
+  G.nx = a.g.nx;
+  G.ny = a.g.ny;
+  G.bc = a.g.bc;
+  G.n = a.g.n;
+  G.lane = threadIdx.x & 31;
+  const long long strips = (G.nx + kVecCols - 1) / kVecCols;
+  const long long units = strips * G.ny;
+  const long long warps = (long long)gridDim.x * kRingWarps;
+  const long long w = (long long)blockIdx.x * kRingWarps + (threadIdx.x >> 5);
+  long long u0, u1;
+  vec_range(units, warps, w, u0, u1);
+  float ly = 0.f, lp = 0.f;
+  for (long long u = u0; u < u1;) {
+    const int strip = (int)(u / G.ny);
+    const int r0 = (int)(u - (long long)strip * G.ny);
+    const long long rr = r0 + (u1 - u);
+    const int r1 = (int)(rr < G.ny ? rr : G.ny);
+    G.x = strip * kVecCols + 4 * G.lane;
+    G.active = G.x < G.nx;
+    ring_run<AUG, ADV>(a, G, ring, r0, r1, yin, yout, p, ig, sh, d, e1, e2, ly, lp);
+    u += r1 - r0;
+  }
+  series_finish(a, (double)ly, (double)lp);
+}
+
+template <bool AUG, int ADV>
+size_t ring_smem_bytes() {
+  return sizeof(float) * (size_t)kRingWarps * RingLayout<AUG, ADV>::STAGES *
+         RingLayout<AUG, ADV>::SIZE;
+}
+
 template <bool AUG, int ADV>
 __global__ void __launch_bounds__(kThreads) leja_iter_f32_k(SeriesArgs a) {
   __shared__ float sy[3][kTileCols + 2];
@@ -712,43 +595,6 @@ __global__ void __launch_bounds__(kThreads) leja_iter_f32_k(SeriesArgs a) {
 }
 
 }  // namespace
-
-// Cooperative persistent series (FP64).  Returns false when the grid is too
-// large or the launch is refused (the caller then uses the per-iteration path).
-bool series_run_persistent(const SeriesArgs& a, unsigned int* gen, cudaStream_t s) {
-  if (a.prec != 0 || a.g.n > kPersistMaxCells) return false;
-  const long long n = a.g.n;
-  const int G = (int)std::min<long long>(152, (n + 31) / 32);
-  const unsigned int cpb = (unsigned int)((n + G - 1) / G);
-  int T = 32;
-  while (T < (int)cpb && T < 1024) T <<= 1;
-  const size_t smem = (size_t)cpb * (a.aug ? 11 : 10) * sizeof(double);
-  void* fn = a.aug ? (void*)leja_persistent_f64_k<true> : (void*)leja_persistent_f64_k<false>;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, T, smem) != cudaSuccess ||
-      per_sm < 1) {
-    cudaGetLastError();
-    return false;
-  }
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if ((long long)per_sm * sms < G) return false;
-  SeriesArgs args = a;
-  args.nblocks = G;
-  unsigned int cpb_arg = cpb;
-  void* params[] = {&args, &cpb_arg, &gen};
-  ++launch_counter();
-  if (cudaLaunchCooperativeKernel(fn, dim3(G), dim3(T), params, smem, s) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return true;
-}
 
 // Failure-detection check of the bounded waits: one block waits on an
 // mbarrier whose phase never completes (two arrivals expected, one made) and
@@ -787,14 +633,49 @@ int series_blocks(int prec, long long n) {
   return -1;  // FP32: depends on the tile count, see series_blocks_grid
 }
 
-bool series_use_bulk(int prec, int nx) {
-  static const bool off = getenv("AD_NO_BULK") != nullptr;
-  return prec == 1 && nx % 4 == 0 && !off;
+int series_f32_kernel(int prec, int nx) {
+  if (prec != 1) return 0;
+  static const int pick = [] {
+    const char* e = getenv("AD_F32_KERNEL");     // tuning override: ring | vec | bulk | tile
+    if (!e) return 3;
+    if (e[0] == 'b') return 1;
+    if (e[0] == 't') return 0;
+    if (e[0] == 'v') return 2;
+    return 3;
+  }();
+  return nx % 4 == 0 ? pick : 0;
 }
 
 int series_blocks_grid(int prec, int nx, int ny) {
   if (prec == 0) return series_blocks(0, (long long)nx * ny);
-  if (series_use_bulk(prec, nx)) {
+  const int kind = series_f32_kernel(prec, nx);
+  if (kind == 3) {
+    static bool attr = false;
+    if (!attr) {   // the rings need more than the default 48 KB of dynamic shared memory
+#define AD_RING_ATTR(AUGV, ADVV)                                                         \
+      cudaFuncSetAttribute((void*)leja_iter_f32_ring_k<AUGV, ADVV>,                      \
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,                  \
+                           (int)ring_smem_bytes<AUGV, ADVV>())
+      AD_RING_ATTR(false, 0); AD_RING_ATTR(false, 1); AD_RING_ATTR(false, 2);
+      AD_RING_ATTR(true, 0); AD_RING_ATTR(true, 1); AD_RING_ATTR(true, 2);
+#undef AD_RING_ATTR
+      attr = true;
+    }
+    // one block of 8 warps per SM; fewer for small grids (>= 16 rows per warp)
+    const long long units = (long long)((nx + kVecCols - 1) / kVecCols) * ny;
+    const long long want = (units + kRingWarps * 16 - 1) / (kRingWarps * 16);
+    const long long cap = 152LL;
+    return (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+  }
+  if (kind == 2) {
+    // one warp per contiguous range of >= 16 (strip, row) pairs; 2 blocks of
+    // 256 threads per SM at up to 128 registers
+    const long long units = (long long)((nx + kVecCols - 1) / kVecCols) * ny;
+    const long long want = (units + 8 * 16 - 1) / (8 * 16);
+    const long long cap = 152LL * 2;
+    return (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+  }
+  if (kind == 1) {
     static bool attr = false;
     if (!attr) {   // the ring needs more than the default 48 KB of dynamic shared memory
       const int smem = kBulkStages * kStageFloats * (int)sizeof(float);
@@ -879,7 +760,36 @@ void series_iteration(const SeriesArgs& a, cudaStream_t s) {
       ++launch_counter();
       leja_iter_f64_k<false><<<a.nblocks, kThreads, 0, s>>>(a);
     }
-  } else if (a.bulk) {
+  } else if (a.f32k == 3) {
+    ++launch_counter();
+#define AD_F32R_LAUNCH(AUGV, ADVV)                                                  \
+    leja_iter_f32_ring_k<AUGV, ADVV><<<a.nblocks, kRingThreads,                      \
+                                       ring_smem_bytes<AUGV, ADVV>(), s>>>(a)
+    if (a.aug) {
+      if (a.adv == 0) AD_F32R_LAUNCH(true, 0);
+      else if (a.adv == 1) AD_F32R_LAUNCH(true, 1);
+      else AD_F32R_LAUNCH(true, 2);
+    } else {
+      if (a.adv == 0) AD_F32R_LAUNCH(false, 0);
+      else if (a.adv == 1) AD_F32R_LAUNCH(false, 1);
+      else AD_F32R_LAUNCH(false, 2);
+    }
+#undef AD_F32R_LAUNCH
+  } else if (a.f32k == 2) {
+    ++launch_counter();
+#define AD_F32V_LAUNCH(AUGV, ADVV) \
+    leja_iter_f32_vec_k<AUGV, ADVV><<<a.nblocks, kVecThreads, 0, s>>>(a)
+    if (a.aug) {
+      if (a.adv == 0) AD_F32V_LAUNCH(true, 0);
+      else if (a.adv == 1) AD_F32V_LAUNCH(true, 1);
+      else AD_F32V_LAUNCH(true, 2);
+    } else {
+      if (a.adv == 0) AD_F32V_LAUNCH(false, 0);
+      else if (a.adv == 1) AD_F32V_LAUNCH(false, 1);
+      else AD_F32V_LAUNCH(false, 2);
+    }
+#undef AD_F32V_LAUNCH
+  } else if (a.f32k == 1) {
     // bulk-copy pipeline
     ++launch_counter();
     const size_t smem = (size_t)kBulkStages * kStageFloats * sizeof(float);

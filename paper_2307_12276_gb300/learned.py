@@ -103,28 +103,27 @@ def train_bound_model(X, Y, device, epochs=3000, lr=3e-3, seed=0, hidden=64) -> 
     return m
 
 
-def predict_bounds(m: MLP, feats: np.ndarray, dxs: Sequence[float], device, margin=1.2,
-                   bf16=True):
-    """alpha_s = -margin * exp(t0) D_par / dx^2 and the predicted iterations."""
+def predict_bounds(m: MLP, feats, dxs: Sequence[float], device, margin=1.1, bf16=True):
+    """alpha_s = -margin * exp(t0) D_par / dx^2 and the predicted iterations.
+    ``feats``: (S, 21) float32 array or device tensor."""
     import torch
-    pred = m.predict(torch.as_tensor(np.ascontiguousarray(feats, dtype=np.float32), device=device),
-                     bf16=bf16).cpu().numpy()
-    dpar = np.exp(feats[:, 0].astype(np.float64))
+    X = torch.as_tensor(feats, device=device, dtype=torch.float32).contiguous()
+    pred = m.predict(X, bf16=bf16).double().cpu().numpy()
+    dpar = np.exp(X[:, 0].double().cpu().numpy())
     dx = np.asarray(dxs, dtype=np.float64)
-    alpha = -margin * np.exp(pred[:, 0].astype(np.float64)) * dpar / (dx * dx)
-    return alpha, np.exp(pred[:, 1].astype(np.float64))
+    alpha = -margin * np.exp(pred[:, 0]) * dpar / (dx * dx)
+    return alpha, np.exp(pred[:, 1])
 
 
 def batched_step_with_fallback(batch, ops, us, t, dt, sources, tol, power_iters=40):
-    """One batched midpoint step; each slice whose series did not converge
-    gets a power-iteration bound and repeats its step alone from its saved
-    state.  Returns (per-slice stats, list of fallback slice indices)."""
-    saved = [u.clone() for u in us]
+    """One batched midpoint step.  A slice whose series did not converge keeps
+    its input state (the batched step leaves it untouched); it then gets a
+    power-iteration bound and repeats its step alone.  Returns (per-slice
+    stats, list of fallback slice indices)."""
     st = batch_midpoint_step(batch, us, t, dt, sources, tol=tol, raise_not_converged=False)
     bad = [s for s in range(len(us)) if not st[s]["converged"]]
     for s in bad:
         spectral_bound(ops[s], BOUND_POWER, seed=s + 1, power_iters=power_iters, safety=1.1)
-        us[s].copy_(saved[s])
         st[s] = expquad_step(ops[s], us[s], t, dt, 1, (0.5,),
                              sources[s] if sources is not None else None, tol=tol)
     return st, bad

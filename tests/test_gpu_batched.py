@@ -107,3 +107,36 @@ def test_autotune_cache_round_trip(tmp_path, monkeypatch):
     _, _, b2 = _build(autotune=True)            # served from the cache
     assert ad().batch_info(b2)["tile_rows"] == info1["tile_rows"]
     assert abs(ad().batch_info(b2)["tuned_ms"] - entry["ms"]) < 1e-6
+
+
+def test_unconverged_slice_keeps_its_state():
+    """A slice whose series cannot converge (a NaN in its state makes the norms
+    non-finite) is left exactly as it was, the others advance as usual and the
+    step reports NotConverged."""
+    need_gpu()
+    slices, ops, batch = _build()
+    dt = _dt(slices)
+    bad = 2
+    srcs = [ad().Source([devT(s[3], 1)], None) for s in slices]
+
+    def states():
+        us = [devT(s[4], 1) for s in slices]
+        us[bad][5] = float("nan")
+        return us
+
+    us = states()
+    before = us[bad].clone()
+    with pytest.raises(ad().NotConverged):
+        ad().batch_midpoint_step(batch, us, 0.0, dt, srcs, tol=1e-6)
+    assert torch.equal(us[bad].view(torch.int32), before.view(torch.int32))
+    for k, (g, A, alpha, src, u0) in enumerate(slices):
+        if k == bad:
+            continue
+        ref, _ = integrators.expquad_step(A, u0.ravel(), 0.0, dt, 1, (0.5,),
+                                          lambda t, src=src: src.ravel(), alpha, tol=1e-10)
+        assert rel(us[k].cpu().numpy(), ref) <= 1e-5, (k, SIZES[k])
+    # the same call without raising gives the flag per slice
+    us = states()
+    st = ad().batch_midpoint_step(batch, us, 0.0, dt, srcs, tol=1e-6, raise_not_converged=False)
+    assert [s["converged"] for s in st] == [k != bad for k in range(len(slices))]
+    assert torch.equal(us[bad].view(torch.int32), before.view(torch.int32))
