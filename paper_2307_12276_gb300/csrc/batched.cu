@@ -32,6 +32,7 @@
 #include "anidiff.h"
 #include "leja_host.h"
 #include "tile_f32.cuh"
+#include "tile_f32_ring.cuh"
 
 namespace ad {
 namespace {
@@ -47,7 +48,8 @@ struct BatchSlice {
   int nsrc;
   float dt;
   double d0;
-  int tile_off, ntiles, tiles_x;
+  int tile_off, ntiles, tiles_x;     // 256 x TY tiles (streaming kernels, tile iteration)
+  int rt_off, rt_n, rt_x;            // 128-column x R-row warp tiles (ring iteration)
 };
 
 // Stopping rule of the Newton series (same reading as the single-operator
@@ -230,6 +232,119 @@ __global__ void __launch_bounds__(kThreads) batch_update_k(const BatchSlice* sli
   }
 }
 
+// Fused Leja iteration over the flat list of warp tiles (128 columns x R
+// rows of one slice) with the register-marching kernel of the single-operator
+// FP32 path (tile_f32_ring.cuh): each warp takes tiles gw, gw + GW, ..., skips
+// tiles of slices that have stopped, marches its tile through its cp.async
+// ring and publishes the tile's two norm partials.  The warp that completes
+// a slice's last tile of the launch (ticket) sums that slice's partials in
+// tile order and applies the stopping rule; the launch's last warp keeps the
+// graph loop running while any slice is active.  Requires nx % 4 == 0 for
+// every slice (rows on 16-byte boundaries).
+template <int ADV>
+__global__ void __launch_bounds__(kRingThreads, 1)
+    batch_ring_k(const BatchSlice* slices, const int* rtile_slice, int nrtiles, int nslices,
+                 int R, double* tile_partials, unsigned int* bticket, unsigned long long handle,
+                 int has_handle) {
+  extern __shared__ __align__(16) float ring_smem[];
+  using L = RingLayout<false, ADV>;
+  float* ring = ring_smem + (size_t)(threadIdx.x >> 5) * L::STAGES * L::SIZE;
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kRingWarps + (threadIdx.x >> 5);
+  const int GW = gridDim.x * kRingWarps;
+  for (int tile = gw; tile < nrtiles; tile += GW) {
+    const int s = rtile_slice[tile];
+    const BatchSlice& S = slices[s];
+    const volatile Ctrl* vc = S.a.ctrl;
+    if (vc->stop) continue;                    // uniform over the warp
+    const int m = vc->m;
+    const LejaCoef lc = S.a.lc[m];
+    const float* yin = static_cast<const float*>(S.a.y[m & 1]);
+    float* yout = static_cast<float*>(S.a.y[(m + 1) & 1]);
+    float* p = static_cast<float*>(S.a.p);
+    const float ig = (float)(1.0 / S.a.gamma);
+    const float sh = (float)(S.a.c / S.a.gamma + lc.xi);
+    const int local = tile - S.rt_off;
+    const int x0 = (local % S.rt_x) * kVecCols, y0 = (local / S.rt_x) * R;
+    const int y1 = min(S.a.g.ny, y0 + R);
+    VGeo G;
+    G.nx = S.a.g.nx;
+    G.ny = S.a.g.ny;
+    G.bc = S.a.g.bc;
+    G.n = S.a.g.n;
+    G.lane = lane;
+    G.x = x0 + 4 * lane;
+    G.active = G.x < G.nx;
+    float ly = 0.f, lp = 0.f;
+    ring_run<false, ADV>(S.a, G, ring, y0, y1, yin, yout, p, ig, sh, (float)lc.d, 0.f, 0.f, ly,
+                         lp);
+    double ty = ly, tp = lp;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ty += __shfl_down_sync(0xffffffffu, ty, o);
+      tp += __shfl_down_sync(0xffffffffu, tp, o);
+    }
+    int last = 0;
+    if (lane == 0) {
+      tile_partials[2 * tile] = ty;
+      tile_partials[2 * tile + 1] = tp;
+      __threadfence();
+      const unsigned int k = atomicAdd(&S.a.ctrl->ticket, 1u);
+      last = (k == (unsigned int)S.rt_n - 1u) ? 1 : 0;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {                                // this slice's last tile: decide for it
+      __threadfence();
+      double ay = 0.0, ap = 0.0;
+      for (int q = lane; q < S.rt_n; q += 32) {
+        ay += __ldcg(&tile_partials[2 * (S.rt_off + q)]);
+        ap += __ldcg(&tile_partials[2 * (S.rt_off + q) + 1]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ay += __shfl_down_sync(0xffffffffu, ay, o);
+        ap += __shfl_down_sync(0xffffffffu, ap, o);
+      }
+      if (lane == 0) {
+        Ctrl* ctrl = S.a.ctrl;
+        const int stop = decide(ctrl, lc, m, ay, ap);
+        ctrl->ticket = 0u;
+        ctrl->stop = stop;
+        ctrl->m = m + 1;
+        __threadfence();
+      }
+    }
+  }
+  // the launch's last warp keeps the loop running while any slice is active
+  if (lane == 0) {
+    __threadfence();
+    const unsigned int k = atomicAdd(bticket, 1u);
+    if (k == (unsigned int)GW - 1u) {
+      __threadfence();
+      int active = 0;
+      for (int s = 0; s < nslices; ++s) active |= !*(volatile int*)&slices[s].a.ctrl->stop;
+      *bticket = 0u;
+      __threadfence();
+      if (has_handle)
+        cudaGraphSetConditional((cudaGraphConditionalHandle)handle, active ? 1u : 0u);
+    }
+  }
+}
+
+template <int ADV>
+size_t batch_ring_smem() {
+  return sizeof(float) * (size_t)kRingWarps * RingLayout<false, ADV>::STAGES *
+         RingLayout<false, ADV>::SIZE;
+}
+
+void* pick_ring(int adv) {
+  return adv == 0 ? (void*)batch_ring_k<0> : (adv == 1 ? (void*)batch_ring_k<1> : (void*)batch_ring_k<2>);
+}
+
+size_t ring_smem_for(int adv) {
+  return adv == 0 ? batch_ring_smem<0>() : (adv == 1 ? batch_ring_smem<1>() : batch_ring_smem<2>());
+}
+
 using IterFn = void (*)(const BatchSlice*, const int*, int, int, double*, unsigned int*,
                         unsigned long long, int);
 
@@ -264,6 +379,11 @@ struct ad_batch {
   int TY = 32;
   int nblocks = 608;
   double tuned_ms = 0.0;
+  bool ring = false;                  // warp-tile ring iteration (every nx % 4 == 0)
+  int R = 64;                         // rows per warp tile
+  int* d_rtile_slice = nullptr;
+  int nrtiles = 0;
+  double* d_rpartials = nullptr;
   std::vector<BatchSlice> hs;
   BatchSlice* d_slices = nullptr;
   int* d_tile_slice = nullptr;
@@ -332,6 +452,36 @@ int upload_tiles(ad_batch* b, int TY) {
   return AD_OK;
 }
 
+// Warp-tile table for rows per tile R: slice s owns ring tiles [rt_off, rt_off + rt_n).
+int upload_ring_tiles(ad_batch* b, int R) {
+  std::vector<int> ts;
+  for (int s = 0; s < b->S; ++s) {
+    BatchSlice& hs = b->hs[s];
+    hs.rt_x = (hs.a.g.nx + kVecCols - 1) / kVecCols;
+    hs.rt_n = hs.rt_x * ((hs.a.g.ny + R - 1) / R);
+    hs.rt_off = (int)ts.size();
+    for (int k = 0; k < hs.rt_n; ++k) ts.push_back(s);
+  }
+  if ((int)ts.size() > b->nrtiles || !b->d_rtile_slice) {
+    if (b->d_rtile_slice) cudaFree(b->d_rtile_slice);
+    if (b->d_rpartials) cudaFree(b->d_rpartials);
+    b->d_rtile_slice = nullptr;
+    b->d_rpartials = nullptr;
+    B_CUDA(cudaMalloc(&b->d_rtile_slice, sizeof(int) * ts.size()));
+    B_CUDA(cudaMalloc(&b->d_rpartials, sizeof(double) * 2 * ts.size()));
+  }
+  b->nrtiles = (int)ts.size();
+  b->R = R;
+  B_CUDA(cudaMemcpyAsync(b->d_rtile_slice, ts.data(), sizeof(int) * ts.size(),
+                         cudaMemcpyHostToDevice, b->stream));
+  B_CUDA(cudaMemcpyAsync(b->d_slices, b->hs.data(), sizeof(BatchSlice) * b->S,
+                         cudaMemcpyHostToDevice, b->stream));
+  B_CUDA(cudaStreamSynchronize(b->stream));
+  return AD_OK;
+}
+
+int ring_grid(const ad_batch* b) { return std::max(1, std::min(152, (b->nrtiles + 7) / 8)); }
+
 void destroy_batch_graph(ad_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
@@ -377,14 +527,27 @@ int build_batch_graph(ad_batch* b, int force, double tol) {
   cp.conditional.size = 1;
   B_CUDA(cudaGraphAddNode(&n_cond, g, &n_init, nullptr, 1, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
+  const int* rts = b->d_rtile_slice;
+  int nrt = b->nrtiles, R = b->R;
+  double* rparts = b->d_rpartials;
   {
     void* args[] = {&sl, &ts, &nt, &S, &parts, &bt, &hv, &one};
-    kp.func = (void*)pick_iter(b->adv, TY);
-    kp.kernelParams = args;
+    void* rargs[] = {&sl, &rts, &nrt, &S, &R, &rparts, &bt, &hv, &one};
+    cudaKernelNodeParams ip = kp;
+    if (b->ring) {
+      ip.func = pick_ring(b->adv);
+      ip.kernelParams = rargs;
+      ip.blockDim = dim3(kRingThreads);
+      ip.gridDim = dim3(ring_grid(b));
+      ip.sharedMemBytes = (unsigned)ring_smem_for(b->adv);
+    } else {
+      ip.func = (void*)pick_iter(b->adv, TY);
+      ip.kernelParams = args;
+    }
     cudaGraphNode_t prev = nullptr;
     for (int u = 0; u < kBatchUnroll; ++u) {
       cudaGraphNode_t nn;
-      B_CUDA(cudaGraphAddKernelNode(&nn, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+      B_CUDA(cudaGraphAddKernelNode(&nn, body, prev ? &prev : nullptr, prev ? 1 : 0, &ip));
       prev = nn;
     }
   }
@@ -454,11 +617,49 @@ void write_cache(const std::map<std::string, TuneEntry>& m) {
 std::string tune_key(const ad_batch* b) {
   std::map<std::pair<int, int>, int> sizes;
   for (const auto& s : b->hs) sizes[{s.a.g.nx, s.a.g.ny}]++;
-  std::string k = "f32-adv" + std::to_string(b->adv) + "-S" + std::to_string(b->S);
+  std::string k = std::string(b->ring ? "ring" : "tile") + "-f32-adv" + std::to_string(b->adv) +
+                  "-S" + std::to_string(b->S);
   for (const auto& kv : sizes)
     k += "-" + std::to_string(kv.first.first) + "x" + std::to_string(kv.first.second) + "*" +
          std::to_string(kv.second);
   return k;
+}
+
+// Time `reps` forced iterations of the ring kernel for R rows per warp tile.
+int time_ring(ad_batch* b, int R, int reps, double* ms_out) {
+  {
+    const int r = upload_ring_tiles(b, R);
+    if (r != AD_OK) return r;
+  }
+  int force = reps, maxit = kMaxIters;
+  double tol = 0.0;
+  const int sgrid = std::min(b->ntiles, b->nblocks);
+  batch_init_k<<<sgrid, kThreads, 0, b->stream>>>(b->d_slices, b->d_tile_slice, b->ntiles, b->TY,
+                                                  b->S, force, maxit, tol, b->d_bticket);
+  void* fn = pick_ring(b->adv);
+  const size_t smem = ring_smem_for(b->adv);
+  const int grid = ring_grid(b);
+  cudaEvent_t e0, e1;
+  B_CUDA(cudaEventCreate(&e0));
+  B_CUDA(cudaEventCreate(&e1));
+  B_CUDA(cudaEventRecord(e0, b->stream));
+  const BatchSlice* sl = b->d_slices;
+  const int* rts = b->d_rtile_slice;
+  int nrt = b->nrtiles, S = b->S, zero = 0;
+  double* rparts = b->d_rpartials;
+  unsigned int* bt = b->d_bticket;
+  unsigned long long hv = 0ULL;
+  void* args[] = {&sl, &rts, &nrt, &S, &R, &rparts, &bt, &hv, &zero};
+  for (int r = 0; r < reps; ++r)
+    B_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(kRingThreads), args, smem, b->stream));
+  B_CUDA(cudaEventRecord(e1, b->stream));
+  B_CUDA(cudaStreamSynchronize(b->stream));
+  float ms = 0.f;
+  B_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = ms / reps;
+  return AD_OK;
 }
 
 // Time `reps` forced iterations of the batched kernel for one (TY, blocks).
@@ -555,6 +756,25 @@ int ad_create_batch(ad_operator* const* ops, int nslices, int autotune, ad_batch
   b->lc_dt.assign(nslices, -1.0);
   b->lc_alpha.assign(nslices, 0.0);
   b->h_ctrl.resize(nslices);
+  // iteration kernel: warp-tile rings when every slice's rows are 16-byte aligned
+  {
+    static const bool tile_only = [] {
+      const char* e = getenv("AD_BATCH_KERNEL");         // tuning override: ring | tile
+      return e && e[0] == 't';
+    }();
+    bool aligned = true;
+    for (const auto& hs : b->hs) aligned = aligned && hs.a.g.nx % 4 == 0;
+    b->ring = aligned && !tile_only;
+    if (b->ring) {
+      static bool attr = false;
+      if (!attr) {
+        for (int adv = 0; adv < 3; ++adv)
+          cudaFuncSetAttribute(pick_ring(adv), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)ring_smem_for(adv));
+        attr = true;
+      }
+    }
+  }
   // tile shape: cached autotune result, a fresh autotune, or the default
   int TY = 32, bps = 4;
   double tuned = 0.0;
@@ -565,6 +785,31 @@ int ad_create_batch(ad_operator* const* ops, int nslices, int autotune, ad_batch
     TY = it->second.ty;
     bps = it->second.bps;
     tuned = it->second.ms;
+  } else if (autotune && b->ring) {
+    // streaming kernels keep 256 x 32 tiles; tune the rows per warp tile
+    {
+      const int r = upload_tiles(b, 32);
+      if (r != AD_OK) {
+        std::string msg = ad_last_error();
+        ad_destroy_batch(b);
+        return bfail(r, msg);
+      }
+    }
+    double best = 1e30;
+    for (int rr : {16, 32, 64, 128}) {
+      double ms = 0.0;
+      const int r = time_ring(b, rr, 6, &ms);
+      if (r != AD_OK) {
+        std::string msg = ad_last_error();
+        ad_destroy_batch(b);
+        return bfail(r, msg);
+      }
+      if (ms < best) { best = ms; TY = rr; }
+    }
+    bps = 1;
+    tuned = best;
+    cache[key] = TuneEntry{TY, bps, best};
+    write_cache(cache);
   } else if (autotune) {
     double best = 1e30;
     for (int ty : {8, 16, 32, 64})
@@ -582,9 +827,16 @@ int ad_create_batch(ad_operator* const* ops, int nslices, int autotune, ad_batch
     cache[key] = TuneEntry{TY, bps, best};
     write_cache(cache);
   }
-  b->nblocks = 152 * bps;
   b->tuned_ms = tuned;
-  const int r = upload_tiles(b, TY);
+  int r;
+  if (b->ring) {
+    b->nblocks = 152 * 4;                 // streaming kernels: 4 blocks of 256 per SM
+    r = upload_tiles(b, 32);
+    if (r == AD_OK) r = upload_ring_tiles(b, TY);
+  } else {
+    b->nblocks = 152 * bps;
+    r = upload_tiles(b, TY);
+  }
   if (r != AD_OK) {
     std::string msg = ad_last_error();
     ad_destroy_batch(b);
@@ -599,7 +851,8 @@ int ad_destroy_batch(ad_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   destroy_batch_graph(b);
   for (void* p : {(void*)b->d_slices, (void*)b->d_tile_slice, (void*)b->d_partials, (void*)b->d_lc,
-                  (void*)b->d_ctrl, (void*)b->d_bticket})
+                  (void*)b->d_ctrl, (void*)b->d_bticket, (void*)b->d_rtile_slice,
+                  (void*)b->d_rpartials})
     if (p) cudaFree(p);
   delete b;
   return AD_OK;
@@ -607,9 +860,9 @@ int ad_destroy_batch(ad_batch* b) {
 
 int ad_batch_info(const ad_batch* b, int* tile_rows, int* blocks, int* ntiles, double* tuned_ms) {
   if (!b) return bfail(AD_ERR_INVALID, "NULL batch");
-  if (tile_rows) *tile_rows = b->TY;
-  if (blocks) *blocks = std::min(b->ntiles, b->nblocks);
-  if (ntiles) *ntiles = b->ntiles;
+  if (tile_rows) *tile_rows = b->ring ? b->R : b->TY;
+  if (blocks) *blocks = b->ring ? ring_grid(b) : std::min(b->ntiles, b->nblocks);
+  if (ntiles) *ntiles = b->ring ? b->nrtiles : b->ntiles;
   if (tuned_ms) *tuned_ms = b->tuned_ms;
   return AD_OK;
 }

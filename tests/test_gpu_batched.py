@@ -22,6 +22,8 @@ from workloads.fields import BC_DIRICHLET0, SeparableSource
 pytestmark = pytest.mark.gpu
 
 SIZES = [(40, 33), (64, 64), (300, 70), (17, 23), (256, 256), (513, 40)]
+# every nx % 4 == 0: the batch runs the warp-tile ring iteration kernel
+SIZES_RING = [(40, 33), (64, 64), (300, 70), (4, 9), (256, 256), (516, 40), (128, 1)]
 
 
 def _slice(nx, ny, dpar):
@@ -34,9 +36,9 @@ def _slice(nx, ny, dpar):
     return g, Dxx, Dxy, Dyy, src, u0
 
 
-def _build(autotune=False):
+def _build(autotune=False, sizes=None):
     slices, ops = [], []
-    for k, (nx, ny) in enumerate(SIZES):
+    for k, (nx, ny) in enumerate(sizes or SIZES):
         g, Dxx, Dxy, Dyy, src, u0 = _slice(nx, ny, 1.0 + 3.0 * k)
         A = oop.assemble(g, Dxx, Dxy, Dyy, 0.05, 0.0)
         alpha = spectral.gershgorin(A)
@@ -103,7 +105,7 @@ def test_autotune_cache_round_trip(tmp_path, monkeypatch):
     data = json.loads(cache.read_text())
     assert len(data) == 1
     entry = next(iter(data.values()))
-    assert entry["ty"] == info1["tile_rows"] and entry["ty"] in (8, 16, 32, 64)
+    assert entry["ty"] == info1["tile_rows"] and entry["ty"] in (8, 16, 32, 64, 128)
     _, _, b2 = _build(autotune=True)            # served from the cache
     assert ad().batch_info(b2)["tile_rows"] == info1["tile_rows"]
     assert abs(ad().batch_info(b2)["tuned_ms"] - entry["ms"]) < 1e-6
@@ -140,3 +142,39 @@ def test_unconverged_slice_keeps_its_state():
     st = ad().batch_midpoint_step(batch, us, 0.0, dt, srcs, tol=1e-6, raise_not_converged=False)
     assert [s["converged"] for s in st] == [k != bad for k in range(len(slices))]
     assert torch.equal(us[bad].view(torch.int32), before.view(torch.int32))
+
+
+@pytest.mark.parametrize("force", [1, 17])
+def test_ring_batch_forced_matches_oracle(force):
+    """All slices 16-byte aligned: the warp-tile ring kernel runs the iterations."""
+    need_gpu()
+    slices, ops, batch = _build(sizes=SIZES_RING)
+    dt = _dt(slices)
+    us = [devT(s[4], 1) for s in slices]
+    srcs = [ad().Source([devT(s[3], 1)], None) for s in slices]
+    st = ad().batch_midpoint_step(batch, us, 0.0, dt, srcs, force_iters=force)
+    for k, (g, A, alpha, src, u0) in enumerate(slices):
+        ref, _ = integrators.expquad_step(A, u0.ravel(), 0.0, dt, 1, (0.5,),
+                                          lambda t, src=src: src.ravel(), alpha,
+                                          force_iters=force)
+        assert st[k]["iters"] == force
+        assert rel(us[k].cpu().numpy(), ref) <= 1e-5, (k, SIZES_RING[k])
+
+
+def test_ring_batch_adaptive_and_tuned(tmp_path, monkeypatch):
+    need_gpu()
+    monkeypatch.setenv("AD_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    slices, ops, batch = _build(autotune=True, sizes=SIZES_RING)
+    info = ad().batch_info(batch)
+    assert info["tile_rows"] in (16, 32, 64, 128)
+    dt = _dt(slices)
+    us = [devT(s[4], 1) for s in slices]
+    srcs = [ad().Source([devT(s[3], 1)], None) for s in slices]
+    st = ad().batch_midpoint_step(batch, us, 0.0, dt, srcs, tol=1e-6)
+    for k, (g, A, alpha, src, u0) in enumerate(slices):
+        ref, _ = integrators.expquad_step(A, u0.ravel(), 0.0, dt, 1, (0.5,),
+                                          lambda t, src=src: src.ravel(), alpha, tol=1e-10)
+        _, ost6 = integrators.expquad_step(A, u0.ravel(), 0.0, dt, 1, (0.5,),
+                                           lambda t, src=src: src.ravel(), alpha, tol=1e-6)
+        assert abs(st[k]["iters"] - ost6.iters) <= 2, (k, st[k]["iters"], ost6.iters)
+        assert rel(us[k].cpu().numpy(), ref) <= 1e-5, (k, SIZES_RING[k])
