@@ -68,8 +68,8 @@ def parse():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--form-steps", type=int, default=5)
     ap.add_argument("--learned-fields", type=int, default=1000)
-    ap.add_argument("--forms", default="fp32,cn,batched,learned",
-                    help="comma list of extra forms to measure: fp32, cn, batched, learned")
+    ap.add_argument("--forms", default="fp32,cn,paper,batched,learned",
+                    help="comma list of extra forms to measure: fp32, cn, batched, learned, paper")
     return ap.parse_args()
 
 
@@ -347,6 +347,85 @@ def measure_cn_vs_exp(ad, dev, stream, T_cfl=1000.0):
             "matvec_ratio_cn_over_exp": round(best["matvecs"] / mv_e, 2)}
 
 
+def measure_paper_cases(ad, dev, stream, nx=128):
+    """The paper's work-precision experiments (Section 3, Figs. 3-5) on this
+    implementation: error against a reference vs matrix-vector products (the
+    paper's cost measure) and GPU time.  Cases I (ring) and II (spiral 2 with
+    advection and time-independent sources): one exponential step of the
+    whole interval T at tolerances 1e-2 .. 1e-10, against Crank-Nicolson with
+    N steps.  Cases III and IV (spirals with time-dependent sources):
+    exponential midpoint and two-stage Gauss quadrature with N steps (tol
+    1e-10) against CN.  References: the exponential step at tol 1e-13 (I, II),
+    Gauss with 64 steps at tol 1e-12 (III, IV).  FP64, Gershgorin bounds."""
+    import numpy as np
+    import torch
+    from workloads.configs import paper_case
+    gauss = (0.5 - 0.5 / 3 ** 0.5, 0.5 + 0.5 / 3 ** 0.5)
+    out = {}
+    for case in ("I", "II", "III", "IV"):
+        p = paper_case(case, nx)
+        g = p.grid
+        T_end = p.dt
+        Tt = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(),
+                                       device=dev)
+        op = ad.create_operator(g.nx, g.ny, g.bc, Tt(p.Dxx), Tt(p.Dxy), Tt(p.Dyy), p.ax, p.ay,
+                                ad.FP64, stream=stream)
+        src = ad.Source([Tt(gk) for gk in p.source.g], list(p.source.h)) if len(p.source) else None
+
+        def run(method, nsteps, tol):
+            dt = T_end / nsteps
+            u = Tt(p.u0)
+            mv, ok = 0, True
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            try:
+                for k in range(nsteps):
+                    if method == "cn":
+                        st = ad.cn_step(op, u, k * dt, dt, src, gmres_tol=1e-10, restart=50)
+                    elif method == "gauss":
+                        st = ad.expquad_step(op, u, k * dt, dt, 2, gauss, src, tol=tol)
+                    else:
+                        st = ad.expquad_step(op, u, k * dt, dt, 1, (0.5,), src, tol=tol)
+                    mv += st["matvecs"]
+            except ad.AdError:
+                ok = False
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return u, e0.elapsed_time(e1), mv, ok
+
+        points = []
+        if case in ("I", "II"):
+            ref, _, _, _ = run("midpoint", 1, 1e-13)
+            nref = float(torch.linalg.norm(ref))
+            for tol in (1e-2, 1e-4, 1e-6, 1e-8, 1e-10):
+                u, ms, mv, ok = run("midpoint", 1, tol)
+                points.append({"method": "exp", "steps": 1, "tol": tol, "matvecs": mv,
+                               "ms": round(ms, 3), "converged": ok,
+                               "err": float(torch.linalg.norm(u - ref)) / nref})
+            for nsteps in (8, 32, 128):
+                u, ms, mv, ok = run("cn", nsteps, 0.0)
+                points.append({"method": "cn", "steps": nsteps, "matvecs": mv, "ms": round(ms, 3),
+                               "converged": ok, "err": float(torch.linalg.norm(u - ref)) / nref})
+        else:
+            ref, _, _, _ = run("gauss", 64, 1e-12)
+            nref = float(torch.linalg.norm(ref))
+            for method in ("midpoint", "gauss"):
+                for nsteps in (1, 2, 4, 8, 16):
+                    u, ms, mv, ok = run(method, nsteps, 1e-10)
+                    points.append({"method": method, "steps": nsteps, "matvecs": mv,
+                                   "ms": round(ms, 3), "converged": ok,
+                                   "err": float(torch.linalg.norm(u - ref)) / nref})
+            for nsteps in (8, 32, 128):
+                u, ms, mv, ok = run("cn", nsteps, 0.0)
+                points.append({"method": "cn", "steps": nsteps, "matvecs": mv, "ms": round(ms, 3),
+                               "converged": ok, "err": float(torch.linalg.norm(u - ref)) / nref})
+        out[case] = {"workload": p.name, "T": T_end, "T_over_cfl": round(T_end / p.cfl, 1),
+                     "points": points}
+        op.close()
+    return out
+
+
 def _slice_operators(ad, dev, stream, nslices, sides):
     """The momentum-slice batch: per slice a side drawn from ``sides`` (seed 3),
     D_par = p^0.5 for p log-spaced in [1, 1e4], D_perp = 1e-3 D_par, circular
@@ -617,6 +696,8 @@ def run_ours(args):
         forms["fp32_4096sq"] = measure_fp32_form(ad, dev, stream, flush, args.form_steps)
     if "cn" in wanted:
         forms["cn_vs_exp"] = measure_cn_vs_exp(ad, dev, stream)
+    if "paper" in wanted:
+        forms["paper_cases"] = measure_paper_cases(ad, dev, stream)
     if "batched" in wanted:
         forms["batched"] = measure_batched_form(
             ad, dev, stream, args.form_steps,

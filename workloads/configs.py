@@ -172,3 +172,38 @@ def small_problem(nx: int, ny: int, bc: int, kind: str = "stream", seed: int = 7
     return Problem(f"small-{nx}x{ny}-{kind}-bc{bc}", g, Dxx, Dxy, Dyy, ax=adv[0], ay=adv[1],
                    ax_field=axf, ay_field=ayf, source=src, u0=u0, dt=dt_factor * cfl,
                    steps=1, s=s, c=tuple(c), tol=tol, cfl=cfl)
+
+
+def paper_case(case: str, nx: int = 128) -> Problem:
+    """The paper's own test problems (Section 3) on [-1,1]^2, zero Dirichlet.
+
+    case "I":   diffusion along rings (Eq. B_ring), no advection, no source, T = 0.75
+    case "II":  spiral 2 (Eq. B_spiral), a = (1, 1), time-independent sources (Eq. TIS), T = 0.85
+    case "III": spiral 1 (Eq. B_spiral), a = (1, 1), time-dependent sources (Eq. TDS), T = 0.10
+    case "IV":  spiral 2 (Eq. B_spiral), a = (1, 2), time-dependent sources (Eq. TDS), T = 0.10
+
+    The paper gives neither the grid, the boundary condition nor the initial
+    field; the readings are an nx^2 grid, zero Dirichlet, and a Gaussian of
+    sigma 0.1 centred on the field lines at (0, 0.6).  ``dt`` holds the final
+    time T and ``cfl`` the explicit step bound.
+    """
+    from .fields import D_ring, D_spiral1, D_spiral2, tds_source, tis_source
+    g = Grid(nx, nx, BC_DIRICHLET0)
+    X, Y = cell_centres(g)
+    if case == "I":
+        Dxx, Dxy, Dyy = D_ring(X, Y)
+        ax, ay, src, T = 0.0, 0.0, SeparableSource(), 0.75
+    elif case == "II":
+        Dxx, Dxy, Dyy = D_spiral2(X, Y)
+        ax, ay, src, T = 1.0, 1.0, tis_source(X, Y), 0.85
+    elif case == "III":
+        Dxx, Dxy, Dyy = D_spiral1(X, Y)
+        ax, ay, src, T = 1.0, 1.0, tds_source(X, Y), 0.10
+    elif case == "IV":
+        Dxx, Dxy, Dyy = D_spiral2(X, Y)
+        ax, ay, src, T = 1.0, 2.0, tds_source(X, Y), 0.10
+    else:
+        raise ValueError(f"unknown case {case!r}")
+    u0 = gaussian(X, Y, 0.0, 0.6, 0.1)
+    return Problem(f"paper-{case}-{nx}sq", g, Dxx, Dxy, Dyy, ax=ax, ay=ay, source=src, u0=u0,
+                   dt=T, steps=1, cfl=cfl_dt(g, Dxx, Dxy, Dyy))
