@@ -230,6 +230,7 @@ def traffic_per_launch(files, summary: str):
 F64_SERIES_SOURCES = ("persistent_f64.cu", "ad_internal.h")
 F32_ITER_SOURCES = ("stencil_kernels.cu", "tile_f32.cuh", "tile_f32_vec.cuh", "tile_f32_ring.cuh",
                     "ad_internal.h")
+F32_PAIR_SOURCES = F32_ITER_SOURCES + ("tile_f32_pair.cuh",)
 
 
 # --------------------------------------------------------------------------- ours
@@ -264,14 +265,24 @@ def measure_fp32_form(ad, dev, stream, flush, steps):
         ms += e0.elapsed_time(e1)
         iters.append(st["iters"])
         t += p.dt
-    ms_launch = ad.profile_leja_iteration(op, aug=0, reps=100)
-    alg_bytes = 28.0 * g.n      # 3 fields + y + p r/w + y_next, 4 B each
-    gbs = alg_bytes / (ms_launch * 1e-3) / 1e9
+    ms_iter = ad.profile_leja_iteration(op, aug=0, reps=100)
     kind = os.environ.get("AD_F32_KERNEL", "ring")[:1]
     kernel = {"b": "leja_iter_f32_bulk_k", "t": "leja_iter_f32_k",
               "v": "leja_iter_f32_vec_k"}.get(kind, "leja_iter_f32_ring_k")
-    traffic = (traffic_per_launch(F32_ITER_SOURCES, "leja_iter_f32_ring_4096sq.md")
-               if kernel == "leja_iter_f32_ring_k" else None)
+    pair = kernel == "leja_iter_f32_ring_k" and os.environ.get("AD_F32_PAIR", "1")[:1] != "0"
+    # one launch: y, p read and written, 3 coefficient fields read, 4 B each;
+    # the two-iteration kernel does this once for two iterations
+    iters_per_launch = 2 if pair else 1
+    ms_launch = ms_iter * iters_per_launch
+    alg_bytes = 28.0 * g.n
+    gbs = alg_bytes / (ms_launch * 1e-3) / 1e9
+    if pair:
+        kernel = "leja_iter2_f32_ring_k"
+        traffic = traffic_per_launch(F32_PAIR_SOURCES, "leja_iter2_f32_ring_4096sq.md")
+    elif kernel == "leja_iter_f32_ring_k":
+        traffic = traffic_per_launch(F32_ITER_SOURCES, "leja_iter_f32_ring_4096sq.md")
+    else:
+        traffic = None
     op.close()
     del u, src
     torch.cuda.empty_cache()
@@ -279,7 +290,8 @@ def measure_fp32_form(ad, dev, stream, flush, steps):
             "value": round(g.n * steps / (ms * 1e-3) / 1e6, 2), "unit": "Mcell-steps/s",
             "ms_per_step": round(ms / steps, 4), "leja_iters_per_step": statistics.mean(iters),
             "tol": p.tol, "dtype": "f32 storage/arithmetic, f64 Leja scalars and norm sums",
-            "roofline": {"bound": "hbm", "kernel": f"{kernel}<0,0>", "ms_per_launch":
+            "roofline": {"bound": "hbm", "kernel": kernel + ("<0>" if pair else "<0,0>"),
+                         "iterations_per_launch": iters_per_launch, "ms_per_launch":
                          round(ms_launch, 5), "achieved": round(gbs, 1), "peak": HBM_PEAK_GBS,
                          "unit": "GB/s", "frac": round(gbs / HBM_PEAK_GBS, 4),
                          "traffic": traffic, "alg_bytes_per_launch": alg_bytes,

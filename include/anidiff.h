@@ -243,8 +243,11 @@ AD_API int ad_field_features(const ad_grid* grid, const double* Dxx, const doubl
  * iteration kernel alone.  Runs a forced series of `reps` iterations (aug =
  * 0: phi_1 form, 1: augmented form) on the operator's stream and returns the
  * mean device time of one iteration in *ms_per_launch: on the persistent FP64
- * path (one cooperative launch per series) the launch time / reps, otherwise
- * the mean of CUDA event pairs around each iteration kernel.  Overwrites the
+ * path (one cooperative launch per series) the launch time / reps; on the
+ * FP32 two-iteration kernel (phi_1 form, nx % 4 == 0, ny >= 2, no varying
+ * advection) the mean of CUDA event pairs around each launch / 2 (an odd
+ * reps runs one more iteration); otherwise the mean of CUDA event pairs
+ * around each iteration kernel.  Overwrites the
  * operator's series workspace; results of earlier calls are unaffected.
  * 1 <= reps <= 500. */
 AD_API int ad_profile_leja_iteration(ad_operator* op, int aug, int reps, double* ms_per_launch);
@@ -259,7 +262,8 @@ AD_API int ad_profile_leja_iteration(ad_operator* op, int aug, int reps, double*
  * and their total Leja iterations, and (kernel may be NULL) the path of the
  * last timed series: 1 persistent kernel with a grid barrier per iteration,
  * 2 persistent kernel with neighbour synchronisation, 3 graph loop of
- * per-iteration kernels, 4 host-driven per-iteration launches, 0 none yet.
+ * per-iteration kernels, 4 host-driven per-iteration launches, 5 and 6 the
+ * same with the FP32 two-iteration kernel, 0 none yet.
  * Recording adds two event records and no synchronisation (each series
  * already ends with one). */
 AD_API int ad_time_series(ad_operator* op, int enable);

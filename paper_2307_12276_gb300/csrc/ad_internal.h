@@ -107,6 +107,11 @@ void series_init(const SeriesArgs& a, const void* src, double d0, int force, int
 // finish reduces the norm partials in a fixed order, applies the stopping rule,
 // advances ctrl->m and, with a.has_handle, sets the graph loop condition.
 void series_iteration(const SeriesArgs& a, cudaStream_t s);
+// FP32 phi_1 series on the ring kernel run two iterations per launch
+// (series_iteration then launches leja_iter2_f32_ring_k); after such a
+// series, series_flush_pair adds the pending last term to p.
+bool series_pair(const SeriesArgs& a);
+void series_flush_pair(const SeriesArgs& a, cudaStream_t s);
 // Whole Newton series in one cooperative launch (FP64, n <= kPersistMaxCells).
 // gen: device barrier generation counter (persists across calls).  Returns
 // false if not applicable or refused; nothing was launched then.

@@ -384,6 +384,7 @@ int run_series(ad_operator* op, int aug, const void* src, double d0, int force, 
         if (op->h_ctrl->stop || launched >= kMaxIters + chunk) break;
       }
     }
+    if (!persist && series_pair(a)) series_flush_pair(a, op->stream);   // the pending last term
     CUDA_TRY(cudaGetLastError());
     if (op->time_series) CUDA_TRY(cudaEventRecord(op->tev[1], op->stream));
     CUDA_TRY(cudaMemcpyAsync(op->h_ctrl, op->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, op->stream));
@@ -395,7 +396,7 @@ int run_series(ad_operator* op, int aug, const void* src, double d0, int force, 
       op->t_ms += ms;
       op->t_series += 1;
       op->t_iters += iters;
-      op->t_path = persist ? pk : (graph_used ? 3 : 4);
+      op->t_path = persist ? pk : (graph_used ? 3 : 4) + (series_pair(a) ? 2 : 0);
     }
     if (!op->h_ctrl->stop) return fail(AD_ERR_TIMEOUT, "Leja series did not reach its stop state");
     {  // the device stores |d_{m+1}| and the squared norms; form the estimate here
@@ -403,9 +404,9 @@ int run_series(ad_operator* op, int aug, const void* src, double d0, int force, 
       op->h_ctrl->err_est = h.pnorm2 > 0.0 ? h.err_est * std::sqrt(h.ynorm2 / h.pnorm2)
                                            : (h.ynorm2 > 0.0 ? INFINITY : 0.0);
     }
-    // graph bodies: one fused iteration kernel per iteration (host launches
-    // are counted by the launchers themselves)
-    if (st && graph_used) st->kernel_launches += iters;
+    // graph bodies: one fused iteration kernel per iteration, or per two in
+    // pair mode (host launches are counted by the launchers themselves)
+    if (st && graph_used) st->kernel_launches += series_pair(a) ? (iters + 1) / 2 : iters;
     if (op->h_ctrl->status == 4) return fail(AD_ERR_TIMEOUT, "a grid barrier wait gave up");
   }
   if (st) {
@@ -1030,9 +1031,12 @@ int ad_profile_leja_iteration(ad_operator* op, int aug, int reps, double* ms_per
     }
     series_init(a, op->W1, d0, reps, op->max_iters, 0.0, op->stream);
   }
-  std::vector<cudaEvent_t> ev(2 * reps);
+  // pair mode: each launch runs two iterations
+  const int per = series_pair(a) ? 2 : 1;
+  const int launches = (reps + per - 1) / per;
+  std::vector<cudaEvent_t> ev(2 * launches);
   for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
-  for (int r = 0; r < reps; ++r) {
+  for (int r = 0; r < launches; ++r) {
     CUDA_TRY(cudaEventRecord(ev[2 * r], op->stream));
     series_iteration(a, op->stream);
     CUDA_TRY(cudaEventRecord(ev[2 * r + 1], op->stream));
@@ -1040,14 +1044,14 @@ int ad_profile_leja_iteration(ad_operator* op, int aug, int reps, double* ms_per
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(op->stream));
   double total = 0.0;
-  for (int r = 0; r < reps; ++r) {
+  for (int r = 0; r < launches; ++r) {
     float ms = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]));
     total += ms;
   }
   for (auto& e : ev) cudaEventDestroy(e);
   op->cache_kind = -1;
-  *ms_per_launch = total / reps;
+  *ms_per_launch = total / ((double)launches * per);
   return AD_OK;
 }
 

@@ -25,6 +25,7 @@
 #include "tile_f32_bulk.cuh"
 #include "tile_f32_vec.cuh"
 #include "tile_f32_ring.cuh"
+#include "tile_f32_pair.cuh"
 
 namespace ad {
 
@@ -85,6 +86,86 @@ __device__ void series_finish(const SeriesArgs& a, double sy, double sp) {
     __threadfence();
     if (a.has_handle)
       cudaGraphSetConditional((cudaGraphConditionalHandle)a.handle, stop ? 0u : 1u);
+  }
+}
+
+// Epilogue of a pair launch (two iterations, m and m + 1, m even): publish the
+// block's four norm partials; the last block sums them in block order and
+// applies the stopping rule after term m + 1, then after term m + 2.  A stop
+// after term m + 1 leaves the stored p complete (ctrl->m becomes m + 1, odd);
+// otherwise ctrl->m becomes m + 2 and d_{m+2} y_{m+2} is pending (added by the
+// next pair launch, or by pair_flush_k after the series).
+__device__ void series_finish2(const SeriesArgs& a, double y1, double p1, double y2, double p2) {
+  __shared__ unsigned int s_last;
+  block_sum2(y1, p1);
+  const double by1 = y1, bp1 = p1;
+  block_sum2(y2, p2);
+  Ctrl* ctrl = a.ctrl;
+  if (threadIdx.x == 0) {
+    double* q = a.partials + 4 * blockIdx.x;
+    q[0] = by1;
+    q[1] = bp1;
+    q[2] = y2;
+    q[3] = p2;
+    __threadfence();
+    const unsigned int t = atomicAdd(&ctrl->ticket, 1u);
+    s_last = (t == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double t1y = 0.0, t1p = 0.0, t2y = 0.0, t2p = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    t1y += __ldcg(&a.partials[4 * b]);
+    t1p += __ldcg(&a.partials[4 * b + 1]);
+    t2y += __ldcg(&a.partials[4 * b + 2]);
+    t2p += __ldcg(&a.partials[4 * b + 3]);
+  }
+  block_sum2(t1y, t1p);
+  block_sum2(t2y, t2p);
+  if (threadIdx.x == 0) {
+    const int m = ctrl->m;
+    const double tol = ctrl->tol;
+    int status = ctrl->status;
+    // the rule of series_finish, applied after `terms` terms
+    auto stop_after = [&](int terms, double absd, double ty, double tp) -> bool {
+      bool stop = false;
+      if (ctrl->force > 0) {
+        stop = terms >= ctrl->force;
+      } else if (!(ty == ty) || !(tp == tp)) {
+        stop = true;
+        status = 3;
+      } else if (terms >= 2 && (absd * absd) * ty <= (tol * tol) * tp) {
+        stop = true;
+      } else if (terms >= ctrl->max_iters) {
+        stop = true;
+        status = 3;
+      }
+      return stop || terms >= kMaxIters;
+    };
+    const LejaCoef& L1 = a.lc[m];
+    if (stop_after(m + 1, L1.absd, t1y, t1p)) {
+      ctrl->ynorm2 = t1y;
+      ctrl->pnorm2 = t1p;
+      ctrl->iters = m + 1;
+      ctrl->err_est = L1.absd;
+      ctrl->m = m + 1;
+      ctrl->stop = 1;
+    } else {
+      const LejaCoef& L2 = a.lc[m + 1];
+      const bool stop = stop_after(m + 2, L2.absd, t2y, t2p);
+      ctrl->ynorm2 = t2y;
+      ctrl->pnorm2 = t2p;
+      ctrl->iters = m + 2;
+      ctrl->err_est = L2.absd;
+      ctrl->m = m + 2;
+      ctrl->stop = stop ? 1 : 0;
+    }
+    ctrl->status = status;
+    ctrl->ticket = 0u;
+    __threadfence();
+    if (a.has_handle)
+      cudaGraphSetConditional((cudaGraphConditionalHandle)a.handle, ctrl->stop ? 0u : 1u);
   }
 }
 
@@ -563,6 +644,67 @@ __global__ void __launch_bounds__(kRingThreads, 1) leja_iter_f32_ring_k(SeriesAr
   series_finish(a, (double)ly, (double)lp);
 }
 
+// Two fused FP32 iterations per launch by register marching over overlapped
+// 120-column strips fed by per-warp cp.async rings (tile_f32_pair.cuh); one
+// block of 8 warps per SM.
+template <int ADV>
+__global__ void __launch_bounds__(kRingThreads, 1) leja_iter2_f32_ring_k(SeriesArgs a) {
+  extern __shared__ __align__(16) float pair_smem[];
+  const volatile Ctrl* vc = a.ctrl;
+  if (vc->stop) return;
+  const int m = vc->m;                                 // even in pair mode
+  const LejaCoef lc1 = a.lc[m], lc2 = a.lc[m + 1];
+  const float d0 = m > 0 ? (float)a.lc[m - 1].d : 0.0f; // pending d_m y_m
+  const float* __restrict__ yin = static_cast<const float*>(a.y[(m >> 1) & 1]);
+  float* __restrict__ yout = static_cast<float*>(a.y[((m >> 1) + 1) & 1]);
+  float* __restrict__ p = static_cast<float*>(a.p);
+  const float ig = (float)(1.0 / a.gamma);
+  const float sh1 = (float)(a.c / a.gamma + lc1.xi), sh2 = (float)(a.c / a.gamma + lc2.xi);
+  const float d1 = (float)lc1.d, d2 = (float)lc2.d;
+  constexpr int per_warp = PairLayout::STAGES * PairLayout::SIZE;
+  float* ring = pair_smem + (size_t)(threadIdx.x >> 5) * per_warp;
+  VGeo G;
+  G.nx = a.g.nx;
+  G.ny = a.g.ny;
+  G.bc = a.g.bc;
+  G.n = a.g.n;
+  G.lane = threadIdx.x & 31;
+  const long long strips = (G.nx + kPairOwn - 1) / kPairOwn;
+  const long long units = strips * G.ny;
+  const long long warps = (long long)gridDim.x * kRingWarps;
+  const long long w = (long long)blockIdx.x * kRingWarps + (threadIdx.x >> 5);
+  long long u0, u1;
+  vec_range(units, warps, w, u0, u1);
+  float ly1 = 0.f, lp1 = 0.f, ly2 = 0.f, lp2 = 0.f;
+  for (long long u = u0; u < u1;) {
+    const int strip = (int)(u / G.ny);
+    const int r0 = (int)(u - (long long)strip * G.ny);
+    const long long rr = r0 + (u1 - u);
+    const int r1 = (int)(rr < G.ny ? rr : G.ny);
+    pair_run<ADV>(a, G, ring, strip * kPairOwn, r0, r1, yin, yout, p, ig, sh1, sh2, d1, d2, d0,
+                  ly1, lp1, ly2, lp2);
+    u += r1 - r0;
+  }
+  series_finish2(a, (double)ly1, (double)lp1, (double)ly2, (double)lp2);
+}
+
+size_t pair_smem_bytes() {
+  return sizeof(float) * (size_t)kRingWarps * PairLayout::STAGES * PairLayout::SIZE;
+}
+
+// After a pair-mode series: add the pending d_m y_m when it stopped after an
+// even count m (y_m in buffer (m / 2) & 1).
+__global__ void pair_flush_k(SeriesArgs a) {
+  const int m = a.ctrl->m;
+  if (m == 0 || (m & 1)) return;
+  const float d = (float)a.lc[m - 1].d;
+  const float* y = static_cast<const float*>(a.y[(m >> 1) & 1]);
+  float* p = static_cast<float*>(a.p);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.g.n;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] = fmaf(d, y[i], p[i]);
+}
+
 template <bool AUG, int ADV>
 size_t ring_smem_bytes() {
   return sizeof(float) * (size_t)kRingWarps * RingLayout<AUG, ADV>::STAGES *
@@ -659,6 +801,10 @@ int series_blocks_grid(int prec, int nx, int ny) {
       AD_RING_ATTR(false, 0); AD_RING_ATTR(false, 1); AD_RING_ATTR(false, 2);
       AD_RING_ATTR(true, 0); AD_RING_ATTR(true, 1); AD_RING_ATTR(true, 2);
 #undef AD_RING_ATTR
+      cudaFuncSetAttribute((void*)leja_iter2_f32_ring_k<0>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem_bytes());
+      cudaFuncSetAttribute((void*)leja_iter2_f32_ring_k<1>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem_bytes());
       attr = true;
     }
     // one block of 8 warps per SM; fewer for small grids (>= 16 rows per warp)
@@ -760,6 +906,10 @@ void series_iteration(const SeriesArgs& a, cudaStream_t s) {
       ++launch_counter();
       leja_iter_f64_k<false><<<a.nblocks, kThreads, 0, s>>>(a);
     }
+  } else if (series_pair(a)) {
+    ++launch_counter();
+    if (a.adv == 0) leja_iter2_f32_ring_k<0><<<a.nblocks, kRingThreads, pair_smem_bytes(), s>>>(a);
+    else leja_iter2_f32_ring_k<1><<<a.nblocks, kRingThreads, pair_smem_bytes(), s>>>(a);
   } else if (a.f32k == 3) {
     ++launch_counter();
 #define AD_F32R_LAUNCH(AUGV, ADVV)                                                  \
@@ -819,6 +969,19 @@ void series_iteration(const SeriesArgs& a, cudaStream_t s) {
     }
 #undef AD_F32_LAUNCH
   }
+}
+
+bool series_pair(const SeriesArgs& a) {
+  static const bool off = [] {
+    const char* e = getenv("AD_F32_PAIR");        // tuning override: 0 = one iteration per launch
+    return e && e[0] == '0';
+  }();
+  return !off && a.prec == 1 && a.f32k == 3 && !a.aug && a.adv != 2 && a.g.ny >= 2;
+}
+
+void series_flush_pair(const SeriesArgs& a, cudaStream_t s) {
+  ++launch_counter();
+  pair_flush_k<<<stream_blocks(a.g.n), kThreads, 0, s>>>(a);
 }
 
 // shifted operator for GMRES: out = s0 u + s1 A u (+ sources)

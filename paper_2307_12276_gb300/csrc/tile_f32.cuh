@@ -14,6 +14,13 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// One face flux of the flux form, a du + q dd, with its rounding fixed: every
+// FP32 kernel forms it the same way, so kernels that evaluate the stencil in
+// different code (one and two iterations per pass) agree bit for bit.
+__device__ __forceinline__ float face_flux(float a, float du, float q, float dd) {
+  return fmaf(a, du, q * dd);
+}
+
 // Deterministic block sum of two values; result valid in thread 0.  Lanes of
 // warp 0 add eight values each, then one butterfly: far fewer FP64 additions
 // than a butterfly in every warp (FP64 is the scarce pipe on this GPU).
@@ -110,10 +117,10 @@ __device__ __forceinline__ float flux_apply_f32(const float* __restrict__ F, lon
   }
   const float uC = U[1][1], uE = U[1][2], uW = U[1][0], uN = U[2][1], uS = U[0][1];
   const float uNE = U[2][2], uNW = U[2][0], uSE = U[0][2], uSW = U[0][0];
-  float fe = axe * (uE - uC) + qe * ((uNE + uN) - (uSE + uS));
-  float fw = axw * (uC - uW) + qw * ((uN + uNW) - (uS + uSW));
-  float fn = ayn * (uN - uC) + qn * ((uNE + uE) - (uNW + uW));
-  float fs = ays * (uC - uS) + qs * ((uE + uSE) - (uW + uSW));
+  float fe = face_flux(axe, uE - uC, qe, (uNE + uN) - (uSE + uS));
+  float fw = face_flux(axw, uC - uW, qw, (uN + uNW) - (uS + uSW));
+  float fn = face_flux(ayn, uN - uC, qn, (uNE + uE) - (uNW + uW));
+  float fs = face_flux(ays, uC - uS, qs, (uE + uSE) - (uW + uSW));
   if (adv != 0) {
     fe = fmaf(be, uC + uE, fe);
     fw = fmaf(bw, uW + uC, fw);
@@ -279,10 +286,10 @@ __device__ __forceinline__ void tile_f32(const SeriesArgs& a, const LejaCoef& lc
       const float qe = dxy_c + sxy[j & 1][t + 2], qw = sxy[j & 1][t] + dxy_c;
       const float qn = dxy_c + sxy[(j + 1) & 1][t + 1], qs = dxy_s + dxy_c;
       const float ayn_ = dyy_c + dyyn, ays = dyy_s + dyy_c;
-      float fe = axe * (uE - uC) + qe * ((uNE + uN) - (uSE + uS));
-      float fw = axw * (uC - uW) + qw * ((uN + uNW) - (uS + uSW));
-      float fn = ayn_ * (uN - uC) + qn * ((uNE + uE) - (uNW + uW));
-      float fs = ays * (uC - uS) + qs * ((uE + uSE) - (uW + uSW));
+      float fe = face_flux(axe, uE - uC, qe, (uNE + uN) - (uSE + uS));
+      float fw = face_flux(axw, uC - uW, qw, (uN + uNW) - (uS + uSW));
+      float fn = face_flux(ayn_, uN - uC, qn, (uNE + uE) - (uNW + uW));
+      float fs = face_flux(ays, uC - uS, qs, (uE + uSE) - (uW + uSW));
       if (ADV == 1) {
         fe = fmaf(a.abx, uC + uE, fe);
         fw = fmaf(a.abx, uW + uC, fw);

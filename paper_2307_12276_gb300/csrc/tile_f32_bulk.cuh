@@ -230,10 +230,10 @@ __device__ void bulk_consumer(const SeriesArgs& a, const LejaCoef& lc, float* yo
         const float qn = xyC + Sp[kOffXY + c], qs = Sm[kOffXY + c] + xyC;
         const float yyC = S0[kOffYY + t];
         const float ayn = yyC + Sp[kOffYY + t], ays = Sm[kOffYY + t] + yyC;
-        float fe = axe * (uE - uC) + qe * ((uNE + uN) - (uSE + uS));
-        float fw = axw * (uC - uW) + qw * ((uN + uNW) - (uS + uSW));
-        float fn = ayn * (uN - uC) + qn * ((uNE + uE) - (uNW + uW));
-        float fs = ays * (uC - uS) + qs * ((uE + uSE) - (uW + uSW));
+        float fe = face_flux(axe, uE - uC, qe, (uNE + uN) - (uSE + uS));
+        float fw = face_flux(axw, uC - uW, qw, (uN + uNW) - (uS + uSW));
+        float fn = face_flux(ayn, uN - uC, qn, (uNE + uE) - (uNW + uW));
+        float fs = face_flux(ays, uC - uS, qs, (uE + uSE) - (uW + uSW));
         if (ADV == 1) {
           fe = fmaf(a.abx, uC + uE, fe);
           fw = fmaf(a.abx, uW + uC, fw);

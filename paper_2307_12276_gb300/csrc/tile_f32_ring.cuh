@@ -200,7 +200,7 @@ __device__ __forceinline__ void ring_run(const SeriesArgs& a, const VGeo& G, flo
       const int Lc = f, Rc = f + 1;
       const float axf = C.xx[Lc] + C.xx[Rc];
       const float qf = B.xy[Lc] + B.xy[Rc];
-      float v = axf * (B.y[Rc] - B.y[Lc]) + qf * ((N.y[Rc] + N.y[Lc]) - (A.y[Rc] + A.y[Lc]));
+      float v = face_flux(axf, B.y[Rc] - B.y[Lc], qf, (N.y[Rc] + N.y[Lc]) - (A.y[Rc] + A.y[Lc]));
       if (ADV == 1) v = fmaf(a.abx, B.y[Lc] + B.y[Rc], v);
       if (ADV == 2) v = fmaf(C.ax[Lc] + C.ax[Rc], B.y[Lc] + B.y[Rc], v);
       fx[f] = v;

@@ -136,7 +136,7 @@ __device__ __forceinline__ void vnorth(float* fn, const VRow<ADV>& B, const VRow
     const int c = k + 1;
     const float ayn = B.yy[k] + N.yy[k];
     const float qn = B.xy[c] + N.xy[c];
-    float f = ayn * (N.y[c] - B.y[c]) + qn * ((N.y[c + 1] + B.y[c + 1]) - (N.y[c - 1] + B.y[c - 1]));
+    float f = face_flux(ayn, N.y[c] - B.y[c], qn, (N.y[c + 1] + B.y[c + 1]) - (N.y[c - 1] + B.y[c - 1]));
     if (ADV == 1) f = fmaf(aby, B.y[c] + N.y[c], f);
     if (ADV == 2) f = fmaf(B.ay[k] + N.ay[k], B.y[c] + N.y[c], f);
     fn[k] = f;
@@ -178,7 +178,7 @@ __device__ __forceinline__ void vec_run(const SeriesArgs& a, const VGeo& G, int 
       const int L = f, R = f + 1;
       const float axf = C.xx[L] + C.xx[R];
       const float qf = B.xy[L] + B.xy[R];
-      float v = axf * (B.y[R] - B.y[L]) + qf * ((N.y[R] + N.y[L]) - (A.y[R] + A.y[L]));
+      float v = face_flux(axf, B.y[R] - B.y[L], qf, (N.y[R] + N.y[L]) - (A.y[R] + A.y[L]));
       if (ADV == 1) v = fmaf(a.abx, B.y[L] + B.y[R], v);
       if (ADV == 2) v = fmaf(C.ax[L] + C.ax[R], B.y[L] + B.y[R], v);
       fx[f] = v;
