@@ -654,36 +654,45 @@ __global__ void __launch_bounds__(kRingThreads, 1) leja_iter2_f32_ring_k(SeriesA
   if (vc->stop) return;
   const int m = vc->m;                                 // even in pair mode
   const LejaCoef lc1 = a.lc[m], lc2 = a.lc[m + 1];
-  const float d0 = m > 0 ? (float)a.lc[m - 1].d : 0.0f; // pending d_m y_m
-  const float* __restrict__ yin = static_cast<const float*>(a.y[(m >> 1) & 1]);
-  float* __restrict__ yout = static_cast<float*>(a.y[((m >> 1) + 1) & 1]);
-  float* __restrict__ p = static_cast<float*>(a.p);
-  const float ig = (float)(1.0 / a.gamma);
-  const float sh1 = (float)(a.c / a.gamma + lc1.xi), sh2 = (float)(a.c / a.gamma + lc2.xi);
-  const float d1 = (float)lc1.d, d2 = (float)lc2.d;
-  constexpr int per_warp = PairLayout::STAGES * PairLayout::SIZE;
-  float* ring = pair_smem + (size_t)(threadIdx.x >> 5) * per_warp;
-  VGeo G;
-  G.nx = a.g.nx;
-  G.ny = a.g.ny;
-  G.bc = a.g.bc;
-  G.n = a.g.n;
-  G.lane = threadIdx.x & 31;
-  const long long strips = (G.nx + kPairOwn - 1) / kPairOwn;
-  const long long units = strips * G.ny;
+  PairCtx X;
+  X.a = &a;
+  X.yin = static_cast<const float*>(a.y[(m >> 1) & 1]);
+  X.yout = static_cast<float*>(a.y[((m >> 1) + 1) & 1]);
+  X.p = static_cast<float*>(a.p);
+  X.ring = pair_smem + (size_t)(threadIdx.x >> 5) * PairLayout::STAGES * PairLayout::SIZE;
+  X.G.nx = a.g.nx;
+  X.G.ny = a.g.ny;
+  X.G.bc = a.g.bc;
+  X.G.n = a.g.n;
+  X.G.lane = threadIdx.x & 31;
+  X.ig = (float)(1.0 / a.gamma);
+  X.sh1 = (float)(a.c / a.gamma + lc1.xi);
+  X.sh2 = (float)(a.c / a.gamma + lc2.xi);
+  X.d0 = m > 0 ? (float)a.lc[m - 1].d : 0.0f;          // pending d_m y_m
+  X.d1 = (float)lc1.d;
+  X.d2 = (float)lc2.d;
+  X.abx = a.abx;
+  X.aby = a.aby;
+  // bands of rows, one per warp of each strip (at least 8 rows each)
+  const int strips = (X.G.nx + kPairOwn - 1) / kPairOwn;
   const long long warps = (long long)gridDim.x * kRingWarps;
+  long long bands = warps / strips;
+  if (bands > X.G.ny / 8) bands = X.G.ny / 8;
+  if (bands < 1) bands = 1;
+  const long long units = bands * strips;
   const long long w = (long long)blockIdx.x * kRingWarps + (threadIdx.x >> 5);
   long long u0, u1;
   vec_range(units, warps, w, u0, u1);
   float ly1 = 0.f, lp1 = 0.f, ly2 = 0.f, lp2 = 0.f;
-  for (long long u = u0; u < u1;) {
-    const int strip = (int)(u / G.ny);
-    const int r0 = (int)(u - (long long)strip * G.ny);
-    const long long rr = r0 + (u1 - u);
-    const int r1 = (int)(rr < G.ny ? rr : G.ny);
-    pair_run<ADV>(a, G, ring, strip * kPairOwn, r0, r1, yin, yout, p, ig, sh1, sh2, d1, d2, d0,
-                  ly1, lp1, ly2, lp2);
-    u += r1 - r0;
+  for (long long u = u0; u < u1; ++u) {
+    const long long b = u / strips;
+    const int X0 = (int)(u - b * strips) * kPairOwn;
+    X.y0 = (int)(X.G.ny * b / bands);
+    X.y1 = (int)(X.G.ny * (b + 1) / bands);
+    X.L = pair_lane(X0, X.G.lane, X.G.nx, X.G.bc);
+    X.gx = X0 - 4 + 4 * X.G.lane;
+    X.fix = X.G.bc != 0 && (X0 == 0 || X0 + kPairOwn >= X.G.nx);
+    pair_run<ADV>(X, ly1, lp1, ly2, lp2);
   }
   series_finish2(a, (double)ly1, (double)lp1, (double)ly2, (double)lp2);
 }

@@ -14,16 +14,23 @@
 //
 // Marching down rows, the warp computes at step j level 1 on row j + 1 (from
 // rows j .. j + 2 of y_m) and level 2 on row j (from rows j - 1 .. j + 1 of
-// y_{m+1}, held in registers).  Rows come through a per-warp ring of
-// cp.async records: a record is refilled with the row S ahead as soon as it
-// has been read into registers, so S - 1 rows stay in flight.
+// y_{m+1}, held in registers; three row slots rotate, with no copies).  Rows
+// come through a per-warp ring of cp.async records: a record is refilled with
+// the row S ahead as soon as it has been read into registers, so S - 1 rows
+// stay in flight.
 //
-// Ghost values.  A group outside [0, nx) is copied from its wrapped source
-// (periodic) or from its mirror group (zero Dirichlet: read back reversed,
-// values negated).  y_{m+1} must obey the boundary condition of every vector
-// the operator acts on, so with zero Dirichlet its ghost column and ghost
-// rows are set to the odd reflection of the computed values; with the
-// periodic wrap they are computed like any other cell.
+// Ghost values.  With the periodic wrap a group outside [0, nx) is copied
+// from its wrapped source and computed like any other.  With zero Dirichlet
+// it is not read: the lanes at columns 0 and nx - 1 mirror their own values
+// into the missing x-neighbour (negated for y), and y_{m+1}, which must obey
+// the boundary condition of every vector the operator acts on, gets its
+// ghost column and ghost rows as the odd reflection of the computed values.
+//
+// Work split: the rows are cut into bands, one per warp of each strip, and a
+// warp takes a band of one strip (band-major order), so the warps of
+// neighbouring strips march the same rows at the same time and the sectors
+// both read at a strip edge come from L2 the second time.  Each band re-reads
+// four halo rows (two above, two below).
 //
 // Traffic per cell and pass: y_m, p, Dxx, Dxy, Dyy read, y_{m+2} and p
 // written (28 bytes for two iterations), plus 8 of every 128 columns of the
@@ -50,86 +57,113 @@ struct PairLayout {                  // one row record, floats (lane l at 4 l)
 
 struct PairLane {
   int src;       // first column of the copied source group
-  bool load;     // the group is needed: -4 <= gx <= nx
-  bool rev;      // zero-Dirichlet ghost group: the mirror group, reversed on read
-  float csg;     // sign of values in the group (-1 for a zero-Dirichlet ghost group)
+  bool load;     // the lane copies its group (periodic: the wrapped one)
   bool own;      // lanes 1 .. 30 inside the domain: produce y_{m+2} and p
+  bool west;     // zero Dirichlet: the group starts at column 0
+  bool east;     // zero Dirichlet: the group ends at column nx - 1
 };
 
 __device__ __forceinline__ PairLane pair_lane(int X0, int lane, int nx, int bc) {
   PairLane L;
   const int gx = X0 - 4 + 4 * lane;
-  L.load = gx >= -4 && gx <= nx;
-  L.rev = false;
-  L.csg = 1.0f;
-  L.src = gx;
-  if (gx < 0) {
-    if (bc == 0) L.src = gx + nx;
-    else { L.src = 0; L.rev = true; L.csg = -1.0f; }
-  } else if (gx >= nx) {
-    if (bc == 0) L.src = gx - nx;
-    else { L.src = nx - 4; L.rev = true; L.csg = -1.0f; }
+  if (bc == 0) {
+    L.load = gx >= -4 && gx <= nx;
+    L.src = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+  } else {                     // ghost groups are not read: their values are mirrored
+    L.load = gx >= 0 && gx < nx;
+    L.src = gx;
   }
   L.own = lane >= 1 && lane <= 30 && gx < nx;
+  L.west = bc != 0 && gx == 0;
+  L.east = bc != 0 && gx + 4 == nx;
   return L;
 }
 
-struct PRow {          // one row of y_m and its Dxy, Dyy around the lane's group
-  float y[6];          // columns gx - 1 .. gx + 4, signs applied
+struct PRow {          // one row around the lane's group, columns gx - 1 .. gx + 4
+  float y[6];          // y_m (Dirichlet ghost signs applied)
   float xy[6];
+  float xx[6];         // rows level 1 computes
   float yy[4];
+  float p[4];          // p_m; after level 1 on an own row, p_{m+1}
 };
 
-struct PCen {          // the row level 1 computes: Dxx (with x-neighbours) and p
-  float xx[6];
-  float4 p;
+struct PairCtx {       // per-run constants
+  const SeriesArgs* a;
+  const float* yin;
+  float* yout;
+  float* p;
+  float* ring;
+  VGeo G;
+  PairLane L;
+  int gx, y0, y1;
+  bool fix;            // zero Dirichlet and the strip reaches column 0 or nx - 1
+  float ig, sh1, sh2, d0, d1, d2, abx, aby;
 };
 
-__device__ __forceinline__ float4 pair_ld4(const float* s, const PairLane& L) {
-  float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (L.load) q = *reinterpret_cast<const float4*>(s);
-  if (L.rev) q = make_float4(q.w, q.z, q.y, q.x);
-  return q;
-}
-
-__device__ __forceinline__ void pair_spread(float* v, float4 q, float s) {
-  v[1] = s * q.x; v[2] = s * q.y; v[3] = s * q.z; v[4] = s * q.w;
+// x-neighbours from the adjacent lanes; zero Dirichlet mirrors at the domain
+// edge (sgn -1 for values, +1 for coefficients).
+__device__ __forceinline__ void pair_spread(float* v, float4 q, const PairCtx& X, float sgn) {
+  v[1] = q.x; v[2] = q.y; v[3] = q.z; v[4] = q.w;
   v[0] = __shfl_up_sync(0xffffffffu, v[4], 1);
   v[5] = __shfl_down_sync(0xffffffffu, v[1], 1);
-}
-
-// Copies of row r into record S: y, Dxy, Dyy always; Dxx for the rows level 1
-// computes; p for own rows on own lanes.
-__device__ __forceinline__ void pair_issue(float* S, const SeriesArgs& a, const VGeo& G,
-                                           const PairLane& L, const float* __restrict__ yin,
-                                           int r, bool want_xx, bool want_p) {
-  using PL = PairLayout;
-  if (!L.load) return;
-  const long long n = G.n;
-  const float* F = static_cast<const float*>(a.coef);
-  const long long off = map_row(r, G.nx, G.ny, G.bc).off + L.src;
-  const int c = 4 * G.lane;
-  cp_async16(S + PL::Y + c, yin + off);
-  cp_async16(S + PL::XY + c, F + 2 * n + off);
-  cp_async16(S + PL::YY + c, F + n + off);
-  if (want_xx) cp_async16(S + PL::XX + c, F + off);
-  if (want_p && L.own) cp_async16(S + PL::P + c, static_cast<const float*>(a.p) + off);
-}
-
-__device__ __forceinline__ void pair_read(PRow& R, PCen* C, const float* S, const VGeo& G,
-                                          const PairLane& L, int r) {
-  using PL = PairLayout;
-  const int c = 4 * G.lane;
-  const float rsg = (G.bc != 0 && (r < 0 || r >= G.ny)) ? -1.0f : 1.0f;
-  pair_spread(R.y, pair_ld4(S + PL::Y + c, L), rsg * L.csg);
-  pair_spread(R.xy, pair_ld4(S + PL::XY + c, L), 1.0f);
-  const float4 b = pair_ld4(S + PL::YY + c, L);
-  R.yy[0] = b.x; R.yy[1] = b.y; R.yy[2] = b.z; R.yy[3] = b.w;
-  if (C) {
-    pair_spread(C->xx, pair_ld4(S + PL::XX + c, L), 1.0f);
-    C->p = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (L.own) C->p = *reinterpret_cast<const float4*>(S + PL::P + c);
+  if (X.fix) {
+    if (X.L.west) v[0] = sgn * v[1];
+    if (X.L.east) v[5] = sgn * v[4];
   }
+}
+
+__device__ __forceinline__ float* pair_slot(const PairCtx& X, int r) {
+  return X.ring + (size_t)((r - (X.y0 - 2)) % PairLayout::STAGES) * PairLayout::SIZE;
+}
+
+// Copies of row r (rows y0 - 2 .. y1 + 1; one commit group per row, empty past
+// the end): y, Dxy, Dyy always; Dxx for the rows level 1 computes; p for own
+// rows on own lanes.
+__device__ __forceinline__ void pair_issue(const PairCtx& X, int r) {
+  using PL = PairLayout;
+  if (r <= X.y1 + 1 && X.L.load) {
+    float* S = pair_slot(X, r);
+    const long long n = X.G.n;
+    const float* F = static_cast<const float*>(X.a->coef);
+    const long long off = map_row(r, X.G.nx, X.G.ny, X.G.bc).off + X.L.src;
+    const int c = 4 * X.G.lane;
+    cp_async16(S + PL::Y + c, X.yin + off);
+    cp_async16(S + PL::XY + c, F + 2 * n + off);
+    cp_async16(S + PL::YY + c, F + n + off);
+    if (r >= X.y0 - 1 && r <= X.y1) cp_async16(S + PL::XX + c, F + off);
+    if (r >= X.y0 && r < X.y1 && X.L.own)
+      cp_async16(S + PL::P + c, static_cast<const float*>(X.a->p) + off);
+  }
+  cp_async_commit();
+}
+
+// Read row r into registers, then refill its record with row r + S.  Row r is
+// the oldest pending group: the S - 1 younger ones stay in flight.
+__device__ __forceinline__ void pair_consume(const PairCtx& X, int r, PRow& R) {
+  using PL = PairLayout;
+  cp_async_wait_group<PL::STAGES - 1>();
+  __syncwarp();
+  const float* S = pair_slot(X, r);
+  const int c = 4 * X.G.lane;
+  const bool ld = X.L.load;
+  float4 y4 = make_float4(0.f, 0.f, 0.f, 0.f), q4 = y4, b4 = y4, x4 = y4, p4 = y4;
+  if (ld) {
+    y4 = *reinterpret_cast<const float4*>(S + PL::Y + c);
+    q4 = *reinterpret_cast<const float4*>(S + PL::XY + c);
+    b4 = *reinterpret_cast<const float4*>(S + PL::YY + c);
+    x4 = *reinterpret_cast<const float4*>(S + PL::XX + c);
+    p4 = *reinterpret_cast<const float4*>(S + PL::P + c);
+  }
+  if (X.G.bc != 0 && (r < 0 || r >= X.G.ny)) {       // zero Dirichlet ghost row
+    y4.x = -y4.x; y4.y = -y4.y; y4.z = -y4.z; y4.w = -y4.w;
+  }
+  pair_spread(R.y, y4, X, -1.0f);
+  pair_spread(R.xy, q4, X, 1.0f);
+  pair_spread(R.xx, x4, X, 1.0f);
+  R.yy[0] = b4.x; R.yy[1] = b4.y; R.yy[2] = b4.z; R.yy[3] = b4.w;
+  R.p[0] = p4.x; R.p[1] = p4.y; R.p[2] = p4.z; R.p[3] = p4.w;
+  __syncwarp();
+  pair_issue(X, r + PL::STAGES);
 }
 
 // North-face fluxes of row B towards row N (the expressions of vnorth).
@@ -149,15 +183,16 @@ __device__ __forceinline__ void pair_north(const float* uB, const float* uN, con
 }
 
 // The fused stencil on row B of one level (rows A, B, N of its input vector
-// u): the north fluxes fn of row B, and z = (A u - c u) / gamma - xi u on the
-// lane's four columns, with the south fluxes fs carried from the row above.
-// The x-face and north-face fluxes of ring_run, term for term.
+// u): z = (A u - c u) / gamma - xi u on the lane's four columns, with the
+// south fluxes fs of row B; on return fs holds the north fluxes of row B
+// (the south fluxes of the next row).  The x-face and north-face fluxes of
+// ring_run, term for term.
 template <int ADV>
 __device__ __forceinline__ void pair_level(const float* uA, const float* uB, const float* uN,
                                            const float* xx, const float* xyB, const float* xyN,
                                            const float* yyB, const float* yyN, float abx,
-                                           float aby, const float* fs, float* fn, float ig,
-                                           float sh, float* z) {
+                                           float aby, float* fs, float ig, float sh, float* z) {
+  float fn[4];
   pair_north<ADV>(uB, uN, xyB, xyN, yyB, yyN, aby, fn);
   float fx[5];
 #pragma unroll
@@ -173,136 +208,112 @@ __device__ __forceinline__ void pair_level(const float* uA, const float* uB, con
   for (int k = 0; k < 4; ++k) {
     const float au = (fx[k + 1] - fx[k]) + (fn[k] - fs[k]);
     z[k] = fmaf(au, ig, -sh * uB[k + 1]);
+    fs[k] = fn[k];
   }
 }
 
 // A row of y_{m+1} from the level-1 values z of the lane's group: with zero
-// Dirichlet, column -1 (in a left ghost group) and column nx (in a right
-// one) become the odd reflection of their mirror; then the x-neighbours.
-__device__ __forceinline__ void pair_y1(float* u, const float* z, bool fix, int gx, int nx) {
+// Dirichlet, column -1 (in the group left of column 0) and column nx (in the
+// group right of nx - 1) become the odd reflection of their mirror; then the
+// x-neighbours.
+__device__ __forceinline__ void pair_y1(float* u, const float* z, const PairCtx& X) {
   u[1] = z[0]; u[2] = z[1]; u[3] = z[2]; u[4] = z[3];
-  if (fix) {                                   // warp-uniform: the strip has a ghost group
+  if (X.fix) {
     const float right_of = __shfl_down_sync(0xffffffffu, z[0], 1);
     const float left_of = __shfl_up_sync(0xffffffffu, z[3], 1);
-    if (gx < 0) u[4] = -right_of;              // column -1 = -(column 0)
-    if (gx == nx) u[1] = -left_of;             // column nx = -(column nx - 1)
+    if (X.gx == -4) u[4] = -right_of;          // column -1 = -(column 0)
+    if (X.gx == X.G.nx) u[1] = -left_of;       // column nx = -(column nx - 1)
   }
   u[0] = __shfl_up_sync(0xffffffffu, u[4], 1);
   u[5] = __shfl_down_sync(0xffffffffu, u[1], 1);
 }
 
-// One marching run of rows [y0, y1) of the strip that starts at column X0.
+// Level 1 on row r (A, B, N: rows r - 1 .. r + 1 of y_m) into u1; on an own
+// row also p_{m+1} = p_m + d_m y_m + d_{m+1} y_{m+1} (stored, and kept in B.p
+// for level 2) and the level-1 norm terms.
 template <int ADV>
-__device__ __forceinline__ void pair_run(const SeriesArgs& a, const VGeo& G, float* ring, int X0,
-                                         int y0, int y1, const float* __restrict__ yin,
-                                         float* __restrict__ yout, float* __restrict__ p,
-                                         float ig, float sh1, float sh2, float d1, float d2,
-                                         float d0, float& ly1, float& lp1, float& ly2,
+__device__ __forceinline__ void pair_level1(const PairCtx& X, int r, const PRow& A, PRow& B,
+                                            const PRow& N, float* fs1, float* u1, float& ly1,
+                                            float& lp1) {
+  float z[4];
+  pair_level<ADV>(A.y, B.y, N.y, B.xx, B.xy, N.xy, B.yy, N.yy, X.abx, X.aby, fs1, X.ig, X.sh1, z);
+  pair_y1(u1, z, X);
+  if (X.L.own && r >= X.y0 && r < X.y1) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float pm = fmaf(X.d0, B.y[k + 1], B.p[k]);   // the pending d_m y_m
+      B.p[k] = fmaf(X.d1, z[k], pm);
+      ly1 = fmaf(z[k], z[k], ly1);
+      lp1 = fmaf(B.p[k], B.p[k], lp1);
+    }
+    const long long idx = (long long)r * X.G.nx + X.gx;
+    *reinterpret_cast<float4*>(X.p + idx) = make_float4(B.p[0], B.p[1], B.p[2], B.p[3]);
+  }
+}
+
+// Step j: level 1 on row j + 1 and level 2 on row j.  On entry A, B hold rows
+// j, j + 1 (B.p: p_m of row j + 1; A.p: p_{m+1} of row j) and Ua, Ub the
+// y_{m+1} rows j - 1, j; N and Un are free.  The next step's roles are
+// (B, N, A) and (Ub, Un, Ua).
+template <int ADV>
+__device__ __forceinline__ void pair_step(const PairCtx& X, int j, PRow& A, PRow& B, PRow& N,
+                                          const float* Ua, const float* Ub, float* Un,
+                                          float* fs1, float* fs2, float& ly1, float& lp1,
+                                          float& ly2, float& lp2) {
+  pair_consume(X, j + 2, N);
+  pair_level1<ADV>(X, j + 1, A, B, N, fs1, Un, ly1, lp1);
+  if (X.G.bc != 0 && j + 1 == X.G.ny) {     // y_{m+1} row ny = -(row ny - 1)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Un[k] = -Ub[k];
+  }
+  // level 2 on row j: coefficient rows j (A) and j + 1 (B)
+  float z[4];
+  pair_level<ADV>(Ua, Ub, Un, A.xx, A.xy, B.xy, A.yy, B.yy, X.abx, X.aby, fs2, X.ig, X.sh2, z);
+  if (X.L.own) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float p2 = fmaf(X.d2, z[k], A.p[k]);
+      ly2 = fmaf(z[k], z[k], ly2);
+      lp2 = fmaf(p2, p2, lp2);
+    }
+    const long long idx = (long long)j * X.G.nx + X.gx;
+    *reinterpret_cast<float4*>(X.yout + idx) = make_float4(z[0], z[1], z[2], z[3]);
+  }
+}
+
+// One marching run of rows [y0, y1) (X.y0, X.y1) of the strip of X.
+template <int ADV>
+__device__ __forceinline__ void pair_run(const PairCtx& X, float& ly1, float& lp1, float& ly2,
                                          float& lp2) {
-  using PL = PairLayout;
-  constexpr int S = PL::STAGES;
-  const PairLane L = pair_lane(X0, G.lane, G.nx, G.bc);
-  const int gx = X0 - 4 + 4 * G.lane;
-  const bool dir = G.bc != 0;
-  const bool fix = dir && (X0 == 0 || X0 + kPairOwn >= G.nx);
-  const float abx = a.abx, aby = a.aby;
-  auto slot = [&](int r) { return ring + (size_t)((r - (y0 - 2)) % S) * PL::SIZE; };
-  auto issue = [&](int r) {            // rows y0 - 2 .. y1 + 1; one commit group each
-    if (r <= y1 + 1)
-      pair_issue(slot(r), a, G, L, yin, r, r >= y0 - 1 && r <= y1, r >= y0 && r < y1);
-    cp_async_commit();
-  };
-  // Read row r into registers, then refill its record with row r + S.  Row r
-  // is the oldest pending group: the S - 1 younger ones stay in flight.
-  auto consume = [&](int r, PRow& R, PCen* C) {
-    cp_async_wait_group<S - 1>();
-    __syncwarp();
-    pair_read(R, C, slot(r), G, L, r);
-    __syncwarp();
-    issue(r + S);
-  };
+  const int y0 = X.y0, y1 = X.y1;
   __syncwarp();
 #pragma unroll 1
-  for (int q = 0; q < S; ++q) issue(y0 - 2 + q);
-
-  PRow A, B, N;
-  PCen C, Cn;
-  float fs1[4], fn1[4], fs2[4], fn2[4], z[4];
-  float U1a[6], U1b[6], U1n[6];       // y_{m+1} on the level-2 rows j - 1, j, j + 1
-  float xx2[6];                       // Dxx of the level-2 row
-  float p1[4] = {0.f, 0.f, 0.f, 0.f}; // p_{m+1} of the last own level-1 row
-
-  // level 1 on the row of B (A, B, N: rows r - 1 .. r + 1; C: row r); own
-  // rows also store p_{m+1} and add to the level-1 norms
-  auto level1 = [&](int r, float* u1) {
-    pair_level<ADV>(A.y, B.y, N.y, C.xx, B.xy, N.xy, B.yy, N.yy, abx, aby, fs1, fn1, ig, sh1, z);
-    pair_y1(u1, z, fix, gx, G.nx);
-    if (L.own && r >= y0 && r < y1) {
-      const float pin[4] = {C.p.x, C.p.y, C.p.z, C.p.w};
+  for (int q = 0; q < PairLayout::STAGES; ++q) pair_issue(X, y0 - 2 + q);
+  PRow r0, r1, r2;
+  float u0[6], u1[6], u2[6], fs1[4], fs2[4];
+  pair_consume(X, y0 - 2, r0);
+  pair_consume(X, y0 - 1, r1);
+  pair_north<ADV>(r0.y, r1.y, r0.xy, r1.xy, r0.yy, r1.yy, X.aby, fs1);   // south faces, row y0 - 1
+  pair_consume(X, y0, r2);
+  pair_level1<ADV>(X, y0 - 1, r0, r1, r2, fs1, u1, ly1, lp1);
+  pair_consume(X, y0 + 1, r0);
+  pair_level1<ADV>(X, y0, r1, r2, r0, fs1, u2, ly1, lp1);
+  if (X.G.bc != 0 && y0 == 0) {               // y_{m+1} row -1 = -(row 0)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float pm = fmaf(d0, B.y[k + 1], pin[k]);   // the pending d_m y_m
-        p1[k] = fmaf(d1, z[k], pm);
-        ly1 = fmaf(z[k], z[k], ly1);
-        lp1 = fmaf(p1[k], p1[k], lp1);
-      }
-      const long long idx = (long long)r * G.nx + gx;
-      *reinterpret_cast<float4*>(p + idx) = make_float4(p1[0], p1[1], p1[2], p1[3]);
-    }
-  };
-
-  consume(y0 - 2, A, nullptr);
-  consume(y0 - 1, B, &C);
-  pair_north<ADV>(A.y, B.y, A.xy, B.xy, A.yy, B.yy, aby, fs1);   // south faces of row y0 - 1
-  // prologue: level 1 on rows y0 - 1 and y0
-  consume(y0, N, &Cn);
-  level1(y0 - 1, U1b);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) fs1[k] = fn1[k];
-  A = B; B = N; C = Cn;
-  consume(y0 + 1, N, &Cn);
-  level1(y0, U1n);
-  if (dir && y0 == 0) {               // y_{m+1} row -1 = -(row 0)
-#pragma unroll
-    for (int k = 0; k < 6; ++k) U1b[k] = -U1n[k];
+    for (int k = 0; k < 6; ++k) u1[k] = -u2[k];
   }
-  // south faces of level 2 on row y0: y_{m+1} rows y0 - 1, y0 with the
-  // coefficient rows y0 - 1 (A) and y0 (B)
-  pair_north<ADV>(U1b, U1n, A.xy, B.xy, A.yy, B.yy, aby, fs2);
-#pragma unroll
-  for (int k = 0; k < 6; ++k) { U1a[k] = U1b[k]; U1b[k] = U1n[k]; xx2[k] = C.xx[k]; }
-#pragma unroll
-  for (int k = 0; k < 4; ++k) fs1[k] = fn1[k];
-  A = B; B = N; C = Cn;
-
+  // south faces of level 2 on row y0: coefficient rows y0 - 1 (r1) and y0 (r2)
+  pair_north<ADV>(u1, u2, r1.xy, r2.xy, r1.yy, r2.yy, X.aby, fs2);
+  // rows: r2 = y0, r0 = y0 + 1, r1 free; y_{m+1}: u1 = y0 - 1, u2 = y0, u0 free
+  int j = y0;
 #pragma unroll 1
-  for (int j = y0; j < y1; ++j) {
-    // here A, B, C hold rows j, j + 1, j + 1; U1a, U1b rows j - 1, j
-    const float p1j[4] = {p1[0], p1[1], p1[2], p1[3]};        // p_{m+1} of row j
-    consume(j + 2, N, &Cn);
-    level1(j + 1, U1n);
-    if (dir && j + 1 == G.ny) {       // y_{m+1} row ny = -(row ny - 1)
-#pragma unroll
-      for (int k = 0; k < 6; ++k) U1n[k] = -U1b[k];
-    }
-    // level 2 on row j: coefficient rows j (A) and j + 1 (B), Dxx of row j
-    pair_level<ADV>(U1a, U1b, U1n, xx2, A.xy, B.xy, A.yy, B.yy, abx, aby, fs2, fn2, ig, sh2, z);
-    if (L.own) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float p2 = fmaf(d2, z[k], p1j[k]);
-        ly2 = fmaf(z[k], z[k], ly2);
-        lp2 = fmaf(p2, p2, lp2);
-      }
-      const long long idx = (long long)j * G.nx + gx;
-      *reinterpret_cast<float4*>(yout + idx) = make_float4(z[0], z[1], z[2], z[3]);
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) { fs2[k] = fn2[k]; fs1[k] = fn1[k]; }
-#pragma unroll
-    for (int k = 0; k < 6; ++k) { U1a[k] = U1b[k]; U1b[k] = U1n[k]; xx2[k] = C.xx[k]; }
-    A = B; B = N; C = Cn;
+  for (; j + 3 <= y1; j += 3) {
+    pair_step<ADV>(X, j, r2, r0, r1, u1, u2, u0, fs1, fs2, ly1, lp1, ly2, lp2);
+    pair_step<ADV>(X, j + 1, r0, r1, r2, u2, u0, u1, fs1, fs2, ly1, lp1, ly2, lp2);
+    pair_step<ADV>(X, j + 2, r1, r2, r0, u0, u1, u2, fs1, fs2, ly1, lp1, ly2, lp2);
   }
+  if (j < y1) pair_step<ADV>(X, j, r2, r0, r1, u1, u2, u0, fs1, fs2, ly1, lp1, ly2, lp2);
+  if (j + 1 < y1) pair_step<ADV>(X, j + 1, r0, r1, r2, u2, u0, u1, fs1, fs2, ly1, lp1, ly2, lp2);
   cp_async_wait_group<0>();          // nothing may land in the ring after the run
   __syncwarp();
 }
