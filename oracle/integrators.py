@@ -23,18 +23,23 @@ from typing import Callable, Sequence
 
 import numpy as np
 
-from .leja import LejaStats, leja_exp_augmented, leja_phi1
+from .leja import MAX_ITERS, LejaStats, leja_exp_augmented, leja_phi1
 
 
 def expquad_step(A, u, t, dt, s, c: Sequence[float], source_at: Callable[[float], np.ndarray],
-                 alpha, tol=1e-10, force_iters=None, rho_max=200.0):
-    """One step of Eq. exp_quad with s in {1, 2}.  Returns (u+, LejaStats)."""
+                 alpha, tol=1e-10, force_iters=None, rho_max=200.0, max_iters=MAX_ITERS,
+                 adaptive=False):
+    """One step of Eq. exp_quad with s in {1, 2}.  Returns (u+, LejaStats).
+    adaptive: the adaptive substep control of oracle.leja (u is returned
+    unchanged if it gives up)."""
     u = np.asarray(u, dtype=np.float64)
     Au = A @ u
     if s == 1:
         v = Au + source_at(t + c[0] * dt)
-        q, st = leja_phi1(A, v, dt, alpha, tol, force_iters, rho_max)
+        q, st = leja_phi1(A, v, dt, alpha, tol, force_iters, rho_max, max_iters, adaptive)
         st.matvecs += 1
+        if not st.converged and adaptive:
+            return u.copy(), st
         return u + dt * q, st
     if s != 2:
         raise ValueError("s must be 1 or 2")
@@ -44,8 +49,10 @@ def expquad_step(A, u, t, dt, s, c: Sequence[float], source_at: Callable[[float]
     w1 = Au + (c2 * S1 - c1 * S2) / (c2 - c1)
     w2 = (S2 - S1) / ((c2 - c1) * dt)
     top, _, st = leja_exp_augmented(A, np.zeros_like(u), np.array([0.0, 1.0]), w1, w2, dt,
-                                    alpha, tol, force_iters, rho_max)
+                                    alpha, tol, force_iters, rho_max, max_iters, adaptive)
     st.matvecs += 1
+    if not st.converged and adaptive:
+        return u.copy(), st
     return u + top, st
 
 

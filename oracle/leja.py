@@ -23,6 +23,14 @@ Readings where the paper is silent (each is listed in the design notes):
     exact number of terms with no test.
   * Substepping: if rho = gamma dt exceeds rho_max, the step is split into K
     equal substeps (K = ceil(rho / rho_max)).
+  * Adaptive substeps (optional; the paper fixes no control): start from the
+    substep of the rule above; a substep whose series reaches the iteration
+    budget max_iters without meeting the stopping rule is rejected and retried
+    at half the size; after an accepted substep of m iterations the next one
+    doubles when 4 m <= max_iters and the previous attempt was not rejected;
+    the last substep is the remainder of the step.  More than MAX_REJECTS
+    rejections or MAX_SUBSTEPS accepted substeps give up (not converged, input
+    returned unchanged).
 
 Pins (tests/test_oracle_leja.py): first Leja points in closed form and the
 greedy-max invariant on a dense grid; divided differences reproduce f at the
@@ -39,6 +47,8 @@ from functools import lru_cache
 import numpy as np
 
 MAX_ITERS = 500
+MAX_REJECTS = 40
+MAX_SUBSTEPS = 4096
 
 
 @lru_cache(maxsize=4)
@@ -123,15 +133,55 @@ def shift_scale(alpha: float):
 class LejaStats:
     iters: int = 0          # Leja iterations (matrix-vector products inside the series)
     matvecs: int = 0        # all matrix-vector products
-    substeps: int = 1
+    substeps: int = 1       # accepted substeps
     err_est: float = 0.0
     converged: bool = True
+    rejected: int = 0       # adaptive substeps rejected
+    sizes: tuple = ()       # accepted substep sizes (adaptive control)
 
 
 def n_substeps(alpha: float, dt: float, rho_max: float) -> int:
     c, gamma = shift_scale(alpha)
     rho = gamma * dt
     return max(1, int(math.ceil(rho / rho_max))) if rho > rho_max else 1
+
+
+def adaptive_substeps(dt: float, K0: int, budget: int, attempt):
+    """The adaptive substep rule of the module docstring.
+
+    ``attempt(h)`` runs one series of substep size h from the current state and
+    returns (ok, iterations); the caller keeps the attempt's result and commits
+    it when the next call is made or the rule returns.  Returns
+    (sizes, rejected, ok, accepted_flags) where accepted_flags lists, per
+    attempt, whether it was accepted.
+    """
+    h = dt / K0
+    done = 0.0
+    rejected = 0
+    grow = True
+    sizes = []
+    flags = []
+    while True:
+        rem = dt - done
+        last = h >= rem or rem - h <= 1e-12 * dt
+        hs = rem if last else h
+        ok, it = attempt(hs)
+        flags.append(bool(ok))
+        if not ok:
+            rejected += 1
+            if rejected > MAX_REJECTS:
+                return sizes, rejected, False, flags
+            h = hs / 2.0
+            grow = False
+            continue
+        sizes.append(hs)
+        done += hs
+        if last:
+            return sizes, rejected, True, flags
+        if len(sizes) >= MAX_SUBSTEPS:
+            return sizes, rejected, False, flags
+        h = 2.0 * hs if (grow and 4 * it <= budget) else hs
+        grow = True
 
 
 def _newton_series(matvec_shifted, y0, d, xi, tol, force_iters, max_iters, top=None):
@@ -165,14 +215,17 @@ def _newton_series(matvec_shifted, y0, d, xi, tol, force_iters, max_iters, top=N
 
 
 def leja_phi1(A, v, dt, alpha, tol=1e-10, force_iters=None, rho_max=200.0,
-              max_iters=MAX_ITERS):
+              max_iters=MAX_ITERS, adaptive=False):
     """out ~ phi_1(dt A) v by Leja interpolation of f(xi) = phi_1((c + gamma xi) h).
 
     Substeps (reading): with h = dt/K, w_0 = 0 and
     w_{k+1} = w_k + h phi_1(h A)(A w_k + v), w_K = dt phi_1(dt A) v, so
-    out = w_K / dt (for K = 1 this is the single series itself).
+    out = w_K / dt (for K = 1 this is the single series itself).  The same
+    recursion holds for unequal substeps (adaptive control).
     Returns (out, LejaStats).
     """
+    if adaptive and not (force_iters is not None and force_iters >= 0):
+        return _leja_phi1_adaptive(A, v, dt, alpha, tol, rho_max, max_iters)
     c, gamma = shift_scale(alpha)
     K = n_substeps(alpha, dt, rho_max)
     h = dt / K
@@ -197,8 +250,43 @@ def leja_phi1(A, v, dt, alpha, tol=1e-10, force_iters=None, rho_max=200.0,
     return acc / K, st
 
 
+def _leja_phi1_adaptive(A, v, dt, alpha, tol, rho_max, max_iters):
+    c, gamma = shift_scale(alpha)
+    xi = leja_points(max_iters + 1)
+    mv = lambda y, m: (A @ y - c * y) / gamma
+    v = np.asarray(v, dtype=np.float64)
+    st = LejaStats()
+    state = {"w": np.zeros_like(v), "rhs": v, "q": None, "n": 0}
+
+    def attempt(h):
+        if state["q"] is not None:            # commit the previous accepted attempt
+            state["w"] = state["w"] + state["h"] * state["q"]
+            state["rhs"] = A @ state["w"] + v
+            st.matvecs += 1
+            state["q"] = None
+        d = divided_differences(xi, phi1_scalar((c + gamma * xi) * h))
+        q, it, est, ok = _newton_series(mv, state["rhs"], d, xi, tol, None, max_iters)
+        st.iters += it
+        st.matvecs += it
+        if ok:
+            st.err_est = max(st.err_est, est)
+            state["q"], state["h"] = q, h
+            state["n"] += 1
+        return ok, it
+
+    K0 = n_substeps(alpha, dt, rho_max)
+    sizes, rejected, ok, _ = adaptive_substeps(dt, K0, max_iters, attempt)
+    st.substeps, st.rejected, st.sizes, st.converged = len(sizes), rejected, tuple(sizes), ok
+    if not ok:
+        return v.copy(), st
+    if len(sizes) == 1:
+        return state["q"], st
+    w = state["w"] + state["h"] * state["q"]
+    return w / dt, st
+
+
 def leja_exp_augmented(A, x0, eta0, w1, w2, dt, alpha, tol=1e-10, force_iters=None,
-                       rho_max=200.0, max_iters=MAX_ITERS):
+                       rho_max=200.0, max_iters=MAX_ITERS, adaptive=False):
     """Top block of exp(dt Atilde) [x0; eta0] for Atilde = [[A, W], [0, J]],
     W = [w2, w1], J = [[0, 1], [0, 0]] (Section 2: the sum of phi_l terms of
     Eq. exp_quad_Gauss is evaluated as the exponential of an augmented matrix).
@@ -212,7 +300,6 @@ def leja_exp_augmented(A, x0, eta0, w1, w2, dt, alpha, tol=1e-10, force_iters=No
     K = n_substeps(alpha, dt, rho_max)
     h = dt / K
     xi = leja_points(max_iters + 1)
-    d = divided_differences(xi, np.exp((c + gamma * xi) * h))
     n = len(x0)
 
     def mv(yt, m):
@@ -224,8 +311,31 @@ def leja_exp_augmented(A, x0, eta0, w1, w2, dt, alpha, tol=1e-10, force_iters=No
         out[n + 1] = 0.0
         return (out - c * yt) / gamma
 
-    st = LejaStats(substeps=K)
     state = np.concatenate([np.asarray(x0, dtype=np.float64), np.asarray(eta0, dtype=np.float64)])
+    top = lambda v: v[:n]
+    if adaptive and not (force_iters is not None and force_iters >= 0):
+        st = LejaStats()
+        cur = {"state": state, "new": None}
+
+        def attempt(hs):
+            if cur["new"] is not None:          # commit the previous accepted attempt
+                cur["state"], cur["new"] = cur["new"], None
+            dd = divided_differences(xi, np.exp((c + gamma * xi) * hs))
+            new, it, est, ok = _newton_series(mv, cur["state"], dd, xi, tol, None, max_iters,
+                                              top=top)
+            st.iters += it
+            st.matvecs += it
+            if ok:
+                st.err_est = max(st.err_est, est)
+                cur["new"] = new
+            return ok, it
+
+        sizes, rejected, ok, _ = adaptive_substeps(dt, K, max_iters, attempt)
+        st.substeps, st.rejected, st.sizes, st.converged = len(sizes), rejected, tuple(sizes), ok
+        final = cur["new"] if ok else state
+        return final[:n], final[n:], st
+    d = divided_differences(xi, np.exp((c + gamma * xi) * h))
+    st = LejaStats(substeps=K)
     for k in range(K):
         state, it, est, ok = _newton_series(mv, state, d, xi, tol, force_iters, max_iters,
                                             top=lambda v: v[:n])

@@ -176,3 +176,20 @@ def test_cn_step_dense_formula():
     ref = np.linalg.solve(I - 0.5 * p.dt * Ad,
                           (I + 0.5 * p.dt * Ad) @ u + 0.5 * p.dt * (S(0.3) + S(0.3 + p.dt)))
     assert np.linalg.norm(got - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_adaptive_two_stage_step_matches_fixed_converged_step():
+    """A two-stage step under adaptive substep control with a 30-iteration budget
+    agrees with the same step taken by one converged series (tol 1e-12)."""
+    p = small_problem(16, 14, BC_DIRICHLET0, "circular", adv=(0.3, 0.1), dt_factor=600, s=2,
+                      c=(1 / 3, 2 / 3))
+    A = op.assemble(p.grid, p.Dxx, p.Dxy, p.Dyy, p.ax_arr(), p.ay_arr())
+    alpha = spectral.gershgorin(A)
+    S = lambda t: p.source_at(t).ravel()
+    ref, st_ref = integrators.expquad_step(A, p.u0.ravel(), 0.1, p.dt, 2, (1 / 3, 2 / 3), S,
+                                           alpha, tol=1e-12, rho_max=1e9)
+    assert st_ref.converged and st_ref.substeps == 1
+    got, st = integrators.expquad_step(A, p.u0.ravel(), 0.1, p.dt, 2, (1 / 3, 2 / 3), S, alpha,
+                                       tol=1e-12, rho_max=1e9, max_iters=30, adaptive=True)
+    assert st.converged and st.rejected >= 1 and st.substeps > 1
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)

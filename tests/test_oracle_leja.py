@@ -150,3 +150,80 @@ def test_augmented_exponential_vs_eigen_phi_functions():
                                                dt, alpha, tol=1e-12, rho_max=rho_max)
         assert np.linalg.norm(top - ref) <= 1e-10 * np.linalg.norm(ref)
         assert abs(eta[0] - dt) < 1e-10 and abs(eta[1] - 1.0) < 1e-12
+
+
+# --- adaptive substep control (a reading: the paper fixes no control) ---------------------
+
+def _model_attempt(model, budget):
+    calls = []
+
+    def attempt(h):
+        it = model(h)
+        calls.append(h)
+        return it <= budget, it
+    return attempt, calls
+
+
+def test_adaptive_rule_hand_computed_sequences():
+    # iterations 100 h^2, budget 40, one initial substep: h = 1 needs 100 (rejected), h = 1/2
+    # needs 25 (accepted; no growth right after a rejection), then the remainder 1/2
+    attempt, calls = _model_attempt(lambda h: round(100 * h * h), 40)
+    sizes, rejected, ok, flags = leja.adaptive_substeps(1.0, 1, 40, attempt)
+    assert (sizes, rejected, ok, calls) == ([0.5, 0.5], 1, True, [1.0, 0.5, 0.5])
+    assert flags == [False, True, True]
+    # iterations 60 h, budget 40, eight initial substeps: 1/8 needs 8 (4*8 <= 40: double),
+    # 1/4 needs 15 (keep), ... and the last substep is the remainder 1/8
+    attempt, calls = _model_attempt(lambda h: round(60 * h), 40)
+    sizes, rejected, ok, _ = leja.adaptive_substeps(1.0, 8, 40, attempt)
+    assert (sizes, rejected, ok) == ([0.125, 0.25, 0.25, 0.25, 0.125], 0, True)
+    # a series that never converges: give up after MAX_REJECTS + 1 attempts
+    attempt, calls = _model_attempt(lambda h: 1000, 40)
+    sizes, rejected, ok, _ = leja.adaptive_substeps(1.0, 1, 40, attempt)
+    assert (sizes, ok) == ([], False) and rejected == leja.MAX_REJECTS + 1
+    assert calls[-1] == 2.0 ** -leja.MAX_REJECTS
+
+
+def test_adaptive_phi1_rejects_and_matches_dense():
+    p = small_problem(12, 12, BC_PERIODIC, "random", dt_factor=4000)
+    A = op.assemble(p.grid, p.Dxx, p.Dxy, p.Dyy)
+    alpha = spectral.gershgorin(A)
+    v = np.random.default_rng(4).standard_normal(p.grid.n)
+    out, st = leja.leja_phi1(A, v, p.dt, alpha, tol=1e-10, rho_max=1e9, max_iters=40,
+                             adaptive=True)
+    assert st.converged and st.rejected >= 3 and st.substeps == len(st.sizes) > 8
+    assert abs(sum(st.sizes) - p.dt) <= 1e-13 * p.dt
+    ref = _dense_phi1(A.toarray(), v, p.dt)
+    assert np.linalg.norm(out - ref) <= 1e-8 * np.linalg.norm(ref)
+    # the fixed rule with one substep cannot converge in 40 iterations
+    _, st_fixed = leja.leja_phi1(A, v, p.dt, alpha, tol=1e-10, rho_max=1e9, max_iters=40)
+    assert not st_fixed.converged
+
+
+def test_adaptive_augmented_matches_eigen_phi_functions():
+    g = Grid(9, 8, BC_DIRICHLET0)
+    rng = np.random.default_rng(8)
+    A = op.assemble(g, rng.uniform(0.5, 1.0, (8, 9)), 0.0, rng.uniform(0.2, 0.6, (8, 9)))
+    lam, V = np.linalg.eigh(A.toarray())
+    dt = 0.02
+    w1 = rng.standard_normal(g.n)
+    w2 = rng.standard_normal(g.n)
+    phi = lambda l: V @ np.diag([leja.phi_l_scalar(dt * t, l) for t in lam]) @ V.T
+    ref = dt * phi(1) @ w1 + dt * dt * phi(2) @ w2
+    alpha = spectral.gershgorin(A)
+    top, eta, st = leja.leja_exp_augmented(A, np.zeros(g.n), np.array([0.0, 1.0]), w1, w2, dt,
+                                           alpha, tol=1e-12, rho_max=1e9, max_iters=8,
+                                           adaptive=True)
+    assert st.converged and st.rejected >= 1 and st.substeps > 1
+    assert np.linalg.norm(top - ref) <= 1e-9 * np.linalg.norm(ref)
+    assert abs(eta[0] - dt) < 1e-10 and abs(eta[1] - 1.0) < 1e-12
+
+
+def test_adaptive_with_ample_budget_is_the_fixed_step():
+    p = small_problem(12, 10, BC_DIRICHLET0, "circular", dt_factor=80)
+    A = op.assemble(p.grid, p.Dxx, p.Dxy, p.Dyy)
+    alpha = spectral.gershgorin(A)
+    v = np.random.default_rng(6).standard_normal(p.grid.n)
+    fixed, st_f = leja.leja_phi1(A, v, p.dt, alpha, tol=1e-10)
+    adapt, st_a = leja.leja_phi1(A, v, p.dt, alpha, tol=1e-10, adaptive=True)
+    assert st_f.substeps == 1 and st_a.rejected == 0 and st_a.substeps == 1
+    assert np.array_equal(fixed, adapt) and st_a.iters == st_f.iters
