@@ -64,14 +64,15 @@ typedef struct {
 } ad_grid;
 
 typedef struct {
-  int iters;                 /* Leja (or GMRES) iterations, summed over substeps */
+  int iters;                 /* Leja (or GMRES) iterations, summed over substeps (and
+                                rejected adaptive attempts) */
   int matvecs;               /* all applications of A, including A u and substep couplings */
-  int substeps;              /* K: the step was split into K equal substeps */
+  int substeps;              /* K: the step was split into K (accepted) substeps */
   int converged;             /* 1 if every series met its stopping rule */
   double err_est;            /* largest |d_{m+1}| ||y_{m+1}|| / ||p_{m+1}|| (GMRES: relative residual) */
   double alpha;              /* spectral bound used */
   int kernel_launches;       /* device kernels this call enqueued (graph-loop bodies included) */
-  int pad_;
+  int rejected;              /* substeps rejected by adaptive substep control */
 } ad_stats;
 
 /* Time profile h_k(t) of a separable source S(x, y, t) = sum_k h_k(t) g_k(x, y).
@@ -116,6 +117,24 @@ AD_API int ad_destroy_operator(ad_operator* op);
  * max_iters caps the number of Leja iterations per series (<= 500).
  * Values <= 0 keep the current setting.  Defaults: rho_max 200, max_iters 500. */
 AD_API int ad_set_options(ad_operator* op, double rho_max, int max_iters);
+
+/* Substep control of the Leja series (the paper fixes none).
+ * adaptive = 0 (default): ceil(gamma dt / rho_max) equal substeps; a series
+ * that reaches max_iters still contributes and the call returns
+ * AD_ERR_NOT_CONVERGED.  adaptive = 1: start from that substep; a substep
+ * whose series reaches max_iters without meeting the stopping rule is
+ * rejected and retried at half the size; after an accepted substep of m
+ * iterations the next one doubles when 4 m <= max_iters (not right after a
+ * rejection); the last substep is the remainder of the step.  Substeps may
+ * then differ in size (phi_1: w_{k+1} = w_k + h_k phi_1(h_k A)(A w_k + v);
+ * augmented exponential: exp(h_k Atilde) applied in turn).  More than 40
+ * rejections or 4096 accepted substeps give up: AD_ERR_NOT_CONVERGED with u
+ * (ad_expquad_step) or out (ad_leja_phi1) not written.  Forced iteration
+ * counts (force_iters >= 0) always use the fixed rule.  Stats: substeps =
+ * accepted, rejected = rejected attempts; iters and matvecs include rejected
+ * work.  Applies to ad_leja_phi1 and ad_expquad_step; ad_batch_midpoint_step
+ * and the no-allocation entry point keep one substep. */
+AD_API int ad_set_substep_control(ad_operator* op, int adaptive);
 
 /* Estimate alpha, the largest-magnitude (negative) eigenvalue of A (Section 2:
  * Gershgorin's disc theorem, smallest eigenvalue taken as 0), store it in the

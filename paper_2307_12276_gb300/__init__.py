@@ -35,10 +35,10 @@ class _Grid(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("matvecs", C.c_int), ("substeps", C.c_int),
                 ("converged", C.c_int), ("err_est", C.c_double), ("alpha", C.c_double),
-                ("kernel_launches", C.c_int), ("pad_", C.c_int)]
+                ("kernel_launches", C.c_int), ("rejected", C.c_int)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _PROFILE = C.CFUNCTYPE(C.c_double, C.c_int, C.c_double, C.c_void_p)
@@ -55,6 +55,7 @@ _sig = {
                                 C.POINTER(_vp)]),
     "ad_destroy_operator": (_i, [_vp]),
     "ad_set_options": (_i, [_vp, _d, _i]),
+    "ad_set_substep_control": (_i, [_vp, _i]),
     "ad_spectral_bound": (_i, [_vp, _i, _vp, C.c_ulonglong, _i, _d, C.POINTER(_d)]),
     "ad_set_spectral_bound": (_i, [_vp, _d]),
     "ad_get_spectral_bound": (_i, [_vp, C.POINTER(_d)]),
@@ -222,6 +223,11 @@ def destroy_operator(op: Operator):
 
 def set_options(op: Operator, rho_max: float = 0.0, max_iters: int = 0):
     _check(_lib.ad_set_options(op.handle, rho_max, max_iters))
+
+
+def set_substep_control(op: Operator, adaptive: bool = True):
+    """ad_set_substep_control: adaptive substeps (True) or the fixed rho_max rule."""
+    _check(_lib.ad_set_substep_control(op.handle, 1 if adaptive else 0))
 
 
 def spectral_bound(op: Operator, method: int = BOUND_GERSHGORIN, x0=None, seed: int = 0,

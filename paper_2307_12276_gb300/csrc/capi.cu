@@ -123,6 +123,7 @@ struct ad_operator {
   bool have_alpha = false;
   double rho_max = 200.0;
   int max_iters = kMaxIters;
+  int adaptive = 0;                            // substep control: 0 fixed, 1 adaptive
   SeriesGraph graphs[2];                       // [aug]
   // cache of the coefficient upload
   int cache_kind = -1;
@@ -471,9 +472,133 @@ double h_at(const ad_source* src, int k, double t) {
   return (src && src->h) ? src->h(k, t, src->ctx) : 1.0;
 }
 
+// The eta part of an augmented series sum, sum_m d_m eta_m (host scalars),
+// after `it` iterations from eta (d: the divided differences last uploaded).
+void advance_eta(const ad_operator* op, int it, double eta[2]) {
+  const std::vector<double>& d = op->d_host;
+  const std::vector<double>& xi = leja_points();
+  double e1 = eta[0], e2 = eta[1];
+  double s1 = d[0] * e1, s2 = d[0] * e2;
+  for (int m = 0; m < it; ++m) {
+    const double n1 = (e2 - op->c * e1) / op->gamma - xi[m] * e1;
+    const double n2 = (-op->c * e2) / op->gamma - xi[m] * e2;
+    e1 = n1;
+    e2 = n2;
+    s1 += d[m + 1] * e1;
+    s2 += d[m + 1] * e2;
+  }
+  eta[0] = s1;
+  eta[1] = s2;
+}
+
+// Adaptive substep control (the paper fixes none).  Starting from the substep
+// of the rho_max rule, a substep whose series reaches the iteration budget
+// (max_iters) without meeting the stopping rule is rejected and retried at
+// half the size; after an accepted substep of m iterations the next one
+// doubles when 4 m <= budget, unless the attempt before was rejected; the
+// last substep is the remainder of the step.  More than kMaxRejects
+// rejections or kMaxSubsteps accepted substeps give up.
+constexpr int kMaxRejects = 40;
+constexpr int kMaxSubsteps = 4096;
+
+struct SubstepCtl {
+  double dt, done = 0.0, h;
+  int budget, accepted = 0, rejected = 0;
+  bool grow = true;
+  SubstepCtl(double dt_, int K0, int budget_) : dt(dt_), h(dt_ / K0), budget(budget_) {}
+  // size of the next attempt; *last: it ends the step
+  double next(bool* last) const {
+    const double rem = dt - done;
+    *last = h >= rem || rem - h <= 1e-12 * dt;
+    return *last ? rem : h;
+  }
+  // false: give up
+  bool reject(double hs) {
+    ++rejected;
+    h = hs / 2.0;
+    grow = false;
+    return rejected <= kMaxRejects;
+  }
+  // after an accepted attempt that was not the last; false: give up
+  bool accept(double hs, int iters) {
+    ++accepted;
+    done += hs;
+    if (accepted >= kMaxSubsteps) return false;
+    h = (grow && 4 * iters <= budget) ? 2.0 * hs : hs;
+    grow = true;
+    return true;
+  }
+};
+
+// Work of one series attempt: iterations always count; the error estimate
+// only for accepted attempts.
+void add_attempt(ad_stats* st, const ad_stats& at, bool accepted) {
+  if (!st) return;
+  st->iters += at.iters;
+  st->matvecs += at.matvecs;
+  st->kernel_launches += at.kernel_launches;
+  if (accepted) st->err_est = std::max(st->err_est, at.err_est);
+}
+
+// phi_1 under adaptive substep control: w_{k+1} = w_k + h_k phi_1(h_k A)(A w_k + v),
+// out = w / dt (a single substep: the series itself).  On giving up, out is not
+// written and AD_ERR_NOT_CONVERGED is returned.
+int phi1_device_adaptive(ad_operator* op, const void* v_dev, void* out_dev, double dt,
+                         double tol, ad_stats* st) {
+  const long long n = op->g.n;
+  SubstepCtl ctl(dt, n_substeps(op, dt), op->max_iters);
+  Sources none{};
+  const void* rhs = v_dev;
+  bool have_w = false;
+  for (;;) {
+    bool last;
+    const double hs = ctl.next(&last);
+    double d0;
+    AD_TRY(upload_series(op, 0, hs, nullptr, &d0, nullptr));
+    ad_stats at{};
+    at.converged = 1;
+    int it = 0;
+    const int r = run_series(op, 0, rhs, d0, -1, tol, &at, &it);
+    if (r != AD_OK && r != AD_ERR_NOT_CONVERGED) return r;
+    add_attempt(st, at, r == AD_OK);
+    if (r != AD_OK) {
+      if (!ctl.reject(hs)) break;
+      continue;
+    }
+    if (last) {
+      ++ctl.accepted;
+      if (!have_w) {
+        axpby(op->prec, n, 1.0, op->P, 0.0, nullptr, out_dev, op->stream);
+      } else {
+        axpby(op->prec, n, 1.0, op->T2, hs, op->P, op->T2, op->stream);
+        axpby(op->prec, n, 1.0 / dt, op->T2, 0.0, nullptr, out_dev, op->stream);
+      }
+      if (st) { st->substeps = ctl.accepted; st->rejected = ctl.rejected; }
+      CUDA_TRY(cudaGetLastError());
+      return AD_OK;
+    }
+    if (!have_w) {   // v kept in T1, w in T2
+      axpby(op->prec, n, 1.0, v_dev, 0.0, nullptr, op->T1, op->stream);
+      axpby(op->prec, n, hs, op->P, 0.0, nullptr, op->T2, op->stream);
+      have_w = true;
+    } else {
+      axpby(op->prec, n, 1.0, op->T2, hs, op->P, op->T2, op->stream);
+    }
+    apply(op, op->T2, op->T3, nullptr, none);
+    axpby(op->prec, n, 1.0, op->T3, 1.0, op->T1, op->T3, op->stream);
+    if (st) st->matvecs += 1;
+    rhs = op->T3;
+    if (!ctl.accept(hs, it)) break;
+  }
+  if (st) { st->substeps = ctl.accepted; st->rejected = ctl.rejected; st->converged = 0; }
+  CUDA_TRY(cudaGetLastError());
+  return AD_ERR_NOT_CONVERGED;
+}
+
 // out_dev (storage type) = phi_1(dt A) v_dev; v_dev must not alias T1/T2/T3.
 int phi1_device(ad_operator* op, const void* v_dev, void* out_dev, double dt, double tol,
                 int force, ad_stats* st) {
+  if (op->adaptive && force < 0) return phi1_device_adaptive(op, v_dev, out_dev, dt, tol, st);
   const int K = n_substeps(op, dt);
   const double h = dt / K;
   double d0;
@@ -641,6 +766,14 @@ int ad_set_options(ad_operator* op, double rho_max, int max_iters) {
   return AD_OK;
 }
 
+int ad_set_substep_control(ad_operator* op, int adaptive) {
+  g_err.clear();
+  if (!op) return fail(AD_ERR_INVALID, "op is NULL");
+  if (adaptive != 0 && adaptive != 1) return fail(AD_ERR_INVALID, "adaptive must be 0 or 1");
+  op->adaptive = adaptive;
+  return AD_OK;
+}
+
 int ad_set_spectral_bound(ad_operator* op, double alpha) {
   g_err.clear();
   if (!op) return fail(AD_ERR_INVALID, "op is NULL");
@@ -721,7 +854,11 @@ int ad_leja_phi1(ad_operator* op, const void* v, void* out, double dt, double to
   if (!od) { AD_TRY(ensure_staging(op)); od = op->S1; }
   int r = phi1_device(op, vd, od, dt, tol, force_iters < 0 ? -1 : force_iters, &st);
   if (r != AD_OK && r != AD_ERR_NOT_CONVERGED) return r;
-  AD_TRY(finish_out(op, out, od));
+  if (r != AD_OK && op->adaptive && force_iters < 0) {   // gave up: out is not written
+    CUDA_TRY(cudaStreamSynchronize(op->stream));
+  } else {
+    AD_TRY(finish_out(op, out, od));
+  }
   st.kernel_launches += (int)(launch_counter() - l0);
   if (stats) *stats = st;
   if (r == AD_ERR_NOT_CONVERGED) return fail(r, "Leja series reached max_iters");
@@ -757,7 +894,10 @@ int ad_expquad_step(ad_operator* op, void* u, double t, double dt, int s, const 
     const int r = phi1_device(op, op->W1, op->W2, dt, tol, force, &st);
     if (r != AD_OK && r != AD_ERR_NOT_CONVERGED) return r;
     status = r;
-    axpby(op->prec, n, 1.0, ud, dt, op->W2, ud, op->stream);
+    // a non-converged fixed step is still applied; adaptive control that gave
+    // up leaves u unchanged
+    if (!(r != AD_OK && op->adaptive && force < 0))
+      axpby(op->prec, n, 1.0, ud, dt, op->W2, ud, op->stream);
   } else {
     // w1 = A u + (c2 S1 - c1 S2)/(c2 - c1), w2 = (S2 - S1)/((c2 - c1) dt);
     // u += top block of exp(dt [[A, W], [0, J]]) [0; 0; 1]
@@ -769,38 +909,60 @@ int ad_expquad_step(ad_operator* op, void* u, double t, double dt, int s, const 
     }
     apply(op, ud, op->W1, op->W2, S);
     st.matvecs += 1;
-    const int K = n_substeps(op, dt);
-    const double h = dt / K;
-    st.substeps = K;
     double eta[2] = {0.0, 1.0};
-    for (int k = 0; k < K; ++k) {
-      double d0, eta_next[2];
-      AD_TRY(upload_series(op, 1, h, eta, &d0, eta_next));
-      int it = 0;
-      const int r = run_series(op, 1, k == 0 ? nullptr : op->T2, d0, force, tol, &st, &it);
-      if (r != AD_OK && r != AD_ERR_NOT_CONVERGED) return r;
-      if (r != AD_OK) status = r;
-      // eta part of the series sum: sum_m d_m eta_m (scalar, host)
-      {
-        const std::vector<double>& d = op->d_host;
-        double e1 = eta[0], e2 = eta[1];
-        double s1 = d[0] * e1, s2 = d[0] * e2;
-        const std::vector<double>& xi = leja_points();
-        for (int m = 0; m < it; ++m) {
-          const double n1 = (e2 - op->c * e1) / op->gamma - xi[m] * e1;
-          const double n2 = (-op->c * e2) / op->gamma - xi[m] * e2;
-          e1 = n1;
-          e2 = n2;
-          s1 += d[m + 1] * e1;
-          s2 += d[m + 1] * e2;
+    if (op->adaptive && force < 0) {
+      // adaptive substep control: exp(h_k Atilde) applied to the accepted state
+      SubstepCtl ctl(dt, n_substeps(op, dt), op->max_iters);
+      bool have_x = false, finished = false;
+      for (;;) {
+        bool last;
+        const double hs = ctl.next(&last);
+        double d0, eta_next[2];
+        AD_TRY(upload_series(op, 1, hs, eta, &d0, eta_next));
+        ad_stats at{};
+        at.converged = 1;
+        int it = 0;
+        const int r = run_series(op, 1, have_x ? op->T2 : nullptr, d0, -1, tol, &at, &it);
+        if (r != AD_OK && r != AD_ERR_NOT_CONVERGED) return r;
+        add_attempt(&st, at, r == AD_OK);
+        if (r != AD_OK) {
+          if (!ctl.reject(hs)) break;
+          continue;
         }
-        eta[0] = s1;
-        eta[1] = s2;
-        (void)eta_next;
+        advance_eta(op, it, eta);
+        if (last) {
+          ++ctl.accepted;
+          finished = true;
+          break;
+        }
+        axpby(op->prec, n, 1.0, op->P, 0.0, nullptr, op->T2, op->stream);
+        have_x = true;
+        if (!ctl.accept(hs, it)) break;
       }
-      if (K > 1) axpby(op->prec, n, 1.0, op->P, 0.0, nullptr, op->T2, op->stream);
+      st.substeps = ctl.accepted;
+      st.rejected = ctl.rejected;
+      if (finished) {
+        axpby(op->prec, n, 1.0, ud, 1.0, op->P, ud, op->stream);
+      } else {   // gave up: u is left unchanged
+        status = AD_ERR_NOT_CONVERGED;
+        st.converged = 0;
+      }
+    } else {
+      const int K = n_substeps(op, dt);
+      const double h = dt / K;
+      st.substeps = K;
+      for (int k = 0; k < K; ++k) {
+        double d0, eta_next[2];
+        AD_TRY(upload_series(op, 1, h, eta, &d0, eta_next));
+        int it = 0;
+        const int r = run_series(op, 1, k == 0 ? nullptr : op->T2, d0, force, tol, &st, &it);
+        if (r != AD_OK && r != AD_ERR_NOT_CONVERGED) return r;
+        if (r != AD_OK) status = r;
+        advance_eta(op, it, eta);
+        if (K > 1) axpby(op->prec, n, 1.0, op->P, 0.0, nullptr, op->T2, op->stream);
+      }
+      axpby(op->prec, n, 1.0, ud, 1.0, K > 1 ? op->T2 : op->P, ud, op->stream);
     }
-    axpby(op->prec, n, 1.0, ud, 1.0, K > 1 ? op->T2 : op->P, ud, op->stream);
   }
   CUDA_TRY(cudaGetLastError());
   AD_TRY(finish_out(op, u, ud));
