@@ -258,6 +258,60 @@ AD_API int ad_field_features(const ad_grid* grid, const double* Dxx, const doubl
                              const double* Dyy, double max_a, double dt, void* cuda_stream,
                              float* out21);
 
+/* ---------------------------------------------------------------------
+ * Momentum coupling (Eq. cr_full, Section 1).  The paper integrates only the
+ * two-dimensional Eq. anidiff and names the momentum terms of Eq. cr_full,
+ *   d/dp(p^2 D_pp d/dp(u/p^2)) - d/dp((pdot - (p/3) div v) u) - (1/tau_f + 1/tau_r) u,
+ * as future work.  This operator adds them on np momentum cells:
+ *   - faces P[0] < ... < P[np] (> 0), centres p_k = sqrt(P[k] P[k+1]);
+ *   - D(x, y, p_k) = beta[k] D(x, y); the constant advection (ax, ay) does not
+ *     depend on p;
+ *   - dpp[f], b[f] = D_pp and pdot - (p/3) div v at face f (f = 0..np; the
+ *     two outer values are unused: no flux leaves the momentum range);
+ *     loss[k] = 1/tau_f + 1/tau_r of cell k;
+ *   - finite volumes in p: the diffusion flux
+ *     P_f^2 D_pp (u_{k+1}/p_{k+1}^2 - u_k/p_k^2)/(p_{k+1} - p_k), the advective
+ *     flux b u taken from the upwind cell.
+ * Vectors are float64, device memory, slice-major: u[k * nx * ny + j * nx + i]
+ * (each momentum slice is one field in the layout of ad_create_operator).
+ * All arrays of ad_momentum are host memory. */
+typedef struct {
+  int np;                    /* momentum cells, 1..1024 */
+  const double* P;           /* np + 1 increasing positive faces */
+  const double* beta;        /* np scales of the spatial diffusion (>= 0) */
+  const double* dpp;         /* np + 1 face values of D_pp (>= 0) */
+  const double* b;           /* np + 1 face values of pdot - (p/3) div v */
+  const double* loss;        /* np loss rates */
+} ad_momentum;
+
+typedef struct ad_momentum_operator ad_momentum_operator;
+
+/* Build the coupled operator (FP64).  Dxx, Dxy, Dyy: device float64 fields
+ * [ny][nx] of the spatial tensor (scaled by beta[k] in slice k).  The
+ * Gershgorin bound of the coupled matrix is computed here (Section 2).
+ * Errors: AD_ERR_INVALID (NULL, bad sizes, non-increasing faces, negative
+ * D_pp or beta, nx * ny * np >= 2^31), AD_ERR_NOMEM, AD_ERR_CUDA. */
+AD_API int ad_create_momentum_operator(const ad_grid* grid, const ad_momentum* mom,
+                                       const double* Dxx, const double* Dxy, const double* Dyy,
+                                       double ax, double ay, void* cuda_stream,
+                                       ad_momentum_operator** out);
+AD_API int ad_destroy_momentum_operator(ad_momentum_operator* op);
+/* The spectral bound alpha in use (Gershgorin unless set). */
+AD_API int ad_momentum_spectral_bound(const ad_momentum_operator* op, double* alpha);
+AD_API int ad_momentum_set_spectral_bound(ad_momentum_operator* op, double alpha);
+/* rho_max and max_iters as in ad_set_options (fixed substep rule). */
+AD_API int ad_momentum_set_options(ad_momentum_operator* op, double rho_max, int max_iters);
+/* Au = A u (device, non-aliasing). */
+AD_API int ad_momentum_apply(ad_momentum_operator* op, const double* u, double* Au);
+/* out = phi_1(dt A) v by the Leja series of Section 2, with the stopping
+ * rule, cap and substeps of ad_leja_phi1.  v, out: device (may alias). */
+AD_API int ad_momentum_leja_phi1(ad_momentum_operator* op, const double* v, double* out,
+                                 double dt, double tol, int force_iters, ad_stats* stats);
+/* u += dt phi_1(dt A)(A u + S): the exponential midpoint rule (Eq. exp_midpoint)
+ * for a time-independent source S (device, or NULL), exact in time for it. */
+AD_API int ad_momentum_step(ad_momentum_operator* op, double* u, double dt, const double* S,
+                            double tol, int force_iters, ad_stats* stats);
+
 /* Measurement helper (no counterpart in the paper): time the fused Leja
  * iteration kernel alone.  Runs a forced series of `reps` iterations (aug =
  * 0: phi_1 form, 1: augmented form) on the operator's stream and returns the

@@ -49,6 +49,12 @@ class _Source(C.Structure):
                 ("ctx", C.c_void_p)]
 
 
+class _Momentum(C.Structure):
+    _fields_ = [("np", C.c_int), ("P", C.POINTER(C.c_double)), ("beta", C.POINTER(C.c_double)),
+                ("dpp", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double)),
+                ("loss", C.POINTER(C.c_double))]
+
+
 _vp, _dp, _i, _d = C.c_void_p, C.c_double, C.c_int, C.c_double
 _sig = {
     "ad_create_operator": (_i, [C.POINTER(_Grid), _vp, _vp, _vp, _vp, _vp, _d, _d, _i, _vp,
@@ -80,6 +86,15 @@ _sig = {
     "ad_mlp_train": (_i, [_vp, _vp, _vp, _i, _i, C.c_float, _i, C.POINTER(C.c_float)]),
     "ad_mlp_predict": (_i, [_vp, _vp, _i, _i, _vp]),
     "ad_field_features": (_i, [C.POINTER(_Grid), _vp, _vp, _vp, _d, _d, _vp, _vp]),
+    "ad_create_momentum_operator": (_i, [C.POINTER(_Grid), C.POINTER(_Momentum), _vp, _vp, _vp,
+                                         _d, _d, _vp, C.POINTER(_vp)]),
+    "ad_destroy_momentum_operator": (_i, [_vp]),
+    "ad_momentum_spectral_bound": (_i, [_vp, C.POINTER(_d)]),
+    "ad_momentum_set_spectral_bound": (_i, [_vp, _d]),
+    "ad_momentum_set_options": (_i, [_vp, _d, _i]),
+    "ad_momentum_apply": (_i, [_vp, _vp, _vp]),
+    "ad_momentum_leja_phi1": (_i, [_vp, _vp, _vp, _d, _d, _i, C.POINTER(Stats)]),
+    "ad_momentum_step": (_i, [_vp, _vp, _d, _vp, _d, _i, C.POINTER(Stats)]),
     "ad_time_series": (_i, [_vp, _i]),
     "ad_series_timing": (_i, [_vp, C.POINTER(_d), C.POINTER(_i), C.POINTER(C.c_longlong),
                               C.POINTER(_i)]),
@@ -498,3 +513,83 @@ def field_features(nx, ny, bc, Dxx, Dxy, Dyy, max_a, dt, stream=None, x0=-1.0, x
 def check_wait_timeout(timeout_ms: float = 50.0, stream=None) -> int:
     """ad_check_wait_timeout: returns the status (AD_ERR_TIMEOUT expected)."""
     return _lib.ad_check_wait_timeout(timeout_ms, _stream_ptr(stream))
+
+
+# ----------------------------------------------------------------------- momentum coupling
+class MomentumOperator:
+    """Handle of an ad_momentum_operator (Eq. cr_full's momentum terms coupling
+    np slices of the spatial operator; FP64, slice-major vectors)."""
+
+    def __init__(self, handle: int, n: int, npm: int):
+        self.handle = handle
+        self.n, self.np = n, npm
+        self.N = n * npm
+
+    def close(self):
+        if self.handle:
+            _lib.ad_destroy_momentum_operator(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def vec(self, x, what):
+        return _ptr(x, "float64", self.N, what)
+
+
+def create_momentum_operator(nx: int, ny: int, bc: int, Dxx, Dxy, Dyy, P, beta, dpp, b, loss,
+                             ax: float = 0.0, ay: float = 0.0, stream=None, x0=-1.0, x1=1.0,
+                             y0=-1.0, y1=1.0) -> MomentumOperator:
+    """ad_create_momentum_operator.  D fields: float64 device tensors [ny][nx];
+    P, dpp, b: np + 1 face values; beta, loss: np cell values (host sequences)."""
+    import numpy as np
+    g = _Grid(nx, ny, x0, x1, y0, y1, bc)
+    n = nx * ny
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (P, beta, dpp, b, loss)]
+    npm = len(arrs[1])
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    mom = _Momentum(npm, dp(arrs[0]), dp(arrs[1]), dp(arrs[2]), dp(arrs[3]), dp(arrs[4]))
+    pf = [_ptr(f, "float64", n, name) for f, name in ((Dxx, "Dxx"), (Dxy, "Dxy"), (Dyy, "Dyy"))]
+    h = _vp()
+    _check(_lib.ad_create_momentum_operator(C.byref(g), C.byref(mom), pf[0], pf[1], pf[2],
+                                            float(ax), float(ay), _stream_ptr(stream),
+                                            C.byref(h)))
+    return MomentumOperator(h.value, n, npm)
+
+
+def momentum_spectral_bound(op: MomentumOperator) -> float:
+    a = _d()
+    _check(_lib.ad_momentum_spectral_bound(op.handle, C.byref(a)))
+    return a.value
+
+
+def momentum_set_spectral_bound(op: MomentumOperator, alpha: float):
+    _check(_lib.ad_momentum_set_spectral_bound(op.handle, alpha))
+
+
+def momentum_set_options(op: MomentumOperator, rho_max: float = 0.0, max_iters: int = 0):
+    _check(_lib.ad_momentum_set_options(op.handle, rho_max, max_iters))
+
+
+def momentum_apply(op: MomentumOperator, u, out):
+    _check(_lib.ad_momentum_apply(op.handle, op.vec(u, "u"), op.vec(out, "out")))
+
+
+def momentum_leja_phi1(op: MomentumOperator, v, out, dt: float, tol: float = 1e-10,
+                       force_iters: int = -1) -> dict:
+    st = Stats()
+    _check(_lib.ad_momentum_leja_phi1(op.handle, op.vec(v, "v"), op.vec(out, "out"), dt, tol,
+                                      force_iters, C.byref(st)), st)
+    return st.as_dict()
+
+
+def momentum_step(op: MomentumOperator, u, dt: float, S=None, tol: float = 1e-10,
+                  force_iters: int = -1) -> dict:
+    """u += dt phi_1(dt A)(A u + S) for a time-independent source S (or None)."""
+    st = Stats()
+    _check(_lib.ad_momentum_step(op.handle, op.vec(u, "u"), dt, op.vec(S, "S"), tol,
+                                 force_iters, C.byref(st)), st)
+    return st.as_dict()
