@@ -68,8 +68,9 @@ def parse():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--form-steps", type=int, default=5)
     ap.add_argument("--learned-fields", type=int, default=1000)
-    ap.add_argument("--forms", default="fp32,cn,paper,batched,learned",
-                    help="comma list of extra forms to measure: fp32, cn, batched, learned, paper")
+    ap.add_argument("--forms", default="fp32,cn,paper,batched,learned,momentum",
+                    help="comma list of extra forms to measure: fp32, cn, batched, learned, "
+                         "paper, momentum")
     return ap.parse_args()
 
 
@@ -296,6 +297,59 @@ def measure_fp32_form(ad, dev, stream, flush, steps):
                          "unit": "GB/s", "frac": round(gbs / HBM_PEAK_GBS, 4),
                          "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
                          "peak_note": "of measured copy bandwidth"}}
+
+
+def measure_momentum_form(ad, dev, stream, steps=3):
+    """The momentum-coupled operator of Eq. cr_full on a 256^2 x 32 grid
+    (2.1 M unknowns, FP64, Dirichlet, circular field, constant advection):
+    exponential midpoint steps with a time-independent source at
+    100 Delta t_CFL of the most diffusive slice, tol 1e-10; and the fused
+    iteration kernel's FP64 rate from a forced 100-iteration series."""
+    import numpy as np
+    import torch
+    from workloads.fields import BC_DIRICHLET0
+    from workloads.momentum import momentum_problem
+    mp = momentum_problem(256, 256, 32, BC_DIRICHLET0, "circular", adv=(0.1, 0.05),
+                          dt_factor=100.0)
+    s = mp.spatial
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(), device=dev)
+    op = ad.create_momentum_operator(s.grid.nx, s.grid.ny, s.grid.bc, T(s.Dxx), T(s.Dxy),
+                                     T(s.Dyy), mp.mom.P, mp.mom.beta, mp.mom.dpp, mp.mom.b,
+                                     mp.mom.loss, ax=s.ax, ay=s.ay, stream=stream)
+    N = op.N
+    u, S = T(mp.u0), T(mp.S)
+    ad.momentum_step(op, u, mp.dt, S, tol=mp.tol)            # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters = []
+    e0.record(stream)
+    for _ in range(steps):
+        iters.append(ad.momentum_step(op, u, mp.dt, S, tol=mp.tol)["iters"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    out = torch.empty_like(u)
+    e0.record(stream)
+    ad.momentum_leja_phi1(op, S, out, mp.dt, force_iters=100)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_iter = e0.elapsed_time(e1) / 100
+    flops = 42.0 * N          # 21 FP64 FMA-class operations per unknown (constant advection)
+    tf = flops / (ms_iter * 1e-3) / 1e12
+    op.close()
+    del u, S, out
+    torch.cuda.empty_cache()
+    return {"workload": "momentum-256sq-x32p-dirichlet-circular-midpoint-fp64", "unknowns": N,
+            "value": round(N / (ms * 1e-3) / 1e6, 2), "unit": "Munknown-steps/s",
+            "ms_per_step": round(ms, 4), "leja_iters_per_step": float(np.mean(iters)),
+            "tol": mp.tol, "dt_over_cfl": 100.0,
+            "roofline": {"bound": "alu", "kernel": "mom_iter_k<true>",
+                         "ms_per_iteration": round(ms_iter, 5),
+                         "alg_flops_per_iteration": flops, "achieved": round(tf, 4),
+                         "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                         "frac": round(tf / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                         "peak_note": "of derived FP64 peak; iteration time includes the "
+                                      "host-driven chunk reads of the control block"}}
 
 
 def measure_cn_vs_exp(ad, dev, stream, T_cfl=1000.0):
@@ -708,6 +762,8 @@ def run_ours(args):
         forms["fp32_4096sq"] = measure_fp32_form(ad, dev, stream, flush, args.form_steps)
     if "cn" in wanted:
         forms["cn_vs_exp"] = measure_cn_vs_exp(ad, dev, stream)
+    if "momentum" in wanted:
+        forms["momentum"] = measure_momentum_form(ad, dev, stream)
     if "paper" in wanted:
         forms["paper_cases"] = measure_paper_cases(ad, dev, stream)
     if "batched" in wanted:
