@@ -258,6 +258,25 @@ AD_API int ad_field_features(const ad_grid* grid, const double* Dxx, const doubl
                              const double* Dyy, double max_a, double dt, void* cuda_stream,
                              float* out21);
 
+/* Penalised IMEX step: the alternative to the exponential method that
+ * Section 4 names (penalise the anisotropic diffusion by an isotropic
+ * operator treated implicitly, the rest explicitly).  The paper gives no
+ * formula; this is the first-order IMEX Euler step
+ *   (I - dt beta L)(u+ - u) = dt (A u + S(t)),
+ * L = the operator of Eq. anidiff for D = I, a = 0 (the 5-point Laplacian of
+ * the same flux form and boundary rule), solved by conjugate gradients to a
+ * relative residual cg_tol (at most max_cg iterations; the CG scalars stay on
+ * the device, the host reads the residual every 8 iterations).  The scheme is
+ * stable for beta >= lambda_max(D) / 2; ad_penalty_beta gives max lambda_max(D).
+ * beta = 0 is the explicit Euler step.  AD_FP64 operators only.  On
+ * AD_ERR_NOT_CONVERGED u is left unchanged.  Stats: iters = CG iterations,
+ * err_est = final relative residual. */
+AD_API int ad_penalised_step(ad_operator* op, void* u, double t, double dt, const ad_source* src,
+                             double beta, double cg_tol, int max_cg, ad_stats* stats);
+/* max over cells of the largest eigenvalue of D (device float64 fields). */
+AD_API int ad_penalty_beta(const ad_grid* grid, const double* Dxx, const double* Dxy,
+                           const double* Dyy, void* cuda_stream, double* beta);
+
 /* ---------------------------------------------------------------------
  * Momentum coupling (Eq. cr_full, Section 1).  The paper integrates only the
  * two-dimensional Eq. anidiff and names the momentum terms of Eq. cr_full,

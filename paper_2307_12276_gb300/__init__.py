@@ -70,6 +70,9 @@ _sig = {
     "ad_expquad_step": (_i, [_vp, _vp, _d, _d, _i, C.POINTER(_d), C.POINTER(_Source), _d, _i,
                              C.POINTER(Stats)]),
     "ad_cn_step": (_i, [_vp, _vp, _d, _d, C.POINTER(_Source), _d, _i, _i, C.POINTER(Stats)]),
+    "ad_penalised_step": (_i, [_vp, _vp, _d, _d, C.POINTER(_Source), _d, _d, _i,
+                               C.POINTER(Stats)]),
+    "ad_penalty_beta": (_i, [C.POINTER(_Grid), _vp, _vp, _vp, _vp, C.POINTER(_d)]),
     "ad_profile_leja_iteration": (_i, [_vp, _i, _i, C.POINTER(_d)]),
     "ad_leja_phi1_noalloc": (_i, [C.POINTER(_Grid), _vp, _vp, _vp, _d, _d, _d, _vp, _vp, _d, _d,
                                   _i, _vp, C.POINTER(Stats)]),
@@ -313,6 +316,29 @@ def cn_step(op: Operator, u, t: float, dt: float, source: Optional[Source] = Non
                            force_iters, C.byref(st)), st)
     del keep
     return st.as_dict()
+
+
+def penalised_step(op: Operator, u, t: float, dt: float, source: Optional[Source] = None,
+                   beta: float = 1.0, cg_tol: float = 1e-12, max_cg: int = 2000) -> dict:
+    """ad_penalised_step: one penalised IMEX Euler step (FP64 operators)."""
+    st = Stats()
+    srcs, keep = _source_struct(op, source)
+    _check(_lib.ad_penalised_step(op.handle, op.vec(u, "u"), t, dt,
+                                  C.byref(srcs) if srcs is not None else None, beta, cg_tol,
+                                  max_cg, C.byref(st)), st)
+    del keep
+    return st.as_dict()
+
+
+def penalty_beta(nx: int, ny: int, Dxx, Dxy, Dyy, stream=None) -> float:
+    """ad_penalty_beta: max over cells of lambda_max(D) (float64 device fields)."""
+    g = _Grid(nx, ny, -1.0, 1.0, -1.0, 1.0, 0)
+    n = nx * ny
+    pf = [_ptr(f, "float64", n, name) for f, name in ((Dxx, "Dxx"), (Dxy, "Dxy"), (Dyy, "Dyy"))]
+    b = _d()
+    _check(_lib.ad_penalty_beta(C.byref(g), pf[0], pf[1], pf[2], _stream_ptr(stream),
+                                C.byref(b)))
+    return b.value
 
 
 def profile_leja_iteration(op: Operator, aug: int = 0, reps: int = 200) -> float:

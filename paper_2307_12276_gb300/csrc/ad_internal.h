@@ -191,5 +191,15 @@ void set_error_message(const char* msg);
 // Kernels enqueued from the host by this thread (every launcher adds one);
 // kernels run inside graph loops are counted by the caller.
 long long& launch_counter();
+// ---------------------------------------------------------------- penalised IMEX step
+// One conjugate-gradient iteration on (I - c L) x = b (L: 5-point Laplacian of
+// the flux form with the grid's boundary rule); scal[3] holds <r, r> on entry
+// (set by a reduction of the initial residual) and on exit.
+void penalty_cg_iteration(const GridDev& g, double dx, double dy, double c, double* x, double* r,
+                          double* p, double* Mp, double* partials, int nblocks, double* scal,
+                          cudaStream_t s);
+// partials[b] = min over the block's cells of -lambda_max(D) (reduce with min).
+void neg_lambda_max_partials(long long n, const double* Dxx, const double* Dxy, const double* Dyy,
+                             double* partials, int nblocks, cudaStream_t s);
 
 }  // namespace ad

@@ -972,6 +972,101 @@ int ad_expquad_step(ad_operator* op, void* u, double t, double dt, int s, const 
   return AD_OK;
 }
 
+int ad_penalty_beta(const ad_grid* grid, const double* Dxx, const double* Dxy, const double* Dyy,
+                    void* cuda_stream, double* beta) {
+  g_err.clear();
+  if (!grid || !Dxx || !Dxy || !Dyy || !beta) return fail(AD_ERR_INVALID, "NULL argument");
+  if (grid->nx < 1 || grid->ny < 1) return fail(AD_ERR_INVALID, "grid: nx, ny must be >= 1");
+  for (const void* p : {(const void*)Dxx, (const void*)Dxy, (const void*)Dyy})
+    if (!is_device_ptr(p)) return fail(AD_ERR_INVALID, "D fields must be device pointers");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const long long n = (long long)grid->nx * grid->ny;
+  const int nb = stream_blocks(n);
+  double* buf = nullptr;
+  CUDA_TRY(cudaMalloc((void**)&buf, sizeof(double) * (nb + 1)));
+  neg_lambda_max_partials(n, Dxx, Dxy, Dyy, buf, nb, s);
+  reduce_partials(buf, nb, 1, buf + nb, s);
+  double v = 0.0;
+  const cudaError_t e1 = cudaMemcpyAsync(&v, buf + nb, sizeof(double), cudaMemcpyDeviceToHost, s);
+  const cudaError_t e2 = cudaStreamSynchronize(s);
+  cudaFree(buf);
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AD_ERR_CUDA, "ad_penalty_beta: reduction failed");
+  }
+  *beta = -v;
+  return AD_OK;
+}
+
+int ad_penalised_step(ad_operator* op, void* u, double t, double dt, const ad_source* src,
+                      double beta, double cg_tol, int max_cg, ad_stats* stats) {
+  g_err.clear();
+  if (!op || !u) return fail(AD_ERR_INVALID, "NULL argument");
+  if (op->prec != AD_FP64) return fail(AD_ERR_INVALID, "ad_penalised_step needs an AD_FP64 operator");
+  if (!(dt > 0) || !std::isfinite(dt) || !std::isfinite(t)) return fail(AD_ERR_INVALID, "bad t or dt");
+  if (!(beta >= 0) || !std::isfinite(beta)) return fail(AD_ERR_INVALID, "beta must be finite and >= 0");
+  if (!(cg_tol > 0)) return fail(AD_ERR_INVALID, "cg_tol must be positive");
+  if (max_cg < 1) return fail(AD_ERR_INVALID, "max_cg must be >= 1");
+  Sources S;
+  AD_TRY(fill_sources(src, kMaxSources, &S));
+  for (int k = 0; k < S.n; ++k) S.a[k] = h_at(src, k, t);
+  ad_stats st{};
+  st.converged = 1;
+  st.alpha = op->alpha;
+  st.substeps = 1;
+  const long long l0 = launch_counter();
+  const void* ud_c;
+  AD_TRY(stage_in(op, u, 0, &ud_c, true));
+  void* ud = const_cast<void*>(ud_c);
+  const long long n = op->g.n;
+  double* r = static_cast<double*>(op->T1);
+  double* pdir = static_cast<double*>(op->T2);
+  double* Mp = static_cast<double*>(op->T3);
+  double* x = static_cast<double*>(op->W1);
+  // b = dt (A u + S(t)); x = 0, r = b, p = b
+  apply(op, ud, r, nullptr, S);
+  axpby(0, n, dt, r, 0.0, nullptr, r, op->stream);
+  axpby(0, n, 0.0, nullptr, 0.0, nullptr, x, op->stream);
+  axpby(0, n, 1.0, r, 0.0, nullptr, pdir, op->stream);
+  st.matvecs += 1;
+  norm2_partials(0, n, r, op->partials, op->nblocks, op->stream);
+  reduce_partials(op->partials, op->nblocks, 0, op->dscal + 3, op->stream);
+  CUDA_TRY(cudaMemcpyAsync(op->h_scal, op->dscal + 3, sizeof(double), cudaMemcpyDeviceToHost,
+                           op->stream));
+  CUDA_TRY(cudaStreamSynchronize(op->stream));
+  const double rr0 = op->h_scal[0];
+  double rr = rr0;
+  int it = 0;
+  const double dx = (op->grid.x1 - op->grid.x0) / op->grid.nx;
+  const double dy = (op->grid.y1 - op->grid.y0) / op->grid.ny;
+  const int chunk = 8;                  // CG iterations between host reads of <r, r>
+  while (rr0 > 0.0 && !(std::sqrt(rr) <= cg_tol * std::sqrt(rr0)) && it < max_cg) {
+    const int q = std::min(chunk, max_cg - it);
+    for (int k = 0; k < q; ++k)
+      penalty_cg_iteration(op->g, dx, dy, dt * beta, x, r, pdir, Mp, op->partials, op->nblocks,
+                           op->dscal, op->stream);
+    it += q;
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(op->h_scal, op->dscal + 3, sizeof(double), cudaMemcpyDeviceToHost,
+                             op->stream));
+    CUDA_TRY(cudaStreamSynchronize(op->stream));
+    rr = op->h_scal[0];
+    if (!std::isfinite(rr)) break;
+  }
+  st.iters = it;
+  st.matvecs += it;
+  st.err_est = rr0 > 0.0 ? std::sqrt(rr / rr0) : 0.0;
+  const bool ok = rr0 == 0.0 || std::sqrt(rr) <= cg_tol * std::sqrt(rr0);
+  if (ok) axpby(0, n, 1.0, ud, 1.0, x, ud, op->stream);     // u += delta
+  else st.converged = 0;                                     // u is left unchanged
+  CUDA_TRY(cudaGetLastError());
+  AD_TRY(finish_out(op, u, ud));
+  st.kernel_launches = (int)(launch_counter() - l0);
+  if (stats) *stats = st;
+  if (!ok) return fail(AD_ERR_NOT_CONVERGED, "conjugate gradients did not reach cg_tol");
+  return AD_OK;
+}
+
 int ad_cn_step(ad_operator* op, void* u, double t, double dt, const ad_source* src,
                double gmres_tol, int restart, int force_iters, ad_stats* stats) {
   g_err.clear();
