@@ -353,10 +353,11 @@ def measure_momentum_form(ad, dev, stream, steps=3):
 
 
 def measure_cn_vs_exp(ad, dev, stream, T_cfl=1000.0):
-    """Crank-Nicolson (GMRES) against two-stage exponential quadrature on the
-    512^2 workload, to T = T_cfl Delta t_CFL: the exponential method at 200
-    Delta t_CFL, CN at the largest step (halving from 200) whose error matches
-    it.  Reference: the FP64 GPU path, Gauss nodes, step 12.5 Delta t_CFL,
+    """Crank-Nicolson (GMRES) and the penalised IMEX step (conjugate gradients)
+    against two-stage exponential quadrature on the 512^2 workload, to
+    T = T_cfl Delta t_CFL: the exponential method at 200 Delta t_CFL, CN at the
+    largest step (halving from 200) whose error matches it, the penalised step
+    at 200, 50, 12.5 and 3.125 Delta t_CFL.  Reference: the FP64 GPU path, Gauss nodes, step 12.5 Delta t_CFL,
     tol 1e-12 (its per-step parity with the oracle is pinned by the GPU tests)."""
     import numpy as np
     import torch
@@ -381,6 +382,8 @@ def measure_cn_vs_exp(ad, dev, stream, T_cfl=1000.0):
         for k in range(n):
             if method == "cn":
                 st = ad.cn_step(op, u, k * dt, dt, src, gmres_tol=1e-10, restart=50)
+            elif method == "penalised":
+                st = ad.penalised_step(op, u, k * dt, dt, src, beta=beta, cg_tol=1e-10)
             elif method == "gauss":
                 st = ad.expquad_step(op, u, k * dt, dt, 2, gauss, src, tol=tol)
             else:
@@ -390,6 +393,7 @@ def measure_cn_vs_exp(ad, dev, stream, T_cfl=1000.0):
         torch.cuda.synchronize()
         return u, e0.elapsed_time(e1), it, n
 
+    beta = ad.penalty_beta(g.nx, g.ny, T(p.Dxx), T(p.Dxy), T(p.Dyy), stream=stream)
     ref, _, _, _ = run("gauss", 12.5, tol=1e-12)
     nref = float(torch.linalg.norm(ref))
     ue, ms_e, mv_e, n_e = run("exp", 200.0)
@@ -403,9 +407,16 @@ def measure_cn_vs_exp(ad, dev, stream, T_cfl=1000.0):
         if err_c <= err_e:
             break
         factor /= 2.0
+    # penalised IMEX Euler (first order): step sizes from 200 Delta t_CFL down by 4
+    pen = []
+    for factor in (200.0, 50.0, 12.5, 3.125):
+        up, ms_p, mv_p, n_p = run("penalised", factor)
+        pen.append({"dt_over_cfl": factor, "err": float(torch.linalg.norm(up - ref)) / nref,
+                    "ms": round(ms_p, 3), "matvecs": mv_p})
     op.close()
     best = tried[-1]
     return {"workload": "c1-512sq-dirichlet-circular", "T_over_cfl": T_cfl,
+            "penalised_imex": pen, "penalty_beta": beta,
             "exp": {"dt_over_cfl": 200.0, "steps": n_e, "err": err_e, "ms": round(ms_e, 3),
                     "matvecs": mv_e},
             "cn_tried": tried, "cn_matched": best["err"] <= err_e,
