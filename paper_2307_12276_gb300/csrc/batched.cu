@@ -33,6 +33,7 @@
 #include "leja_host.h"
 #include "tile_f32.cuh"
 #include "tile_f32_ring.cuh"
+#include "tile_f32_pair.cuh"
 
 namespace ad {
 namespace {
@@ -331,6 +332,143 @@ __global__ void __launch_bounds__(kRingThreads, 1)
   }
 }
 
+// Two fused Leja iterations per launch (temporal blocking, tile_f32_pair.cuh)
+// over the flat list of warp tiles (120 produced columns x R rows of one
+// slice).  In pair mode a slice's y_m lives in y buffer (m / 2) & 1, p holds
+// p_{m-1} + pending d_m y_m (added by the next launch or by batch_flush_k).
+// The warp completing a slice's last tile sums the tile partials of both
+// iterations in tile order and applies the stopping rule after iteration m
+// and, if it does not fire, after iteration m + 1.  Eligible batches: every
+// slice with nx % 4 == 0 and ny >= 2, constant or no advection.
+template <int ADV>
+__global__ void __launch_bounds__(kRingThreads, 1)
+    batch_pair_k(const BatchSlice* slices, const int* rtile_slice, int nrtiles, int nslices,
+                 int R, double* tile_partials, unsigned int* bticket, unsigned long long handle,
+                 int has_handle) {
+  extern __shared__ __align__(16) float pair_smem[];
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kRingWarps + (threadIdx.x >> 5);
+  const int GW = gridDim.x * kRingWarps;
+  float* ring = pair_smem + (size_t)(threadIdx.x >> 5) * PairLayout::STAGES * PairLayout::SIZE;
+  for (int tile = gw; tile < nrtiles; tile += GW) {
+    const int s = rtile_slice[tile];
+    const BatchSlice& S = slices[s];
+    const volatile Ctrl* vc = S.a.ctrl;
+    if (vc->stop) continue;                    // uniform over the warp
+    const int m = vc->m;                       // even
+    const LejaCoef lc1 = S.a.lc[m], lc2 = S.a.lc[m + 1];
+    PairCtx X;
+    X.a = &S.a;
+    X.yin = static_cast<const float*>(S.a.y[(m >> 1) & 1]);
+    X.yout = static_cast<float*>(S.a.y[((m >> 1) + 1) & 1]);
+    X.p = static_cast<float*>(S.a.p);
+    X.ring = ring;
+    X.G.nx = S.a.g.nx;
+    X.G.ny = S.a.g.ny;
+    X.G.bc = S.a.g.bc;
+    X.G.n = S.a.g.n;
+    X.G.lane = lane;
+    X.ig = (float)(1.0 / S.a.gamma);
+    X.sh1 = (float)(S.a.c / S.a.gamma + lc1.xi);
+    X.sh2 = (float)(S.a.c / S.a.gamma + lc2.xi);
+    X.d0 = m > 0 ? (float)S.a.lc[m - 1].d : 0.0f;
+    X.d1 = (float)lc1.d;
+    X.d2 = (float)lc2.d;
+    X.abx = S.a.abx;
+    X.aby = S.a.aby;
+    const int local = tile - S.rt_off;
+    const int X0 = (local % S.rt_x) * kPairOwn;
+    X.y0 = (local / S.rt_x) * R;
+    X.y1 = min(S.a.g.ny, X.y0 + R);
+    X.L = pair_lane(X0, lane, X.G.nx, X.G.bc);
+    X.gx = X0 - 4 + 4 * lane;
+    X.fix = X.G.bc != 0 && (X0 == 0 || X0 + kPairOwn >= X.G.nx);
+    float ly1 = 0.f, lp1 = 0.f, ly2 = 0.f, lp2 = 0.f;
+    pair_run<ADV>(X, ly1, lp1, ly2, lp2);
+    double q[4] = {ly1, lp1, ly2, lp2};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) q[k] += __shfl_down_sync(0xffffffffu, q[k], o);
+    int last = 0;
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) tile_partials[4 * tile + k] = q[k];
+      __threadfence();
+      const unsigned int k = atomicAdd(&S.a.ctrl->ticket, 1u);
+      last = (k == (unsigned int)S.rt_n - 1u) ? 1 : 0;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {                                // this slice's last tile: decide for it
+      __threadfence();
+      double t4[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int r = lane; r < S.rt_n; r += 32)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t4[k] += __ldcg(&tile_partials[4 * (S.rt_off + r) + k]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t4[k] += __shfl_down_sync(0xffffffffu, t4[k], o);
+      if (lane == 0) {
+        Ctrl* ctrl = S.a.ctrl;
+        int stop = decide(ctrl, lc1, m, t4[0], t4[1]);
+        if (stop) {
+          ctrl->m = m + 1;                     // p is complete (no pending term)
+        } else {
+          stop = decide(ctrl, lc2, m + 1, t4[2], t4[3]);
+          ctrl->m = m + 2;
+        }
+        ctrl->ticket = 0u;
+        ctrl->stop = stop;
+        __threadfence();
+      }
+    }
+  }
+  if (lane == 0) {
+    __threadfence();
+    const unsigned int k = atomicAdd(bticket, 1u);
+    if (k == (unsigned int)GW - 1u) {
+      __threadfence();
+      int active = 0;
+      for (int s = 0; s < nslices; ++s) active |= !*(volatile int*)&slices[s].a.ctrl->stop;
+      *bticket = 0u;
+      __threadfence();
+      if (has_handle)
+        cudaGraphSetConditional((cudaGraphConditionalHandle)handle, active ? 1u : 0u);
+    }
+  }
+}
+
+// After a pair-mode series: a slice that stopped after an even count m still
+// owes d_m y_m (y_m in buffer (m / 2) & 1).
+__global__ void __launch_bounds__(kThreads) batch_flush_k(const BatchSlice* slices,
+                                                         const int* tile_slice, int ntiles,
+                                                         int TY) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const BatchSlice& S = slices[tile_slice[t]];
+    const int m = S.a.ctrl->m;
+    if (m == 0 || (m & 1)) continue;
+    const GridDev g = S.a.g;
+    const int local = t - S.tile_off;
+    const int x0 = (local % S.tiles_x) * kTileCols, y0 = (local / S.tiles_x) * TY;
+    const int i = x0 + threadIdx.x;
+    if (i >= g.nx) continue;
+    const float d = (float)S.a.lc[m - 1].d;
+    const float* y = static_cast<const float*>(S.a.y[(m >> 1) & 1]);
+    float* p = static_cast<float*>(S.a.p);
+    for (int j = y0; j < min(g.ny, y0 + TY); ++j) {
+      const long long idx = (long long)j * g.nx + i;
+      p[idx] = fmaf(d, y[idx], p[idx]);
+    }
+  }
+}
+
+size_t batch_pair_smem() {
+  return sizeof(float) * (size_t)kRingWarps * PairLayout::STAGES * PairLayout::SIZE;
+}
+
+void* pick_pair(int adv) { return adv == 0 ? (void*)batch_pair_k<0> : (void*)batch_pair_k<1>; }
+
 template <int ADV>
 size_t batch_ring_smem() {
   return sizeof(float) * (size_t)kRingWarps * RingLayout<false, ADV>::STAGES *
@@ -380,6 +518,7 @@ struct ad_batch {
   int nblocks = 608;
   double tuned_ms = 0.0;
   bool ring = false;                  // warp-tile ring iteration (every nx % 4 == 0)
+  bool pair = false;                  // ... two iterations per launch (see batch_pair_k)
   int R = 64;                         // rows per warp tile
   int* d_rtile_slice = nullptr;
   int nrtiles = 0;
@@ -457,7 +596,8 @@ int upload_ring_tiles(ad_batch* b, int R) {
   std::vector<int> ts;
   for (int s = 0; s < b->S; ++s) {
     BatchSlice& hs = b->hs[s];
-    hs.rt_x = (hs.a.g.nx + kVecCols - 1) / kVecCols;
+    const int cols = b->pair ? kPairOwn : kVecCols;
+    hs.rt_x = (hs.a.g.nx + cols - 1) / cols;
     hs.rt_n = hs.rt_x * ((hs.a.g.ny + R - 1) / R);
     hs.rt_off = (int)ts.size();
     for (int k = 0; k < hs.rt_n; ++k) ts.push_back(s);
@@ -468,7 +608,7 @@ int upload_ring_tiles(ad_batch* b, int R) {
     b->d_rtile_slice = nullptr;
     b->d_rpartials = nullptr;
     B_CUDA(cudaMalloc(&b->d_rtile_slice, sizeof(int) * ts.size()));
-    B_CUDA(cudaMalloc(&b->d_rpartials, sizeof(double) * 2 * ts.size()));
+    B_CUDA(cudaMalloc(&b->d_rpartials, sizeof(double) * 4 * ts.size()));
   }
   b->nrtiles = (int)ts.size();
   b->R = R;
@@ -535,11 +675,11 @@ int build_batch_graph(ad_batch* b, int force, double tol) {
     void* rargs[] = {&sl, &rts, &nrt, &S, &R, &rparts, &bt, &hv, &one};
     cudaKernelNodeParams ip = kp;
     if (b->ring) {
-      ip.func = pick_ring(b->adv);
+      ip.func = b->pair ? pick_pair(b->adv) : pick_ring(b->adv);
       ip.kernelParams = rargs;
       ip.blockDim = dim3(kRingThreads);
       ip.gridDim = dim3(ring_grid(b));
-      ip.sharedMemBytes = (unsigned)ring_smem_for(b->adv);
+      ip.sharedMemBytes = (unsigned)(b->pair ? batch_pair_smem() : ring_smem_for(b->adv));
     } else {
       ip.func = (void*)pick_iter(b->adv, TY);
       ip.kernelParams = args;
@@ -551,11 +691,20 @@ int build_batch_graph(ad_batch* b, int force, double tol) {
       prev = nn;
     }
   }
+  cudaGraphNode_t n_before_upd = n_cond;
+  if (b->pair) {                       // the pending last term of even counts
+    cudaGraphNode_t n_flush;
+    void* args[] = {&sl, &ts, &nt, &TY};
+    kp.func = (void*)batch_flush_k;
+    kp.kernelParams = args;
+    B_CUDA(cudaGraphAddKernelNode(&n_flush, g, &n_cond, 1, &kp));
+    n_before_upd = n_flush;
+  }
   {
     void* args[] = {&sl, &ts, &nt, &TY};
     kp.func = (void*)batch_update_k;
     kp.kernelParams = args;
-    B_CUDA(cudaGraphAddKernelNode(&n_upd, g, &n_cond, 1, &kp));
+    B_CUDA(cudaGraphAddKernelNode(&n_upd, g, &n_before_upd, 1, &kp));
   }
   B_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
   b->graph_force = force;
@@ -617,7 +766,8 @@ void write_cache(const std::map<std::string, TuneEntry>& m) {
 std::string tune_key(const ad_batch* b) {
   std::map<std::pair<int, int>, int> sizes;
   for (const auto& s : b->hs) sizes[{s.a.g.nx, s.a.g.ny}]++;
-  std::string k = std::string(b->ring ? "ring" : "tile") + "-f32-adv" + std::to_string(b->adv) +
+  std::string k = std::string(b->pair ? "pair" : (b->ring ? "ring" : "tile")) + "-f32-adv" +
+                  std::to_string(b->adv) +
                   "-S" + std::to_string(b->S);
   for (const auto& kv : sizes)
     k += "-" + std::to_string(kv.first.first) + "x" + std::to_string(kv.first.second) + "*" +
@@ -631,13 +781,13 @@ int time_ring(ad_batch* b, int R, int reps, double* ms_out) {
     const int r = upload_ring_tiles(b, R);
     if (r != AD_OK) return r;
   }
-  int force = reps, maxit = kMaxIters;
+  int force = b->pair ? 2 * reps : reps, maxit = kMaxIters;
   double tol = 0.0;
   const int sgrid = std::min(b->ntiles, b->nblocks);
   batch_init_k<<<sgrid, kThreads, 0, b->stream>>>(b->d_slices, b->d_tile_slice, b->ntiles, b->TY,
                                                   b->S, force, maxit, tol, b->d_bticket);
-  void* fn = pick_ring(b->adv);
-  const size_t smem = ring_smem_for(b->adv);
+  void* fn = b->pair ? pick_pair(b->adv) : pick_ring(b->adv);
+  const size_t smem = b->pair ? batch_pair_smem() : ring_smem_for(b->adv);
   const int grid = ring_grid(b);
   cudaEvent_t e0, e1;
   B_CUDA(cudaEventCreate(&e0));
@@ -765,12 +915,22 @@ int ad_create_batch(ad_operator* const* ops, int nslices, int autotune, ad_batch
     bool aligned = true;
     for (const auto& hs : b->hs) aligned = aligned && hs.a.g.nx % 4 == 0;
     b->ring = aligned && !tile_only;
+    static const bool no_pair = [] {
+      const char* e = getenv("AD_F32_PAIR");             // tuning override: 0 = one iteration
+      return e && e[0] == '0';
+    }();
+    bool rows2 = true;
+    for (const auto& hs : b->hs) rows2 = rows2 && hs.a.g.ny >= 2;
+    b->pair = b->ring && b->adv <= 1 && rows2 && !no_pair;
     if (b->ring) {
       static bool attr = false;
       if (!attr) {
         for (int adv = 0; adv < 3; ++adv)
           cudaFuncSetAttribute(pick_ring(adv), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)ring_smem_for(adv));
+        for (int adv = 0; adv < 2; ++adv)
+          cudaFuncSetAttribute(pick_pair(adv), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)batch_pair_smem());
         attr = true;
       }
     }
@@ -951,8 +1111,9 @@ int ad_batch_midpoint_step(ad_batch* b, void* const* u, double t, double dt,
     // every loop-body run (kBatchUnroll per run, enough runs for the slowest slice)
     int max_it = 0;
     for (int s = 0; s < b->S; ++s) max_it = std::max(max_it, b->h_ctrl[s].iters);
-    const int launches = (int)(launch_counter() - l0) + 3 +
-                         kBatchUnroll * ((max_it + kBatchUnroll - 1) / kBatchUnroll);
+    const int per_run = kBatchUnroll * (b->pair ? 2 : 1);     // iterations per body run
+    const int launches = (int)(launch_counter() - l0) + 3 + (b->pair ? 1 : 0) +
+                         kBatchUnroll * ((max_it + per_run - 1) / per_run);
     for (int s = 0; s < b->S; ++s) per_slice[s].kernel_launches = launches;
   }
   if (status != AD_OK) return bfail(status, "a slice's Leja series reached max_iters");

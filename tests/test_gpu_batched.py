@@ -178,3 +178,94 @@ def test_ring_batch_adaptive_and_tuned(tmp_path, monkeypatch):
                                            lambda t, src=src: src.ravel(), alpha, tol=1e-6)
         assert abs(st[k]["iters"] - ost6.iters) <= 2, (k, st[k]["iters"], ost6.iters)
         assert rel(us[k].cpu().numpy(), ref) <= 1e-5, (k, SIZES_RING[k])
+
+
+# every nx % 4 == 0 and ny >= 2: the two-iteration kernel (batch_pair_k)
+SIZES_PAIR = [(40, 33), (64, 64), (300, 70), (4, 9), (256, 256), (516, 40), (124, 2)]
+
+
+@pytest.mark.parametrize("force", [1, 2, 7, 20])
+def test_pair_batch_forced_matches_oracle(force):
+    """Odd counts stop after the first iteration of a launch; even counts leave
+    d_m y_m to the flush kernel."""
+    need_gpu()
+    slices, ops, batch = _build(sizes=SIZES_PAIR)
+    dt = _dt(slices)
+    us = [devT(s[4], 1) for s in slices]
+    srcs = [ad().Source([devT(s[3], 1)], None) for s in slices]
+    st = ad().batch_midpoint_step(batch, us, 0.0, dt, srcs, force_iters=force)
+    for k, (g, A, alpha, src, u0) in enumerate(slices):
+        ref, _ = integrators.expquad_step(A, u0.ravel(), 0.0, dt, 1, (0.5,),
+                                          lambda t, src=src: src.ravel(), alpha,
+                                          force_iters=force)
+        assert st[k]["iters"] == force
+        assert rel(us[k].cpu().numpy(), ref) <= 1e-5, (k, SIZES_PAIR[k])
+
+
+def test_pair_batch_adaptive_and_unconverged_slice():
+    need_gpu()
+    slices, ops, batch = _build(sizes=SIZES_PAIR)
+    dt = _dt(slices)
+    srcs = [ad().Source([devT(s[3], 1)], None) for s in slices]
+    us = [devT(s[4], 1) for s in slices]
+    st = ad().batch_midpoint_step(batch, us, 0.0, dt, srcs, tol=1e-6)
+    for k, (g, A, alpha, src, u0) in enumerate(slices):
+        ref, _ = integrators.expquad_step(A, u0.ravel(), 0.0, dt, 1, (0.5,),
+                                          lambda t, src=src: src.ravel(), alpha, tol=1e-10)
+        _, ost6 = integrators.expquad_step(A, u0.ravel(), 0.0, dt, 1, (0.5,),
+                                           lambda t, src=src: src.ravel(), alpha, tol=1e-6)
+        assert abs(st[k]["iters"] - ost6.iters) <= 2, (k, st[k]["iters"], ost6.iters)
+        assert rel(us[k].cpu().numpy(), ref) <= 1e-5, (k, SIZES_PAIR[k])
+    bad = 1
+    us = [devT(s[4], 1) for s in slices]
+    us[bad][5] = float("nan")
+    before = us[bad].clone()
+    st = ad().batch_midpoint_step(batch, us, 0.0, dt, srcs, tol=1e-6, raise_not_converged=False)
+    assert [s["converged"] for s in st] == [k != bad for k in range(len(slices))]
+    assert torch.equal(us[bad].view(torch.int32), before.view(torch.int32))
+
+
+PAIR_CHILD = r"""
+import json, sys
+import numpy as np, torch
+sys.path.insert(0, {root!r})
+sys.path.insert(0, {tests!r})
+import test_gpu_batched as tb
+from gpu_util import ad, devT
+slices, ops, batch = tb._build(sizes=tb.SIZES_PAIR)
+dt = tb._dt(slices)
+srcs = [ad().Source([devT(s[3], 1)], None) for s in slices]
+out, stats = {{}}, {{}}
+for key, kw in (("f7", dict(force_iters=7)), ("f8", dict(force_iters=8)), ("tol", dict(tol=1e-6))):
+    us = [devT(s[4], 1) for s in slices]
+    st = ad().batch_midpoint_step(batch, us, 0.0, dt, srcs, **kw)
+    stats[key] = [s["iters"] for s in st]
+    for k, u in enumerate(us):
+        out["%s_%d" % (key, k)] = u.cpu().numpy()
+np.savez({prefix!r}, **out)
+print(json.dumps(stats))
+"""
+
+
+def test_pair_batch_equals_ring_batch(tmp_path):
+    """The two-iteration batch kernel forms every entry as the one-iteration
+    ring kernel does (AD_F32_PAIR=0): with equal counts, identical results."""
+    need_gpu()
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = {}
+    for tag, env_extra in (("pair", {}), ("ring", {"AD_F32_PAIR": "0"})):
+        env = dict(os.environ)
+        env.update(env_extra)
+        env["AD_AUTOTUNE_CACHE"] = str(tmp_path / f"tune_{tag}.json")
+        prefix = str(tmp_path / tag)
+        code = PAIR_CHILD.format(root=root, tests=os.path.join(root, "tests"), prefix=prefix)
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        res[tag] = (json.loads(r.stdout.strip().splitlines()[-1]), np.load(prefix + ".npz"))
+    (sp, ap), (sr, ar) = res["pair"], res["ring"]
+    assert sp == sr
+    for key in ar.files:
+        assert np.array_equal(ap[key], ar[key]), key
