@@ -232,6 +232,7 @@ F64_SERIES_SOURCES = ("persistent_f64.cu", "ad_internal.h")
 F32_ITER_SOURCES = ("stencil_kernels.cu", "tile_f32.cuh", "tile_f32_vec.cuh", "tile_f32_ring.cuh",
                     "ad_internal.h")
 F32_PAIR_SOURCES = F32_ITER_SOURCES + ("tile_f32_pair.cuh",)
+MOM_SOURCES = ("momentum.cu", "series_finish.cuh", "tile_f32.cuh", "ad_internal.h")
 
 
 # --------------------------------------------------------------------------- ours
@@ -347,7 +348,8 @@ def measure_momentum_form(ad, dev, stream, steps=3):
                          "ms_per_iteration": round(ms_iter, 5),
                          "alg_flops_per_iteration": flops, "achieved": round(tf, 4),
                          "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-                         "frac": round(tf / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                         "frac": round(tf / FP64_PEAK_TFLOPS, 4),
+                         "traffic": traffic_per_launch(MOM_SOURCES, "mom_iter_256sq_x32p.md"),
                          "peak_note": "of derived FP64 peak; iteration time includes the "
                                       "host-driven chunk reads of the control block"}}
 
