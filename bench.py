@@ -756,6 +756,8 @@ def run_ours(args):
     traffic = None
     if kernel == "leja_nsync_f64_k":
         traffic = traffic_per_launch(F64_SERIES_SOURCES, "leja_nsync_f64_512sq.md")
+    elif kernel == "leja_tile_f64_k":
+        traffic = traffic_per_launch(F64_SERIES_SOURCES, "leja_tile_f64_512sq.md")
     roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
             "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
             "traffic": traffic, "kernel": f"{kernel}<aug>",

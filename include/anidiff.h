@@ -353,7 +353,8 @@ AD_API int ad_profile_leja_iteration(ad_operator* op, int aug, int reps, double*
  * returns the totals since the last enable: milliseconds, number of series
  * and their total Leja iterations, and (kernel may be NULL) the path of the
  * last timed series: 1 persistent kernel with a grid barrier per iteration,
- * 2 persistent kernel with neighbour synchronisation, 3 graph loop of
+ * 2 persistent kernel with neighbour synchronisation (row ranges), 7 the same
+ * on 2-D tiles, 3 graph loop of
  * per-iteration kernels, 4 host-driven per-iteration launches, 5 and 6 the
  * same with the FP32 two-iteration kernel, 0 none yet.
  * Recording adds two event records and no synchronisation (each series

@@ -652,11 +652,300 @@ __global__ void __launch_bounds__(256) leja_nsync_f64_k(SeriesArgs a, NsyncGeom 
   }
 }
 
+// ---------------------------------------------------------------- 2-D tile kernel
+// leja_tile_f64_k: the protocol of leja_nsync_f64_k (neighbour flags,
+// write-once norm slots, the decision two iterations late, bounded waits) on
+// a 2-D decomposition.  Block b owns a tile of tw x th cells (TX x TY tiles
+// cover the grid; the last column and row of tiles may be smaller).  Its
+// window holds y on the tile plus a one-cell halo ring, (tw + 2) x (th + 2)
+// values per buffer, so every stencil offset is constant (the halo carries the
+// wrapped values, or zeros outside a zero-Dirichlet domain where the folded
+// weights are 0).  Only the tile's outer ring ("ring cells") depends on other
+// blocks; the interior -- most of the tile, unlike the row kernel whose
+// cells within one grid row of either end all wait for the halo -- is
+// computed while warp 1 waits for the up to 8 neighbours and copies the halo.
+// Ring cells are also stored to global y_{m+1}, where the neighbours read them.
+struct TileGeom {
+  int TX, TY;   // tiles per grid row / column (G = TX * TY)
+  int tw, th;   // tile width / height (full tiles)
+  int S;        // window row stride, tw + 2
+};
+
+// tile-local (li, lj) of ring cell q of a tw x th tile
+__device__ __forceinline__ void ring_cell(int q, int tw, int th, int& li, int& lj) {
+  if (q < tw) { li = q; lj = 0; return; }
+  if (th > 1 && q < 2 * tw) { li = q - tw; lj = th - 1; return; }
+  const int r = q - (th > 1 ? 2 * tw : tw);
+  if (r < th - 2) { li = 0; lj = 1 + r; } else { li = tw - 1; lj = 1 + r - (th - 2); }
+}
+
+// halo position q of a tw x th tile: (hx, hy) in the ring around it
+__device__ __forceinline__ void halo_cell(int q, int tw, int th, int& hx, int& hy) {
+  if (q < tw + 2) { hx = q - 1; hy = -1; return; }
+  if (q < 2 * (tw + 2)) { hx = q - (tw + 2) - 1; hy = th; return; }
+  const int r = q - 2 * (tw + 2);
+  if (r < th) { hx = -1; hy = r; } else { hx = tw; hy = r - th; }
+}
+
+template <bool AUG>
+__global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom geo, double* slots,
+                                                       unsigned int* flags, unsigned int* gen) {
+  extern __shared__ double smem[];
+  __shared__ double ra[256], rb[256];
+  __shared__ int s_nb[8];
+  __shared__ int s_nnb, s_final, s_status, s_fail;
+  __shared__ double s_ty, s_tp;
+  const GridDev g = a.g;
+  const int n = (int)g.n, nx = g.nx, ny = g.ny;
+  const bool periodic = g.bc == 0;
+  const int G = gridDim.x, b = blockIdx.x, T = blockDim.x, t = threadIdx.x;
+  const int warp = t >> 5, lane = t & 31, nwarps = T >> 5;
+  const int bx = b % geo.TX, by = b / geo.TX;
+  const int x0 = bx * geo.tw, y0 = by * geo.th;
+  const int tw = min(geo.tw, nx - x0), th = min(geo.th, ny - y0);
+  const int nc = tw * th;
+  const int cpb = geo.tw * geo.th;                 // plane stride of the resident data
+  const int S = geo.S;
+  const int WB = S * (geo.th + 2);                 // one window buffer
+  const int nI = (tw > 2 && th > 2) ? (tw - 2) * (th - 2) : 0;
+  const int nR = nc - nI;
+  const int nH = 2 * (tw + 2) + 2 * th;
+  const int poll_warp = nwarps >= 2 ? 1 : 0;
+  const int wA = nwarps >= 3 ? warp - 2 : warp, nwA = nwarps >= 3 ? nwarps - 2 : nwarps;
+  double* sW = smem;                        // [9][cpb] scaled weights
+  double* sP = sW + 9 * cpb;                // [2][cpb]: P after iteration k in buffer (k + 1) & 1
+  double* sW2 = sP + 2 * cpb;               // [cpb] (augmented)
+  double* win = sW2 + (AUG ? cpb : 0);      // [2][WB]: y_m lives in buffer m & 1
+  const double* __restrict__ Ws = static_cast<const double*>(a.coef);
+  const double* __restrict__ w1 = static_cast<const double*>(a.w1);
+  const double* __restrict__ w2 = static_cast<const double*>(a.w2);
+  Ctrl* ctrl = a.ctrl;
+  const int force = ctrl->force;
+  const int max_it = min(ctrl->max_iters, kMaxIters);
+  const double tol = ctrl->tol;
+  auto gidx = [&](int li, int lj) { return (y0 + lj) * nx + x0 + li; };
+  auto widx = [&](int li, int lj) { return (lj + 1) * S + li + 1; };
+
+  // ---- reset this block's slots and flag, load the resident data
+  for (int k = t; k < kMaxIters; k += T) {
+    double* s2 = slots + 2LL * ((long long)k * kNsyncMaxBlocks + b);
+    reinterpret_cast<unsigned long long*>(s2)[0] = kSlotEmpty;
+    reinterpret_cast<unsigned long long*>(s2)[1] = kSlotEmpty;
+  }
+  if (t == 0) {
+    flags[b] = 0u;
+    s_fail = 0;
+    int cnt = 0;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (dx == 0 && dy == 0) continue;
+        int tx = bx + dx, ty = by + dy;
+        if (periodic) {
+          tx = (tx + geo.TX) % geo.TX;
+          ty = (ty + geo.TY) % geo.TY;
+        } else if (tx < 0 || ty < 0 || tx >= geo.TX || ty >= geo.TY) {
+          continue;
+        }
+        const int nb = ty * geo.TX + tx;
+        bool seen = nb == b;
+        for (int q = 0; q < cnt; ++q) seen = seen || s_nb[q] == nb;
+        if (!seen) s_nb[cnt++] = nb;
+      }
+    s_nnb = cnt;
+  }
+  for (int k = t; k < nc; k += T) {
+    const int li = k % tw, lj = k / tw;
+    const int idx = gidx(li, lj);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) sW[q * cpb + k] = Ws[(long long)q * n + idx];
+    sP[k] = static_cast<const double*>(a.p)[idx];
+    if (AUG) sW2[k] = w2[idx];
+  }
+  {  // both window buffers zero (the Dirichlet halo stays 0), then y_0 on tile + halo
+    for (int q = t; q < 2 * WB; q += T) win[q] = 0.0;
+    __syncthreads();
+    const double* y0g = static_cast<const double*>(a.y[0]);
+    for (int k = t; k < nc; k += T) win[widx(k % tw, k / tw)] = y0g[gidx(k % tw, k / tw)];
+    for (int q = t; q < nH; q += T) {
+      int hx, hy;
+      halo_cell(q, tw, th, hx, hy);
+      int gx = x0 + hx, gy = y0 + hy;
+      if (periodic) {
+        gx = (gx + nx) % nx;
+        gy = (gy + ny) % ny;
+      } else if (gx < 0 || gy < 0 || gx >= nx || gy >= ny) {
+        continue;
+      }
+      win[(hy + 1) * S + hx + 1] = y0g[gy * nx + gx];
+    }
+  }
+  // ---- one grid barrier: no block reads a slot or flag before its owner reset it
+  __threadfence();
+  __syncthreads();
+  if (t == 0) {
+    const unsigned int my_gen = *(volatile unsigned int*)gen;
+    __threadfence();
+    const unsigned int tk = atomicAdd(&ctrl->ticket, 1u);
+    if (tk == (unsigned int)G - 1) {
+      ctrl->ticket = 0u;
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*(volatile unsigned int*)gen == my_gen) {
+        if (global_ns() - t0 > kBarrierTimeoutNs) { s_fail = 1; break; }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+
+  int m = 0;
+  int fin = -1;
+  if (!s_fail) {
+    for (;;) {
+      const LejaCoef lc = a.lc[m];
+      const double* wy = win + (m & 1) * WB;
+      double* wz = win + ((m + 1) & 1) * WB;
+      // ---- phase A
+      if (warp == 0) {                              // the lagged decisions
+        int f = -1, st = 0;
+        double ty = 0.0, tp = 0.0;
+        bool ok = true;
+        if (force <= 0 && m >= 2) {                 // norm test on iteration m - 2
+          ok = nsync_read_norms(slots, m - 2, G, ty, tp);
+          const int r = nsync_test(a.lc[m - 2], m - 1, tol, ty, tp);
+          if (ok && r >= 0) { f = m - 2; st = r; }
+        }
+        if (ok && f < 0 && m >= 1) {                // count-based stop after iteration m - 1
+          const bool cnt = (force > 0 ? m >= force : m >= max_it) || m >= kMaxIters;
+          if (cnt) {
+            f = m - 1;
+            if (b == 0) {                           // norms for the report (block 0 only)
+              ok = nsync_read_norms(slots, m - 1, G, ty, tp);
+              if (force <= 0) {
+                const int r = nsync_test(a.lc[m - 1], m, tol, ty, tp);
+                st = r == 0 ? 0 : 3;
+              }
+            }
+          }
+        }
+        if (lane == 0) {
+          s_final = f;
+          s_status = st;
+          s_ty = ty;
+          s_tp = tp;
+          if (!ok) s_fail = 1;
+        }
+      }
+      if (warp == poll_warp && m >= 1) {            // neighbours, then the halo of y_m
+        if (lane < s_nnb) {
+          const unsigned int* fl = flags + s_nb[lane];
+          if (*(const volatile unsigned int*)fl < (unsigned int)m) {
+            const unsigned long long t0 = global_ns();
+            while (*(const volatile unsigned int*)fl < (unsigned int)m) {
+              if (global_ns() - t0 > kBarrierTimeoutNs) { s_fail = 1; break; }
+            }
+          }
+          __threadfence();
+        }
+        __syncwarp();
+        const double* yg = static_cast<const double*>(a.y[m & 1]);
+        double* wh = win + (m & 1) * WB;
+        for (int q = lane; q < nH; q += 32) {
+          int hx, hy;
+          halo_cell(q, tw, th, hx, hy);
+          int gx = x0 + hx, gy = y0 + hy;
+          if (periodic) {
+            gx = (gx + nx) % nx;
+            gy = (gy + ny) % ny;
+          } else if (gx < 0 || gy < 0 || gx >= nx || gy >= ny) {
+            continue;
+          }
+          cp_async8(wh + (hy + 1) * S + hx + 1, yg + gy * nx + gx);
+        }
+        cp_async_wait_all();
+      }
+      if (warp >= 2 || nwarps < 3) {                // interior cells (own data only)
+        for (int q = wA * 32 + lane; q < nI; q += nwA * 32) {
+          const int li = 1 + q % (tw - 2), lj = 1 + q / (tw - 2);
+          const int k = lj * tw + li;
+          const int w = widx(li, lj);
+          const int idx = gidx(li, lj);
+          const Nb9 y = gather9(wy + w, -1, 1, -S, S);
+          wz[w] = f64_cell<AUG>(sW, cpb, k, y, lc, AUG ? sW2[k] : 0.0, w1, idx);
+        }
+      }
+      __syncthreads();
+      if (s_fail || s_final >= 0) break;
+      // ---- phase C: ring cells, into the window and global y_{m+1}
+      double* yout = static_cast<double*>(a.y[(m + 1) & 1]);
+      for (int q = t; q < nR; q += T) {
+        int li, lj;
+        ring_cell(q, tw, th, li, lj);
+        const int k = lj * tw + li;
+        const int w = widx(li, lj);
+        const int idx = gidx(li, lj);
+        const Nb9 y = gather9(wy + w, -1, 1, -S, S);
+        const double z = f64_cell<AUG>(sW, cpb, k, y, lc, AUG ? sW2[k] : 0.0, w1, idx);
+        wz[w] = z;
+        __stcg(yout + idx, z);
+      }
+      __syncthreads();
+      if (t == 0) {
+        __threadfence();
+        *(volatile unsigned int*)(flags + b) = (unsigned int)(m + 1);
+      }
+      // ---- phase D: p and the norms
+      const double* Pin = sP + (m & 1) * cpb;
+      double* Pout = sP + ((m + 1) & 1) * cpb;
+      double sy = 0.0, sp = 0.0;
+      for (int k = t; k < nc; k += T) {
+        const double z = wz[widx(k % tw, k / tw)];
+        const double pn = fma(lc.d, z, Pin[k]);
+        Pout[k] = pn;
+        sy = fma(z, z, sy);
+        sp = fma(pn, pn, sp);
+      }
+      block_tree_sum2(sy, sp, ra, rb);
+      if (t == 0) {                                 // the slot value itself is the signal
+        double* s2 = slots + 2LL * ((long long)m * kNsyncMaxBlocks + b);
+        s2[0] = sy;
+        s2[1] = sp;
+      }
+      ++m;
+    }
+    fin = s_final;
+  }
+  if (s_fail) {
+    if (t == 0) {
+      atomicMax(&ctrl->status, 4);           // AD_ERR_TIMEOUT
+      ctrl->stop = 1;
+    }
+    return;
+  }
+  const double* Pf = sP + ((fin + 1) & 1) * cpb;
+  double* p = static_cast<double*>(a.p);
+  for (int k = t; k < nc; k += T) p[gidx(k % tw, k / tw)] = Pf[k];
+  if (b == 0 && t == 0) {
+    ctrl->iters = fin + 1;
+    ctrl->m = fin + 1;
+    ctrl->ynorm2 = s_ty;
+    ctrl->pnorm2 = s_tp;
+    ctrl->err_est = a.lc[fin].absd;
+    atomicMax(&ctrl->status, s_status);
+    ctrl->stop = 1;
+  }
+}
+
 }  // namespace
 
-// Cooperative persistent series (FP64).  Returns 2 (neighbour-synchronised
-// kernel) or 1 (grid-barrier kernel) when launched, 0 when the grid is too
-// large or the launch is refused (the caller then uses the per-iteration path).
+// Cooperative persistent series (FP64).  Returns 7 (2-D tile kernel), 2 (row
+// kernel with neighbour synchronisation) or 1 (grid-barrier kernel) when
+// launched, 0 when the grid is too large or the launch is refused (the caller
+// then uses the per-iteration path).  AD_F64_KERNEL=row selects the row
+// kernel, AD_NO_NSYNC the grid-barrier kernel (tuning and A/B overrides).
 int series_run_persistent(const SeriesArgs& a, unsigned int* gen, const NsyncScratch* ns,
                           cudaStream_t s) {
   if (a.prec != 0 || a.g.n > kPersistMaxCells) return 0;
@@ -686,6 +975,64 @@ int series_run_persistent(const SeriesArgs& a, unsigned int* gen, const NsyncScr
     if (ok) ++launch_counter();
     return ok;
   };
+  static const bool row_kernel = [] {
+    const char* e = getenv("AD_F64_KERNEL");
+    return e && e[0] == 'r';
+  }();
+  if (ns && ns->slots && ns->flags && !no_nsync && !row_kernel) {
+    // tiles: the fewest cells per block (most blocks), then the shortest perimeter
+    const int nx = a.g.nx, ny = a.g.ny;
+    TileGeom best{};
+    long long best_cells = -1;
+    int best_G = 0;
+    for (int TX = 1; TX <= std::min(nx, 152); ++TX) {
+      const int tw = (nx + TX - 1) / TX;
+      const int TXa = (nx + tw - 1) / tw;
+      const int TY = std::min(ny, 152 / TX);
+      if (TY < 1) break;
+      const int th = (ny + TY - 1) / TY;
+      const int TYa = (ny + th - 1) / th;
+      const int Ga = TXa * TYa;
+      if (Ga > kNsyncMaxBlocks) continue;
+      const long long cells = (long long)tw * th;
+      const size_t smem_t =
+          sizeof(double) * ((size_t)cells * (a.aug ? 12 : 11) + 2 * (size_t)(tw + 2) * (th + 2));
+      if (smem_t + 8 * 1024 > (size_t)optin) continue;
+      const bool better = best_cells < 0 || cells < best_cells ||
+                          (cells == best_cells && tw + th < best.tw + best.th);
+      if (better) {
+        best = TileGeom{TXa, TYa, tw, th, tw + 2};
+        best_cells = cells;
+        best_G = Ga;
+      }
+    }
+    if (best_cells > 0) {
+      const size_t smem = sizeof(double) * ((size_t)best_cells * (a.aug ? 12 : 11) +
+                                            2 * (size_t)best.S * (best.th + 2));
+      void* fn = a.aug ? (void*)leja_tile_f64_k<true> : (void*)leja_tile_f64_k<false>;
+      SeriesArgs targs = a;
+      targs.nblocks = best_G;
+      double* slots = ns->slots;
+      unsigned int* flags = ns->flags;
+      void* params[] = {&targs, &best, &slots, &flags, &gen};
+      cudaFuncAttributes fa{};
+      int per_sm = 0;
+      const bool ok =
+          cudaFuncGetAttributes(&fa, fn) == cudaSuccess &&
+          smem + fa.sharedSizeBytes <= (size_t)optin &&
+          cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+              cudaSuccess &&
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem) == cudaSuccess &&
+          (long long)per_sm * sms >= best_G &&
+          cudaLaunchCooperativeKernel(fn, dim3(best_G), dim3(256), params, smem, s) ==
+              cudaSuccess;
+      if (!ok) cudaGetLastError();
+      if (ok) {
+        ++launch_counter();
+        return 7;
+      }
+    }
+  }
   if (ns && ns->slots && ns->flags && !no_nsync && G <= kNsyncMaxBlocks) {
     NsyncGeom geo;
     geo.cpb = (int)cpb;

@@ -77,12 +77,29 @@ def _run(case, prefix, env_extra):
 @pytest.mark.parametrize("case", CASES)
 def test_neighbour_sync_kernel_equals_grid_barrier_kernel(case, tmp_path):
     need_gpu()
-    s_new, phi_new, u_new = _run(case, str(tmp_path / "nsync"), {})
+    s_new, phi_new, u_new = _run(case, str(tmp_path / "nsync"), {"AD_F64_KERNEL": "row"})
     s_old, phi_old, u_old = _run(case, str(tmp_path / "grid"), {"AD_NO_NSYNC": "1"})
     for key in ("phi", "step"):
         assert s_new[key]["iters"] == s_old[key]["iters"], (key, s_new[key], s_old[key])
         assert s_new[key]["converged"] == s_old[key]["converged"]
         assert s_new[key]["err_est"] == s_old[key]["err_est"]
+    assert np.array_equal(phi_new, phi_old)
+    assert np.array_equal(u_new, u_old)
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_tile_kernel_equals_grid_barrier_kernel(case, tmp_path):
+    """The 2-D tile kernel (default) forms every entry as the grid-barrier
+    kernel does; its norm sums run over another cell-to-block assignment, so
+    the error estimates agree to rounding."""
+    need_gpu()
+    s_new, phi_new, u_new = _run(case, str(tmp_path / "tile"), {})
+    s_old, phi_old, u_old = _run(case, str(tmp_path / "grid"), {"AD_NO_NSYNC": "1"})
+    for key in ("phi", "step"):
+        assert s_new[key]["iters"] == s_old[key]["iters"], (key, s_new[key], s_old[key])
+        assert s_new[key]["converged"] == s_old[key]["converged"]
+        assert s_new[key]["err_est"] == pytest.approx(s_old[key]["err_est"], rel=1e-12,
+                                                      abs=1e-300)
     assert np.array_equal(phi_new, phi_old)
     assert np.array_equal(u_new, u_old)
 
@@ -105,7 +122,7 @@ def test_series_timing_counts_every_series():
     assert t["series"] == st["substeps"]
     assert t["iters"] == st["iters"]
     assert t["ms"] > 0.0
-    assert t["kernel"] == "leja_nsync_f64_k"
+    assert t["kernel"] == "leja_tile_f64_k"
     ad().time_series(op, False)
     ad().expquad_step(op, u, p.dt, p.dt, 2, (1 / 3, 2 / 3), src, tol=1e-10)
     assert ad().series_timing(op) == t
