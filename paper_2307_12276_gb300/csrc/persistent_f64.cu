@@ -665,6 +665,11 @@ __global__ void __launch_bounds__(256) leja_nsync_f64_k(SeriesArgs a, NsyncGeom 
 // cells within one grid row of either end all wait for the halo -- is
 // computed while warp 1 waits for the up to 8 neighbours and copies the halo.
 // Ring cells are also stored to global y_{m+1}, where the neighbours read them.
+// p and the two squared norms are formed with z, cell by cell, in both compute
+// phases (no separate pass): three p buffers keep the result that the lagged
+// decision may still return (P after iteration m - 2) out of the way.  After
+// the ring cells, thread 0 adds the per-warp norm sums in warp order, writes
+// the slot (m, b) and then publishes flags[b] = m + 1.
 struct TileGeom {
   int TX, TY;   // tiles per grid row / column (G = TX * TY)
   int tw, th;   // tile width / height (full tiles)
@@ -691,7 +696,7 @@ template <bool AUG>
 __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom geo, double* slots,
                                                        unsigned int* flags, unsigned int* gen) {
   extern __shared__ double smem[];
-  __shared__ double ra[256], rb[256];
+  __shared__ double s_wy[8], s_wp[8];        // per-warp norm partials
   __shared__ int s_nb[8];
   __shared__ int s_nnb, s_final, s_status, s_fail;
   __shared__ double s_ty, s_tp;
@@ -713,8 +718,8 @@ __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom ge
   const int poll_warp = nwarps >= 2 ? 1 : 0;
   const int wA = nwarps >= 3 ? warp - 2 : warp, nwA = nwarps >= 3 ? nwarps - 2 : nwarps;
   double* sW = smem;                        // [9][cpb] scaled weights
-  double* sP = sW + 9 * cpb;                // [2][cpb]: P after iteration k in buffer (k + 1) & 1
-  double* sW2 = sP + 2 * cpb;               // [cpb] (augmented)
+  double* sP = sW + 9 * cpb;                // [3][cpb]: P after iteration k in buffer (k + 1) % 3
+  double* sW2 = sP + 3 * cpb;               // [cpb] (augmented)
   double* win = sW2 + (AUG ? cpb : 0);      // [2][WB]: y_m lives in buffer m & 1
   const double* __restrict__ Ws = static_cast<const double*>(a.coef);
   const double* __restrict__ w1 = static_cast<const double*>(a.w1);
@@ -808,6 +813,13 @@ __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom ge
       const LejaCoef lc = a.lc[m];
       const double* wy = win + (m & 1) * WB;
       double* wz = win + ((m + 1) & 1) * WB;
+      // p of iteration m is formed with z, cell by cell: P after iteration
+      // m - 1 in buffer m % 3, after iteration m into (m + 1) % 3.  The lagged
+      // decision of this iteration may still return P after iteration m - 2,
+      // in the third buffer, which nothing here overwrites.
+      const double* Pin = sP + (m % 3) * cpb;
+      double* Pout = sP + ((m + 1) % 3) * cpb;
+      double sy = 0.0, sp = 0.0;
       // ---- phase A
       if (warp == 0) {                              // the lagged decisions
         int f = -1, st = 0;
@@ -874,7 +886,12 @@ __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom ge
           const int w = widx(li, lj);
           const int idx = gidx(li, lj);
           const Nb9 y = gather9(wy + w, -1, 1, -S, S);
-          wz[w] = f64_cell<AUG>(sW, cpb, k, y, lc, AUG ? sW2[k] : 0.0, w1, idx);
+          const double z = f64_cell<AUG>(sW, cpb, k, y, lc, AUG ? sW2[k] : 0.0, w1, idx);
+          wz[w] = z;
+          const double pn = fma(lc.d, z, Pin[k]);
+          Pout[k] = pn;
+          sy = fma(z, z, sy);
+          sp = fma(pn, pn, sp);
         }
       }
       __syncthreads();
@@ -891,28 +908,34 @@ __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom ge
         const double z = f64_cell<AUG>(sW, cpb, k, y, lc, AUG ? sW2[k] : 0.0, w1, idx);
         wz[w] = z;
         __stcg(yout + idx, z);
-      }
-      __syncthreads();
-      if (t == 0) {
-        __threadfence();
-        *(volatile unsigned int*)(flags + b) = (unsigned int)(m + 1);
-      }
-      // ---- phase D: p and the norms
-      const double* Pin = sP + (m & 1) * cpb;
-      double* Pout = sP + ((m + 1) & 1) * cpb;
-      double sy = 0.0, sp = 0.0;
-      for (int k = t; k < nc; k += T) {
-        const double z = wz[widx(k % tw, k / tw)];
         const double pn = fma(lc.d, z, Pin[k]);
         Pout[k] = pn;
         sy = fma(z, z, sy);
         sp = fma(pn, pn, sp);
       }
-      block_tree_sum2(sy, sp, ra, rb);
-      if (t == 0) {                                 // the slot value itself is the signal
+      // block sums: a shuffle tree per warp, then thread 0 adds the warp sums
+      // in warp order and writes the slot (m, b) before the flag
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sp += __shfl_xor_sync(0xffffffffu, sp, o);
+      }
+      if (lane == 0) {
+        s_wy[warp] = sy;
+        s_wp[warp] = sp;
+      }
+      __syncthreads();
+      if (t == 0) {
+        double ty = 0.0, tp = 0.0;
+        for (int q = 0; q < nwarps; ++q) {
+          ty += s_wy[q];
+          tp += s_wp[q];
+        }
         double* s2 = slots + 2LL * ((long long)m * kNsyncMaxBlocks + b);
-        s2[0] = sy;
-        s2[1] = sp;
+        s2[0] = ty;                                 // the slot value itself is the signal
+        s2[1] = tp;
+        __threadfence();
+        *(volatile unsigned int*)(flags + b) = (unsigned int)(m + 1);
       }
       ++m;
     }
@@ -925,7 +948,7 @@ __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom ge
     }
     return;
   }
-  const double* Pf = sP + ((fin + 1) & 1) * cpb;
+  const double* Pf = sP + ((fin + 1) % 3) * cpb;
   double* p = static_cast<double*>(a.p);
   for (int k = t; k < nc; k += T) p[gidx(k % tw, k / tw)] = Pf[k];
   if (b == 0 && t == 0) {
@@ -996,7 +1019,7 @@ int series_run_persistent(const SeriesArgs& a, unsigned int* gen, const NsyncScr
       if (Ga > kNsyncMaxBlocks) continue;
       const long long cells = (long long)tw * th;
       const size_t smem_t =
-          sizeof(double) * ((size_t)cells * (a.aug ? 12 : 11) + 2 * (size_t)(tw + 2) * (th + 2));
+          sizeof(double) * ((size_t)cells * (a.aug ? 13 : 12) + 2 * (size_t)(tw + 2) * (th + 2));
       if (smem_t + 8 * 1024 > (size_t)optin) continue;
       const bool better = best_cells < 0 || cells < best_cells ||
                           (cells == best_cells && tw + th < best.tw + best.th);
@@ -1007,7 +1030,7 @@ int series_run_persistent(const SeriesArgs& a, unsigned int* gen, const NsyncScr
       }
     }
     if (best_cells > 0) {
-      const size_t smem = sizeof(double) * ((size_t)best_cells * (a.aug ? 12 : 11) +
+      const size_t smem = sizeof(double) * ((size_t)best_cells * (a.aug ? 13 : 12) +
                                             2 * (size_t)best.S * (best.th + 2));
       void* fn = a.aug ? (void*)leja_tile_f64_k<true> : (void*)leja_tile_f64_k<false>;
       SeriesArgs targs = a;
