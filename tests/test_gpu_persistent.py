@@ -1,10 +1,10 @@
-"""The two persistent FP64 series kernels agree bit for bit.
+"""The three persistent FP64 series kernels agree bit for bit.
 
 Small FP64 grids run a whole Newton series in one cooperative launch.  The
-default kernel synchronises each block with its neighbours only and applies
-the stopping rule two iterations late (dropping the extra iteration); the
-grid-barrier kernel (selected with AD_NO_NSYNC) decides after every
-iteration.  Both sum the same terms in the same order, so results, iteration
+default kernel (2-D tiles) and the row kernel (AD_F64_KERNEL=row) synchronise
+each block with its neighbours only and apply the stopping rule two
+iterations late (dropping the extra iteration); the grid-barrier kernel
+(selected with AD_NO_NSYNC) decides after every iteration.  Both sum the same terms in the same order, so results, iteration
 counts and norms must be identical, not merely close.  Accuracy against the
 oracle is covered by the parity tests, which run the default kernel.
 
