@@ -4,9 +4,13 @@ Small FP64 grids run a whole Newton series in one cooperative launch.  The
 default kernel (2-D tiles) and the row kernel (AD_F64_KERNEL=row) synchronise
 each block with its neighbours only and apply the stopping rule two
 iterations late (dropping the extra iteration); the grid-barrier kernel
-(selected with AD_NO_NSYNC) decides after every iteration.  Both sum the same terms in the same order, so results, iteration
-counts and norms must be identical, not merely close.  Accuracy against the
-oracle is covered by the parity tests, which run the default kernel.
+(selected with AD_NO_NSYNC) decides after every iteration.  All three form
+every entry of the result by the same operations, so results and iteration
+counts must be identical, not merely close; the row and grid kernels also sum
+the norms in the same order (identical error estimates), the tile kernel over
+another cell-to-block assignment (estimates equal to rounding).  Accuracy
+against the oracle is covered by the parity tests, which run the default
+kernel.
 
 Also checks the series timing counters against the step statistics.
 """
