@@ -967,8 +967,9 @@ __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom ge
 // Cooperative persistent series (FP64).  Returns 7 (2-D tile kernel), 2 (row
 // kernel with neighbour synchronisation) or 1 (grid-barrier kernel) when
 // launched, 0 when the grid is too large or the launch is refused (the caller
-// then uses the per-iteration path).  AD_F64_KERNEL=row selects the row
-// kernel, AD_NO_NSYNC the grid-barrier kernel (tuning and A/B overrides).
+// then uses the per-iteration path).  The tile kernel runs when a tile holds at
+// least kTileMinCells cells, else the row kernel; AD_F64_KERNEL=row|tile forces
+// either, AD_NO_NSYNC the grid-barrier kernel (tuning and A/B overrides).
 int series_run_persistent(const SeriesArgs& a, unsigned int* gen, const NsyncScratch* ns,
                           cudaStream_t s) {
   if (a.prec != 0 || a.g.n > kPersistMaxCells) return 0;
@@ -998,11 +999,12 @@ int series_run_persistent(const SeriesArgs& a, unsigned int* gen, const NsyncScr
     if (ok) ++launch_counter();
     return ok;
   };
-  static const bool row_kernel = [] {
+  // 0 by tile size, 1 rows, 2 tiles (AD_F64_KERNEL=row|tile: tuning and A/B overrides)
+  static const int f64_kernel = [] {
     const char* e = getenv("AD_F64_KERNEL");
-    return e && e[0] == 'r';
+    return !e ? 0 : (e[0] == 'r' ? 1 : (e[0] == 't' ? 2 : 0));
   }();
-  if (ns && ns->slots && ns->flags && !no_nsync && !row_kernel) {
+  if (ns && ns->slots && ns->flags && !no_nsync && f64_kernel != 1) {
     // tiles: the fewest cells per block (most blocks), then the shortest perimeter
     const int nx = a.g.nx, ny = a.g.ny;
     TileGeom best{};
@@ -1029,7 +1031,11 @@ int series_run_persistent(const SeriesArgs& a, unsigned int* gen, const NsyncScr
         best_G = Ga;
       }
     }
-    if (best_cells > 0) {
+    // Measured on GB300 (two-stage 512x512-type workloads): below about 1000
+    // cells per tile the row kernel is faster (64^2 .. 384^2: 6.6 .. 8.8 us
+    // against 8.4 .. 9.1 us per iteration); from 448^2 up the tiles win.
+    constexpr long long kTileMinCells = 1024;
+    if (best_cells > 0 && (best_cells >= kTileMinCells || f64_kernel == 2)) {
       const size_t smem = sizeof(double) * ((size_t)best_cells * (a.aug ? 13 : 12) +
                                             2 * (size_t)best.S * (best.th + 2));
       void* fn = a.aug ? (void*)leja_tile_f64_k<true> : (void*)leja_tile_f64_k<false>;

@@ -1,7 +1,8 @@
 """The three persistent FP64 series kernels agree bit for bit.
 
 Small FP64 grids run a whole Newton series in one cooperative launch.  The
-default kernel (2-D tiles) and the row kernel (AD_F64_KERNEL=row) synchronise
+tile kernel (AD_F64_KERNEL=tile; the default for tiles of >= 1024 cells) and
+the row kernel (AD_F64_KERNEL=row; the default below) synchronise
 each block with its neighbours only and apply the stopping rule two
 iterations late (dropping the extra iteration); the grid-barrier kernel
 (selected with AD_NO_NSYNC) decides after every iteration.  All three form
@@ -93,11 +94,12 @@ def test_neighbour_sync_kernel_equals_grid_barrier_kernel(case, tmp_path):
 
 @pytest.mark.parametrize("case", CASES)
 def test_tile_kernel_equals_grid_barrier_kernel(case, tmp_path):
-    """The 2-D tile kernel (default) forms every entry as the grid-barrier
-    kernel does; its norm sums run over another cell-to-block assignment, so
-    the error estimates agree to rounding."""
+    """The 2-D tile kernel (forced here: by default it runs for large tiles
+    only) forms every entry as the grid-barrier kernel does; its norm sums run
+    over another cell-to-block assignment, so the error estimates agree to
+    rounding."""
     need_gpu()
-    s_new, phi_new, u_new = _run(case, str(tmp_path / "tile"), {})
+    s_new, phi_new, u_new = _run(case, str(tmp_path / "tile"), {"AD_F64_KERNEL": "tile"})
     s_old, phi_old, u_old = _run(case, str(tmp_path / "grid"), {"AD_NO_NSYNC": "1"})
     for key in ("phi", "step"):
         assert s_new[key]["iters"] == s_old[key]["iters"], (key, s_new[key], s_old[key])
@@ -126,7 +128,7 @@ def test_series_timing_counts_every_series():
     assert t["series"] == st["substeps"]
     assert t["iters"] == st["iters"]
     assert t["ms"] > 0.0
-    assert t["kernel"] == "leja_tile_f64_k"
+    assert t["kernel"] in ("leja_tile_f64_k", "leja_nsync_f64_k")
     ad().time_series(op, False)
     ad().expquad_step(op, u, p.dt, p.dt, 2, (1 / 3, 2 / 3), src, tol=1e-10)
     assert ad().series_timing(op) == t
