@@ -659,6 +659,19 @@ def measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, fields, dt, 
             "steps_in_comparison": steps}
 
 
+def job_throughput(dev_ms, cells, steps, world, device):
+    """Whole-job throughput of `world` replicas: every rank advanced `cells`
+    cells by `steps` steps; the job took as long as its slowest rank (max
+    over ranks).  Returns (max ms, Mcell-steps/s over all ranks)."""
+    import torch
+    import torch.distributed as dist
+    tmax = torch.tensor([float(dev_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    ms = float(tmax.item())
+    return ms, cells * steps * world / (ms * 1e-3) / 1e6
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -725,11 +738,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    tmax = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    dev_ms = float(tmax.item())
-    value = g.n * args.steps * world / (dev_ms * 1e-3) / 1e6
+    dev_ms, value = job_throughput(dev_ms, g.n, args.steps, world, dev)
 
     # e2e: the state lives in pinned host memory; the C ABI stages it per call
     uh = torch.empty(g.n, dtype=torch.float64, pin_memory=True)
