@@ -68,9 +68,9 @@ def parse():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--form-steps", type=int, default=5)
     ap.add_argument("--learned-fields", type=int, default=1000)
-    ap.add_argument("--forms", default="fp32,cn,paper,batched,learned,momentum",
+    ap.add_argument("--forms", default="fp32,cn,paper,batched,learned,momentum,adaptive",
                     help="comma list of extra forms to measure: fp32, cn, batched, learned, "
-                         "paper, momentum")
+                         "paper, momentum, adaptive")
     return ap.parse_args()
 
 
@@ -352,6 +352,45 @@ def measure_momentum_form(ad, dev, stream, steps=3):
                          "traffic": traffic_per_launch(MOM_SOURCES, "mom_iter_256sq_x32p.md"),
                          "peak_note": "of derived FP64 peak; iteration time includes the "
                                       "host-driven chunk reads of the control block"}}
+
+
+def measure_adaptive_substeps(ad, dev, stream, dt_factor=2000.0):
+    """Adaptive substep control on the 512^2 workload: one two-stage step of
+    dt_factor Delta t_CFL with the fixed rule (rho_max 200, equal substeps) and
+    with the adaptive controller (no rho_max, a 100-iteration budget per
+    series).  Error against the same step with the fixed rule at tol 1e-12."""
+    import numpy as np
+    import torch
+    from workloads import config1
+    p = config1(nx=512, dt_factor=dt_factor)
+    g = p.grid
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(), device=dev)
+    op = ad.create_operator(g.nx, g.ny, g.bc, T(p.Dxx), T(p.Dxy), T(p.Dyy), p.ax, p.ay, ad.FP64,
+                            stream=stream)
+    src = ad.Source([T(gk) for gk in p.source.g], list(p.source.h))
+    ref = T(p.u0)
+    ad.expquad_step(op, ref, 0.0, p.dt, p.s, p.c, src, tol=1e-12)
+    out = {}
+    for name, adaptive, rho_max, budget in (("fixed", False, 200.0, 500),
+                                            ("adaptive", True, 1e9, 100)):
+        ad.set_options(op, rho_max=rho_max, max_iters=budget)
+        ad.set_substep_control(op, adaptive)
+        u = T(p.u0)
+        ad.expquad_step(op, u, 0.0, p.dt, p.s, p.c, src, tol=p.tol)    # warm-up
+        u = T(p.u0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = ad.expquad_step(op, u, 0.0, p.dt, p.s, p.c, src, tol=p.tol)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"ms": round(e0.elapsed_time(e1), 3), "iters": st["iters"],
+                     "substeps": st["substeps"], "rejected": st["rejected"],
+                     "err_vs_tol1e-12_step": float(torch.linalg.norm(u - ref) /
+                                                   torch.linalg.norm(ref))}
+    op.close()
+    return {"workload": f"c1-512sq-dirichlet-circular-expquad2-dt{int(dt_factor)}cfl",
+            "tol": p.tol, **out}
 
 
 def measure_cn_vs_exp(ad, dev, stream, T_cfl=1000.0):
@@ -788,6 +827,8 @@ def run_ours(args):
         forms["cn_vs_exp"] = measure_cn_vs_exp(ad, dev, stream)
     if "momentum" in wanted:
         forms["momentum"] = measure_momentum_form(ad, dev, stream)
+    if "adaptive" in wanted:
+        forms["adaptive_substeps"] = measure_adaptive_substeps(ad, dev, stream)
     if "paper" in wanted:
         forms["paper_cases"] = measure_paper_cases(ad, dev, stream)
     if "batched" in wanted:
