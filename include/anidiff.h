@@ -178,6 +178,29 @@ AD_API int ad_leja_phi1(ad_operator* op, const void* v, void* out, double dt, do
 AD_API int ad_expquad_step(ad_operator* op, void* u, double t, double dt, int s, const double* c,
                     const ad_source* src, double tol, int force_iters, ad_stats* stats);
 
+/* ad_expquad_step without the synchronisation, for running many steps with no
+ * host round trip between them.  When u is a device pointer, the substep
+ * control is the fixed rule and the step takes one substep (gamma dt <=
+ * rho_max), the call only enqueues the step on the operator's stream and
+ * returns; its iteration count and convergence status are accumulated on the
+ * device.  Otherwise it runs ad_expquad_step (synchronously) and adds that
+ * step to the same totals.  u must stay valid until the stream has run the
+ * step.  Returns AD_OK, or AD_ERR_INVALID / AD_ERR_CUDA / AD_ERR_TIMEOUT when
+ * enqueueing (or the synchronous run) fails; a series that misses the
+ * tolerance is reported by ad_async_totals, not here.  Same arguments as
+ * ad_expquad_step with force_iters = -1. */
+AD_API int ad_expquad_step_async(ad_operator* op, void* u, double t, double dt, int s,
+                                 const double* c, const ad_source* src, double tol);
+
+/* Synchronises the operator's stream and returns the totals of the
+ * ad_expquad_step_async calls since the previous ad_async_totals call, then
+ * resets them: iters, matvecs, substeps, rejected and kernel_launches summed;
+ * err_est the largest; converged 0 if any series missed the tolerance; alpha
+ * the current bound.  stats may be NULL.  Returns the worst status among those
+ * steps: AD_OK, AD_ERR_NOT_CONVERGED (a series reached max_iters; its step was
+ * still applied, as in ad_expquad_step) or AD_ERR_TIMEOUT. */
+AD_API int ad_async_totals(ad_operator* op, ad_stats* stats);
+
 /* One Crank-Nicolson step (the paper's comparison solver; its linear solver
  * is unspecified): (I - dt/2 A) u+ = (I + dt/2 A) u + dt (S(t) + S(t+dt))/2,
  * solved by restarted GMRES(restart) from x0 = u to relative residual

@@ -69,6 +69,9 @@ _sig = {
     "ad_leja_phi1": (_i, [_vp, _vp, _vp, _d, _d, _i, C.POINTER(Stats)]),
     "ad_expquad_step": (_i, [_vp, _vp, _d, _d, _i, C.POINTER(_d), C.POINTER(_Source), _d, _i,
                              C.POINTER(Stats)]),
+    "ad_expquad_step_async": (_i, [_vp, _vp, _d, _d, _i, C.POINTER(_d), C.POINTER(_Source),
+                                   _d]),
+    "ad_async_totals": (_i, [_vp, C.POINTER(Stats)]),
     "ad_cn_step": (_i, [_vp, _vp, _d, _d, C.POINTER(_Source), _d, _i, _i, C.POINTER(Stats)]),
     "ad_penalised_step": (_i, [_vp, _vp, _d, _d, C.POINTER(_Source), _d, _d, _i,
                                C.POINTER(Stats)]),
@@ -304,6 +307,28 @@ def expquad_step(op: Operator, u, t: float, dt: float, s: int = 1, c: Sequence[f
                                 C.byref(srcs) if srcs is not None else None, tol, force_iters,
                                 C.byref(st)), st)
     del keep
+    return st.as_dict()
+
+
+def expquad_step_async(op: Operator, u, t: float, dt: float, s: int = 1,
+                       c: Sequence[float] = (0.5,), source: Optional[Source] = None,
+                       tol: float = 1e-10) -> None:
+    """ad_expquad_step_async: enqueue one step (no synchronisation for a device
+    tensor u under the fixed one-substep rule); read the totals with
+    async_totals.  u must stay alive until then."""
+    carr = (C.c_double * max(2, len(c)))(*list(c) + [0.0] * (max(2, len(c)) - len(c)))
+    srcs, keep = _source_struct(op, source)
+    _check(_lib.ad_expquad_step_async(op.handle, op.vec(u, "u"), t, dt, s, carr,
+                                      C.byref(srcs) if srcs is not None else None, tol))
+    del keep
+
+
+def async_totals(op: Operator) -> dict:
+    """ad_async_totals: synchronise and return the totals of the asynchronous
+    steps since the last call (raises NotConverged / AdError as the steps'
+    worst status says)."""
+    st = Stats()
+    _check(_lib.ad_async_totals(op.handle, C.byref(st)), st)
     return st.as_dict()
 
 

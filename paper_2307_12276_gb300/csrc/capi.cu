@@ -79,6 +79,16 @@ struct SeriesGraph {
   bool tried = false;
 };
 
+// Totals of asynchronous steps, accumulated on the device (one thread).
+struct AsyncTotals {
+  long long iters;         // Leja iterations of all series
+  long long timed_iters;   // ... of the series that ran with timing events
+  long long launches;      // graph-body kernel launches (known on the device only)
+  int series;
+  int status;              // worst: 0 ok, 3 not converged, 4 no stop state / timeout
+  double err_est;          // largest error estimate
+};
+
 struct ad_operator {
   ad_grid grid{};
   GridDev g{};
@@ -107,6 +117,14 @@ struct ad_operator {
   double* dscal = nullptr;                     // device scalars [64]
   NsyncScratch nsync{nullptr, nullptr};        // persistent-kernel scratch (FP64, small grids)
   int nblocks = 1;
+  // asynchronous steps (ad_expquad_step_async): what the device knows is
+  // accumulated there by async_collect_k, what the host knows here
+  AsyncTotals* totals = nullptr;               // device
+  AsyncTotals* h_totals = nullptr;             // pinned mirror
+  ad_stats async_host{};
+  int async_worst = 0;                         // worst status of synchronous fallbacks
+  std::vector<cudaEvent_t> atev;               // event pairs around async series (timing)
+  int atev_used = 0;
   // series timing (ad_time_series)
   bool time_series = false;
   cudaEvent_t tev[2] = {nullptr, nullptr};
@@ -128,6 +146,7 @@ struct ad_operator {
   // cache of the coefficient upload
   int cache_kind = -1;
   double cache_h = 0.0, cache_alpha = 0.0;
+  double cache_eta[2] = {0.0, 0.0};            // eta_0 of the uploaded table (augmented)
   std::vector<double> d_host;                  // divided differences of the current series
 };
 
@@ -300,6 +319,9 @@ int upload_series(ad_operator* op, int kind, double h, const double eta0[2], dou
   const std::vector<double>& xi = leja_points();
   const int M = kMaxIters + 1;
   const bool cached = op->cache_kind == kind && op->cache_h == h && op->cache_alpha == op->alpha;
+  // the device table already holds exactly these coefficients
+  const bool same_table =
+      cached && (kind == 0 || (op->cache_eta[0] == eta0[0] && op->cache_eta[1] == eta0[1]));
   if (!cached) {
     std::vector<double> f(M);
     for (int m = 0; m < M; ++m) {
@@ -317,6 +339,12 @@ int upload_series(ad_operator* op, int kind, double h, const double eta0[2], dou
     pe1 = d[0] * e1;
     pe2 = d[0] * e2;
   }
+  *d0 = d[0];
+  if (kind == 1) {
+    eta_out[0] = pe1;
+    eta_out[1] = pe2;
+  }
+  if (same_table) return AD_OK;
   for (int m = 0; m < kMaxIters; ++m) {
     LejaCoef& L = op->h_lc[m];
     L.xi = xi[m];
@@ -337,20 +365,63 @@ int upload_series(ad_operator* op, int kind, double h, const double eta0[2], dou
   op->cache_kind = kind;
   op->cache_h = h;
   op->cache_alpha = op->alpha;
-  *d0 = d[0];
   if (kind == 1) {
-    eta_out[0] = pe1;
-    eta_out[1] = pe2;
+    op->cache_eta[0] = eta0[0];
+    op->cache_eta[1] = eta0[1];
   }
   return AD_OK;
+}
+
+// Vector updates that need no host decision, enqueued right after a series
+// and before the synchronisation that reads its result, so that the device
+// does not wait for the host between the series and them.
+struct Tail {
+  struct Op {
+    double a;
+    const void* x;
+    double b;
+    const void* y;
+    void* z;
+  };
+  int k = 0;
+  Op op[3];
+  void add(double a, const void* x, double b, const void* y, void* z) { op[k++] = Op{a, x, b, y, z}; }
+  void add(const Tail* t) {
+    if (t)
+      for (int i = 0; i < t->k; ++i) op[k++] = t->op[i];
+  }
+};
+
+void enqueue_tail(const ad_operator* op, const Tail* t) {
+  if (!t) return;
+  for (int i = 0; i < t->k; ++i)
+    axpby(op->prec, op->g.n, t->op[i].a, t->op[i].x, t->op[i].b, t->op[i].y, t->op[i].z,
+          op->stream);
 }
 
 // Run one Newton series from src (device vector of the storage type, or null
 // for a zero start); the result is left in op->P.  *iters receives the
 // number of iterations; the eta part (augmented series) is accumulated on
-// the host into eta_sum using the uploaded d.
+// the host into eta_sum using the uploaded d.  tail (optional) is enqueued
+// after the series and before the synchronisation.  async: no
+// synchronisation; async_collect_k adds the series to the device totals and
+// *iters_out is -1 (unknown to the host).
+__global__ void async_collect_k(const Ctrl* c, AsyncTotals* t, int per_launch, int timed) {
+  const int it = c->iters;
+  t->iters += it;
+  if (timed) t->timed_iters += it;
+  if (per_launch > 0) t->launches += (it + per_launch - 1) / per_launch;
+  t->series += 1;
+  const int st = c->stop ? (c->status == 4 ? 4 : c->status) : 4;
+  if (st > t->status) t->status = st;
+  // the estimate as the synchronous path forms it on the host
+  const double e = c->pnorm2 > 0.0 ? c->err_est * sqrt(c->ynorm2 / c->pnorm2)
+                                   : (c->ynorm2 > 0.0 ? INFINITY : 0.0);
+  if (e > t->err_est) t->err_est = e;
+}
+
 int run_series(ad_operator* op, int aug, const void* src, double d0, int force, double tol,
-               ad_stats* st, int* iters_out) {
+               ad_stats* st, int* iters_out, const Tail* tail = nullptr, bool async = false) {
   SeriesArgs a = series_args(op, aug);
   series_init(a, src, d0, force, op->max_iters, tol, op->stream);
   CUDA_TRY(cudaGetLastError());
@@ -360,9 +431,21 @@ int run_series(ad_operator* op, int aug, const void* src, double d0, int force, 
     iters = 0;
     op->h_ctrl->status = 0;
     op->h_ctrl->err_est = 0.0;
+    enqueue_tail(op, tail);
   } else {
     SeriesGraph& sg = op->graphs[aug];
-    if (op->time_series) CUDA_TRY(cudaEventRecord(op->tev[0], op->stream));
+    cudaEvent_t ev[2] = {op->tev[0], op->tev[1]};
+    if (op->time_series && async) {   // one event pair per series, read by ad_async_totals
+      while ((int)op->atev.size() < 2 * (op->atev_used + 1)) {
+        cudaEvent_t e = nullptr;
+        CUDA_TRY(cudaEventCreate(&e));
+        op->atev.push_back(e);
+      }
+      ev[0] = op->atev[2 * op->atev_used];
+      ev[1] = op->atev[2 * op->atev_used + 1];
+      ++op->atev_used;
+    }
+    if (op->time_series) CUDA_TRY(cudaEventRecord(ev[0], op->stream));
     // small and medium FP64 grids: the whole series in one cooperative launch
     const int pk = getenv("AD_NO_PERSIST") ? 0
                    : series_run_persistent(a, &op->ctrl->gen, &op->nsync, op->stream);
@@ -387,7 +470,18 @@ int run_series(ad_operator* op, int aug, const void* src, double d0, int force, 
     }
     if (!persist && series_pair(a)) series_flush_pair(a, op->stream);   // the pending last term
     CUDA_TRY(cudaGetLastError());
-    if (op->time_series) CUDA_TRY(cudaEventRecord(op->tev[1], op->stream));
+    if (op->time_series) CUDA_TRY(cudaEventRecord(ev[1], op->stream));
+    enqueue_tail(op, tail);
+    if (async) {
+      const int per_launch = graph_used ? (series_pair(a) ? 2 : 1) : 0;
+      async_collect_k<<<1, 1, 0, op->stream>>>(op->ctrl, op->totals, per_launch,
+                                               op->time_series ? 1 : 0);
+      ++launch_counter();
+      CUDA_TRY(cudaGetLastError());
+      if (op->time_series) op->t_path = persist ? pk : (graph_used ? 3 : 4) + (series_pair(a) ? 2 : 0);
+      *iters_out = -1;
+      return AD_OK;
+    }
     CUDA_TRY(cudaMemcpyAsync(op->h_ctrl, op->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, op->stream));
     CUDA_TRY(cudaStreamSynchronize(op->stream));
     iters = op->h_ctrl->iters;
@@ -596,8 +690,10 @@ int phi1_device_adaptive(ad_operator* op, const void* v_dev, void* out_dev, doub
 }
 
 // out_dev (storage type) = phi_1(dt A) v_dev; v_dev must not alias T1/T2/T3.
+// post (optional, fixed substeps only): the caller's own updates after out,
+// enqueued with the last series.  async: one substep only (see run_series).
 int phi1_device(ad_operator* op, const void* v_dev, void* out_dev, double dt, double tol,
-                int force, ad_stats* st) {
+                int force, ad_stats* st, const Tail* post = nullptr, bool async = false) {
   if (op->adaptive && force < 0) return phi1_device_adaptive(op, v_dev, out_dev, dt, tol, st);
   const int K = n_substeps(op, dt);
   const double h = dt / K;
@@ -607,10 +703,12 @@ int phi1_device(ad_operator* op, const void* v_dev, void* out_dev, double dt, do
   int status = AD_OK, it = 0;
   const long long n = op->g.n;
   if (K == 1) {
-    int r = run_series(op, 0, v_dev, d0, force, tol, st, &it);
+    Tail tail;
+    tail.add(1.0, op->P, 0.0, nullptr, out_dev);
+    tail.add(post);
+    int r = run_series(op, 0, v_dev, d0, force, tol, st, &it, &tail, async);
     if (r != AD_OK && r != AD_ERR_NOT_CONVERGED) return r;
     status = r;
-    axpby(op->prec, n, 1.0, op->P, 0.0, nullptr, out_dev, op->stream);
   } else {
     // w_{k+1} = w_k + h phi_1(h A)(A w_k + v), w_0 = 0; out = w_K / dt
     axpby(op->prec, n, 1.0, v_dev, 0.0, nullptr, op->T1, op->stream);   // v
@@ -624,12 +722,16 @@ int phi1_device(ad_operator* op, const void* v_dev, void* out_dev, double dt, do
         rhs = op->T3;
         if (st) st->matvecs += 1;
       }
-      int r = run_series(op, 0, rhs, d0, force, tol, st, &it);
+      Tail tail;
+      tail.add(1.0, op->T2, h, op->P, op->T2);
+      if (k == K - 1) {
+        tail.add(1.0 / dt, op->T2, 0.0, nullptr, out_dev);
+        tail.add(post);
+      }
+      int r = run_series(op, 0, rhs, d0, force, tol, st, &it, &tail);
       if (r != AD_OK && r != AD_ERR_NOT_CONVERGED) return r;
       if (r != AD_OK) status = r;
-      axpby(op->prec, n, 1.0, op->T2, h, op->P, op->T2, op->stream);
     }
-    axpby(op->prec, n, 1.0 / dt, op->T2, 0.0, nullptr, out_dev, op->stream);
   }
   CUDA_TRY(cudaGetLastError());
   return status;
@@ -698,6 +800,7 @@ int ad_create_operator(const ad_grid* grid, const double* Dxx, const double* Dxy
   ok = ok && alloc((void**)&op->partials, sizeof(double) * op->partials_len);
   ok = ok && alloc((void**)&op->lc, sizeof(LejaCoef) * kMaxIters);
   ok = ok && alloc((void**)&op->ctrl, sizeof(Ctrl));
+  ok = ok && alloc((void**)&op->totals, sizeof(AsyncTotals));
   ok = ok && alloc((void**)&op->dscal, sizeof(double) * 4 * (kMaxGmres + 2));
   if (precision == AD_FP64 && n <= kPersistMaxCells) {
     ok = ok && alloc((void**)&op->nsync.slots, nsync_slots_bytes());
@@ -705,6 +808,7 @@ int ad_create_operator(const ad_grid* grid, const double* Dxx, const double* Dxy
   }
   if (ok) ok = cudaMallocHost((void**)&op->h_lc, sizeof(LejaCoef) * kMaxIters) == cudaSuccess;
   if (ok) ok = cudaMallocHost((void**)&op->h_ctrl, sizeof(Ctrl)) == cudaSuccess;
+  if (ok) ok = cudaMallocHost((void**)&op->h_totals, sizeof(AsyncTotals)) == cudaSuccess;
   if (ok) ok = cudaMallocHost((void**)&op->h_scal, sizeof(double) * 4 * (kMaxGmres + 2)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -713,6 +817,7 @@ int ad_create_operator(const ad_grid* grid, const double* Dxx, const double* Dxy
   }
   std::memset(op->h_ctrl, 0, sizeof(Ctrl));
   cudaMemsetAsync(op->ctrl, 0, sizeof(Ctrl), op->stream);
+  cudaMemsetAsync(op->totals, 0, sizeof(AsyncTotals), op->stream);
   if (precision == AD_FP64)
     pack_weights_f64(op->g, dx, dy, Dxx, Dxy, Dyy, ax, ay, ax_c, ay_c, op->W, op->stream);
   else
@@ -745,13 +850,16 @@ int ad_destroy_operator(ad_operator* op) {
   if (op->cap_stream) cudaStreamDestroy(op->cap_stream);
   for (void* p : {(void*)op->W, (void*)op->Ws, (void*)op->F, op->Y0, op->Y1, op->P, op->W1, op->W2,
                   op->T1, op->T2, op->T3, op->S0, op->S1, (void*)op->Vk, (void*)op->lc,
-                  (void*)op->ctrl, (void*)op->partials, (void*)op->dscal,
+                  (void*)op->ctrl, (void*)op->totals, (void*)op->partials, (void*)op->dscal,
                   (void*)op->nsync.slots, (void*)op->nsync.flags})
     if (p) cudaFree(p);
   for (cudaEvent_t e : op->tev)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : op->atev)
+    if (e) cudaEventDestroy(e);
   if (op->h_lc) cudaFreeHost(op->h_lc);
   if (op->h_ctrl) cudaFreeHost(op->h_ctrl);
+  if (op->h_totals) cudaFreeHost(op->h_totals);
   if (op->h_scal) cudaFreeHost(op->h_scal);
   delete op;
   return AD_OK;
@@ -865,9 +973,14 @@ int ad_leja_phi1(ad_operator* op, const void* v, void* out, double dt, double to
   return AD_OK;
 }
 
-int ad_expquad_step(ad_operator* op, void* u, double t, double dt, int s, const double* c,
-                    const ad_source* src, double tol, int force_iters, ad_stats* stats) {
-  g_err.clear();
+}  // extern "C"
+
+namespace {
+
+// One step (ad_expquad_step).  async (device u, fixed rule, one substep): no
+// synchronisation; the series report to the operator's async totals.
+int expquad_impl(ad_operator* op, void* u, double t, double dt, int s, const double* c,
+                 const ad_source* src, double tol, int force_iters, ad_stats* stats, bool async) {
   if (!op || !u || !c) return fail(AD_ERR_INVALID, "NULL argument");
   if (!(dt > 0) || !std::isfinite(dt) || !std::isfinite(t)) return fail(AD_ERR_INVALID, "bad t or dt");
   if (s != 1 && s != 2) return fail(AD_ERR_INVALID, "s must be 1 or 2");
@@ -891,13 +1004,16 @@ int ad_expquad_step(ad_operator* op, void* u, double t, double dt, int s, const 
     for (int k = 0; k < S.n; ++k) S.a[k] = h_at(src, k, t + c[0] * dt);
     apply(op, ud, op->W1, nullptr, S);
     st.matvecs += 1;
-    const int r = phi1_device(op, op->W1, op->W2, dt, tol, force, &st);
+    // a non-converged fixed step is still applied (with the last series);
+    // adaptive control that gave up leaves u unchanged
+    const bool fixed = !(op->adaptive && force < 0);
+    Tail post;
+    post.add(1.0, ud, dt, op->W2, ud);
+    const int r =
+        phi1_device(op, op->W1, op->W2, dt, tol, force, &st, fixed ? &post : nullptr, async);
     if (r != AD_OK && r != AD_ERR_NOT_CONVERGED) return r;
     status = r;
-    // a non-converged fixed step is still applied; adaptive control that gave
-    // up leaves u unchanged
-    if (!(r != AD_OK && op->adaptive && force < 0))
-      axpby(op->prec, n, 1.0, ud, dt, op->W2, ud, op->stream);
+    if (!fixed && r == AD_OK) axpby(op->prec, n, 1.0, ud, dt, op->W2, ud, op->stream);
   } else {
     // w1 = A u + (c2 S1 - c1 S2)/(c2 - c1), w2 = (S2 - S1)/((c2 - c1) dt);
     // u += top block of exp(dt [[A, W], [0, J]]) [0; 0; 1]
@@ -955,20 +1071,90 @@ int ad_expquad_step(ad_operator* op, void* u, double t, double dt, int s, const 
         double d0, eta_next[2];
         AD_TRY(upload_series(op, 1, h, eta, &d0, eta_next));
         int it = 0;
-        const int r = run_series(op, 1, k == 0 ? nullptr : op->T2, d0, force, tol, &st, &it);
+        // the next substep starts from P (copied: its series rewrites P); the
+        // last one adds P to u
+        Tail tail;
+        if (k + 1 < K) tail.add(1.0, op->P, 0.0, nullptr, op->T2);
+        else tail.add(1.0, ud, 1.0, op->P, ud);
+        const int r = run_series(op, 1, k == 0 ? nullptr : op->T2, d0, force, tol, &st, &it,
+                                 &tail, async);
         if (r != AD_OK && r != AD_ERR_NOT_CONVERGED) return r;
         if (r != AD_OK) status = r;
-        advance_eta(op, it, eta);
-        if (K > 1) axpby(op->prec, n, 1.0, op->P, 0.0, nullptr, op->T2, op->stream);
+        if (k + 1 < K) advance_eta(op, it, eta);
       }
-      axpby(op->prec, n, 1.0, ud, 1.0, K > 1 ? op->T2 : op->P, ud, op->stream);
     }
   }
   CUDA_TRY(cudaGetLastError());
-  AD_TRY(finish_out(op, u, ud));
+  if (!async) AD_TRY(finish_out(op, u, ud));
   st.kernel_launches += (int)(launch_counter() - l0);
   if (stats) *stats = st;
   if (status == AD_ERR_NOT_CONVERGED) return fail(status, "Leja series reached max_iters");
+  return AD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ad_expquad_step(ad_operator* op, void* u, double t, double dt, int s, const double* c,
+                    const ad_source* src, double tol, int force_iters, ad_stats* stats) {
+  g_err.clear();
+  return expquad_impl(op, u, t, dt, s, c, src, tol, force_iters, stats, false);
+}
+
+int ad_expquad_step_async(ad_operator* op, void* u, double t, double dt, int s, const double* c,
+                          const ad_source* src, double tol) {
+  g_err.clear();
+  if (!op || !u) return fail(AD_ERR_INVALID, "NULL argument");
+  const bool async = is_device_ptr(u) && !op->adaptive && std::isfinite(dt) && dt > 0 &&
+                     n_substeps(op, dt) == 1;
+  ad_stats st{};
+  const int r = expquad_impl(op, u, t, dt, s, c, src, tol, -1, &st, async);
+  if (r != AD_OK && r != AD_ERR_NOT_CONVERGED) return r;
+  // what the host knows of this step (the device adds the series)
+  ad_stats& h = op->async_host;
+  h.iters += st.iters;
+  h.matvecs += st.matvecs;
+  h.substeps += st.substeps;
+  h.rejected += st.rejected;
+  h.kernel_launches += st.kernel_launches;
+  h.err_est = std::max(h.err_est, st.err_est);
+  if (r == AD_ERR_NOT_CONVERGED) op->async_worst = std::max(op->async_worst, (int)AD_ERR_NOT_CONVERGED);
+  g_err.clear();
+  return AD_OK;
+}
+
+int ad_async_totals(ad_operator* op, ad_stats* stats) {
+  g_err.clear();
+  if (!op) return fail(AD_ERR_INVALID, "op is NULL");
+  CUDA_TRY(cudaMemcpyAsync(op->h_totals, op->totals, sizeof(AsyncTotals), cudaMemcpyDeviceToHost,
+                           op->stream));
+  CUDA_TRY(cudaStreamSynchronize(op->stream));
+  const AsyncTotals T = *op->h_totals;
+  ad_stats r = op->async_host;
+  r.iters += (int)T.iters;
+  r.matvecs += (int)T.iters;
+  r.kernel_launches += (int)T.launches;
+  r.err_est = std::max(r.err_est, T.err_est);
+  r.alpha = op->alpha;
+  const int worst = std::max(op->async_worst, T.status);
+  r.converged = worst == 0 ? 1 : 0;
+  if (op->time_series) {   // the event pairs of the series enqueued with timing
+    for (int k = 0; k < op->atev_used; ++k) {
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, op->atev[2 * k], op->atev[2 * k + 1]));
+      op->t_ms += ms;
+    }
+    op->t_series += op->atev_used;
+    op->t_iters += T.timed_iters;
+  }
+  op->atev_used = 0;
+  op->async_host = ad_stats{};
+  op->async_worst = 0;
+  CUDA_TRY(cudaMemsetAsync(op->totals, 0, sizeof(AsyncTotals), op->stream));
+  if (stats) *stats = r;
+  if (worst == 4) return fail(AD_ERR_TIMEOUT, "an asynchronous series did not reach its stop state");
+  if (worst == 3) return fail(AD_ERR_NOT_CONVERGED, "an asynchronous series reached max_iters");
   return AD_OK;
 }
 
@@ -1105,14 +1291,12 @@ int ad_cn_step(ad_operator* op, void* u, double t, double dt, const ad_source* s
   // b = u + dt/2 A u + dt/2 (S(t) + S(t + dt))
   for (int k = 0; k < S.n; ++k) S.a[k] = 0.5 * dt * (h_at(src, k, t) + h_at(src, k, t + dt));
   {
-    Sources none{};
     apply_shifted_f64(op->g, op->W, x, b, 1.0, 0.5 * dt, s);
     if (S.n > 0) {
       // add the source combination: b += sum a_k g_k  (apply with zero field -> sources only)
       for (int k = 0; k < S.n; ++k)
         axpby(0, n, S.a[k], S.g[k], 1.0, b, b, s);
     }
-    (void)none;
   }
   st.matvecs += 1;
   auto read_scalars = [&](int count) -> int {

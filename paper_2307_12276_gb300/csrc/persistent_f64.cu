@@ -13,6 +13,8 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <mutex>
+#include <vector>
 
 namespace ad {
 namespace {
@@ -668,8 +670,12 @@ __global__ void __launch_bounds__(256) leja_nsync_f64_k(SeriesArgs a, NsyncGeom 
 // p and the two squared norms are formed with z, cell by cell, in both compute
 // phases (no separate pass): three p buffers keep the result that the lagged
 // decision may still return (P after iteration m - 2) out of the way.  After
-// the ring cells, thread 0 adds the per-warp norm sums in warp order, writes
-// the slot (m, b) and then publishes flags[b] = m + 1.
+// the ring cells thread 0 publishes flags[b] = m + 1; the per-thread norm
+// partials of iteration m are added by warp 0 at the start of iteration m + 1
+// (one packed shuffle tree instead of one per warp: GB300's FP64 pipe is
+// shared by the SM's four sub-partitions, so every FP64 instruction of the
+// block counts) and written to the slot (m, b) before warp 0 waits for
+// anything.
 struct TileGeom {
   int TX, TY;   // tiles per grid row / column (G = TX * TY)
   int tw, th;   // tile width / height (full tiles)
@@ -696,7 +702,7 @@ template <bool AUG>
 __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom geo, double* slots,
                                                        unsigned int* flags, unsigned int* gen) {
   extern __shared__ double smem[];
-  __shared__ double s_wy[8], s_wp[8];        // per-warp norm partials
+  __shared__ double s_py[2][256], s_pp[2][256];   // per-thread norm partials, double-buffered
   __shared__ int s_nb[8];
   __shared__ int s_nnb, s_final, s_status, s_fail;
   __shared__ double s_ty, s_tp;
@@ -821,7 +827,32 @@ __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom ge
       double* Pout = sP + ((m + 1) % 3) * cpb;
       double sy = 0.0, sp = 0.0;
       // ---- phase A
-      if (warp == 0) {                              // the lagged decisions
+      if (warp == 0) {
+        // the block's norm sums of iteration m - 1 into slot (m - 1, b): the
+        // per-thread partials (double-buffered) in thread order per lane, then
+        // one shuffle tree that carries both sums (lanes 0-15 the y sum, lanes
+        // 16-31 the p sum)
+        if (m >= 1) {
+          const double* py = s_py[(m - 1) & 1];
+          const double* pp = s_pp[(m - 1) & 1];
+          double ty = 0.0, tp = 0.0;
+          for (int q = lane; q < T; q += 32) {
+            ty += py[q];
+            tp += pp[q];
+          }
+          const bool lo = lane < 16;
+          double v = (lo ? ty : tp) + __shfl_xor_sync(0xffffffffu, lo ? tp : ty, 16);
+#pragma unroll
+          for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          const double vp = __shfl_sync(0xffffffffu, v, 16);
+          if (lane == 0) {                          // the slot value itself is the signal
+            double* s2 = slots + 2LL * ((long long)(m - 1) * kNsyncMaxBlocks + b);
+            s2[0] = v;
+            s2[1] = vp;
+          }
+          __syncwarp();
+        }
+        // the lagged decisions
         int f = -1, st = 0;
         double ty = 0.0, tp = 0.0;
         bool ok = true;
@@ -913,27 +944,12 @@ __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom ge
         sy = fma(z, z, sy);
         sp = fma(pn, pn, sp);
       }
-      // block sums: a shuffle tree per warp, then thread 0 adds the warp sums
-      // in warp order and writes the slot (m, b) before the flag
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        sy += __shfl_xor_sync(0xffffffffu, sy, o);
-        sp += __shfl_xor_sync(0xffffffffu, sp, o);
-      }
-      if (lane == 0) {
-        s_wy[warp] = sy;
-        s_wp[warp] = sp;
-      }
+      // the norm partials go to warp 0 (reduced there during the next
+      // iteration); the flag publishes the ring cells of y_{m+1}
+      s_py[m & 1][t] = sy;
+      s_pp[m & 1][t] = sp;
       __syncthreads();
       if (t == 0) {
-        double ty = 0.0, tp = 0.0;
-        for (int q = 0; q < nwarps; ++q) {
-          ty += s_wy[q];
-          tp += s_wp[q];
-        }
-        double* s2 = slots + 2LL * ((long long)m * kNsyncMaxBlocks + b);
-        s2[0] = ty;                                 // the slot value itself is the signal
-        s2[1] = tp;
         __threadfence();
         *(volatile unsigned int*)(flags + b) = (unsigned int)(m + 1);
       }
@@ -964,12 +980,95 @@ __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom ge
 
 }  // namespace
 
+namespace {
+
+// Cooperative launch of fn on G blocks of T threads with smem bytes of dynamic
+// shared memory, if they fit (shared memory, co-residency); false, with no
+// error left pending, if not.  The checks are cached per (device, kernel,
+// smem, T): a series is launched on every step, and the attribute and
+// occupancy queries would otherwise keep the device waiting for the host.
+bool coop_launch(const void* fn, int G, int T, size_t smem, void** params, cudaStream_t s) {
+  struct DevInfo {
+    int dev, sms, optin;
+  };
+  struct FnInfo {
+    int dev;
+    const void* fn;
+    size_t static_smem;
+    bool ok;
+  };
+  struct Fit {
+    int dev;
+    const void* fn;
+    size_t smem;
+    int T, per_sm;
+  };
+  static std::mutex mu;
+  static std::vector<DevInfo> devs;
+  static std::vector<FnInfo> fns;
+  static std::vector<Fit> fits;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int per_sm = -1, sms = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    const DevInfo* di = nullptr;
+    for (const DevInfo& d : devs)
+      if (d.dev == dev) di = &d;
+    if (!di) {
+      DevInfo d{dev, 0, 0};
+      cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaDeviceGetAttribute(&d.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      devs.push_back(d);
+      di = &devs.back();
+    }
+    sms = di->sms;
+    const FnInfo* fi = nullptr;
+    for (const FnInfo& f : fns)
+      if (f.dev == dev && f.fn == fn) fi = &f;
+    if (!fi) {   // once per kernel: allow all the dynamic shared memory the device has
+      cudaFuncAttributes fa{};
+      FnInfo f{dev, fn, 0, false};
+      if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess && fa.sharedSizeBytes <= (size_t)di->optin) {
+        f.static_smem = fa.sharedSizeBytes;
+        f.ok = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    di->optin - (int)fa.sharedSizeBytes) == cudaSuccess;
+      }
+      cudaGetLastError();
+      fns.push_back(f);
+      fi = &fns.back();
+    }
+    if (!fi->ok || smem + fi->static_smem > (size_t)di->optin) return false;
+    for (const Fit& f : fits)
+      if (f.dev == dev && f.fn == fn && f.smem == smem && f.T == T) per_sm = f.per_sm;
+    if (per_sm < 0) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, T, smem) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 0;
+      }
+      fits.push_back(Fit{dev, fn, smem, T, per_sm});
+    }
+  }
+  if ((long long)per_sm * sms < G) return false;
+  if (cudaLaunchCooperativeKernel(fn, dim3(G), dim3(T), params, smem, s) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  ++launch_counter();
+  return true;
+}
+
+}  // namespace
+
 // Cooperative persistent series (FP64).  Returns 7 (2-D tile kernel), 2 (row
 // kernel with neighbour synchronisation) or 1 (grid-barrier kernel) when
 // launched, 0 when the grid is too large or the launch is refused (the caller
-// then uses the per-iteration path).  The tile kernel runs when a tile holds at
-// least kTileMinCells cells, else the row kernel; AD_F64_KERNEL=row|tile forces
-// either, AD_NO_NSYNC the grid-barrier kernel (tuning and A/B overrides).
+// then uses the per-iteration path).  The tile kernel runs whenever its tiles
+// fit in shared memory, else the row kernel; AD_F64_KERNEL=row forces the row
+// kernel, AD_NO_NSYNC the grid-barrier kernel (A/B overrides).
 int series_run_persistent(const SeriesArgs& a, unsigned int* gen, const NsyncScratch* ns,
                           cudaStream_t s) {
   if (a.prec != 0 || a.g.n > kPersistMaxCells) return 0;
@@ -977,29 +1076,19 @@ int series_run_persistent(const SeriesArgs& a, unsigned int* gen, const NsyncScr
   const int G = (int)std::min<long long>(152, (n + 31) / 32);
   const unsigned int cpb = (unsigned int)((n + G - 1) / G);
   const int T = persist_threads((int)cpb);
-  int dev = 0, sms = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  static const int optin = [] {   // the geometry search below needs the device's limit
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+  }();
   static const bool no_nsync = getenv("AD_NO_NSYNC") != nullptr;
   SeriesArgs args = a;
   args.nblocks = G;
-  // true if launched; false (and no error left pending) if it does not fit
   auto try_launch = [&](void* fn, size_t smem, void** params) -> bool {
-    cudaFuncAttributes fa{};
-    int per_sm = 0;
-    const bool ok =
-        cudaFuncGetAttributes(&fa, fn) == cudaSuccess && smem + fa.sharedSizeBytes <= (size_t)optin &&
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
-            cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, T, smem) == cudaSuccess &&
-        (long long)per_sm * sms >= G &&
-        cudaLaunchCooperativeKernel(fn, dim3(G), dim3(T), params, smem, s) == cudaSuccess;
-    if (!ok) cudaGetLastError();
-    if (ok) ++launch_counter();
-    return ok;
+    return coop_launch(fn, G, T, smem, params, s);
   };
-  // 0 by tile size, 1 rows, 2 tiles (AD_F64_KERNEL=row|tile: tuning and A/B overrides)
+  // 0 tiles where they fit, 1 rows (AD_F64_KERNEL=row|tile: A/B overrides)
   static const int f64_kernel = [] {
     const char* e = getenv("AD_F64_KERNEL");
     return !e ? 0 : (e[0] == 'r' ? 1 : (e[0] == 't' ? 2 : 0));
@@ -1022,7 +1111,7 @@ int series_run_persistent(const SeriesArgs& a, unsigned int* gen, const NsyncScr
       const long long cells = (long long)tw * th;
       const size_t smem_t =
           sizeof(double) * ((size_t)cells * (a.aug ? 13 : 12) + 2 * (size_t)(tw + 2) * (th + 2));
-      if (smem_t + 8 * 1024 > (size_t)optin) continue;
+      if (smem_t + 12 * 1024 > (size_t)optin) continue;   // + the static shared arrays
       const bool better = best_cells < 0 || cells < best_cells ||
                           (cells == best_cells && tw + th < best.tw + best.th);
       if (better) {
@@ -1031,11 +1120,10 @@ int series_run_persistent(const SeriesArgs& a, unsigned int* gen, const NsyncScr
         best_G = Ga;
       }
     }
-    // Measured on GB300 (two-stage 512x512-type workloads): below about 1000
-    // cells per tile the row kernel is faster (64^2 .. 384^2: 6.6 .. 8.8 us
-    // against 8.4 .. 9.1 us per iteration); from 448^2 up the tiles win.
-    constexpr long long kTileMinCells = 1024;
-    if (best_cells > 0 && (best_cells >= kTileMinCells || f64_kernel == 2)) {
+    // Measured on GB300 (two-stage workloads, us per iteration, tile / row):
+    // 64^2 5.9 / 6.5, 128^2 5.4 / 5.2, 192^2 5.6 / 5.7, 256^2 6.3 / 6.7,
+    // 384^2 6.9 / 8.8, 512^2 9.0 / 10.9: the tiles win or tie at every size.
+    if (best_cells > 0) {
       const size_t smem = sizeof(double) * ((size_t)best_cells * (a.aug ? 13 : 12) +
                                             2 * (size_t)best.S * (best.th + 2));
       void* fn = a.aug ? (void*)leja_tile_f64_k<true> : (void*)leja_tile_f64_k<false>;
@@ -1044,22 +1132,7 @@ int series_run_persistent(const SeriesArgs& a, unsigned int* gen, const NsyncScr
       double* slots = ns->slots;
       unsigned int* flags = ns->flags;
       void* params[] = {&targs, &best, &slots, &flags, &gen};
-      cudaFuncAttributes fa{};
-      int per_sm = 0;
-      const bool ok =
-          cudaFuncGetAttributes(&fa, fn) == cudaSuccess &&
-          smem + fa.sharedSizeBytes <= (size_t)optin &&
-          cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
-              cudaSuccess &&
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem) == cudaSuccess &&
-          (long long)per_sm * sms >= best_G &&
-          cudaLaunchCooperativeKernel(fn, dim3(best_G), dim3(256), params, smem, s) ==
-              cudaSuccess;
-      if (!ok) cudaGetLastError();
-      if (ok) {
-        ++launch_counter();
-        return 7;
-      }
+      if (coop_launch(fn, best_G, 256, smem, params, s)) return 7;
     }
   }
   if (ns && ns->slots && ns->flags && !no_nsync && G <= kNsyncMaxBlocks) {

@@ -1,8 +1,8 @@
 """The three persistent FP64 series kernels agree bit for bit.
 
 Small FP64 grids run a whole Newton series in one cooperative launch.  The
-tile kernel (AD_F64_KERNEL=tile; the default for tiles of >= 1024 cells) and
-the row kernel (AD_F64_KERNEL=row; the default below) synchronise
+tile kernel (the default wherever its tiles fit in shared memory) and the row
+kernel (AD_F64_KERNEL=row; the fallback) synchronise
 each block with its neighbours only and apply the stopping rule two
 iterations late (dropping the extra iteration); the grid-barrier kernel
 (selected with AD_NO_NSYNC) decides after every iteration.  All three form
@@ -94,10 +94,9 @@ def test_neighbour_sync_kernel_equals_grid_barrier_kernel(case, tmp_path):
 
 @pytest.mark.parametrize("case", CASES)
 def test_tile_kernel_equals_grid_barrier_kernel(case, tmp_path):
-    """The 2-D tile kernel (forced here: by default it runs for large tiles
-    only) forms every entry as the grid-barrier kernel does; its norm sums run
-    over another cell-to-block assignment, so the error estimates agree to
-    rounding."""
+    """The 2-D tile kernel forms every entry as the grid-barrier kernel does;
+    its norm sums run over another cell-to-block assignment, so the error
+    estimates agree to rounding."""
     need_gpu()
     s_new, phi_new, u_new = _run(case, str(tmp_path / "tile"), {"AD_F64_KERNEL": "tile"})
     s_old, phi_old, u_old = _run(case, str(tmp_path / "grid"), {"AD_NO_NSYNC": "1"})
