@@ -124,10 +124,40 @@ struct NsyncScratch {
 };
 size_t nsync_slots_bytes();
 int nsync_max_blocks();
-// ns == nullptr selects the grid-barrier kernel.  Returns 2 (neighbour-
-// synchronised kernel launched), 1 (grid-barrier kernel launched) or 0.
+// Totals of asynchronous steps, accumulated on the device (one thread).
+struct AsyncTotals {
+  long long iters;         // Leja iterations of all series
+  long long timed_iters;   // ... of the series that ran with timing events
+  long long launches;      // graph-body kernel launches (known on the device only)
+  int series;
+  int status;              // worst: 0 ok, 3 not converged, 4 no stop state / timeout
+  double err_est;          // largest error estimate
+};
+
+// A whole exponential step in the persistent tile kernel (fixed rule, one
+// substep, FP64).  Prologue: w1 = A u + sum a_k g_k (to global w1) and
+// w2 = sum b_k g_k, as the apply kernel forms them, then the series start of
+// series_init (s = 2: y_0 = 0, p_0 = d0 y_0; s = 1: y_0 = w1, p_0 = d0 w1);
+// epilogue: u = u + b P in place of the axpby (b = 1 for s = 2, dt for s = 1).
+// With totals set, block 0 also adds the series to them (asynchronous steps).
+struct StepFuse {
+  int s;                   // 1 or 2
+  const double* W;         // unscaled weights of A
+  double* u;               // the step's state (read by the prologue, updated by the epilogue)
+  double* w1;              // global scratch for w1
+  Sources src;
+  double d0, b;
+  int force, max_iters;
+  double tol;
+  AsyncTotals* totals;     // null: synchronous step
+  int timed;
+};
+
+// ns == nullptr selects the grid-barrier kernel.  Returns 7 (tile kernel),
+// 2 (row kernel), 1 (grid-barrier kernel) when launched, or 0.  With fuse,
+// only the tile kernel is tried (0: the caller runs the step unfused).
 int series_run_persistent(const SeriesArgs& a, unsigned int* gen, const NsyncScratch* ns,
-                           cudaStream_t s);
+                          cudaStream_t s, const StepFuse* fuse = nullptr);
 
 // grid size of the fused iteration kernel (FP64: by cell count; FP32: by tile count)
 int series_blocks(int prec, long long n);

@@ -79,16 +79,6 @@ struct SeriesGraph {
   bool tried = false;
 };
 
-// Totals of asynchronous steps, accumulated on the device (one thread).
-struct AsyncTotals {
-  long long iters;         // Leja iterations of all series
-  long long timed_iters;   // ... of the series that ran with timing events
-  long long launches;      // graph-body kernel launches (known on the device only)
-  int series;
-  int status;              // worst: 0 ok, 3 not converged, 4 no stop state / timeout
-  double err_est;          // largest error estimate
-};
-
 struct ad_operator {
   ad_grid grid{};
   GridDev g{};
@@ -123,6 +113,7 @@ struct ad_operator {
   AsyncTotals* h_totals = nullptr;             // pinned mirror
   ad_stats async_host{};
   int async_worst = 0;                         // worst status of synchronous fallbacks
+  bool ctrl_dirty = false;                     // a series gave up: reset ctrl before a fused step
   std::vector<cudaEvent_t> atev;               // event pairs around async series (timing)
   int atev_used = 0;
   // series timing (ad_time_series)
@@ -420,10 +411,21 @@ __global__ void async_collect_k(const Ctrl* c, AsyncTotals* t, int per_launch, i
   if (e > t->err_est) t->err_est = e;
 }
 
+constexpr int kNotFused = -100;   // run_series: the fused step did not launch
+
+// fuse (optional): run the whole step in the tile kernel (see StepFuse); src
+// and tail are then unused, and kNotFused is returned when it cannot launch
+// (nothing was enqueued: the caller runs the step unfused).
 int run_series(ad_operator* op, int aug, const void* src, double d0, int force, double tol,
-               ad_stats* st, int* iters_out, const Tail* tail = nullptr, bool async = false) {
+               ad_stats* st, int* iters_out, const Tail* tail = nullptr, bool async = false,
+               const StepFuse* fuse = nullptr) {
   SeriesArgs a = series_args(op, aug);
-  series_init(a, src, d0, force, op->max_iters, tol, op->stream);
+  if (fuse && (force == 0 || getenv("AD_NO_PERSIST") || getenv("AD_NO_FUSE"))) return kNotFused;
+  if (fuse && op->ctrl_dirty) {   // the fused kernel relies on a clean barrier ticket
+    CUDA_TRY(cudaMemsetAsync(op->ctrl, 0, sizeof(Ctrl), op->stream));
+    op->ctrl_dirty = false;
+  }
+  if (!fuse) series_init(a, src, d0, force, op->max_iters, tol, op->stream);
   CUDA_TRY(cudaGetLastError());
   int iters = 0;
   bool graph_used = false;
@@ -448,7 +450,11 @@ int run_series(ad_operator* op, int aug, const void* src, double d0, int force, 
     if (op->time_series) CUDA_TRY(cudaEventRecord(ev[0], op->stream));
     // small and medium FP64 grids: the whole series in one cooperative launch
     const int pk = getenv("AD_NO_PERSIST") ? 0
-                   : series_run_persistent(a, &op->ctrl->gen, &op->nsync, op->stream);
+                   : series_run_persistent(a, &op->ctrl->gen, &op->nsync, op->stream, fuse);
+    if (fuse && !pk) {
+      if (op->time_series && async) --op->atev_used;   // the event pair is reused
+      return kNotFused;
+    }
     const bool persist = pk != 0;
     if (!persist && !sg.tried) build_graph(op, aug);
     if (persist) {
@@ -473,10 +479,12 @@ int run_series(ad_operator* op, int aug, const void* src, double d0, int force, 
     if (op->time_series) CUDA_TRY(cudaEventRecord(ev[1], op->stream));
     enqueue_tail(op, tail);
     if (async) {
-      const int per_launch = graph_used ? (series_pair(a) ? 2 : 1) : 0;
-      async_collect_k<<<1, 1, 0, op->stream>>>(op->ctrl, op->totals, per_launch,
-                                               op->time_series ? 1 : 0);
-      ++launch_counter();
+      if (!fuse) {   // (the fused kernel reports to the totals itself)
+        const int per_launch = graph_used ? (series_pair(a) ? 2 : 1) : 0;
+        async_collect_k<<<1, 1, 0, op->stream>>>(op->ctrl, op->totals, per_launch,
+                                                 op->time_series ? 1 : 0);
+        ++launch_counter();
+      }
       CUDA_TRY(cudaGetLastError());
       if (op->time_series) op->t_path = persist ? pk : (graph_used ? 3 : 4) + (series_pair(a) ? 2 : 0);
       *iters_out = -1;
@@ -493,6 +501,7 @@ int run_series(ad_operator* op, int aug, const void* src, double d0, int force, 
       op->t_iters += iters;
       op->t_path = persist ? pk : (graph_used ? 3 : 4) + (series_pair(a) ? 2 : 0);
     }
+    if (!op->h_ctrl->stop || op->h_ctrl->status == 4) op->ctrl_dirty = true;
     if (!op->h_ctrl->stop) return fail(AD_ERR_TIMEOUT, "Leja series did not reach its stop state");
     {  // the device stores |d_{m+1}| and the squared norms; form the estimate here
       const Ctrl& h = *op->h_ctrl;
@@ -999,9 +1008,43 @@ int expquad_impl(ad_operator* op, void* u, double t, double dt, int s, const dou
   const long long n = op->g.n;
   const int force = force_iters < 0 ? -1 : force_iters;
   int status = AD_OK;
+  // FP64 steps of one substep under the fixed rule: the whole step in one
+  // launch of the tile kernel when it fits (apply, series start, series and
+  // update fused); false if it cannot run, with nothing enqueued.
+  auto try_fused = [&](int kind, double b, int* r_out) -> bool {
+    if (op->prec != 0 || (op->adaptive && force < 0) || n_substeps(op, dt) != 1) return false;
+    double d0 = 0.0, eta0[2] = {0.0, 1.0}, eta_next[2];
+    if (upload_series(op, kind, dt, eta0, &d0, eta_next) != AD_OK) return false;
+    StepFuse F{};
+    F.s = kind == 1 ? 2 : 1;
+    F.W = op->W;
+    F.u = static_cast<double*>(ud);
+    F.w1 = static_cast<double*>(op->W1);
+    F.src = S;
+    F.d0 = d0;
+    F.b = b;
+    F.force = force;
+    F.max_iters = op->max_iters;
+    F.tol = tol;
+    F.totals = async ? op->totals : nullptr;
+    F.timed = op->time_series ? 1 : 0;
+    int it = 0;
+    const int r = run_series(op, kind, nullptr, d0, force, tol, &st, &it, nullptr, async, &F);
+    if (r == kNotFused) return false;
+    st.matvecs += 1;
+    st.substeps = 1;
+    *r_out = r;
+    return true;
+  };
+  int rf = AD_OK;
   if (s == 1) {
     // v = A u + S(t + c1 dt);  u += dt phi_1(dt A) v   (Eq. exp_midpoint for c1 = 1/2)
     for (int k = 0; k < S.n; ++k) S.a[k] = h_at(src, k, t + c[0] * dt);
+  }
+  if (s == 1 && try_fused(0, dt, &rf)) {
+    if (rf != AD_OK && rf != AD_ERR_NOT_CONVERGED) return rf;
+    status = rf;
+  } else if (s == 1) {
     apply(op, ud, op->W1, nullptr, S);
     st.matvecs += 1;
     // a non-converged fixed step is still applied (with the last series);
@@ -1023,10 +1066,17 @@ int expquad_impl(ad_operator* op, void* u, double t, double dt, int s, const dou
       S.a[k] = (c2 * h1 - c1 * h2) / (c2 - c1);
       S.b[k] = (h2 - h1) / ((c2 - c1) * dt);
     }
-    apply(op, ud, op->W1, op->W2, S);
-    st.matvecs += 1;
+    const bool fused = try_fused(1, 1.0, &rf);
+    if (fused && rf != AD_OK && rf != AD_ERR_NOT_CONVERGED) return rf;
+    if (fused) status = rf;
+    if (!fused) {
+      apply(op, ud, op->W1, op->W2, S);
+      st.matvecs += 1;
+    }
     double eta[2] = {0.0, 1.0};
-    if (op->adaptive && force < 0) {
+    if (fused) {
+      // done in the tile kernel
+    } else if (op->adaptive && force < 0) {
       // adaptive substep control: exp(h_k Atilde) applied to the accepted state
       SubstepCtl ctl(dt, n_substeps(op, dt), op->max_iters);
       bool have_x = false, finished = false;
@@ -1153,6 +1203,7 @@ int ad_async_totals(ad_operator* op, ad_stats* stats) {
   op->async_worst = 0;
   CUDA_TRY(cudaMemsetAsync(op->totals, 0, sizeof(AsyncTotals), op->stream));
   if (stats) *stats = r;
+  if (worst == 4) op->ctrl_dirty = true;
   if (worst == 4) return fail(AD_ERR_TIMEOUT, "an asynchronous series did not reach its stop state");
   if (worst == 3) return fail(AD_ERR_NOT_CONVERGED, "an asynchronous series reached max_iters");
   return AD_OK;

@@ -10,6 +10,7 @@
 //    neighbourhood of a block is too wide for the first kernel's window or
 //    its shared memory does not fit.
 #include "ad_internal.h"
+#include "stencil9.cuh"
 
 #include <algorithm>
 #include <cstdlib>
@@ -79,10 +80,12 @@ struct Nb9 {
   double sw, s, se, w, c, e, nw, n, ne;
 };
 
+// w1 is read with a plain (coherent) load: the fused step of the tile kernel
+// writes it in the same launch.
 template <bool AUG>
 __device__ __forceinline__ double f64_cell(const double* __restrict__ sW, int cpb, int k,
                                            const Nb9& y, const LejaCoef& lc, double w2v,
-                                           const double* __restrict__ w1, int idx) {
+                                           const double* w1, int idx) {
   double z = sW[4 * cpb + k] * y.c;
   z = fma(sW[0 * cpb + k], y.sw, z);
   z = fma(sW[1 * cpb + k], y.s, z);
@@ -95,7 +98,7 @@ __device__ __forceinline__ double f64_cell(const double* __restrict__ sW, int cp
   z = fma(-lc.xi, y.c, z);
   if (AUG) {
     if (lc.e1 != 0.0) z = fma(lc.e1, w2v, z);
-    if (lc.e2 != 0.0) z = fma(lc.e2, __ldg(w1 + idx), z);
+    if (lc.e2 != 0.0) z = fma(lc.e2, w1[idx], z);
   }
   return z;
 }
@@ -700,7 +703,8 @@ __device__ __forceinline__ void halo_cell(int q, int tw, int th, int& hx, int& h
 
 template <bool AUG>
 __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom geo, double* slots,
-                                                       unsigned int* flags, unsigned int* gen) {
+                                                       unsigned int* flags, unsigned int* gen,
+                                                       StepFuse F) {
   extern __shared__ double smem[];
   __shared__ double s_py[2][256], s_pp[2][256];   // per-thread norm partials, double-buffered
   __shared__ int s_nb[8];
@@ -728,12 +732,13 @@ __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom ge
   double* sW2 = sP + 3 * cpb;               // [cpb] (augmented)
   double* win = sW2 + (AUG ? cpb : 0);      // [2][WB]: y_m lives in buffer m & 1
   const double* __restrict__ Ws = static_cast<const double*>(a.coef);
-  const double* __restrict__ w1 = static_cast<const double*>(a.w1);
+  const double* w1 = static_cast<const double*>(a.w1);
   const double* __restrict__ w2 = static_cast<const double*>(a.w2);
   Ctrl* ctrl = a.ctrl;
-  const int force = ctrl->force;
-  const int max_it = min(ctrl->max_iters, kMaxIters);
-  const double tol = ctrl->tol;
+  const bool fused = F.s != 0;                     // a whole step (see StepFuse)
+  const int force = fused ? F.force : ctrl->force;
+  const int max_it = min(fused ? F.max_iters : ctrl->max_iters, kMaxIters);
+  const double tol = fused ? F.tol : ctrl->tol;
   auto gidx = [&](int li, int lj) { return (y0 + lj) * nx + x0 + li; };
   auto widx = [&](int li, int lj) { return (lj + 1) * S + li + 1; };
 
@@ -764,17 +769,48 @@ __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom ge
       }
     s_nnb = cnt;
   }
+  for (int q = t; q < 2 * WB; q += T) win[q] = 0.0;   // the Dirichlet halo stays 0
+  if (fused && t == 0 && b == 0) {                 // what series_init resets
+    ctrl->m = 0;
+    ctrl->stop = 0;
+    ctrl->iters = 0;
+    ctrl->status = 0;
+    ctrl->force = F.force;
+    ctrl->max_iters = F.max_iters;
+    ctrl->tol = F.tol;
+    ctrl->err_est = 0.0;
+    ctrl->ynorm2 = 0.0;
+    ctrl->pnorm2 = 0.0;
+  }
+  __syncthreads();
   for (int k = t; k < nc; k += T) {
     const int li = k % tw, lj = k / tw;
     const int idx = gidx(li, lj);
 #pragma unroll
     for (int q = 0; q < 9; ++q) sW[q * cpb + k] = Ws[(long long)q * n + idx];
-    sP[k] = static_cast<const double*>(a.p)[idx];
-    if (AUG) sW2[k] = w2[idx];
+    if (!fused) {
+      sP[k] = static_cast<const double*>(a.p)[idx];
+      if (AUG) sW2[k] = w2[idx];
+      continue;
+    }
+    // the step's right-hand sides, as the apply kernel forms them
+    const double au = stencil9(F.W, n, F.u, x0 + li, y0 + lj, nx, ny, g.bc, idx);
+    double r = 1.0 * au, r2 = 0.0;
+    for (int q = 0; q < F.src.n; ++q) {
+      const double gq = static_cast<const double*>(F.src.g[q])[idx];
+      r = fma(F.src.a[q], gq, r);
+      r2 = fma(F.src.b[q], gq, r2);
+    }
+    F.w1[idx] = r;
+    if (F.s == 2) {                                // y_0 = 0: the window stays 0
+      if (AUG) sW2[k] = r2;
+      sP[k] = F.d0 * 0.0;
+    } else {                                       // y_0 = w1
+      win[widx(li, lj)] = r;
+      sP[k] = F.d0 * r;
+    }
   }
-  {  // both window buffers zero (the Dirichlet halo stays 0), then y_0 on tile + halo
-    for (int q = t; q < 2 * WB; q += T) win[q] = 0.0;
-    __syncthreads();
+  if (!fused) {  // y_0 on tile + halo (a fused phi_1 step loads its halo after the barrier)
     const double* y0g = static_cast<const double*>(a.y[0]);
     for (int k = t; k < nc; k += T) win[widx(k % tw, k / tw)] = y0g[gidx(k % tw, k / tw)];
     for (int q = t; q < nH; q += T) {
@@ -811,6 +847,21 @@ __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom ge
     __threadfence();
   }
   __syncthreads();
+  if (fused && F.s == 1) {   // the halo of y_0 = w1, which the neighbours wrote before the barrier
+    for (int q = t; q < nH; q += T) {
+      int hx, hy;
+      halo_cell(q, tw, th, hx, hy);
+      int gx = x0 + hx, gy = y0 + hy;
+      if (periodic) {
+        gx = (gx + nx) % nx;
+        gy = (gy + ny) % ny;
+      } else if (gx < 0 || gy < 0 || gx >= nx || gy >= ny) {
+        continue;
+      }
+      win[(hy + 1) * S + hx + 1] = __ldcg(F.w1 + gy * nx + gx);
+    }
+    __syncthreads();
+  }
 
   int m = 0;
   int fin = -1;
@@ -961,12 +1012,20 @@ __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom ge
     if (t == 0) {
       atomicMax(&ctrl->status, 4);           // AD_ERR_TIMEOUT
       ctrl->stop = 1;
+      if (fused && F.totals) atomicMax(&F.totals->status, 4);
     }
     return;
   }
   const double* Pf = sP + ((fin + 1) % 3) * cpb;
-  double* p = static_cast<double*>(a.p);
-  for (int k = t; k < nc; k += T) p[gidx(k % tw, k / tw)] = Pf[k];
+  if (fused) {   // u = 1 u + b P, as the axpby kernel forms it
+    for (int k = t; k < nc; k += T) {
+      const int idx = gidx(k % tw, k / tw);
+      F.u[idx] = fma(F.b, Pf[k], 1.0 * F.u[idx]);
+    }
+  } else {
+    double* p = static_cast<double*>(a.p);
+    for (int k = t; k < nc; k += T) p[gidx(k % tw, k / tw)] = Pf[k];
+  }
   if (b == 0 && t == 0) {
     ctrl->iters = fin + 1;
     ctrl->m = fin + 1;
@@ -975,6 +1034,17 @@ __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom ge
     ctrl->err_est = a.lc[fin].absd;
     atomicMax(&ctrl->status, s_status);
     ctrl->stop = 1;
+    if (fused && F.totals) {   // the asynchronous step's report
+      AsyncTotals* tt = F.totals;
+      const int it = fin + 1;
+      tt->iters += it;
+      if (F.timed) tt->timed_iters += it;
+      tt->series += 1;
+      if (s_status > tt->status) tt->status = s_status;
+      const double e = s_tp > 0.0 ? a.lc[fin].absd * sqrt(s_ty / s_tp)
+                                  : (s_ty > 0.0 ? INFINITY : 0.0);
+      if (e > tt->err_est) tt->err_est = e;
+    }
   }
 }
 
@@ -1070,8 +1140,9 @@ bool coop_launch(const void* fn, int G, int T, size_t smem, void** params, cudaS
 // fit in shared memory, else the row kernel; AD_F64_KERNEL=row forces the row
 // kernel, AD_NO_NSYNC the grid-barrier kernel (A/B overrides).
 int series_run_persistent(const SeriesArgs& a, unsigned int* gen, const NsyncScratch* ns,
-                          cudaStream_t s) {
+                          cudaStream_t s, const StepFuse* fuse) {
   if (a.prec != 0 || a.g.n > kPersistMaxCells) return 0;
+  if (fuse && (fuse->s == 2) != (a.aug != 0)) return 0;
   const long long n = a.g.n;
   const int G = (int)std::min<long long>(152, (n + 31) / 32);
   const unsigned int cpb = (unsigned int)((n + G - 1) / G);
@@ -1131,10 +1202,13 @@ int series_run_persistent(const SeriesArgs& a, unsigned int* gen, const NsyncScr
       targs.nblocks = best_G;
       double* slots = ns->slots;
       unsigned int* flags = ns->flags;
-      void* params[] = {&targs, &best, &slots, &flags, &gen};
+      StepFuse F{};
+      if (fuse) F = *fuse;
+      void* params[] = {&targs, &best, &slots, &flags, &gen, &F};
       if (coop_launch(fn, best_G, 256, smem, params, s)) return 7;
     }
   }
+  if (fuse) return 0;   // only the tile kernel runs whole steps
   if (ns && ns->slots && ns->flags && !no_nsync && G <= kNsyncMaxBlocks) {
     NsyncGeom geo;
     geo.cpb = (int)cpb;

@@ -56,7 +56,10 @@ def test_async_steps_equal_synchronous_steps(case):
     assert tot["iters"] == sum(x["iters"] for x in st)
     assert tot["matvecs"] == sum(x["matvecs"] for x in st)
     assert tot["substeps"] == steps
-    assert tot["kernel_launches"] == sum(x["kernel_launches"] for x in st) + steps  # + collect
+    # FP64 steps run whole in the tile kernel, which reports itself; an
+    # unfused series adds one collect kernel
+    extra = 0 if prec == 0 else steps
+    assert tot["kernel_launches"] == sum(x["kernel_launches"] for x in st) + extra
     assert tot["converged"]
     assert tot["err_est"] == pytest.approx(max(x["err_est"] for x in st), rel=1e-12, abs=1e-300)
 

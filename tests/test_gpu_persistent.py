@@ -109,6 +109,59 @@ def test_tile_kernel_equals_grid_barrier_kernel(case, tmp_path):
     assert np.array_equal(u_new, u_old)
 
 
+# Two midpoint (s = 1) and two two-stage (s = 2) steps from u0; prints the
+# stats of every step and writes the two final states.
+STEPS_CHILD = r"""
+import json, sys
+import numpy as np, torch
+sys.path.insert(0, {root!r})
+import paper_2307_12276_gb300 as ad
+from workloads import small_problem
+nx, ny, bc, kind, adv, advf, f = {case!r}
+out = {{}}
+for s, c in ((1, (0.5,)), (2, (1 / 3, 2 / 3))):
+    p = small_problem(nx, ny, bc, kind, adv=tuple(adv), adv_field=advf, dt_factor=f, s=s, c=c)
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(),
+                                  device="cuda:0")
+    g = p.grid
+    ax, ay = (T(p.ax_arr()), T(p.ay_arr())) if advf else (float(p.ax), float(p.ay))
+    op = ad.create_operator(g.nx, g.ny, g.bc, T(p.Dxx), T(p.Dxy), T(p.Dyy), ax, ay, ad.FP64)
+    src = ad.Source([T(gk) for gk in p.source.g], list(p.source.h)) if len(p.source) else None
+    u = T(p.u0)
+    st = [ad.expquad_step(op, u, k * p.dt, p.dt, s, c, src, tol=1e-10) for k in range(2)]
+    np.save({prefix!r} + f"_s{{s}}.npy", u.cpu().numpy())
+    out[s] = st
+print(json.dumps(out))
+"""
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[2], CASES[4]])
+def test_fused_step_equals_unfused_step(case, tmp_path):
+    """A whole step in one launch of the tile kernel (its prologue forms
+    A u + sources as the apply kernel does, its epilogue adds P to u as the
+    axpby kernel does) gives the unfused sequence's result bit for bit."""
+    need_gpu()
+    res = {}
+    for tag, env in (("fused", {}), ("unfused", {"AD_NO_FUSE": "1"})):
+        e = dict(os.environ)
+        e.update(env)
+        prefix = str(tmp_path / tag)
+        code = STEPS_CHILD.format(root=ROOT, case=case, prefix=prefix)
+        r = subprocess.run([sys.executable, "-c", code], env=e, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        res[tag] = (json.loads(r.stdout.strip().splitlines()[-1]),
+                    {s: np.load(f"{prefix}_s{s}.npy") for s in (1, 2)})
+    (sf, uf), (su, uu) = res["fused"], res["unfused"]
+    for s in ("1", "2"):
+        for a, b in zip(sf[s], su[s]):
+            assert a["iters"] == b["iters"] and a["err_est"] == b["err_est"]
+            assert a["kernel_launches"] == 1          # the whole step is one launch
+            assert b["kernel_launches"] > 1
+    for s in (1, 2):
+        assert np.array_equal(uf[s], uu[s])
+
+
 def test_series_timing_counts_every_series():
     need_gpu()
     from workloads import small_problem
