@@ -645,6 +645,33 @@ def measure_batched_form(ad, dev, stream, steps, nslices=128, sides=(256, 512, 1
     ev1.record(stream)
     torch.cuda.synchronize()
     ms_seq = ev0.elapsed_time(ev1) / steps
+    # the plain FP64 GPU method on the same slices (one call per slice, the
+    # same bounds, steps and tolerance): the batch's speedup at the accuracy
+    # both reach, and how far the batch's FP32 states are from the FP64 ones
+    ops64, u64, srcs64 = [], [], []
+    for op, D, p, u0, src in zip(ops, fields, probs, u_start, srcs):
+        o = ad.create_operator(p.grid.nx, p.grid.ny, p.grid.bc, *D, 0.05, 0.0, ad.FP64,
+                               stream=stream)
+        ad.set_spectral_bound(o, ad.get_spectral_bound(op))
+        ops64.append(o)
+        u64.append(u0.double())
+        srcs64.append(ad.Source([src.g[0].double()], None))
+    for o, u, src in zip(ops64, u64, srcs64):
+        ad.expquad_step(o, u, 0.0, dt, 1, (0.5,), src, tol=1e-6)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for k in range(steps):
+        for o, u, src in zip(ops64, u64, srcs64):
+            ad.expquad_step(o, u, (k + 1) * dt, dt, 1, (0.5,), src, tol=1e-6)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_fp64 = ev0.elapsed_time(ev1) / steps
+    err_fp64 = max(float(torch.linalg.vector_norm(a.double() - b) / torch.linalg.vector_norm(b))
+                   for a, b in zip(us, u64))
+    for o in ops64:
+        o.close()
+    del ops64, u64, srcs64
+    torch.cuda.empty_cache()
     # algorithmic HBM bytes of the iteration passes: 28 B per cell and iteration
     per_slice_iters = [s["iters"] for s in st]
     alg_bytes = sum(28.0 * p.grid.n * it for p, it in zip(probs, per_slice_iters))
@@ -653,6 +680,10 @@ def measure_batched_form(ad, dev, stream, steps, nslices=128, sides=(256, 512, 1
            "unit": "Mcell-steps/s", "ms_per_step": round(ms_batch, 4),
            "sequential_ms_per_step": round(ms_seq, 4),
            "speedup_vs_one_call_per_slice": round(ms_seq / ms_batch, 3),
+           "plain_fp64": {"ms_per_step": round(ms_fp64, 4), "tol": 1e-6,
+                          "speedup_batch_over_plain_fp64": round(ms_fp64 / ms_batch, 3),
+                          "max_slice_rel_l2_batch_vs_fp64": err_fp64,
+                          "note": "one FP64 call per slice, same bounds, steps and tolerance"},
            "leja_iters_per_slice": {"min": int(min(per_slice_iters)), "max": int(max(per_slice_iters)),
                                     "mean": round(float(np.mean(per_slice_iters)), 1)},
            "alg_GBps_whole_step": round(alg_bytes / (ms_batch * 1e-3) / 1e9, 1),
