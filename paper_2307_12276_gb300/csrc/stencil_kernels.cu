@@ -41,9 +41,9 @@ namespace {
 // next pair launch, or by pair_flush_k after the series).
 __device__ void series_finish2(const SeriesArgs& a, double y1, double p1, double y2, double p2) {
   __shared__ unsigned int s_last;
-  block_sum2(y1, p1);
+  block_sum2<kPairWarps * 32>(y1, p1);
   const double by1 = y1, bp1 = p1;
-  block_sum2(y2, p2);
+  block_sum2<kPairWarps * 32>(y2, p2);
   Ctrl* ctrl = a.ctrl;
   if (threadIdx.x == 0) {
     double* q = a.partials + 4 * blockIdx.x;
@@ -65,8 +65,8 @@ __device__ void series_finish2(const SeriesArgs& a, double y1, double p1, double
     t2y += __ldcg(&a.partials[4 * b + 2]);
     t2p += __ldcg(&a.partials[4 * b + 3]);
   }
-  block_sum2(t1y, t1p);
-  block_sum2(t2y, t2p);
+  block_sum2<kPairWarps * 32>(t1y, t1p);
+  block_sum2<kPairWarps * 32>(t2y, t2p);
   if (threadIdx.x == 0) {
     const int m = ctrl->m;
     const double tol = ctrl->tol;
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) leja_iter_f32_ring_k(SeriesAr
 // 120-column strips fed by per-warp cp.async rings (tile_f32_pair.cuh); one
 // block of 8 warps per SM.
 template <int ADV>
-__global__ void __launch_bounds__(kRingThreads, 1) leja_iter2_f32_ring_k(SeriesArgs a) {
+__global__ void __launch_bounds__(kPairWarps * 32, 1) leja_iter2_f32_ring_k(SeriesArgs a) {
   extern __shared__ __align__(16) float pair_smem[];
   const volatile Ctrl* vc = a.ctrl;
   if (vc->stop) return;
@@ -583,12 +583,12 @@ __global__ void __launch_bounds__(kRingThreads, 1) leja_iter2_f32_ring_k(SeriesA
   X.aby = a.aby;
   // bands of rows, one per warp of each strip (at least 8 rows each)
   const int strips = (X.G.nx + kPairOwn - 1) / kPairOwn;
-  const long long warps = (long long)gridDim.x * kRingWarps;
+  const long long warps = (long long)gridDim.x * kPairWarps;
   long long bands = warps / strips;
   if (bands > X.G.ny / 8) bands = X.G.ny / 8;
   if (bands < 1) bands = 1;
   const long long units = bands * strips;
-  const long long w = (long long)blockIdx.x * kRingWarps + (threadIdx.x >> 5);
+  const long long w = (long long)blockIdx.x * kPairWarps + (threadIdx.x >> 5);
   long long u0, u1;
   vec_range(units, warps, w, u0, u1);
   float ly1 = 0.f, lp1 = 0.f, ly2 = 0.f, lp2 = 0.f;
@@ -606,7 +606,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) leja_iter2_f32_ring_k(SeriesA
 }
 
 size_t pair_smem_bytes() {
-  return sizeof(float) * (size_t)kRingWarps * PairLayout::STAGES * PairLayout::SIZE;
+  return sizeof(float) * (size_t)kPairWarps * PairLayout::STAGES * PairLayout::SIZE;
 }
 
 // After a pair-mode series: add the pending d_m y_m when it stopped after an
@@ -825,8 +825,8 @@ void series_iteration(const SeriesArgs& a, cudaStream_t s) {
     }
   } else if (series_pair(a)) {
     ++launch_counter();
-    if (a.adv == 0) leja_iter2_f32_ring_k<0><<<a.nblocks, kRingThreads, pair_smem_bytes(), s>>>(a);
-    else leja_iter2_f32_ring_k<1><<<a.nblocks, kRingThreads, pair_smem_bytes(), s>>>(a);
+    if (a.adv == 0) leja_iter2_f32_ring_k<0><<<a.nblocks, kPairWarps * 32, pair_smem_bytes(), s>>>(a);
+    else leja_iter2_f32_ring_k<1><<<a.nblocks, kPairWarps * 32, pair_smem_bytes(), s>>>(a);
   } else if (a.f32k == 3) {
     ++launch_counter();
 #define AD_F32R_LAUNCH(AUGV, ADVV)                                                  \

@@ -24,8 +24,9 @@ __device__ __forceinline__ float face_flux(float a, float du, float q, float dd)
 // Deterministic block sum of two values; result valid in thread 0.  Lanes of
 // warp 0 add eight values each, then one butterfly: far fewer FP64 additions
 // than a butterfly in every warp (FP64 is the scarce pipe on this GPU).
+template <int CAP = kThreads + 32>   // CAP: the most threads a calling block has
 __device__ __forceinline__ void block_sum2(double& a, double& b) {
-  __shared__ double sa[kThreads + 32], sb[kThreads + 32];   // up to 9 warps
+  __shared__ double sa[CAP], sb[CAP];
   const int t = threadIdx.x;
   __syncthreads();
   sa[t] = a;
