@@ -24,6 +24,7 @@ import numpy as np
 import pytest
 
 from gpu_util import DEV, ad, dev64, need_gpu, oracle_operator, torch
+from workloads import small_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -164,7 +165,6 @@ def test_fused_step_equals_unfused_step(case, tmp_path):
 
 def test_series_timing_counts_every_series():
     need_gpu()
-    from workloads import small_problem
     p = small_problem(96, 80, 1, "circular", dt_factor=900.0, s=2, c=(1 / 3, 2 / 3))
     A, alpha = oracle_operator(p)
     op = ad().create_operator(p.grid.nx, p.grid.ny, p.grid.bc, dev64(p.Dxx), dev64(p.Dxy),
@@ -186,3 +186,44 @@ def test_series_timing_counts_every_series():
     assert ad().series_timing(op) == t
     ad().time_series(op)                             # re-enabling resets the totals
     assert ad().series_timing(op) == {"ms": 0.0, "series": 0, "iters": 0, "kernel": None}
+
+
+# FP64 grids across the switch points of the series path: tiles while they fit
+# in shared memory, then the row or grid-barrier kernel, up to 152 x 2048 cells
+# (the largest persistent grid), and the per-iteration graph loop above it.
+SWITCH_SIZES = [(448, 448), (512, 512), (520, 560), (556, 558), (557, 559), (560, 560)]
+
+
+def test_fp64_kernel_switch_points_match_oracle():
+    """A forced two-stage step on each grid against the oracle (1e-11); the
+    kernels that ran are recorded and must include the tile kernel and the
+    graph loop."""
+    need_gpu()
+    from oracle import integrators
+    seen = {}
+    for nx, ny in SWITCH_SIZES:
+        p = small_problem(nx, ny, 1, "circular", adv=(0.1, 0.05), dt_factor=200.0, s=2,
+                          c=(1 / 3, 2 / 3))
+        A, alpha = oracle_operator(p)
+        S = lambda t, p=p: p.source_at(t).ravel()
+        ref, _ = integrators.expquad_step(A, p.u0.ravel(), 0.0, p.dt, 2, (1 / 3, 2 / 3), S,
+                                          alpha, tol=1e-10, force_iters=12)
+        op = ad().create_operator(nx, ny, 1, dev64(p.Dxx), dev64(p.Dxy), dev64(p.Dyy), 0.1, 0.05,
+                                  ad().FP64)
+        ad().set_spectral_bound(op, alpha)
+        src = ad().Source([dev64(gk) for gk in p.source.g], list(p.source.h))
+        u = dev64(p.u0)
+        ad().time_series(op)
+        st = ad().expquad_step(op, u, 0.0, p.dt, 2, (1 / 3, 2 / 3), src, tol=1e-10,
+                               force_iters=12)
+        kernel = ad().series_timing(op)["kernel"]
+        ad().time_series(op, False)
+        assert st["iters"] == 12 * st["substeps"]
+        err = float(np.linalg.norm(u.cpu().numpy() - ref) / np.linalg.norm(ref))
+        assert err <= 1e-11, (nx, ny, kernel, err)
+        seen[(nx, ny)] = kernel
+    kinds = set(seen.values())
+    assert "leja_tile_f64_k" in kinds, seen
+    assert seen[(560, 560)] not in ("leja_tile_f64_k", "leja_nsync_f64_k",
+                                    "leja_persistent_f64_k"), seen
+    print(seen)
