@@ -103,6 +103,11 @@ struct SeriesArgs {
 // y[0] = src (or 0 if src == null), p = d0 * y[0]; resets ctrl.
 void series_init(const SeriesArgs& a, const void* src, double d0, int force, int max_iters,
                  double tol, cudaStream_t s);
+// FP32 phi_1 series start from u: y[0] = A u + sum_k a_k g_k (S, at most two
+// terms), p = d0 * y[0], ctrl reset -- one pass of the ring kernel.  false
+// (nothing enqueued) where the ring kernels do not apply.
+bool series_start_f32(const SeriesArgs& a, const void* u, const Sources& S, double d0, int force,
+                      int max_iters, double tol, cudaStream_t s);
 // One fused Leja iteration over the grid (a.nblocks blocks).  The last block to
 // finish reduces the norm partials in a fixed order, applies the stopping rule,
 // advances ctrl->m and, with a.has_handle, sets the graph loop condition.

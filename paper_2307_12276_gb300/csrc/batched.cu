@@ -214,25 +214,6 @@ __global__ void __launch_bounds__(kThreads) batch_iter_k(const BatchSlice* slice
   }
 }
 
-__global__ void __launch_bounds__(kThreads) batch_update_k(const BatchSlice* slices,
-                                                          const int* tile_slice, int ntiles,
-                                                          int TY) {
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const BatchSlice& S = slices[tile_slice[t]];
-    if (S.a.ctrl->status != 0) continue;      // not converged: keep the input state
-    const GridDev g = S.a.g;
-    const int local = t - S.tile_off;
-    const int x0 = (local % S.tiles_x) * kTileCols, y0 = (local / S.tiles_x) * TY;
-    const int i = x0 + threadIdx.x;
-    if (i >= g.nx) continue;
-    const float* p = static_cast<const float*>(S.a.p);
-    for (int j = y0; j < min(g.ny, y0 + TY); ++j) {
-      const long long idx = (long long)j * g.nx + i;
-      S.u[idx] = fmaf(S.dt, p[idx], S.u[idx]);
-    }
-  }
-}
-
 // Fused Leja iteration over the flat list of warp tiles (128 columns x R
 // rows of one slice) with the register-marching kernel of the single-operator
 // FP32 path (tile_f32_ring.cuh): each warp takes tiles gw, gw + GW, ..., skips
@@ -335,7 +316,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
 // Two fused Leja iterations per launch (temporal blocking, tile_f32_pair.cuh)
 // over the flat list of warp tiles (120 produced columns x R rows of one
 // slice).  In pair mode a slice's y_m lives in y buffer (m / 2) & 1, p holds
-// p_{m-1} + pending d_m y_m (added by the next launch or by batch_flush_k).
+// p_{m-1} + pending d_m y_m (added by the next launch or by batch_finish_k).
 // The warp completing a slice's last tile sums the tile partials of both
 // iterations in tile order and applies the stopping rule after iteration m
 // and, if it does not fire, after iteration m + 1.  Eligible batches: every
@@ -439,26 +420,109 @@ __global__ void __launch_bounds__(kRingThreads, 1)
   }
 }
 
-// After a pair-mode series: a slice that stopped after an even count m still
-// owes d_m y_m (y_m in buffer (m / 2) & 1).
-__global__ void __launch_bounds__(kThreads) batch_flush_k(const BatchSlice* slices,
-                                                         const int* tile_slice, int ntiles,
-                                                         int TY) {
+// Series start of every slice in one marching pass (the ring kernels'
+// run with scale 1, shift 0 and p taken as 0): y_0 = A u + c0 g0 + c1 g1,
+// p_0 = d0 y_0, over 128-column x TY-row units (the two halves of each
+// streaming tile); block 0 resets every slice's control block as
+// batch_init_k does.  SRC: some slice has sources (at most two per slice; a
+// slice without points the coupling fields at its own u with coefficient 0,
+// which the run skips).  Replaces batch_apply_k + batch_init_k in the ring
+// and pair modes.
+template <bool SRC, int ADV>
+__global__ void __launch_bounds__(kRingThreads, 1)
+    batch_start_k(const BatchSlice* slices, const int* tile_slice, int ntiles, int TY,
+                  int nslices, int force, int max_iters, double tol, unsigned int* bticket) {
+  extern __shared__ __align__(16) float ring_smem[];
+  if (blockIdx.x == 0) {
+    for (int s = threadIdx.x; s < nslices; s += blockDim.x) {
+      Ctrl* c = slices[s].a.ctrl;
+      c->m = 0;
+      c->stop = 0;
+      c->iters = 0;
+      c->status = 0;
+      c->force = force;
+      c->max_iters = max_iters;
+      c->ticket = 0u;
+      c->tol = tol;
+      c->err_est = 0.0;
+      c->ynorm2 = 0.0;
+      c->pnorm2 = 0.0;
+    }
+    if (threadIdx.x == 0) *bticket = 0u;
+  }
+  using L = RingLayout<SRC, ADV>;
+  float* ring = ring_smem + (size_t)(threadIdx.x >> 5) * L::STAGES * L::SIZE;
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kRingWarps + (threadIdx.x >> 5);
+  const int GW = gridDim.x * kRingWarps;
+  for (int unit = gw; unit < 2 * ntiles; unit += GW) {
+    const int t = unit >> 1;
+    const BatchSlice& S = slices[tile_slice[t]];
+    const int local = t - S.tile_off;
+    const int x0 = (local % S.tiles_x) * kTileCols + (unit & 1) * kVecCols;
+    if (x0 >= S.a.g.nx) continue;              // uniform over the warp
+    const int y0 = (local / S.tiles_x) * TY, y1 = min(S.a.g.ny, y0 + TY);
+    SeriesArgs b = S.a;
+    b.w2 = S.nsrc > 0 ? S.src_g[0] : S.u;
+    b.w1 = S.nsrc > 1 ? S.src_g[1] : S.u;
+    const float c0 = S.nsrc > 0 ? S.src_c[0] : 0.0f, c1 = S.nsrc > 1 ? S.src_c[1] : 0.0f;
+    VGeo G;
+    G.nx = S.a.g.nx;
+    G.ny = S.a.g.ny;
+    G.bc = S.a.g.bc;
+    G.n = S.a.g.n;
+    G.lane = lane;
+    G.x = x0 + 4 * lane;
+    G.active = G.x < G.nx;
+    float ly = 0.f, lp = 0.f;
+    ring_run<SRC, ADV>(b, G, ring, y0, y1, S.u, static_cast<float*>(S.a.y[0]),
+                       static_cast<float*>(S.a.p), 1.0f, 0.0f, (float)S.d0, c0, c1, ly, lp, true);
+  }
+}
+
+template <bool SRC, int ADV>
+size_t batch_start_smem() {
+  return sizeof(float) * (size_t)kRingWarps * RingLayout<SRC, ADV>::STAGES *
+         RingLayout<SRC, ADV>::SIZE;
+}
+
+void* pick_start(bool src, int adv) {
+  if (src) return adv == 0 ? (void*)batch_start_k<true, 0>
+                           : (adv == 1 ? (void*)batch_start_k<true, 1> : (void*)batch_start_k<true, 2>);
+  return adv == 0 ? (void*)batch_start_k<false, 0>
+                  : (adv == 1 ? (void*)batch_start_k<false, 1> : (void*)batch_start_k<false, 2>);
+}
+
+size_t start_smem_for(bool src, int adv) {
+  if (src) return adv == 0 ? batch_start_smem<true, 0>()
+                           : (adv == 1 ? batch_start_smem<true, 1>() : batch_start_smem<true, 2>());
+  return adv == 0 ? batch_start_smem<false, 0>()
+                  : (adv == 1 ? batch_start_smem<false, 1>() : batch_start_smem<false, 2>());
+}
+
+// The end of the step in one pass: a converged slice gets u += dt (p + the
+// pending d_m y_m of an even pair-mode count: p is completed in registers,
+// not written back); a slice that did not converge keeps its input state.
+__global__ void __launch_bounds__(kThreads) batch_finish_k(const BatchSlice* slices,
+                                                          const int* tile_slice, int ntiles,
+                                                          int TY, int pair) {
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const BatchSlice& S = slices[tile_slice[t]];
-    const int m = S.a.ctrl->m;
-    if (m == 0 || (m & 1)) continue;
+    if (S.a.ctrl->status != 0) continue;      // not converged: keep the input state
     const GridDev g = S.a.g;
     const int local = t - S.tile_off;
     const int x0 = (local % S.tiles_x) * kTileCols, y0 = (local / S.tiles_x) * TY;
     const int i = x0 + threadIdx.x;
     if (i >= g.nx) continue;
-    const float d = (float)S.a.lc[m - 1].d;
+    const int m = S.a.ctrl->m;
+    const bool pending = pair && m > 0 && !(m & 1);
+    const float d = pending ? (float)S.a.lc[m - 1].d : 0.0f;
     const float* y = static_cast<const float*>(S.a.y[(m >> 1) & 1]);
-    float* p = static_cast<float*>(S.a.p);
+    const float* p = static_cast<const float*>(S.a.p);
     for (int j = y0; j < min(g.ny, y0 + TY); ++j) {
       const long long idx = (long long)j * g.nx + i;
-      p[idx] = fmaf(d, y[idx], p[idx]);
+      const float pv = pending ? fmaf(d, y[idx], p[idx]) : p[idx];
+      S.u[idx] = fmaf(S.dt, pv, S.u[idx]);
     }
   }
 }
@@ -538,6 +602,7 @@ struct ad_batch {
   cudaGraph_t graph = nullptr;
   int graph_force = -2;
   double graph_tol = -1.0;
+  int graph_start = -1;               // start_mode the graph was built with
 };
 
 namespace {
@@ -629,7 +694,8 @@ void destroy_batch_graph(ad_batch* b) {
   b->graph = nullptr;
 }
 
-int build_batch_graph(ad_batch* b, int force, double tol) {
+// start_mode: 0 apply + init kernels, 1 batch_start_k without sources, 2 with.
+int build_batch_graph(ad_batch* b, int force, double tol, int start_mode) {
   destroy_batch_graph(b);
   cudaGraph_t g;
   B_CUDA(cudaGraphCreate(&g, 0));
@@ -648,17 +714,28 @@ int build_batch_graph(ad_batch* b, int force, double tol) {
   kp.blockDim = dim3(kThreads);
   kp.gridDim = dim3(grid);
   cudaGraphNode_t n_apply, n_init, n_cond, n_upd;
-  {
-    void* args[] = {&sl, &ts, &nt, &TY};
-    kp.func = pick_apply(b->adv);
-    kp.kernelParams = args;
-    B_CUDA(cudaGraphAddKernelNode(&n_apply, g, nullptr, 0, &kp));
-  }
-  {
+  if (start_mode > 0) {   // the series start in one ring pass (batch_start_k)
     void* args[] = {&sl, &ts, &nt, &TY, &S, &force, &maxit, &tol, &bt};
-    kp.func = (void*)batch_init_k;
-    kp.kernelParams = args;
-    B_CUDA(cudaGraphAddKernelNode(&n_init, g, &n_apply, 1, &kp));
+    cudaKernelNodeParams sp = kp;
+    sp.func = pick_start(start_mode == 2, b->adv);
+    sp.kernelParams = args;
+    sp.blockDim = dim3(kRingThreads);
+    sp.gridDim = dim3(std::max(1, std::min(152, (2 * nt + kRingWarps - 1) / kRingWarps)));
+    sp.sharedMemBytes = (unsigned)start_smem_for(start_mode == 2, b->adv);
+    B_CUDA(cudaGraphAddKernelNode(&n_init, g, nullptr, 0, &sp));
+  } else {
+    {
+      void* args[] = {&sl, &ts, &nt, &TY};
+      kp.func = pick_apply(b->adv);
+      kp.kernelParams = args;
+      B_CUDA(cudaGraphAddKernelNode(&n_apply, g, nullptr, 0, &kp));
+    }
+    {
+      void* args[] = {&sl, &ts, &nt, &TY, &S, &force, &maxit, &tol, &bt};
+      kp.func = (void*)batch_init_k;
+      kp.kernelParams = args;
+      B_CUDA(cudaGraphAddKernelNode(&n_init, g, &n_apply, 1, &kp));
+    }
   }
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
@@ -691,24 +768,17 @@ int build_batch_graph(ad_batch* b, int force, double tol) {
       prev = nn;
     }
   }
-  cudaGraphNode_t n_before_upd = n_cond;
-  if (b->pair) {                       // the pending last term of even counts
-    cudaGraphNode_t n_flush;
-    void* args[] = {&sl, &ts, &nt, &TY};
-    kp.func = (void*)batch_flush_k;
+  {   // u += dt (p + the pending term of even pair-mode counts)
+    int pr = b->pair ? 1 : 0;
+    void* args[] = {&sl, &ts, &nt, &TY, &pr};
+    kp.func = (void*)batch_finish_k;
     kp.kernelParams = args;
-    B_CUDA(cudaGraphAddKernelNode(&n_flush, g, &n_cond, 1, &kp));
-    n_before_upd = n_flush;
-  }
-  {
-    void* args[] = {&sl, &ts, &nt, &TY};
-    kp.func = (void*)batch_update_k;
-    kp.kernelParams = args;
-    B_CUDA(cudaGraphAddKernelNode(&n_upd, g, &n_before_upd, 1, &kp));
+    B_CUDA(cudaGraphAddKernelNode(&n_upd, g, &n_cond, 1, &kp));
   }
   B_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
   b->graph_force = force;
   b->graph_tol = tol;
+  b->graph_start = start_mode;
   return AD_OK;
 }
 
@@ -931,6 +1001,11 @@ int ad_create_batch(ad_operator* const* ops, int nslices, int autotune, ad_batch
         for (int adv = 0; adv < 2; ++adv)
           cudaFuncSetAttribute(pick_pair(adv), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)batch_pair_smem());
+        for (int src = 0; src < 2; ++src)
+          for (int adv = 0; adv < 3; ++adv)
+            cudaFuncSetAttribute(pick_start(src != 0, adv),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)start_smem_for(src != 0, adv));
         attr = true;
       }
     }
@@ -1080,8 +1155,14 @@ int ad_batch_midpoint_step(ad_batch* b, void* const* u, double t, double dt,
   B_CUDA(cudaMemcpyAsync(b->d_slices, b->hs.data(), sizeof(BatchSlice) * b->S,
                          cudaMemcpyHostToDevice, b->stream));
   const int force = force_iters < 0 ? -1 : force_iters;
-  if (!b->exec || b->graph_force != force || b->graph_tol != tol) {
-    const int r = build_batch_graph(b, force, tol);
+  // the one-pass series start serves the ring and pair modes with at most two
+  // source terms per slice
+  int max_src = 0;
+  for (const BatchSlice& hs : b->hs) max_src = std::max(max_src, hs.nsrc);
+  const int start_mode = (b->ring && max_src <= 2) ? (max_src > 0 ? 2 : 1) : 0;
+  if (!b->exec || b->graph_force != force || b->graph_tol != tol ||
+      b->graph_start != start_mode) {
+    const int r = build_batch_graph(b, force, tol, start_mode);
     if (r != AD_OK) return r;
   }
   if (force == 0) return bfail(AD_ERR_INVALID, "force_iters == 0 is not supported in batches");

@@ -416,16 +416,17 @@ constexpr int kNotFused = -100;   // run_series: the fused step did not launch
 // fuse (optional): run the whole step in the tile kernel (see StepFuse); src
 // and tail are then unused, and kNotFused is returned when it cannot launch
 // (nothing was enqueued: the caller runs the step unfused).
+// started: the series start (y_0, p_0, ctrl reset) is already enqueued.
 int run_series(ad_operator* op, int aug, const void* src, double d0, int force, double tol,
                ad_stats* st, int* iters_out, const Tail* tail = nullptr, bool async = false,
-               const StepFuse* fuse = nullptr) {
+               const StepFuse* fuse = nullptr, bool started = false) {
   SeriesArgs a = series_args(op, aug);
   if (fuse && (force == 0 || getenv("AD_NO_PERSIST") || getenv("AD_NO_FUSE"))) return kNotFused;
   if (fuse && op->ctrl_dirty) {   // the fused kernel relies on a clean barrier ticket
     CUDA_TRY(cudaMemsetAsync(op->ctrl, 0, sizeof(Ctrl), op->stream));
     op->ctrl_dirty = false;
   }
-  if (!fuse) series_init(a, src, d0, force, op->max_iters, tol, op->stream);
+  if (!fuse && !started) series_init(a, src, d0, force, op->max_iters, tol, op->stream);
   CUDA_TRY(cudaGetLastError());
   int iters = 0;
   bool graph_used = false;
@@ -1036,12 +1037,30 @@ int expquad_impl(ad_operator* op, void* u, double t, double dt, int s, const dou
     *r_out = r;
     return true;
   };
+  // FP32 midpoint steps of one substep under the fixed rule: the series start
+  // y_0 = A u + sources, p_0 = d0 y_0 in one ring pass (series_start_f32)
+  // instead of the apply and start kernels, and u += dt P as the tail.
+  auto try_started_f32 = [&](int* r_out) -> bool {
+    if (op->prec != 1 || (op->adaptive && force < 0) || n_substeps(op, dt) != 1 || force == 0)
+      return false;
+    double d0 = 0.0, eta_next[2];
+    if (upload_series(op, 0, dt, nullptr, &d0, eta_next) != AD_OK) return false;
+    if (!series_start_f32(series_args(op, 0), ud, S, d0, force, op->max_iters, tol, op->stream))
+      return false;
+    Tail tail;
+    tail.add(1.0, ud, dt, op->P, ud);
+    int it = 0;
+    *r_out = run_series(op, 0, nullptr, d0, force, tol, &st, &it, &tail, async, nullptr, true);
+    st.matvecs += 1;
+    st.substeps = 1;
+    return true;
+  };
   int rf = AD_OK;
   if (s == 1) {
     // v = A u + S(t + c1 dt);  u += dt phi_1(dt A) v   (Eq. exp_midpoint for c1 = 1/2)
     for (int k = 0; k < S.n; ++k) S.a[k] = h_at(src, k, t + c[0] * dt);
   }
-  if (s == 1 && try_fused(0, dt, &rf)) {
+  if (s == 1 && (try_fused(0, dt, &rf) || try_started_f32(&rf))) {
     if (rf != AD_OK && rf != AD_ERR_NOT_CONVERGED) return rf;
     status = rf;
   } else if (s == 1) {

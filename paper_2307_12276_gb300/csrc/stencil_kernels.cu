@@ -628,6 +628,61 @@ size_t ring_smem_bytes() {
          RingLayout<AUG, ADV>::SIZE;
 }
 
+// The start of an FP32 phi_1 series whose vector is w1 = A u + sum_k c_k g_k
+// (the midpoint step's right-hand side), in one marching pass of the ring
+// kernel: the pass reads u with scale 1 and shift 0, the source fields as the
+// couplings of the augmented form (g0 through w2, g1 through w1; SRC: any
+// source at all), and p as 0, and writes y_0 = w1 and p_0 = d0 y_0.  Block 0
+// resets the control block as series_init does.  Replaces the apply kernel,
+// which forms each cell from 21 cached loads, and the series start.
+template <bool SRC, int ADV>
+__global__ void __launch_bounds__(kRingThreads, 1)
+    series_start_f32_ring_k(SeriesArgs a, const float* __restrict__ u, float c0, float c1,
+                            float d0, int force, int max_iters, double tol) {
+  extern __shared__ __align__(16) float ring_smem[];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Ctrl* c = a.ctrl;
+    c->m = 0;
+    c->stop = 0;
+    c->iters = 0;
+    c->status = 0;
+    c->force = force;
+    c->max_iters = max_iters;
+    c->ticket = 0u;
+    c->tol = tol;
+    c->err_est = 0.0;
+    c->ynorm2 = 0.0;
+    c->pnorm2 = 0.0;
+  }
+  float* __restrict__ y0 = static_cast<float*>(a.y[0]);
+  float* __restrict__ p = static_cast<float*>(a.p);
+  using L = RingLayout<SRC, ADV>;
+  float* ring = ring_smem + (size_t)(threadIdx.x >> 5) * L::STAGES * L::SIZE;
+  VGeo G;
+  G.nx = a.g.nx;
+  G.ny = a.g.ny;
+  G.bc = a.g.bc;
+  G.n = a.g.n;
+  G.lane = threadIdx.x & 31;
+  const long long strips = (G.nx + kVecCols - 1) / kVecCols;
+  const long long units = strips * G.ny;
+  const long long warps = (long long)gridDim.x * kRingWarps;
+  const long long w = (long long)blockIdx.x * kRingWarps + (threadIdx.x >> 5);
+  long long u0, u1;
+  vec_range(units, warps, w, u0, u1);
+  float ly = 0.f, lp = 0.f;
+  for (long long q = u0; q < u1;) {
+    const int strip = (int)(q / G.ny);
+    const int r0 = (int)(q - (long long)strip * G.ny);
+    const long long rr = r0 + (u1 - q);
+    const int r1 = (int)(rr < G.ny ? rr : G.ny);
+    G.x = strip * kVecCols + 4 * G.lane;
+    G.active = G.x < G.nx;
+    ring_run<SRC, ADV>(a, G, ring, r0, r1, u, y0, p, 1.0f, 0.0f, d0, c0, c1, ly, lp, true);
+    q += r1 - r0;
+  }
+}
+
 template <bool AUG, int ADV>
 __global__ void __launch_bounds__(kThreads) leja_iter_f32_k(SeriesArgs a) {
   __shared__ float sy[3][kTileCols + 2];
@@ -899,6 +954,41 @@ bool series_pair(const SeriesArgs& a) {
 void series_flush_pair(const SeriesArgs& a, cudaStream_t s) {
   ++launch_counter();
   pair_flush_k<<<stream_blocks(a.g.n), kThreads, 0, s>>>(a);
+}
+
+bool series_start_f32(const SeriesArgs& a, const void* u, const Sources& S, double d0, int force,
+                      int max_iters, double tol, cudaStream_t s) {
+  if (a.prec != 1 || a.aug || a.f32k != 3 || S.n > 2) return false;
+  SeriesArgs b = a;
+  b.w2 = S.n > 0 ? S.g[0] : nullptr;
+  b.w1 = S.n > 1 ? S.g[1] : nullptr;
+  const float c0 = S.n > 0 ? (float)S.a[0] : 0.0f, c1 = S.n > 1 ? (float)S.a[1] : 0.0f;
+  const float* uf = static_cast<const float*>(u);
+  const float fd0 = (float)d0;
+  const bool src = S.n > 0;
+  void* fn = nullptr;
+  size_t smem = 0;
+#define AD_START(SRCV, ADVV)                                                  \
+  fn = (void*)series_start_f32_ring_k<SRCV, ADVV>;                            \
+  smem = ring_smem_bytes<SRCV, ADVV>();
+  if (src) {
+    if (a.adv == 0) { AD_START(true, 0) } else if (a.adv == 1) { AD_START(true, 1) } else { AD_START(true, 2) }
+  } else {
+    if (a.adv == 0) { AD_START(false, 0) } else if (a.adv == 1) { AD_START(false, 1) } else { AD_START(false, 2) }
+  }
+#undef AD_START
+  static bool attr[2][3] = {};
+  if (!attr[src][a.adv]) {   // the rings need more than the default 48 KB of shared memory
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    attr[src][a.adv] = true;
+  }
+  void* args[] = {&b, &uf, (void*)&c0, (void*)&c1, (void*)&fd0, &force, &max_iters, &tol};
+  ++launch_counter();
+  return cudaLaunchKernel(fn, dim3(a.nblocks), dim3(kRingThreads), args, smem, s) == cudaSuccess;
 }
 
 // shifted operator for GMRES: out = s0 u + s1 A u (+ sources)

@@ -63,10 +63,11 @@ __device__ __forceinline__ void cp_async_wait_group() {
 }
 
 // Issue the copies of row r (centre: also Dxx, p, w2, ax) into record S.
+// pzero: p is taken as 0 and not read.
 template <bool AUG, int ADV>
 __device__ __forceinline__ void ring_issue(float* S, const SeriesArgs& a, const VGeo& G,
                                            const float* __restrict__ yin, int r, bool centre,
-                                           int x0, int wcols) {
+                                           int x0, int wcols, bool pzero = false) {
   using L = RingLayout<AUG, ADV>;
   const long long n = G.n;
   const float* F = static_cast<const float*>(a.coef);
@@ -85,7 +86,7 @@ __device__ __forceinline__ void ring_issue(float* S, const SeriesArgs& a, const 
     if (ADV == 2) cp_async16(S + L::AY + c, Fay + off + G.x);
     if (centre) {
       cp_async16(S + L::XX + 4 + c, Fxx + off + G.x);
-      cp_async16(S + L::P + c, static_cast<const float*>(a.p) + off + G.x);
+      if (!pzero) cp_async16(S + L::P + c, static_cast<const float*>(a.p) + off + G.x);
       if (AUG) cp_async16(S + L::W2 + c, static_cast<const float*>(a.w2) + off + G.x);
       if (ADV == 2) cp_async16(S + L::AX + 4 + c, Fax + off + G.x);
     }
@@ -142,7 +143,7 @@ __device__ __forceinline__ void ring_read_row(VRow<ADV>& R, const float* S, cons
 
 template <bool AUG, int ADV>
 __device__ __forceinline__ void ring_read_cen(VCen<ADV, AUG>& C, const float* S, const VGeo& G,
-                                              int wcols) {
+                                              int wcols, bool pzero = false) {
   using L = RingLayout<AUG, ADV>;
   ring_read6(C.xx, S + L::XX, G, wcols, 1.0f);
   if (ADV == 2) ring_read6(C.ax, S + L::AX, G, wcols, 1.0f);
@@ -150,18 +151,21 @@ __device__ __forceinline__ void ring_read_cen(VCen<ADV, AUG>& C, const float* S,
   C.p = make_float4(0.f, 0.f, 0.f, 0.f);
   C.w2 = C.p;
   if (G.active) {
-    C.p = *reinterpret_cast<const float4*>(S + L::P + c);
+    if (!pzero) C.p = *reinterpret_cast<const float4*>(S + L::P + c);
     if (AUG) C.w2 = *reinterpret_cast<const float4*>(S + L::W2 + c);
   }
 }
 
-// One marching run of rows [y0, y1) through this warp's ring.
+// One marching run of rows [y0, y1) through this warp's ring.  pzero: p
+// starts from 0 (not read), which with ig = 1, sh = 0 and the couplings
+// holding source fields makes the run a series start: y_0 = A u + sources,
+// p_0 = d y_0.
 template <bool AUG, int ADV>
 __device__ __forceinline__ void ring_run(const SeriesArgs& a, const VGeo& G, float* ring, int y0,
                                          int y1, const float* __restrict__ yin,
                                          float* __restrict__ yout, float* __restrict__ p, float ig,
                                          float sh, float d, float e1, float e2, float& ly,
-                                         float& lp) {
+                                         float& lp, bool pzero = false) {
   using L = RingLayout<AUG, ADV>;
   constexpr int S = L::STAGES;
   const int x0 = G.x - 4 * G.lane;
@@ -173,7 +177,7 @@ __device__ __forceinline__ void ring_run(const SeriesArgs& a, const VGeo& G, flo
 #pragma unroll 1
   for (int q = 0; q < S; ++q) {
     const int r = y0 - 1 + q;
-    if (r <= y1) ring_issue<AUG, ADV>(slot(r), a, G, yin, r, r >= y0 && r < y1, x0, wcols);
+    if (r <= y1) ring_issue<AUG, ADV>(slot(r), a, G, yin, r, r >= y0 && r < y1, x0, wcols, pzero);
     cp_async_commit();
   }
   cp_async_wait_group<S - 3>();      // rows y0 - 1, y0 and y0 + 1 complete
@@ -191,7 +195,7 @@ __device__ __forceinline__ void ring_run(const SeriesArgs& a, const VGeo& G, flo
       __syncwarp();
     }
     ring_read_row<AUG, ADV>(N, slot(j + 1), G, j + 1, wcols);
-    ring_read_cen<AUG, ADV>(C, slot(j), G, wcols);
+    ring_read_cen<AUG, ADV>(C, slot(j), G, wcols, pzero);
     float fn[4];
     vnorth<ADV>(fn, B, N, a.aby);
     float fx[5];
@@ -232,7 +236,7 @@ __device__ __forceinline__ void ring_run(const SeriesArgs& a, const VGeo& G, flo
     // row j - 1 is no longer read: refill its slot with row j + S - 1
     __syncwarp();
     const int r = j + S - 1;
-    if (r <= y1) ring_issue<AUG, ADV>(slot(r), a, G, yin, r, r < y1, x0, wcols);
+    if (r <= y1) ring_issue<AUG, ADV>(slot(r), a, G, yin, r, r < y1, x0, wcols, pzero);
     cp_async_commit();
 #pragma unroll
     for (int k = 0; k < 4; ++k) fs[k] = fn[k];
