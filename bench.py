@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=9)
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--form-steps", type=int, default=5)
     ap.add_argument("--learned-fields", type=int, default=1000)
@@ -863,7 +863,7 @@ def run_ours(args):
     uh = torch.empty(g.n, dtype=torch.float64, pin_memory=True)
     uh.copy_(u0.cpu())
     ue = uh.numpy()
-    te = 0.0
+    te = []
     for k in range(args.e2e_steps + 1):
         flush.zero_()
         torch.cuda.synchronize()
@@ -871,8 +871,11 @@ def run_ours(args):
         ad.expquad_step(op, ue, k * p.dt, p.dt, p.s, p.c, src, tol=p.tol)
         el = time.perf_counter() - t0
         if k > 0:                       # the first call allocates the staging buffers
-            te += el
-    e2e_value = g.n * args.e2e_steps / te / 1e6
+            te.append(el)
+    # host wall time per step: the median (a single host hiccup of a few ms
+    # would otherwise dominate a short run); the mean is reported beside it
+    e2e_value = g.n / statistics.median(te) / 1e6
+    e2e_mean_ms = 1e3 * statistics.mean(te)
 
     # roofline of the series kernel, from the event pairs around its launches in the timed steps
     flops = 28.0 * g.n        # 14 FP64 FMA per cell: 9 stencil, shift, coupling, p, 2 norms
@@ -938,7 +941,9 @@ def run_ours(args):
             "err_vs_oracle_step1": err,
             "gpu_launches": launches,
             "e2e": {"value": round(e2e_value, 4), "unit": "Mcell-steps/s",
-                    "h2d_bytes_per_step": 8 * g.n, "d2h_bytes_per_step": 8 * g.n},
+                    "h2d_bytes_per_step": 8 * g.n, "d2h_bytes_per_step": 8 * g.n,
+                    "steps": len(te), "stat": "median of per-step host wall times",
+                    "mean_ms_per_step": round(e2e_mean_ms, 4)},
             "roofline": roof,
             "clocks": clk.summary(),
         }

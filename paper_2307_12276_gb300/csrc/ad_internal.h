@@ -117,6 +117,9 @@ void series_iteration(const SeriesArgs& a, cudaStream_t s);
 // series, series_flush_pair adds the pending last term to p.
 bool series_pair(const SeriesArgs& a);
 void series_flush_pair(const SeriesArgs& a, cudaStream_t s);
+// Pair mode, after the series: u += b (p + the pending term), FP32, one pass
+// (the flush and the update axpby together; p is not written).
+void series_finish_pair_update(const SeriesArgs& a, void* u, double b, cudaStream_t s);
 // Whole Newton series in one cooperative launch (FP64, n <= kPersistMaxCells).
 // gen: device barrier generation counter (persists across calls).  Returns
 // false if not applicable or refused; nothing was launched then.

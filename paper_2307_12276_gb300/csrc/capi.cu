@@ -417,9 +417,12 @@ constexpr int kNotFused = -100;   // run_series: the fused step did not launch
 // and tail are then unused, and kNotFused is returned when it cannot launch
 // (nothing was enqueued: the caller runs the step unfused).
 // started: the series start (y_0, p_0, ctrl reset) is already enqueued.
+// update_u (FP32 pair mode only): the tail is u += update_b P, done with the
+// pending term in one pass (series_finish_pair_update); tail is then unused.
 int run_series(ad_operator* op, int aug, const void* src, double d0, int force, double tol,
                ad_stats* st, int* iters_out, const Tail* tail = nullptr, bool async = false,
-               const StepFuse* fuse = nullptr, bool started = false) {
+               const StepFuse* fuse = nullptr, bool started = false, void* update_u = nullptr,
+               double update_b = 0.0) {
   SeriesArgs a = series_args(op, aug);
   if (fuse && (force == 0 || getenv("AD_NO_PERSIST") || getenv("AD_NO_FUSE"))) return kNotFused;
   if (fuse && op->ctrl_dirty) {   // the fused kernel relies on a clean barrier ticket
@@ -475,10 +478,13 @@ int run_series(ad_operator* op, int aug, const void* src, double d0, int force, 
         if (op->h_ctrl->stop || launched >= kMaxIters + chunk) break;
       }
     }
-    if (!persist && series_pair(a)) series_flush_pair(a, op->stream);   // the pending last term
+    const bool finish_update = update_u && !persist && series_pair(a);
+    if (!persist && series_pair(a) && !finish_update)
+      series_flush_pair(a, op->stream);                                  // the pending last term
     CUDA_TRY(cudaGetLastError());
     if (op->time_series) CUDA_TRY(cudaEventRecord(ev[1], op->stream));
-    enqueue_tail(op, tail);
+    if (finish_update) series_finish_pair_update(a, update_u, update_b, op->stream);
+    else enqueue_tail(op, tail);
     if (async) {
       if (!fuse) {   // (the fused kernel reports to the totals itself)
         const int per_launch = graph_used ? (series_pair(a) ? 2 : 1) : 0;
@@ -1050,7 +1056,8 @@ int expquad_impl(ad_operator* op, void* u, double t, double dt, int s, const dou
     Tail tail;
     tail.add(1.0, ud, dt, op->P, ud);
     int it = 0;
-    *r_out = run_series(op, 0, nullptr, d0, force, tol, &st, &it, &tail, async, nullptr, true);
+    *r_out = run_series(op, 0, nullptr, d0, force, tol, &st, &it, &tail, async, nullptr, true,
+                        ud, dt);
     st.matvecs += 1;
     st.substeps = 1;
     return true;

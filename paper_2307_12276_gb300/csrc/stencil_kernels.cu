@@ -956,6 +956,28 @@ void series_flush_pair(const SeriesArgs& a, cudaStream_t s) {
   pair_flush_k<<<stream_blocks(a.g.n), kThreads, 0, s>>>(a);
 }
 
+// u = 1 u + b (p + the pending d_m y_m of an even count) in one pass: the
+// flush and the axpby that follows it, with their arithmetic (p is completed
+// in registers, not written back).
+__global__ void pair_finish_update_k(SeriesArgs a, float* u, float b) {
+  const int m = a.ctrl->m;
+  const bool pending = m > 0 && !(m & 1);
+  const float d = pending ? (float)a.lc[m - 1].d : 0.0f;
+  const float* y = static_cast<const float*>(a.y[(m >> 1) & 1]);
+  const float* p = static_cast<const float*>(a.p);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.g.n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float pv = pending ? fmaf(d, y[i], p[i]) : p[i];
+    u[i] = fmaf(b, pv, 1.0f * u[i]);
+  }
+}
+
+void series_finish_pair_update(const SeriesArgs& a, void* u, double b, cudaStream_t s) {
+  ++launch_counter();
+  pair_finish_update_k<<<stream_blocks(a.g.n), kThreads, 0, s>>>(a, static_cast<float*>(u),
+                                                                  (float)b);
+}
+
 bool series_start_f32(const SeriesArgs& a, const void* u, const Sources& S, double d0, int force,
                       int max_iters, double tol, cudaStream_t s) {
   if (a.prec != 1 || a.aug || a.f32k != 3 || S.n > 2) return false;
