@@ -783,6 +783,13 @@ __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom ge
     ctrl->pnorm2 = 0.0;
   }
   __syncthreads();
+  // The prologue only reads u, the weights and the sources and only writes
+  // w1 (all distinct buffers): restrict-qualified pointers and two cells per
+  // round let the loads of one cell overlap the work of the other.
+  const double* __restrict__ Wu = F.W;
+  const double* __restrict__ uu = F.u;
+  double* __restrict__ w1o = F.w1;
+#pragma unroll 2
   for (int k = t; k < nc; k += T) {
     const int li = k % tw, lj = k / tw;
     const int idx = gidx(li, lj);
@@ -794,14 +801,14 @@ __global__ void __launch_bounds__(256) leja_tile_f64_k(SeriesArgs a, TileGeom ge
       continue;
     }
     // the step's right-hand sides, as the apply kernel forms them
-    const double au = stencil9(F.W, n, F.u, x0 + li, y0 + lj, nx, ny, g.bc, idx);
+    const double au = stencil9(Wu, n, uu, x0 + li, y0 + lj, nx, ny, g.bc, idx);
     double r = 1.0 * au, r2 = 0.0;
     for (int q = 0; q < F.src.n; ++q) {
       const double gq = static_cast<const double*>(F.src.g[q])[idx];
       r = fma(F.src.a[q], gq, r);
       r2 = fma(F.src.b[q], gq, r2);
     }
-    F.w1[idx] = r;
+    w1o[idx] = r;
     if (F.s == 2) {                                // y_0 = 0: the window stays 0
       if (AUG) sW2[k] = r2;
       sP[k] = F.d0 * 0.0;
