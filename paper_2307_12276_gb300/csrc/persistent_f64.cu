@@ -1,14 +1,16 @@
 // Persistent FP64 Newton series (Section 2): one cooperative launch runs
-// every Leja iteration of a series for grids up to kPersistMaxCells.  Block b
-// owns a contiguous chunk of cells; its 9 scaled weights, p and w2 stay in
-// shared memory for the whole series (loaded once).
+// every Leja iteration of a series for grids up to kPersistMaxCells.  Each
+// block's 9 scaled weights, p and w2 stay in shared memory for the whole
+// series (loaded once).
 //
-// Two kernels:
-//  * leja_nsync_f64_k (default): blocks synchronise with their neighbours
-//    only, and the stopping rule runs two iterations behind (see below);
-//  * leja_persistent_f64_k: one grid barrier per iteration, used when the
-//    neighbourhood of a block is too wide for the first kernel's window or
-//    its shared memory does not fit.
+// Three kernels:
+//  * leja_tile_f64_k (default wherever its tiles fit): block b owns a 2-D
+//    tile, synchronises with its up to 8 neighbours only, and the stopping
+//    rule runs two iterations behind; for a step of one substep it also runs
+//    the step's right-hand side and update (StepFuse), so a step is one launch;
+//  * leja_nsync_f64_k: the same protocol on contiguous row ranges;
+//  * leja_persistent_f64_k: one grid barrier per iteration, used when neither
+//    window fits in shared memory.
 #include "ad_internal.h"
 #include "stencil9.cuh"
 
