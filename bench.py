@@ -726,6 +726,7 @@ def measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, fields, dt, 
     train_s = time.perf_counter() - t0
     hold = model.predict(torch.as_tensor(X[nfields:], device=dev)).cpu().numpy()
     alpha_err = np.abs(np.exp(hold[:, 0] - Y[nfields:, 0]) - 1.0)
+    iters_err = np.abs(np.exp(hold[:, 1] - Y[nfields:, 1]) - 1.0)   # the second output
     # bounds for the slices: features of the resident fields + one batched inference
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -760,7 +761,11 @@ def measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, fields, dt, 
     plain_total = power_s + steps * ms_batch * 1e-3
     learned_total = predict_s + steps * ms_learned * 1e-3
     ratio = np.asarray(alpha) / np.asarray(power_alpha)
+    actual = np.array([max(s["iters"], 1) for s in st], dtype=np.float64)
+    slice_iters_err = np.abs(np.asarray(it_pred, dtype=np.float64) / actual - 1.0)
     return {"training_fields": nfields, "label_s": round(label_s, 1), "train_s": round(train_s, 2),
+            "heldout_iters_rel_err_median": round(float(np.median(iters_err)), 4),
+            "slice_iters_pred_rel_err_median": round(float(np.median(slice_iters_err)), 4),
             "heldout_alpha_rel_err_median": round(float(np.median(alpha_err)), 4),
             "heldout_alpha_rel_err_p90": round(float(np.quantile(alpha_err, 0.9)), 4),
             "margin": margin, "bounds_s": round(predict_s, 4),
