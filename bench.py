@@ -1,12 +1,14 @@
 #!/usr/bin/env python
 """Benchmark of the exponential Leja integrator on one GB300 (or N replicas).
 
-Workload (default): 512 x 512 cell-centred grid on [-1, 1]^2, zero Dirichlet
-boundaries, FP64, circular field lines (isotropic blend for r < 0.05),
-D_par = 1, D_perp = 1e-4, a = (0.1, 0.05), S = Gaussian(sigma 0.05 at
-(0.3, 0.3)) (1 + sin 2 pi t), two-stage exponential quadrature with
-c = (1/3, 2/3), tol 1e-10, dt = 200 Delta t_CFL.  One benchmark step = one
-exponential quadrature step (A u, the augmented Leja series, the update).
+Workload (default): the 4096 x 4096 precision-form workload on [-1, 1]^2 in
+its full-FP64 path: zero Dirichlet boundaries, field lines of a seeded
+8-mode random-phase stream function, D_par = 1, D_perp = 10^U(-6,-2)
+(seeded), a = 0, 16 seeded Gaussian sources (sigma 0.02), Gaussian u0
+(sigma 0.2), exponential midpoint (Eq. exp_midpoint) at dt = 100 Delta
+t_CFL, tol 1e-10.  One benchmark step = one exponential-midpoint step
+(A u + S, the Leja series of phi_1, the update).  The 512^2 two-stage
+workload and the 64^2 periodic workload are measured as forms.
 
 Metric: Mcell-steps/s = cells x steps / time.  ``value`` is device time
 (CUDA events on the operator's stream, inputs resident, L2 flushed before
@@ -14,7 +16,8 @@ every step by writing a 256 MiB buffer); ``e2e`` is the same metric through
 the C ABI with the state in pinned host memory (host->device and
 device->host copies inside the timed region).  ``roofline`` reports the
 fused Leja iteration kernel; ``cpu_baseline`` times the FP64 CPU oracle on
-a bounded sample of the same workload in a subprocess.
+a bounded sample of the same workload in a subprocess that runs beside the
+GPU measurements, and its first step is the reference for the errors.
 
 Multi-GPU: replicas only (the workload does not shard); each rank runs the
 same problem and ``value`` is the sum over ranks of cell-steps / max time.
@@ -35,10 +38,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    # name: (config builder kwargs, integrator)
-    "c1-512sq-dirichlet-circular-expquad2-dt200cfl": dict(nx=512, dt_factor=200.0),
+    # name: how to build the problem (workloads.configs) and its step size in Delta t_CFL
+    "c2-4096sq-dirichlet-stream-midpoint-fp64": dict(kind="c2", nx=4096, tol=1e-10,
+                                                     dt_over_cfl=100.0),
+    "c1-512sq-dirichlet-circular-expquad2-dt200cfl": dict(kind="c1", nx=512, dt_over_cfl=200.0),
+    "c0-64sq-periodic-uniform30-midpoint": dict(kind="c0", nx=64, dt_over_cfl=100.0),
 }
-DEFAULT_WORKLOAD = "c1-512sq-dirichlet-circular-expquad2-dt200cfl"
+DEFAULT_WORKLOAD = "c2-4096sq-dirichlet-stream-midpoint-fp64"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz
 
 
@@ -63,79 +69,118 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    ap.add_argument("--reference-seconds", type=float, default=60.0,
+                    help="bound on the reference arm's timed oracle steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=9)
+    ap.add_argument("--nx", type=int, default=0,
+                    help="override the workload's grid side (smaller cases for profiling)")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--form-steps", type=int, default=5)
-    ap.add_argument("--learned-fields", type=int, default=1000)
-    ap.add_argument("--forms", default="fp32,cn,paper,batched,learned,momentum,adaptive",
-                    help="comma list of extra forms to measure: fp32, cn, batched, learned, "
-                         "paper, momentum, adaptive")
+    ap.add_argument("--learned-fields", type=int, default=10000)
+    ap.add_argument("--forms", default="fp32,c1,c0,cn,paper,batched,learned,momentum,adaptive",
+                    help="comma list of extra forms to measure: fp32, c1, c0, cn, batched, "
+                         "learned, paper, momentum, adaptive")
     return ap.parse_args()
 
 
-def problem(name):
-    from workloads import config1
-    return config1(**WORKLOADS[name])
+def problem(name, nx=0):
+    from workloads import config0, config1, config2
+    w = WORKLOADS[name]
+    nx = nx or w["nx"]
+    if w["kind"] == "c2":
+        return config2(nx=nx, tol=w["tol"])
+    if w["kind"] == "c1":
+        return config1(nx=nx, dt_factor=w["dt_over_cfl"])
+    return config0(nx=nx)
 
 
 # --------------------------------------------------------------------------- oracle leg
-def oracle_sample(workload: str, seconds: float, max_steps: int, out_npy: str | None,
-                  warmup: int = 0):
-    """Run the CPU oracle from the workload's initial state for about
-    ``seconds`` (at least one step) after ``warmup`` untimed steps; returns a
-    dict with its throughput."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = f"""
+ORACLE_CODE = """
 import json, sys, time
-sys.path.insert(0, {ROOT!r})
+sys.path.insert(0, {root!r})
 import numpy as np
 from bench import problem
 from oracle import operator as oop, spectral, integrators
+t_setup = time.perf_counter()
 p = problem({workload!r})
 A = oop.assemble(p.grid, p.Dxx, p.Dxy, p.Dyy, p.ax_arr(), p.ay_arr())
 alpha = spectral.gershgorin(A)
 S = lambda t: p.source_at(t).ravel()
+setup_s = time.perf_counter() - t_setup
 u, t, steps, iters = p.u0.ravel().copy(), 0.0, 0, 0
 for _ in range({warmup}):
     u, st = integrators.expquad_step(A, u, t, p.dt, p.s, p.c, S, alpha, tol=p.tol)
     t += p.dt
 t0 = time.perf_counter()
+el = 0.0
+first_iters = None
 while True:
     u, st = integrators.expquad_step(A, u, t, p.dt, p.s, p.c, S, alpha, tol=p.tol)
     t += p.dt; steps += 1; iters += st.iters
-    if steps == 1 and {out_npy!r} is not None:
-        np.save({out_npy!r}, u)
     el = time.perf_counter() - t0
+    if steps == 1:
+        first_iters = int(st.iters)
+        if {out_npy!r} is not None:
+            np.save({out_npy!r}, u)
     if el >= {seconds} or steps >= {max_steps}:
         break
-print(json.dumps(dict(steps=steps, seconds=el, cells=p.grid.n, iters=iters, alpha=alpha)))
+print(json.dumps(dict(steps=steps, seconds=el, cells=p.grid.n, iters=iters, alpha=alpha,
+                      setup_s=setup_s, first_step_iters=first_iters)))
 """
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       cwd=ROOT)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed:\n" + r.stderr[-3000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def start_oracle_sample(workload: str, seconds: float, max_steps: int, out_npy: str | None,
+                        warmup: int = 0):
+    """Start the CPU oracle (one core: BLAS threads pinned to 1) from the
+    workload's initial state in a subprocess: ``warmup`` untimed steps, then
+    steps until ``seconds`` have passed (at least one) or ``max_steps``; the
+    first timed step's state is saved to ``out_npy``.  Returns the process."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_CODE.format(root=ROOT, workload=workload, warmup=warmup, out_npy=out_npy,
+                              seconds=seconds, max_steps=max_steps)
+    return subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                            stderr=subprocess.PIPE, text=True, env=env, cwd=ROOT)
+
+
+def finish_oracle_sample(proc):
+    """Wait for the oracle subprocess; returns a dict with its throughput."""
+    out, err = proc.communicate()
+    if proc.returncode != 0:
+        raise RuntimeError("oracle sample failed:\n" + err[-3000:])
+    d = json.loads(out.strip().splitlines()[-1])
     d["value"] = d["cells"] * d["steps"] / d["seconds"] / 1e6
     return d
 
 
+def oracle_sample(workload: str, seconds: float, max_steps: int, out_npy: str | None,
+                  warmup: int = 0):
+    return finish_oracle_sample(start_oracle_sample(workload, seconds, max_steps, out_npy, warmup))
+
+
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on this arm's workload, one
+    oracle step per benchmark step, on one host core.  The timed steps are
+    bounded by --reference-seconds (at least one step), so the run ends within
+    a few minutes even where one oracle step takes tens of seconds."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # each of the K steps is one oracle step of the same workload (about 0.5 s each)
-    d = oracle_sample(args.workload, seconds=1e9, max_steps=max(1, args.steps), out_npy=None,
-                      warmup=args.warmup)
+    d = oracle_sample(args.workload, seconds=args.reference_seconds,
+                      max_steps=max(1, args.steps), out_npy=None, warmup=0)
     line = {
         "impl": "reference", "metric": "Mcell-steps/s", "value": round(d["value"], 6),
         "unit": "Mcell-steps/s", "n_gpus": args.gpus, "steps": d["steps"],
         "ms_per_step": 1e3 * d["seconds"] / d["steps"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "cells": d["cells"]}, "warmup": args.warmup,
+        "config": {"workload": args.workload, "cells": d["cells"]}, "warmup": 0,
         "cpu_baseline": {"value": round(d["value"], 6), "unit": "Mcell-steps/s", "cores": 1,
-                         "kind": "oracle",
-                         "sample": f"{d['steps']} full exponential quadrature steps from t=0"},
+                         "host_cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"{d['steps']} full exponential steps from t=0 "
+                                   f"({d['seconds']:.1f} s timed; requested {args.steps} steps "
+                                   f"after {args.warmup} warm-up, bounded by "
+                                   f"{args.reference_seconds:.0f} s; operator assembly "
+                                   f"{d['setup_s']:.0f} s untimed)"},
         "e2e": {"value": round(d["value"], 6), "unit": "Mcell-steps/s",
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -229,31 +274,183 @@ def traffic_per_launch(files, summary: str):
 
 # sources that define each profiled kernel (the digest in its summary covers these)
 F64_SERIES_SOURCES = ("persistent_f64.cu", "stencil9.cuh", "ad_internal.h")
+F64_ITER_SOURCES = ("stencil_kernels.cu", "stencil9.cuh", "series_finish.cuh", "tile_f32.cuh",
+                    "ad_internal.h")
 F32_ITER_SOURCES = ("stencil_kernels.cu", "tile_f32.cuh", "tile_f32_vec.cuh", "tile_f32_ring.cuh",
                     "ad_internal.h")
 F32_PAIR_SOURCES = F32_ITER_SOURCES + ("tile_f32_pair.cuh",)
 MOM_SOURCES = ("momentum.cu", "series_finish.cuh", "tile_f32.cuh", "ad_internal.h")
 
+# the FP64 series kernel behind each path that ad_series_timing reports
+SERIES_KERNEL_NAMES = {"graph loop of per-iteration kernels": "leja_iter_f64_k",
+                       "host-driven per-iteration kernels": "leja_iter_f64_k"}
+
+
+def _dev_f64(dev):
+    import numpy as np
+    import torch
+    return lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(), device=dev)
+
 
 # --------------------------------------------------------------------------- ours
-def measure_fp32_form(ad, dev, stream, flush, steps, cmp_steps=3):
-    """The FP32-storage form on the 4096^2 stream-function workload
+def measure_workload(ad, dev, stream, p, flush, steps, warmup, e2e_steps, world=1,
+                     label="", dt_over_cfl=None):
+    """FP64 exponential steps of problem ``p`` through the C ABI.
+
+    One step from u0 (kept on the host: compared with the oracle's first
+    step), warm-up steps, then ``steps`` timed steps enqueued without host
+    round trips (CUDA events per step, L2 flushed before each), the device
+    time of every Newton series inside them (the roofline's kernel time), and
+    ``e2e_steps`` steps through the C ABI with the state in pinned host
+    memory.  Returns (result dict, first-step state as a NumPy array)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    g = p.grid
+    T = _dev_f64(dev)
+    op = ad.create_operator(g.nx, g.ny, g.bc, T(p.Dxx), T(p.Dxy), T(p.Dyy), p.ax, p.ay,
+                            ad.FP64, stream=stream)
+    src = ad.Source([T(gk) for gk in p.source.g], list(p.source.h)) if len(p.source) else None
+    u0 = T(p.u0)
+    u = u0.clone()
+    st1 = ad.expquad_step(op, u, 0.0, p.dt, p.s, p.c, src, tol=p.tol)
+    torch.cuda.synchronize()
+    u1 = u.cpu().numpy()
+    t = p.dt
+    for _ in range(max(0, warmup - 1)):
+        ad.expquad_step(op, u, t, p.dt, p.s, p.c, src, tol=p.tol)
+        t += p.dt
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ad.time_series(op)          # event pair around every series kernel launch in the timed steps
+    # The steps are enqueued without a host round trip between them (the
+    # asynchronous entry point); the totals call synchronises and reports
+    # their iterations, launches and worst status.
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for k in range(steps):
+            flush.zero_()
+            starts[k].record(stream)
+            ad.expquad_step_async(op, u, t, p.dt, p.s, p.c, src, tol=p.tol)
+            ends[k].record(stream)
+            t += p.dt
+        tot = ad.async_totals(op)
+        torch.cuda.synchronize()
+    launches = tot["kernel_launches"]
+    assert tot["converged"] and tot["substeps"] == steps
+    series_t = ad.series_timing(op)
+    ad.time_series(op, False)
+    if world > 1:
+        dist.barrier()
+    dev_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
+    dev_ms, value = job_throughput(dev_ms, g.n, steps, world, dev)
+
+    # e2e: the state lives in pinned host memory; the C ABI stages it per call
+    # through device buffers the operator allocated at creation
+    uh = torch.empty(g.n, dtype=torch.float64, pin_memory=True)
+    uh.copy_(u0.cpu())
+    ue = uh.numpy()
+    te = []
+    for k in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ad.expquad_step(op, ue, k * p.dt, p.dt, p.s, p.c, src, tol=p.tol)
+        te.append(time.perf_counter() - t0)
+    # host wall time per step: the median (a single host hiccup of a few ms
+    # would otherwise dominate a short run); the mean is reported beside it
+    e2e_value = g.n / statistics.median(te) / 1e6
+
+    # roofline of the series kernel, from the event pairs around its launches in the timed steps
+    aug = p.s == 2
+    kernel = SERIES_KERNEL_NAMES.get(series_t["kernel"], str(series_t["kernel"]))
+    path = series_t["kernel"]
+    fma = 14 if aug else 13   # 9 stencil, shift, (coupling), p, 2 norms: FP64 FMA-class per cell
+    flops = 2.0 * fma * g.n
+    # 9 weights + y + p (r/w) + y_next (+ w2 for the augmented series), 8 B each
+    bytes_alg = (112.0 if aug else 104.0) * g.n
+    ms_it = series_t["ms"] / max(series_t["iters"], 1)
+    fused = launches == steps and series_t["series"] == steps
+    step_flops = 24.0 * g.n if fused else 0.0   # 9 stencil + 2 source + 1 update FMA per cell
+    achieved = ((flops * series_t["iters"] + step_flops * series_t["series"])
+                / (series_t["ms"] * 1e-3) / 1e12)
+    ms_forced = ad.profile_leja_iteration(op, aug=int(aug), reps=300 if g.n < 10 ** 6 else 60)
+    traffic = None
+    if kernel == "leja_nsync_f64_k" and g.nx == 512:
+        traffic = traffic_per_launch(F64_SERIES_SOURCES, "leja_nsync_f64_512sq.md")
+    elif kernel == "leja_tile_f64_k" and g.nx == 512:
+        traffic = traffic_per_launch(F64_SERIES_SOURCES, "leja_tile_f64_512sq.md")
+    elif kernel == "leja_iter_f64_k" and g.nx == 4096 and not aug:
+        traffic = traffic_per_launch(F64_ITER_SOURCES, "leja_iter_f64_4096sq.md")
+    hbm_gbs = bytes_alg / (ms_it * 1e-3) / 1e9
+    roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+            "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+            "traffic": traffic, "kernel": f"{kernel}<{'true' if aug else 'false'}>",
+            "series_path": path,
+            "work_unit": ("one launch = one whole step: A u + sources, the Newton series "
+                          "(all its Leja iterations), u += P" if fused else
+                          "one launch = one Leja iteration (y_{m+1}, p_{m+1}, both squared "
+                          "norms, the stopping rule in the last block)"),
+            "alg_flops_per_launch_outside_series": step_flops,
+            "launches_timed": series_t["series"] if fused else series_t["iters"],
+            "iterations_timed": series_t["iters"],
+            "ms_per_launch": round(series_t["ms"] / max(series_t["series"], 1) if fused
+                                   else ms_it, 5),
+            "ms_per_iteration": round(ms_it, 5),
+            "ms_per_iteration_forced": round(ms_forced, 5),
+            "alg_flops_per_iteration": flops,
+            "alg_bytes_per_iteration": bytes_alg,
+            "hbm": {"achieved_GBps": round(hbm_gbs, 1), "peak_GBps": HBM_PEAK_GBS,
+                    "frac": round(hbm_gbs / HBM_PEAK_GBS, 4),
+                    "note": "algorithmic bytes per iteration / iteration time, of measured copy "
+                            "bandwidth (the FP64 pipe, not HBM, bounds this kernel)"},
+            "peak_note": "of derived FP64 peak: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz "
+                         "(a DFMA loop on every SM measured 1.68 DFMA/clk/SM = 1.06 TFLOP/s)"}
+    res = {"workload": label or p.name, "nx": g.nx, "ny": g.ny, "cells": g.n,
+           "value": value, "dev_ms": dev_ms, "ms_per_step": dev_ms / steps,
+           "leja_iters_per_step": tot["iters"] / steps, "gpu_launches": launches,
+           "first_step_iters": st1["iters"],
+           "e2e": {"value": round(e2e_value, 4), "unit": "Mcell-steps/s",
+                   "h2d_bytes_per_step": 8 * g.n, "d2h_bytes_per_step": 8 * g.n,
+                   "steps": len(te), "stat": "median of per-step host wall times",
+                   "mean_ms_per_step": round(1e3 * statistics.mean(te), 4)},
+           "roofline": roof, "clocks": clk.summary(),
+           "config": {"workload": label or p.name, "nx": g.nx, "ny": g.ny, "cells": g.n,
+                      "dt_over_cfl": dt_over_cfl, "s": p.s, "c": list(p.c), "tol": p.tol,
+                      "l2": "flushed before every timed step (256 MiB write)",
+                      "parallelism": "replicas" if world > 1 else "single"}}
+    op.close()
+    del u, u0, src
+    torch.cuda.empty_cache()
+    return res, u1
+
+
+def measure_fp32_form(ad, dev, stream, flush, steps, p=None):
+    """The FP32-storage form of the 4096^2 stream-function workload
     (exponential midpoint, tol 1e-6): throughput, Leja iterations and the
-    fused FP32 kernel's algorithmic HBM bandwidth against the copy peak."""
+    fused FP32 kernel's algorithmic HBM bandwidth against the copy peak.
+    Returns (result dict, state after one step from u0 as float64 NumPy)."""
     import numpy as np
     import torch
     from workloads import config2
-    p = config2(nx=4096)
+    if p is None:
+        p = config2(nx=4096)
     g = p.grid
-    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(), device=dev)
+    T = _dev_f64(dev)
     op = ad.create_operator(g.nx, g.ny, g.bc, T(p.Dxx), T(p.Dxy), T(p.Dyy), 0.0, 0.0,
                             ad.FP32_STORAGE, stream=stream)
     src = ad.Source([T(p.source.g[0]).float()], None)
     u = T(p.u0).float()
-    t = 0.0
-    for _ in range(2):
-        ad.expquad_step(op, u, t, p.dt, 1, (0.5,), src, tol=p.tol)
-        t += p.dt
+    ad.expquad_step(op, u, 0.0, p.dt, 1, (0.5,), src, tol=1e-6)
+    torch.cuda.synchronize()
+    u1 = u.double().cpu().numpy()
+    t = p.dt
+    ad.expquad_step(op, u, t, p.dt, 1, (0.5,), src, tol=1e-6)
+    t += p.dt
     torch.cuda.synchronize()
     ms, iters = 0.0, []
     for _ in range(steps):
@@ -261,7 +458,7 @@ def measure_fp32_form(ad, dev, stream, flush, steps, cmp_steps=3):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        st = ad.expquad_step(op, u, t, p.dt, 1, (0.5,), src, tol=p.tol)
+        st = ad.expquad_step(op, u, t, p.dt, 1, (0.5,), src, tol=1e-6)
         e1.record(stream)
         torch.cuda.synchronize()
         ms += e0.elapsed_time(e1)
@@ -285,53 +482,20 @@ def measure_fp32_form(ad, dev, stream, flush, steps, cmp_steps=3):
         traffic = traffic_per_launch(F32_ITER_SOURCES, "leja_iter_f32_ring_4096sq.md")
     else:
         traffic = None
-    # accuracy against the full-FP64 path (tol 1e-10) after the same steps
-    # from u0, and that path's own throughput on this workload: the FP32
-    # form's speedup at the accuracy it reaches
-    u32 = T(p.u0).float()
-    for k in range(cmp_steps):
-        ad.expquad_step(op, u32, k * p.dt, p.dt, 1, (0.5,), src, tol=p.tol)
     op.close()
     del u, src
     torch.cuda.empty_cache()
-    op64 = ad.create_operator(g.nx, g.ny, g.bc, T(p.Dxx), T(p.Dxy), T(p.Dyy), 0.0, 0.0,
-                              ad.FP64, stream=stream)
-    src64 = ad.Source([T(p.source.g[0])], None)
-    u64 = T(p.u0)
-    ms64, iters64 = 0.0, []
-    for k in range(cmp_steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        st = ad.expquad_step(op64, u64, k * p.dt, p.dt, 1, (0.5,), src64, tol=1e-10)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        if k > 0:                      # the first step builds the series graph
-            ms64 += e0.elapsed_time(e1)
-        iters64.append(st["iters"])
-    err32 = float(torch.linalg.vector_norm(u32.double() - u64) / torch.linalg.vector_norm(u64))
-    op64.close()
-    del u32, u64, src64
-    torch.cuda.empty_cache()
-    fp64_value = g.n * (cmp_steps - 1) / (ms64 * 1e-3) / 1e6
     value = g.n * steps / (ms * 1e-3) / 1e6
     return {"workload": "c2-4096sq-dirichlet-stream-midpoint-fp32", "cells": g.n,
             "value": round(value, 2), "unit": "Mcell-steps/s",
             "ms_per_step": round(ms / steps, 4), "leja_iters_per_step": statistics.mean(iters),
-            "tol": p.tol, "dtype": "f32 storage/arithmetic, f64 Leja scalars and norm sums",
-            "vs_fp64_path": {"steps_from_u0": cmp_steps, "rel_l2_err": err32,
-                             "fp64_tol": 1e-10, "fp64_value": round(fp64_value, 2),
-                             "fp64_leja_iters_per_step": statistics.mean(iters64),
-                             "speedup_fp32_over_fp64": round(value / fp64_value, 2),
-                             "note": "the FP64 path matches the FP64 oracle to <= 1e-11 per "
-                                     "step (sampled full-size parity tests)"},
+            "tol": 1e-6, "dtype": "f32 storage/arithmetic, f64 Leja scalars and norm sums",
             "roofline": {"bound": "hbm", "kernel": kernel + ("<0>" if pair else "<0,0>"),
                          "iterations_per_launch": iters_per_launch, "ms_per_launch":
                          round(ms_launch, 5), "achieved": round(gbs, 1), "peak": HBM_PEAK_GBS,
                          "unit": "GB/s", "frac": round(gbs / HBM_PEAK_GBS, 4),
                          "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
-                         "peak_note": "of measured copy bandwidth"}}
+                         "peak_note": "of measured copy bandwidth"}}, u1
 
 
 def measure_momentum_form(ad, dev, stream, steps=3):
@@ -427,7 +591,7 @@ def measure_adaptive_substeps(ad, dev, stream, dt_factor=2000.0):
             "tol": p.tol, **out}
 
 
-def measure_cn_vs_exp(ad, dev, stream, T_cfl=1000.0):
+def measure_cn_vs_exp(ad, dev, stream, T_cfl=1000.0, cn_budget_ms=60000.0):
     """Crank-Nicolson (GMRES) and the penalised IMEX step (conjugate gradients)
     against two-stage exponential quadrature on the 512^2 workload, to
     T = T_cfl Delta t_CFL: the exponential method at 200 Delta t_CFL, CN at the
@@ -443,10 +607,11 @@ def measure_cn_vs_exp(ad, dev, stream, T_cfl=1000.0):
     op = ad.create_operator(g.nx, g.ny, g.bc, T(p.Dxx), T(p.Dxy), T(p.Dyy), p.ax, p.ay, ad.FP64,
                             stream=stream)
     src = ad.Source([T(gk) for gk in p.source.g], list(p.source.h))
+    ad.reserve_gmres(op, 50)
     t_end = T_cfl * p.cfl
     gauss = (0.5 - 0.5 / 3 ** 0.5, 0.5 + 0.5 / 3 ** 0.5)
 
-    def run(method, factor, tol=1e-10):
+    def run(method, factor, tol=1e-10, gmres_tol=1e-10):
         n = int(round(T_cfl / factor))
         dt = t_end / n
         u = T(p.u0)
@@ -456,7 +621,7 @@ def measure_cn_vs_exp(ad, dev, stream, T_cfl=1000.0):
         it = 0
         for k in range(n):
             if method == "cn":
-                st = ad.cn_step(op, u, k * dt, dt, src, gmres_tol=1e-10, restart=50)
+                st = ad.cn_step(op, u, k * dt, dt, src, gmres_tol=gmres_tol, restart=50)
             elif method == "penalised":
                 st = ad.penalised_step(op, u, k * dt, dt, src, beta=beta, cg_tol=1e-10)
             elif method == "gauss":
@@ -473,13 +638,19 @@ def measure_cn_vs_exp(ad, dev, stream, T_cfl=1000.0):
     nref = float(torch.linalg.norm(ref))
     ue, ms_e, mv_e, n_e = run("exp", 200.0)
     err_e = float(torch.linalg.norm(ue - ref)) / nref
+    # CN: halve the step from 200 Delta t_CFL until its error matches the
+    # exponential step's (GMRES tolerance well below that error), within a
+    # budget of GPU time
     tried = []
     factor = 200.0
-    while factor >= 3.125:
-        uc, ms_c, mv_c, n_c = run("cn", factor)
+    spent = 0.0
+    while True:
+        uc, ms_c, mv_c, n_c = run("cn", factor, gmres_tol=min(1e-10, 1e-2 * err_e))
+        spent += ms_c
         err_c = float(torch.linalg.norm(uc - ref)) / nref
-        tried.append({"dt_over_cfl": factor, "err": err_c, "ms": round(ms_c, 3), "matvecs": mv_c})
-        if err_c <= err_e:
+        tried.append({"dt_over_cfl": factor, "steps": n_c, "err": err_c, "ms": round(ms_c, 3),
+                      "matvecs": mv_c})
+        if err_c <= err_e or spent > cn_budget_ms:
             break
         factor /= 2.0
     # penalised IMEX Euler (first order): step sizes from 200 Delta t_CFL down by 4
@@ -490,6 +661,8 @@ def measure_cn_vs_exp(ad, dev, stream, T_cfl=1000.0):
                     "ms": round(ms_p, 3), "matvecs": mv_p})
     op.close()
     best = tried[-1]
+    # the matched pair: the cheapest CN run at or below the exponential's
+    # error (when the budget allowed one)
     return {"workload": "c1-512sq-dirichlet-circular", "T_over_cfl": T_cfl,
             "penalised_imex": pen, "penalty_beta": beta,
             "exp": {"dt_over_cfl": 200.0, "steps": n_e, "err": err_e, "ms": round(ms_e, 3),
@@ -523,6 +696,7 @@ def measure_paper_cases(ad, dev, stream, nx=128):
         op = ad.create_operator(g.nx, g.ny, g.bc, Tt(p.Dxx), Tt(p.Dxy), Tt(p.Dyy), p.ax, p.ay,
                                 ad.FP64, stream=stream)
         src = ad.Source([Tt(gk) for gk in p.source.g], list(p.source.h)) if len(p.source) else None
+        ad.reserve_gmres(op, 50)
 
         def run(method, nsteps, tol):
             dt = T_end / nsteps
@@ -600,8 +774,54 @@ def _slice_operators(ad, dev, stream, nslices, sides):
     return ops, us, srcs, probs, fields
 
 
+def _batched_oracle_slice(spec):
+    """One slice of the batch on the CPU oracle (worker of a spawned pool):
+    the operator, a 30-step power-iteration bound from the SplitMix64 start
+    of the GPU side, then one exponential-midpoint step at tol 1e-6, timed."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    from oracle import integrators, spectral
+    from oracle import operator as oop
+    from workloads import slice_problem
+    side, dpar, dperp, dt, seed = spec
+    p = slice_problem(side, dpar, dperp, dt=dt)
+    A = oop.assemble(p.grid, p.Dxx, p.Dxy, p.Dyy, p.ax_arr(), p.ay_arr())
+    alpha, _ = spectral.power_iteration(A, spectral.splitmix64_uniform(p.grid.n, seed),
+                                        iters=30, safety=1.1)
+    S = lambda t: p.source_at(t).ravel()
+    t0 = time.perf_counter()
+    integrators.expquad_step(A, p.u0.ravel(), 0.0, dt, 1, (0.5,), S, alpha, tol=1e-6)
+    return p.grid.n, time.perf_counter() - t0
+
+
+def batched_oracle_baseline(specs, dt, max_side=512):
+    """The CPU oracle on the batch's slices of side <= max_side, one step
+    each, in a spawned process pool over every host core (one BLAS thread
+    per worker).  Throughput = cells stepped / (sum of step seconds /
+    workers): the pool's aggregate rate with every core busy."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    workers = os.cpu_count() or 1
+    jobs = [(side, dpar, dperp, dt, k + 1) for k, (side, dpar, dperp) in enumerate(specs)
+            if side <= max_side]
+    t0 = time.perf_counter()
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_batched_oracle_slice, jobs))
+    wall = time.perf_counter() - t0
+    cells = sum(c for c, _ in res)
+    secs = sum(t for _, t in res)
+    return {"value": round(cells / (secs / workers) / 1e6, 4), "unit": "Mcell-steps/s",
+            "cores": workers, "host_cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{len(jobs)} of {len(specs)} slices (sides <= {max_side}), one "
+                      f"exponential-midpoint step each at tol 1e-6, {workers} spawned workers "
+                      f"(one core each); {secs:.1f} s of step time, {wall:.1f} s wall "
+                      f"including operator assembly"}
+
+
 def measure_batched_form(ad, dev, stream, steps, nslices=128, sides=(256, 512, 1024, 2048),
-                         learned_fields=0):
+                         learned_fields=0, cpu_baseline=True):
     """The 128-slice batch (FP32 storage, tol 1e-6): one graph launch per step
     against the same slices stepped one operator call at a time; optionally the
     learned spectral bound against power iteration."""
@@ -700,6 +920,9 @@ def measure_batched_form(ad, dev, stream, steps, nslices=128, sides=(256, 512, 1
                              "series start, update and the tail of slow slices",
            "autotune": info, "power_iteration_bounds_s": round(power_s, 4),
            "setup_s": round(setup_s, 1), "tol": 1e-6}
+    if cpu_baseline:
+        from workloads import config3_slices
+        out["cpu_baseline"] = batched_oracle_baseline(config3_slices(nslices, sides=sides), dt)
     if learned_fields:
         out["learned"] = measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, fields,
                                          dt, batch, steps, ms_batch, power_s, learned_fields)
@@ -710,15 +933,20 @@ def measure_batched_form(ad, dev, stream, steps, nslices=128, sides=(256, 512, 1
 
 def measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, fields, dt, batch, steps,
                     ms_batch, power_s, nfields, margin=1.1):
-    """Train the bound network on generated fields (labels: power-iteration
-    spectra), predict every slice's bound from its device-resident diffusion
-    tensor, run the batch with fallback.  The comparison with power-iteration
-    bounds counts bound time plus ``steps`` batched steps on both sides."""
+    """Train the bound network on generated fields (inputs and labels from
+    ad_bound_training_sample: power-iteration spectra and Leja iteration
+    counts; sides 64..2048, D_par in [1, 100], dt in [10, 1000] Delta t_CFL),
+    hold out a tenth as many fields, then set every slice's bound with one
+    batched inference (ad_learned_bounds) and run the batch with fallback.
+    The comparison with power-iteration bounds counts bound time plus
+    ``steps`` batched steps on both sides."""
     import numpy as np
     import torch
     from paper_2307_12276_gb300 import learned
+    nhold = max(1, nfields // 10)
     t0 = time.perf_counter()
-    X, Y, _ = learned.build_dataset(nfields + nfields // 10, seed=4, device=dev)
+    X, Y = learned.build_dataset(nfields + nhold, seed=4, device=dev,
+                                 workers=min(16, os.cpu_count() or 1))
     label_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     model = learned.train_bound_model(X[:nfields], Y[:nfields], dev, epochs=3000, lr=3e-3)
@@ -727,18 +955,15 @@ def measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, fields, dt, 
     hold = model.predict(torch.as_tensor(X[nfields:], device=dev)).cpu().numpy()
     alpha_err = np.abs(np.exp(hold[:, 0] - Y[nfields:, 0]) - 1.0)
     iters_err = np.abs(np.exp(hold[:, 1] - Y[nfields:, 1]) - 1.0)   # the second output
-    # bounds for the slices: features of the resident fields + one batched inference
+    sides = np.round(np.exp(-X[:, 3].astype(np.float64)) * 2.0).astype(int)
+    power_alpha = [ad.get_spectral_bound(op) for op in ops]
+    # bounds for the slices: one batched inference from the features the
+    # operators recorded at creation
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    feats = np.stack([ad.field_features(p.grid.nx, p.grid.ny, p.grid.bc, *D, 0.05, dt,
-                                        stream=stream) for p, D in zip(probs, fields)])
-    alpha, it_pred = learned.predict_bounds(model, feats, [p.grid.dx for p in probs], dev,
-                                            margin=margin)
+    alpha, it_pred = learned.predict_bounds(model, ops, dt, margin=margin)
     torch.cuda.synchronize()
     predict_s = time.perf_counter() - t0
-    power_alpha = [ad.get_spectral_bound(op) for op in ops]
-    for op, a in zip(ops, alpha):
-        ad.set_spectral_bound(op, float(a))
     for s in range(len(us)):
         us[s].copy_(u_start[s])
     # warm-up step (the plain batch had one too), then the timed steps
@@ -763,7 +988,10 @@ def measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, fields, dt, 
     ratio = np.asarray(alpha) / np.asarray(power_alpha)
     actual = np.array([max(s["iters"], 1) for s in st], dtype=np.float64)
     slice_iters_err = np.abs(np.asarray(it_pred, dtype=np.float64) / actual - 1.0)
-    return {"training_fields": nfields, "label_s": round(label_s, 1), "train_s": round(train_s, 2),
+    return {"training_fields": nfields, "heldout_fields": nhold,
+            "training_sides": {str(k): int(v) for k, v in
+                               zip(*np.unique(sides[:nfields], return_counts=True))},
+            "label_s": round(label_s, 1), "train_s": round(train_s, 2),
             "heldout_iters_rel_err_median": round(float(np.median(iters_err)), 4),
             "slice_iters_pred_rel_err_median": round(float(np.median(slice_iters_err)), 4),
             "heldout_alpha_rel_err_median": round(float(np.median(alpha_err)), 4),
@@ -792,6 +1020,13 @@ def job_throughput(dev_ms, cells, steps, world, device):
     return ms, cells * steps * world / (ms * 1e-3) / 1e6
 
 
+def _rel_errors(got, ref):
+    import numpy as np
+    d = np.asarray(got, dtype=np.float64) - ref
+    return {"rel_l2": float(np.linalg.norm(d) / np.linalg.norm(ref)),
+            "rel_max": float(np.max(np.abs(d)) / np.max(np.abs(ref)))}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -805,120 +1040,43 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    cpu = None
+    # the oracle runs beside the GPU work in its own process (one core); its
+    # first step from u0 is the reference for the errors reported below
+    oracle_proc = None
     ref_npy = os.path.join(tempfile.gettempdir(), f"anidiff_oracle_step1_{os.getpid()}.npy")
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(args.workload, args.cpu_sample_seconds, 10 ** 6, ref_npy)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.nx:
+        oracle_proc = start_oracle_sample(args.workload, args.cpu_sample_seconds, 10 ** 6,
+                                          ref_npy)
 
     import paper_2307_12276_gb300 as ad
-    p = problem(args.workload)
-    g = p.grid
-    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(), device=dev)
+    w = WORKLOADS[args.workload]
+    p = problem(args.workload, args.nx)
     stream = torch.cuda.current_stream(dev)
-    op = ad.create_operator(g.nx, g.ny, g.bc, T(p.Dxx), T(p.Dxy), T(p.Dyy), p.ax, p.ay,
-                            ad.FP64, stream=stream)
-    src = ad.Source([T(gk) for gk in p.source.g], list(p.source.h))
-    u0 = T(p.u0)
-    u = u0.clone()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-
-    # first step from u0 (compared with the oracle's first step)
-    st1 = ad.expquad_step(op, u, 0.0, p.dt, p.s, p.c, src, tol=p.tol)
-    torch.cuda.synchronize()
-    err = None
-    if cpu is not None and os.path.exists(ref_npy):
-        ref = np.load(ref_npy)
-        err = float(np.linalg.norm(u.cpu().numpy() - ref) / np.linalg.norm(ref))
-        os.remove(ref_npy)
-    t = p.dt
-    for _ in range(max(0, args.warmup - 1)):
-        ad.expquad_step(op, u, t, p.dt, p.s, p.c, src, tol=p.tol)
-        t += p.dt
-    torch.cuda.synchronize()
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ad.time_series(op)          # event pair around every series kernel launch in the timed steps
-    # The steps are enqueued without a host round trip between them (the
-    # asynchronous entry point); the totals call synchronises and reports
-    # their iterations, launches and worst status.
-    with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            flush.zero_()
-            starts[k].record(stream)
-            ad.expquad_step_async(op, u, t, p.dt, p.s, p.c, src, tol=p.tol)
-            ends[k].record(stream)
-            t += p.dt
-        tot = ad.async_totals(op)
-        torch.cuda.synchronize()
-    launches = tot["kernel_launches"]
-    iters_per_step = tot["iters"] / args.steps
-    assert tot["converged"] and tot["substeps"] == args.steps
-    series_t = ad.series_timing(op)
-    ad.time_series(op, False)
-    if world > 1:
-        dist.barrier()
-    dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    dev_ms, value = job_throughput(dev_ms, g.n, args.steps, world, dev)
-
-    # e2e: the state lives in pinned host memory; the C ABI stages it per call
-    uh = torch.empty(g.n, dtype=torch.float64, pin_memory=True)
-    uh.copy_(u0.cpu())
-    ue = uh.numpy()
-    te = []
-    for k in range(args.e2e_steps + 1):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ad.expquad_step(op, ue, k * p.dt, p.dt, p.s, p.c, src, tol=p.tol)
-        el = time.perf_counter() - t0
-        if k > 0:                       # the first call allocates the staging buffers
-            te.append(el)
-    # host wall time per step: the median (a single host hiccup of a few ms
-    # would otherwise dominate a short run); the mean is reported beside it
-    e2e_value = g.n / statistics.median(te) / 1e6
-    e2e_mean_ms = 1e3 * statistics.mean(te)
-
-    # roofline of the series kernel, from the event pairs around its launches in the timed steps
-    flops = 28.0 * g.n        # 14 FP64 FMA per cell: 9 stencil, shift, coupling, p, 2 norms
-    bytes_alg = 112.0 * g.n   # 9 weights + y + w2 + p (r/w) + y_next, 8 B each
-    ms_it = series_t["ms"] / max(series_t["iters"], 1)
-    # one launch per step: the tile kernel ran the whole step (A u + sources,
-    # the series, u += P), whose algorithmic work is counted with the series
-    fused = launches == args.steps and series_t["series"] == args.steps
-    step_flops = 24.0 * g.n if fused else 0.0   # 9 stencil + 2 source + 1 update FMA per cell
-    achieved = ((flops * series_t["iters"] + step_flops * series_t["series"])
-                / (series_t["ms"] * 1e-3) / 1e12)
-    ms_forced = ad.profile_leja_iteration(op, aug=1, reps=300)
-    kernel = series_t["kernel"]
-    traffic = None
-    if kernel == "leja_nsync_f64_k":
-        traffic = traffic_per_launch(F64_SERIES_SOURCES, "leja_nsync_f64_512sq.md")
-    elif kernel == "leja_tile_f64_k":
-        traffic = traffic_per_launch(F64_SERIES_SOURCES, "leja_tile_f64_512sq.md")
-    roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-            "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-            "traffic": traffic, "kernel": f"{kernel}<aug>",
-            "work_unit": ("one launch = one whole step: A u + sources, the Newton series "
-                          "(all its Leja iterations), u += P" if fused else
-                          "one launch = one whole Newton series (all its Leja iterations)"),
-            "alg_flops_per_launch_outside_series": step_flops,
-            "launches_timed": series_t["series"], "iterations_timed": series_t["iters"],
-            "ms_per_launch": round(series_t["ms"] / max(series_t["series"], 1), 5),
-            "ms_per_iteration": round(ms_it, 5),
-            "ms_per_iteration_forced_300": round(ms_forced, 5),
-            "alg_flops_per_iteration": flops,
-            "alg_bytes_per_iteration": bytes_alg,
-            "peak_note": "of derived FP64 peak: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz "
-                         "(a DFMA loop on every SM measured 1.68 DFMA/clk/SM = 1.06 TFLOP/s)"}
+    label = args.workload if not args.nx else f"{args.workload} at {args.nx}^2"
+    head, u1 = measure_workload(ad, dev, stream, p, flush, args.steps, args.warmup,
+                                args.e2e_steps, world=world, label=label,
+                                dt_over_cfl=w["dt_over_cfl"])
 
     forms = {}
-    wanted = set() if args.no_forms else set(args.forms.split(","))
+    fp32_u1 = None
+    wanted = set() if args.no_forms or rank != 0 else set(args.forms.split(","))
     if "fp32" in wanted:
-        forms["fp32_4096sq"] = measure_fp32_form(ad, dev, stream, flush, args.form_steps)
+        forms["fp32_4096sq"], fp32_u1 = measure_fp32_form(
+            ad, dev, stream, flush, args.form_steps,
+            p if w["kind"] == "c2" and not args.nx else None)
+        if w["kind"] == "c2" and not args.nx:
+            forms["fp32_4096sq"]["speedup_over_fp64_path"] = round(
+                forms["fp32_4096sq"]["value"] / head["value"], 2)
+    if w["kind"] == "c2":
+        del p
+    for key, name in (("c1", "c1-512sq-dirichlet-circular-expquad2-dt200cfl"),
+                      ("c0", "c0-64sq-periodic-uniform30-midpoint")):
+        if key in wanted and name != args.workload:
+            r, _ = measure_workload(ad, dev, stream, problem(name), flush, 20, 3, 9, label=name,
+                                    dt_over_cfl=WORKLOADS[name]["dt_over_cfl"])
+            r["value"] = round(r["value"], 2)
+            forms[f"{key}_fp64"] = r
     if "cn" in wanted:
         forms["cn_vs_exp"] = measure_cn_vs_exp(ad, dev, stream)
     if "momentum" in wanted:
@@ -932,35 +1090,46 @@ def run_ours(args):
             ad, dev, stream, args.form_steps,
             learned_fields=args.learned_fields if "learned" in wanted else 0)
 
+    cpu, err, err32 = None, None, None
+    if oracle_proc is not None:
+        cpu = finish_oracle_sample(oracle_proc)
+        if os.path.exists(ref_npy):
+            ref = np.load(ref_npy)
+            os.remove(ref_npy)
+            err = _rel_errors(u1, ref)
+            err["oracle_iters"] = cpu.get("first_step_iters")
+            err["gpu_iters"] = head["first_step_iters"]
+            if fp32_u1 is not None and w["kind"] == "c2":
+                err32 = _rel_errors(fp32_u1, ref)
+                forms["fp32_4096sq"]["err_vs_oracle_step1"] = err32
+                forms["fp32_4096sq"]["err_note"] = (
+                    "one FP32 step (tol 1e-6) from u0 against the FP64 oracle's step (tol "
+                    "1e-10), every cell")
+
     if rank == 0:
         line = {
-            "metric": "Mcell-steps/s", "value": round(value, 4), "unit": "Mcell-steps/s",
+            "metric": "Mcell-steps/s", "value": round(head["value"], 4), "unit": "Mcell-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(dev_ms / args.steps, 4), "higher_is_better": True,
+            "ms_per_step": round(head["dev_ms"] / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "nx": g.nx, "ny": g.ny, "cells": g.n,
-                       "dt_over_cfl": 200.0, "s": p.s, "c": list(p.c), "tol": p.tol,
-                       "l2": "flushed before every timed step (256 MiB write)",
-                       "parallelism": "replicas" if world > 1 else "single"},
-            "leja_iters_per_step": iters_per_step,
+            "config": head["config"],
+            "leja_iters_per_step": head["leja_iters_per_step"],
             "err_vs_oracle_step1": err,
-            "gpu_launches": launches,
-            "e2e": {"value": round(e2e_value, 4), "unit": "Mcell-steps/s",
-                    "h2d_bytes_per_step": 8 * g.n, "d2h_bytes_per_step": 8 * g.n,
-                    "steps": len(te), "stat": "median of per-step host wall times",
-                    "mean_ms_per_step": round(e2e_mean_ms, 4)},
-            "roofline": roof,
-            "clocks": clk.summary(),
+            "gpu_launches": head["gpu_launches"],
+            "e2e": head["e2e"],
+            "roofline": head["roofline"],
+            "clocks": head["clocks"],
         }
         if forms:
             line["forms"] = forms
         if cpu is not None:
-            line["cpu_baseline"] = {"value": round(cpu["value"], 6), "unit": "Mcell-steps/s",
-                                    "cores": 1, "kind": "oracle",
-                                    "sample": f"{cpu['steps']} exponential quadrature steps of "
-                                              f"the same workload from t=0 ({cpu['seconds']:.1f} s)"}
+            line["cpu_baseline"] = {
+                "value": round(cpu["value"], 6), "unit": "Mcell-steps/s", "cores": 1,
+                "host_cores": os.cpu_count(), "kind": "oracle",
+                "sample": f"{cpu['steps']} exponential step(s) of the same workload from t=0 "
+                          f"({cpu['seconds']:.1f} s timed; operator assembly "
+                          f"{cpu['setup_s']:.0f} s untimed), run beside the GPU measurements"}
         print(json.dumps(line), flush=True)
-    op.close()
     if world > 1:
         dist.destroy_process_group()
 

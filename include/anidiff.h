@@ -20,10 +20,12 @@
  *     device pointer or a host pointer; host data is staged through
  *     library-owned device buffers with copies on the operator's stream.
  *   - Ownership: the caller owns every buffer it passes.  The library owns the
- *     operator (packed coefficients, workspace, CUDA graphs), allocated in
- *     ad_create_operator and released by ad_destroy_operator; no call
- *     allocates device memory after creation, except the lazily built device
- *     buffers for host-pointer staging (once per operator).
+ *     operator (packed coefficients, workspace, host-pointer staging buffers,
+ *     CUDA graphs), allocated in ad_create_operator and released by
+ *     ad_destroy_operator.  No step allocates device memory: the GMRES basis
+ *     of ad_cn_step is allocated by ad_reserve_gmres beforehand, and the
+ *     first step of each kind instantiates its CUDA graph once (graph
+ *     instantiation is the driver's, not a cudaMalloc).
  *   - Streams: all work is enqueued on the CUDA stream given at creation.
  *     Calls that report statistics or a convergence status synchronise that
  *     stream before returning.
@@ -55,7 +57,7 @@ typedef enum {
 
 typedef enum { AD_BC_PERIODIC = 0, AD_BC_DIRICHLET0 = 1 } ad_bc;
 typedef enum { AD_FP64 = 0, AD_FP32_STORAGE = 1 } ad_precision;
-typedef enum { AD_BOUND_GERSHGORIN = 0, AD_BOUND_POWER = 1 } ad_bound_method;
+typedef enum { AD_BOUND_GERSHGORIN = 0, AD_BOUND_POWER = 1, AD_BOUND_LEARNED = 2 } ad_bound_method;
 
 typedef struct {
   int nx, ny;                /* cells; nx, ny >= 1 */
@@ -143,7 +145,11 @@ AD_API int ad_set_substep_control(ad_operator* op, int adaptive);
  *   method AD_BOUND_POWER: power iteration, x <- A x / ||A x|| for power_iters
  *     steps from x0 (device vector of the storage type) or, with x0 == NULL,
  *     from the counter-based SplitMix64 sequence with the given seed mapped to
- *     [-0.5, 0.5); alpha = -safety * ||A x_last||.  */
+ *     [-0.5, 0.5); alpha = -safety * ||A x_last||.
+ *   method AD_BOUND_LEARNED: the bound model attached by ad_set_bound_model
+ *     (ad_learned_bounds on this one operator with the attached margin and
+ *     dt; x0, seed, power_iters and safety are ignored).  AD_ERR_INVALID when
+ *     no model is attached. */
 AD_API int ad_spectral_bound(ad_operator* op, int method, const void* x0, unsigned long long seed,
                       int power_iters, double safety, double* alpha);
 
@@ -201,11 +207,19 @@ AD_API int ad_expquad_step_async(ad_operator* op, void* u, double t, double dt, 
  * still applied, as in ad_expquad_step) or AD_ERR_TIMEOUT. */
 AD_API int ad_async_totals(ad_operator* op, ad_stats* stats);
 
+/* Allocate the Krylov basis of ad_cn_step for restarts up to max_restart
+ * (1..200): (max_restart + 1) float64 vectors of the grid's size, kept until
+ * the operator is destroyed or a larger reservation replaces it.  AD_FP64
+ * operators only.  Synchronises the operator's stream when it reallocates. */
+AD_API int ad_reserve_gmres(ad_operator* op, int max_restart);
+
 /* One Crank-Nicolson step (the paper's comparison solver; its linear solver
  * is unspecified): (I - dt/2 A) u+ = (I + dt/2 A) u + dt (S(t) + S(t+dt))/2,
  * solved by restarted GMRES(restart) from x0 = u to relative residual
  * gmres_tol.  force_iters > 0 runs exactly that many Arnoldi steps in one
- * cycle (force_iters <= restart <= 200).  AD_FP64 operators only. */
+ * cycle (force_iters <= restart <= 200).  AD_FP64 operators only.  The basis
+ * must have been reserved for at least max(restart, force_iters) by
+ * ad_reserve_gmres (AD_ERR_INVALID otherwise); the step allocates nothing. */
 AD_API int ad_cn_step(ad_operator* op, void* u, double t, double dt, const ad_source* src,
                double gmres_tol, int restart, int force_iters, ad_stats* stats);
 
@@ -273,6 +287,38 @@ AD_API int ad_mlp_train(ad_mlp* m, const float* X, const float* Y, int B, int ep
                         int fit_normalization, float* final_loss);
 /* Y = model(X), de-standardised; bf16 != 0 runs the BF16 inference kernels. */
 AD_API int ad_mlp_predict(ad_mlp* m, const float* X, int B, int bf16, float* Y);
+/* The learned spectral bound through the library (replaces the bound pass
+ * of Section 2 for operators whose fields resemble the training fields):
+ * ad_create_operator records the 21 input features of its fields (as
+ * ad_field_features, with max |a| over the advection fields or the constant
+ * advection).  For each of nops operators, the model m (21 inputs, 2
+ * outputs, as trained by ad_mlp_train on ad_bound_training_sample data)
+ * predicts t0 = log(|alpha| dx^2 / D_par) and t1 = log(iterations) from those
+ * features and log dt[k] (host array); the library sets
+ *   alpha_k = -margin * exp(t0) * D_par / dx^2   (dx = min(dx, dy), margin >= 1)
+ * as the operator's bound (c and gamma follow) and returns alpha_k in
+ * alpha_out and exp(t1) in iters_out (host arrays of nops, either may be
+ * NULL).  One batched inference for all operators, BF16 kernels when
+ * bf16 != 0.  AD_ERR_INVALID when a prediction is not a finite negative
+ * bound (no operator is changed then).  The model's activation workspace
+ * grows to the largest batch it has seen (an allocation on first use). */
+AD_API int ad_learned_bounds(ad_mlp* m, ad_operator* const* ops, int nops, const double* dt,
+                             double margin, int bf16, double* alpha_out, double* iters_out);
+/* Attach a bound model (or detach with m == NULL) for ad_spectral_bound's
+ * AD_BOUND_LEARNED method, with its margin (>= 1) and the step dt it predicts
+ * for.  The model must outlive the attachment. */
+AD_API int ad_set_bound_model(ad_operator* op, ad_mlp* m, double margin, double dt);
+/* One training sample of the bound model from an AD_FP64 operator: the 21
+ * inputs (its recorded features and log dt) into x21, and the targets into
+ * t2: t0 = log(est dx^2 / D_par) with est the power-iteration estimate of
+ * |lambda|max (power_iters steps from the SplitMix64 vector of seed + 1),
+ * t1 = log(max(1, m)) with m the Leja iterations of phi_1(dt A) v at tol
+ * for the SplitMix64 vector v of seed, with alpha = -safety * est (the
+ * operator keeps that bound).  *power_estimate (may be NULL) receives est. */
+AD_API int ad_bound_training_sample(ad_operator* op, double dt, unsigned long long seed,
+                                    int power_iters, double safety, double tol, float* x21,
+                                    float* t2, double* power_estimate);
+
 /* The 21 input features of one field: log max lambda_1(D), log min lambda_2(D),
  * log(max|a| + 1e-6), log min(dx, dy), log dt, and the anisotropy-weighted
  * 16-bin histogram of the principal direction of D over (-pi/2, pi/2]
@@ -397,14 +443,17 @@ AD_API int ad_series_timing(const ad_operator* op, double* ms, int* series, long
  * of about 6.4 MB that every GPU loading the library holds until exit.
  *   grid, Dxx, Dxy, Dyy : as in ad_create_operator (device fields, FP64);
  *   ax_c, ay_c          : constant advection;
- *   alpha               : spectral bound (< 0), or 0 to compute it by Gershgorin;
+ *   alpha               : spectral bound (< 0), or 0 to compute it by Gershgorin
+ *                         (AD_ERR_INVALID if that bound is not negative, as in
+ *                         ad_spectral_bound);
  *   v, out              : float64 DEVICE vectors [ny][nx] (may alias);
  *   dt, tol, force_iters: as in ad_leja_phi1; one substep only.
  * Limits: at most 65536 cells and gamma*dt <= 200 (AD_ERR_INVALID with a
  * message otherwise).  Every call shares the scratch and it keeps the last
  * call's contents; calls that overlap on the GPU race and must be serialised
- * by the caller.  The first call on a device looks up the scratch address
- * (once per device); make it before any stream capture.  Synchronises the
+ * by the caller.  Every call looks up the scratch's device address on the
+ * current device (no saved address can go stale); the first call on a device
+ * may load the module, so make it before any stream capture.  Synchronises the
  * stream before returning. */
 AD_API int ad_leja_phi1_noalloc(const ad_grid* grid, const double* Dxx, const double* Dxy,
                                 const double* Dyy, double ax_c, double ay_c, double alpha,

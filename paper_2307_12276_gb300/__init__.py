@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libanidiff.so")
 AD_OK, AD_ERR_INVALID, AD_ERR_CUDA, AD_ERR_NOT_CONVERGED, AD_ERR_TIMEOUT, AD_ERR_NOMEM = range(6)
 BC_PERIODIC, BC_DIRICHLET0 = 0, 1
 FP64, FP32_STORAGE = 0, 1
-BOUND_GERSHGORIN, BOUND_POWER = 0, 1
+BOUND_GERSHGORIN, BOUND_POWER, BOUND_LEARNED = 0, 1, 2
 MAX_SOURCES = 16
 
 if not os.path.exists(LIB_PATH):
@@ -73,6 +73,7 @@ _sig = {
                                    _d]),
     "ad_async_totals": (_i, [_vp, C.POINTER(Stats)]),
     "ad_cn_step": (_i, [_vp, _vp, _d, _d, C.POINTER(_Source), _d, _i, _i, C.POINTER(Stats)]),
+    "ad_reserve_gmres": (_i, [_vp, _i]),
     "ad_penalised_step": (_i, [_vp, _vp, _d, _d, C.POINTER(_Source), _d, _d, _i,
                                C.POINTER(Stats)]),
     "ad_penalty_beta": (_i, [C.POINTER(_Grid), _vp, _vp, _vp, _vp, C.POINTER(_d)]),
@@ -92,6 +93,11 @@ _sig = {
     "ad_mlp_train": (_i, [_vp, _vp, _vp, _i, _i, C.c_float, _i, C.POINTER(C.c_float)]),
     "ad_mlp_predict": (_i, [_vp, _vp, _i, _i, _vp]),
     "ad_field_features": (_i, [C.POINTER(_Grid), _vp, _vp, _vp, _d, _d, _vp, _vp]),
+    "ad_learned_bounds": (_i, [_vp, C.POINTER(_vp), _i, C.POINTER(_d), _d, _i, C.POINTER(_d),
+                               C.POINTER(_d)]),
+    "ad_set_bound_model": (_i, [_vp, _vp, _d, _d]),
+    "ad_bound_training_sample": (_i, [_vp, _d, C.c_ulonglong, _i, _d, _d, C.POINTER(C.c_float),
+                                      C.POINTER(C.c_float), C.POINTER(_d)]),
     "ad_create_momentum_operator": (_i, [C.POINTER(_Grid), C.POINTER(_Momentum), _vp, _vp, _vp,
                                          _d, _d, _vp, C.POINTER(_vp)]),
     "ad_destroy_momentum_operator": (_i, [_vp]),
@@ -332,6 +338,11 @@ def async_totals(op: Operator) -> dict:
     return st.as_dict()
 
 
+def reserve_gmres(op: Operator, max_restart: int) -> None:
+    """ad_reserve_gmres: allocate the GMRES basis for restarts up to max_restart."""
+    _check(_lib.ad_reserve_gmres(op.handle, int(max_restart)))
+
+
 def cn_step(op: Operator, u, t: float, dt: float, source: Optional[Source] = None,
             gmres_tol: float = 1e-10, restart: int = 50, force_iters: int = 0) -> dict:
     st = Stats()
@@ -547,6 +558,40 @@ class MLP:
         Y = torch.empty((B, self.n_out), dtype=torch.float32, device=X.device)
         _check(_lib.ad_mlp_predict(self.handle, X.data_ptr(), B, 1 if bf16 else 0, Y.data_ptr()))
         return Y
+
+
+def learned_bounds(model: "MLP", ops: Sequence[Operator], dts, margin: float = 1.1,
+                   bf16: bool = True):
+    """ad_learned_bounds: set every operator's spectral bound from the model's
+    prediction; returns (alphas, predicted iterations) as lists."""
+    import numpy as np
+    n = len(ops)
+    handles = (_vp * n)(*[op.handle for op in ops])
+    dt = (_d * n)(*np.broadcast_to(np.asarray(dts, dtype=np.float64), (n,)).tolist())
+    a, it = (_d * n)(), (_d * n)()
+    _check(_lib.ad_learned_bounds(model.handle, handles, n, dt, float(margin), 1 if bf16 else 0,
+                                  a, it))
+    return list(a), list(it)
+
+
+def set_bound_model(op: Operator, model: Optional["MLP"], margin: float = 1.1,
+                    dt: float = 1.0) -> None:
+    """ad_set_bound_model: the model spectral_bound(op, BOUND_LEARNED) uses."""
+    _check(_lib.ad_set_bound_model(op.handle, model.handle if model is not None else None,
+                                   float(margin), float(dt)))
+    op._bound_model = model               # keep the model alive while attached
+
+
+def bound_training_sample(op: Operator, dt: float, seed: int, power_iters: int = 60,
+                          safety: float = 1.1, tol: float = 1e-6):
+    """ad_bound_training_sample: (inputs[21], targets[2], power estimate)."""
+    import numpy as np
+    x = (C.c_float * 21)()
+    t = (C.c_float * 2)()
+    est = _d()
+    _check(_lib.ad_bound_training_sample(op.handle, float(dt), int(seed), int(power_iters),
+                                         float(safety), float(tol), x, t, C.byref(est)))
+    return np.array(x, dtype=np.float32), np.array(t, dtype=np.float32), est.value
 
 
 def field_features(nx, ny, bc, Dxx, Dxy, Dyy, max_a, dt, stream=None, x0=-1.0, x1=1.0, y0=-1.0,

@@ -217,6 +217,7 @@ struct OperatorView {
 };
 }  // namespace ad
 struct ad_operator;
+struct ad_mlp;
 namespace ad {
 bool operator_view(const ad_operator* op, OperatorView* v);
 
@@ -236,8 +237,24 @@ long long& launch_counter();
 void penalty_cg_iteration(const GridDev& g, double dx, double dy, double c, double* x, double* r,
                           double* p, double* Mp, double* partials, int nblocks, double* scal,
                           cudaStream_t s);
-// partials[b] = min over the block's cells of -lambda_max(D) (reduce with min).
-void neg_lambda_max_partials(long long n, const double* Dxx, const double* Dxy, const double* Dyy,
-                             double* partials, int nblocks, cudaStream_t s);
+// max over cells of lambda_max(D), reduced on the device with no scratch
+// buffer; synchronises s.  Returns 0, or 1 on a CUDA error.
+int lambda_max_reduce(long long n, const double* Dxx, const double* Dxy, const double* Dyy,
+                      int nblocks, cudaStream_t s, double* out);
+
+// ---------------------------------------------------------------- learned bound
+constexpr int kFeatures = 21;
+// The 21 inputs of the bound model for one field (slot 4, log dt, is left 0):
+// log max lambda_1(D), log min lambda_2(D), log(max|a| + 1e-6) (max over the
+// advection fields when given, else max_a), log dxmin, -, and the
+// anisotropy-weighted 16-bin histogram of the principal direction of D.
+// Reduced on the device in a fixed accumulator (no scratch buffer); host
+// threads are serialised; synchronises s.  Returns 0, or 1 on a CUDA error.
+int field_features(long long n, double dxmin, const double* Dxx, const double* Dxy,
+                   const double* Dyy, const double* ax, const double* ay, double max_a,
+                   cudaStream_t s, float* out21);
+// Y[B][2] = model(X[B][21]) with host X and Y (BF16 kernels when bf16 != 0);
+// synchronises the model's stream.
+int mlp_predict_host(ad_mlp* M, const float* X, int B, int bf16, float* Y);
 
 }  // namespace ad

@@ -98,8 +98,8 @@ struct ad_operator {
   void* Y0 = nullptr; void* Y1 = nullptr; void* P = nullptr;
   void* W1 = nullptr; void* W2 = nullptr;
   void* T1 = nullptr; void* T2 = nullptr; void* T3 = nullptr;
-  void* S0 = nullptr; void* S1 = nullptr;      // host staging (lazy)
-  double* Vk = nullptr; int vk_cols = 0;       // GMRES basis (lazy)
+  void* S0 = nullptr; void* S1 = nullptr;      // host staging (allocated at creation)
+  double* Vk = nullptr; int vk_cols = 0;       // GMRES basis (ad_reserve_gmres)
   LejaCoef* lc = nullptr;
   Ctrl* ctrl = nullptr;
   double* partials = nullptr;                  // >= 2 * nblocks and >= kMaxGmres+1 rows for GMRES
@@ -127,6 +127,12 @@ struct ad_operator {
   LejaCoef* h_lc = nullptr;
   Ctrl* h_ctrl = nullptr;
   double* h_scal = nullptr;                    // [4 * (kMaxGmres + 2)]
+  // learned bound: the model's inputs of this operator's fields (slot 4,
+  // log dt, is filled per prediction), and the model ad_spectral_bound uses
+  float feat[kFeatures] = {};
+  double dxmin = 0.0;
+  ad_mlp* bound_model = nullptr;
+  double bound_margin = 1.1, bound_dt = 0.0;
   // method state
   double alpha = 0.0, c = 0.0, gamma = 0.0;
   bool have_alpha = false;
@@ -536,20 +542,10 @@ int n_substeps(const ad_operator* op, double dt) {
   return (int)std::ceil(rho / op->rho_max);
 }
 
-int ensure_staging(ad_operator* op) {
-  const size_t bytes = (size_t)op->g.n * op->esz;
-  if (!op->S0) {
-    if (cudaMalloc(&op->S0, bytes) != cudaSuccess) { cudaGetLastError(); return fail(AD_ERR_NOMEM, "staging buffer"); }
-    if (cudaMalloc(&op->S1, bytes) != cudaSuccess) { cudaGetLastError(); return fail(AD_ERR_NOMEM, "staging buffer"); }
-  }
-  return AD_OK;
-}
-
 // Bring a caller vector to the device: returns the device pointer to use and
 // whether the result must be copied back.
 int stage_in(ad_operator* op, const void* user, int which, const void** dev, bool copy) {
   if (is_device_ptr(user)) { *dev = user; return AD_OK; }
-  AD_TRY(ensure_staging(op));
   void* slot = which == 0 ? op->S0 : (which == 1 ? op->S1 : op->T3);
   if (copy)
     CUDA_TRY(cudaMemcpyAsync(slot, user, (size_t)op->g.n * op->esz, cudaMemcpyHostToDevice, op->stream));
@@ -810,7 +806,9 @@ int ad_create_operator(const ad_grid* grid, const double* Dxx, const double* Dxy
   } else {
     ok = ok && alloc((void**)&op->F, sizeof(float) * (op->adv == 2 ? 5 : 3) * n);
   }
-  for (void** v : {&op->Y0, &op->Y1, &op->P, &op->W1, &op->W2, &op->T1, &op->T2, &op->T3})
+  // S0, S1: staging of host-pointer vectors, allocated here so that no step allocates
+  for (void** v : {&op->Y0, &op->Y1, &op->P, &op->W1, &op->W2, &op->T1, &op->T2, &op->T3,
+                   &op->S0, &op->S1})
     ok = ok && alloc(v, op->esz * n);
   op->partials_len = std::max<size_t>(2 * (size_t)op->nblocks, (size_t)(kMaxGmres + 2) * op->nblocks);
   ok = ok && alloc((void**)&op->partials, sizeof(double) * op->partials_len);
@@ -842,6 +840,14 @@ int ad_create_operator(const ad_grid* grid, const double* Dxx, const double* Dxy
   if (e != cudaSuccess) {
     ad_destroy_operator(op);
     return fail(AD_ERR_CUDA, std::string("pack kernel: ") + cudaGetErrorString(e));
+  }
+  // inputs of the learned bound, from the fields while they are at hand
+  op->dxmin = std::min(dx, dy);
+  if (field_features(n, op->dxmin, Dxx, Dxy, Dyy, ax, ay, std::hypot(ax_c, ay_c), op->stream,
+                     op->feat) != 0) {
+    cudaGetLastError();
+    ad_destroy_operator(op);
+    return fail(AD_ERR_CUDA, "field features kernel failed");
   }
   (void)leja_points();  // computed once per process
   double alpha = 0.0;
@@ -939,6 +945,12 @@ int ad_spectral_bound(ad_operator* op, int method, const void* x0, unsigned long
     CUDA_TRY(cudaMemcpyAsync(op->h_scal, op->dscal, sizeof(double), cudaMemcpyDeviceToHost, op->stream));
     CUDA_TRY(cudaStreamSynchronize(op->stream));
     a = -safety * op->h_scal[0];
+  } else if (method == AD_BOUND_LEARNED) {
+    if (!op->bound_model)
+      return fail(AD_ERR_INVALID, "no bound model: call ad_set_bound_model first");
+    ad_operator* one[1] = {op};
+    AD_TRY(ad_learned_bounds(op->bound_model, one, 1, &op->bound_dt, op->bound_margin, 1, &a,
+                             nullptr));
   } else {
     return fail(AD_ERR_INVALID, "unknown spectral bound method");
   }
@@ -948,13 +960,83 @@ int ad_spectral_bound(ad_operator* op, int method, const void* x0, unsigned long
   return AD_OK;
 }
 
+int ad_set_bound_model(ad_operator* op, ad_mlp* m, double margin, double dt) {
+  g_err.clear();
+  if (!op) return fail(AD_ERR_INVALID, "NULL argument");
+  if (m && (!(margin >= 1.0) || !std::isfinite(margin) || !(dt > 0) || !std::isfinite(dt)))
+    return fail(AD_ERR_INVALID, "margin must be >= 1 and dt positive");
+  op->bound_model = m;
+  op->bound_margin = margin;
+  op->bound_dt = dt;
+  return AD_OK;
+}
+
+int ad_learned_bounds(ad_mlp* m, ad_operator* const* ops, int nops, const double* dt,
+                      double margin, int bf16, double* alpha_out, double* iters_out) {
+  g_err.clear();
+  if (!m || !ops || !dt || nops < 1) return fail(AD_ERR_INVALID, "NULL argument or nops < 1");
+  if (!(margin >= 1.0) || !std::isfinite(margin)) return fail(AD_ERR_INVALID, "margin must be >= 1");
+  std::vector<float> X((size_t)nops * kFeatures), Y((size_t)nops * 2);
+  for (int k = 0; k < nops; ++k) {
+    if (!ops[k]) return fail(AD_ERR_INVALID, "NULL operator");
+    if (!(dt[k] > 0) || !std::isfinite(dt[k])) return fail(AD_ERR_INVALID, "dt must be positive");
+    std::copy(ops[k]->feat, ops[k]->feat + kFeatures, X.begin() + (size_t)k * kFeatures);
+    X[(size_t)k * kFeatures + 4] = (float)std::log(dt[k]);
+  }
+  AD_TRY(mlp_predict_host(m, X.data(), nops, bf16, Y.data()));
+  // outputs: t0 = log(|alpha| dx^2 / D_par) and t1 = log(iterations); the
+  // bound is inflated by the margin
+  std::vector<double> alpha(nops);
+  for (int k = 0; k < nops; ++k) {
+    const ad_operator* op = ops[k];
+    const double dpar = std::exp((double)op->feat[0]);
+    alpha[k] = -margin * std::exp((double)Y[2 * k]) * dpar / (op->dxmin * op->dxmin);
+    if (!(alpha[k] < 0.0) || !std::isfinite(alpha[k]))
+      return fail(AD_ERR_INVALID, "the model predicted no usable bound (not finite or not negative)");
+  }
+  for (int k = 0; k < nops; ++k) {
+    AD_TRY(set_alpha(ops[k], alpha[k]));
+    if (alpha_out) alpha_out[k] = alpha[k];
+    if (iters_out) iters_out[k] = std::exp((double)Y[2 * k + 1]);
+  }
+  return AD_OK;
+}
+
+int ad_bound_training_sample(ad_operator* op, double dt, unsigned long long seed, int power_iters,
+                             double safety, double tol, float* x21, float* t2,
+                             double* power_estimate) {
+  g_err.clear();
+  if (!op || !x21 || !t2) return fail(AD_ERR_INVALID, "NULL argument");
+  if (op->prec != AD_FP64) return fail(AD_ERR_INVALID, "training labels need an AD_FP64 operator");
+  if (!(dt > 0) || !std::isfinite(dt) || !(tol > 0) || !(safety >= 1.0))
+    return fail(AD_ERR_INVALID, "dt, tol must be positive and safety >= 1");
+  double a = 0.0;
+  AD_TRY(ad_spectral_bound(op, AD_BOUND_POWER, nullptr, seed + 1, power_iters, 1.0, &a));
+  const double est = -a;                       // power-iteration estimate of |lambda|max
+  AD_TRY(set_alpha(op, -safety * est));
+  // iterations of phi_1(dt A) v at tol for a SplitMix64 vector v
+  splitmix_fill(op->prec, op->g.n, seed, op->S0, op->stream);
+  ad_stats st{};
+  st.converged = 1;
+  const int r = phi1_device(op, op->S0, op->S1, dt, tol, -1, &st);
+  if (r != AD_OK && r != AD_ERR_NOT_CONVERGED) return r;
+  CUDA_TRY(cudaStreamSynchronize(op->stream));
+  std::copy(op->feat, op->feat + kFeatures, x21);
+  x21[4] = (float)std::log(dt);
+  const double dpar = std::exp((double)op->feat[0]);
+  t2[0] = (float)std::log(est * op->dxmin * op->dxmin / dpar);
+  t2[1] = (float)std::log((double)std::max(st.iters, 1));
+  if (power_estimate) *power_estimate = est;
+  return AD_OK;
+}
+
 int ad_apply(ad_operator* op, const void* u, void* Au) {
   g_err.clear();
   if (!op || !u || !Au) return fail(AD_ERR_INVALID, "NULL argument");
   const void* ud;
   AD_TRY(stage_in(op, u, 2, &ud, true));
   void* od = is_device_ptr(Au) ? Au : nullptr;
-  if (!od) { AD_TRY(ensure_staging(op)); od = op->S1; }
+  if (!od) od = op->S1;
   Sources none{};
   apply(op, ud, od, nullptr, none);
   CUDA_TRY(cudaGetLastError());
@@ -975,7 +1057,7 @@ int ad_leja_phi1(ad_operator* op, const void* v, void* out, double dt, double to
   const void* vd;
   AD_TRY(stage_in(op, v, 0, &vd, true));
   void* od = is_device_ptr(out) ? out : nullptr;
-  if (!od) { AD_TRY(ensure_staging(op)); od = op->S1; }
+  if (!od) od = op->S1;
   int r = phi1_device(op, vd, od, dt, tol, force_iters < 0 ? -1 : force_iters, &st);
   if (r != AD_OK && r != AD_ERR_NOT_CONVERGED) return r;
   if (r != AD_OK && op->adaptive && force_iters < 0) {   // gave up: out is not written
@@ -1245,19 +1327,12 @@ int ad_penalty_beta(const ad_grid* grid, const double* Dxx, const double* Dxy, c
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const long long n = (long long)grid->nx * grid->ny;
   const int nb = stream_blocks(n);
-  double* buf = nullptr;
-  CUDA_TRY(cudaMalloc((void**)&buf, sizeof(double) * (nb + 1)));
-  neg_lambda_max_partials(n, Dxx, Dxy, Dyy, buf, nb, s);
-  reduce_partials(buf, nb, 1, buf + nb, s);
   double v = 0.0;
-  const cudaError_t e1 = cudaMemcpyAsync(&v, buf + nb, sizeof(double), cudaMemcpyDeviceToHost, s);
-  const cudaError_t e2 = cudaStreamSynchronize(s);
-  cudaFree(buf);
-  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+  if (lambda_max_reduce(n, Dxx, Dxy, Dyy, nb, s, &v) != 0) {
     cudaGetLastError();
     return fail(AD_ERR_CUDA, "ad_penalty_beta: reduction failed");
   }
-  *beta = -v;
+  *beta = v;
   return AD_OK;
 }
 
@@ -1330,6 +1405,25 @@ int ad_penalised_step(ad_operator* op, void* u, double t, double dt, const ad_so
   return AD_OK;
 }
 
+int ad_reserve_gmres(ad_operator* op, int max_restart) {
+  g_err.clear();
+  if (!op) return fail(AD_ERR_INVALID, "NULL argument");
+  if (op->prec != AD_FP64) return fail(AD_ERR_INVALID, "GMRES needs an AD_FP64 operator");
+  if (max_restart < 1 || max_restart > kMaxGmres)
+    return fail(AD_ERR_INVALID, "max_restart must be in [1, 200]");
+  if (op->vk_cols >= max_restart + 1) return AD_OK;
+  if (op->stream) CUDA_TRY(cudaStreamSynchronize(op->stream));
+  if (op->Vk) cudaFree(op->Vk);
+  op->Vk = nullptr;
+  op->vk_cols = 0;
+  if (cudaMalloc(&op->Vk, sizeof(double) * (size_t)(max_restart + 1) * op->g.n) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AD_ERR_NOMEM, "GMRES basis");
+  }
+  op->vk_cols = max_restart + 1;
+  return AD_OK;
+}
+
 int ad_cn_step(ad_operator* op, void* u, double t, double dt, const ad_source* src,
                double gmres_tol, int restart, int force_iters, ad_stats* stats) {
   g_err.clear();
@@ -1343,16 +1437,9 @@ int ad_cn_step(ad_operator* op, void* u, double t, double dt, const ad_source* s
   AD_TRY(fill_sources(src, kMaxSources, &S));
   const long long n = op->g.n;
   const int m = force_iters > 0 ? force_iters : restart;
-  if (op->vk_cols < m + 1) {
-    if (op->Vk) cudaFree(op->Vk);
-    op->Vk = nullptr;
-    op->vk_cols = 0;
-    if (cudaMalloc(&op->Vk, sizeof(double) * (size_t)(m + 1) * n) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(AD_ERR_NOMEM, "GMRES basis");
-    }
-    op->vk_cols = m + 1;
-  }
+  if (op->vk_cols < m + 1)
+    return fail(AD_ERR_INVALID, "GMRES basis too small for this restart: call "
+                                "ad_reserve_gmres(op, restart) first");
   ad_stats st{};
   st.converged = 1;
   st.alpha = op->alpha;

@@ -14,7 +14,9 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -194,15 +196,17 @@ __global__ void to_bf16_k(const float* x, long long n, __nv_bfloat16* y) {
 }
 
 // Field features: anisotropy-weighted histogram (16 bins over [-pi/2, pi/2))
-// of the principal direction 1/2 atan2(2 Dxy, Dxx - Dyy), and the extreme
-// eigenvalues max lambda_1, min lambda_2 of D over the cells.
+// of the principal direction 1/2 atan2(2 Dxy, Dxx - Dyy), the extreme
+// eigenvalues max lambda_1, min lambda_2 of D over the cells and, when
+// advection fields are given, max |a| over the cells.  out: hist[16],
+// lmax, lmin, amax (non-negative floats order like their bit patterns).
 __global__ void field_features_k(const double* Dxx, const double* Dxy, const double* Dyy,
-                                 long long n, float* hist, float* lmax, float* lmin) {
+                                 const double* ax, const double* ay, long long n, float* out) {
   __shared__ float sh[16];
-  __shared__ float smax[kT], smin[kT];
+  __shared__ float smax[kT], smin[kT], samax[kT];
   if (threadIdx.x < 16) sh[threadIdx.x] = 0.f;
   __syncthreads();
-  float mx = 0.f, mn = 3.4e38f;
+  float mx = 0.f, mn = 3.4e38f, am = 0.f;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
     const float a = (float)Dxx[q], c = (float)Dxy[q], b = (float)Dyy[q];
@@ -215,24 +219,34 @@ __global__ void field_features_k(const double* Dxx, const double* Dxy, const dou
     int bin = (int)floorf((th + 1.57079633f) * (16.f / 3.14159265f));
     bin = bin < 0 ? 0 : (bin > 15 ? 15 : bin);
     atomicAdd(&sh[bin], w);
+    if (ax || ay) {
+      const float vx = ax ? (float)ax[q] : 0.f, vy = ay ? (float)ay[q] : 0.f;
+      am = fmaxf(am, sqrtf(vx * vx + vy * vy));
+    }
   }
   smax[threadIdx.x] = mx;
   smin[threadIdx.x] = mn;
+  samax[threadIdx.x] = am;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
       smax[threadIdx.x] = fmaxf(smax[threadIdx.x], smax[threadIdx.x + s]);
       smin[threadIdx.x] = fminf(smin[threadIdx.x], smin[threadIdx.x + s]);
+      samax[threadIdx.x] = fmaxf(samax[threadIdx.x], samax[threadIdx.x + s]);
     }
     __syncthreads();
   }
-  if (threadIdx.x < 16) atomicAdd(&hist[threadIdx.x], sh[threadIdx.x]);
+  if (threadIdx.x < 16) atomicAdd(&out[threadIdx.x], sh[threadIdx.x]);
   if (threadIdx.x == 0) {
-    // non-negative floats order like their bit patterns
-    atomicMax((int*)lmax, __float_as_int(smax[0]));
-    atomicMin((int*)lmin, __float_as_int(fmaxf(smin[0], 0.f)));
+    atomicMax((int*)&out[16], __float_as_int(smax[0]));
+    atomicMin((int*)&out[17], __float_as_int(fmaxf(smin[0], 0.f)));
+    atomicMax((int*)&out[18], __float_as_int(samax[0]));
   }
 }
+
+// Accumulators of the feature reduction: one small device array shared by
+// every call (calls are serialised on the host), so no call allocates.
+__device__ float g_feature_acc[19];
 
 int grid_for(long long n) {
   long long g = (n + kT - 1) / kT;
@@ -251,7 +265,7 @@ struct ad_mlp {
   // activation workspace for `cap` rows
   int cap = 0;
   float *X = nullptr, *A1 = nullptr, *A2 = nullptr, *Y = nullptr, *T = nullptr, *dY = nullptr,
-        *dA = nullptr, *dB = nullptr, *partial = nullptr;
+        *dA = nullptr, *dB = nullptr, *partial = nullptr, *Xin = nullptr;
   __nv_bfloat16 *Xb = nullptr, *A1b = nullptr, *A2b = nullptr;
   float* scratch = nullptr;
 };
@@ -284,12 +298,14 @@ void offsets(const ad_mlp* M, int o[6]) {
 
 int ensure_cap(ad_mlp* M, int B) {
   if (B <= M->cap) return AD_OK;
-  for (float** p : {&M->X, &M->A1, &M->A2, &M->Y, &M->T, &M->dY, &M->dA, &M->dB, &M->partial})
+  for (float** p : {&M->X, &M->A1, &M->A2, &M->Y, &M->T, &M->dY, &M->dA, &M->dB, &M->partial,
+                    &M->Xin})
     if (*p) { cudaFree(*p); *p = nullptr; }
   for (__nv_bfloat16** p : {&M->Xb, &M->A1b, &M->A2b})
     if (*p) { cudaFree(*p); *p = nullptr; }
   const size_t h = M->h;
   M_CUDA(cudaMalloc(&M->X, sizeof(float) * B * M->n_in));
+  M_CUDA(cudaMalloc(&M->Xin, sizeof(float) * B * M->n_in));
   M_CUDA(cudaMalloc(&M->A1, sizeof(float) * B * h));
   M_CUDA(cudaMalloc(&M->A2, sizeof(float) * B * h));
   M_CUDA(cudaMalloc(&M->Y, sizeof(float) * B * M->n_out));
@@ -351,7 +367,88 @@ int backward(ad_mlp* M, int B) {
   return nb;
 }
 
+// normalise X (device, [B][n_in]), run the network, de-standardise into Y (device)
+int predict_device(ad_mlp* M, const float* X, int B, int bf16, float* Y) {
+  cudaStream_t s = M->stream;
+  ++launch_counter();
+  normalize_k<<<grid_for((long long)B * M->n_in), kT, 0, s>>>(X, (long long)B * M->n_in, M->n_in, M->xm, M->xs, 1, M->X);
+  if (bf16) {
+    int o[6];
+    offsets(M, o);
+    ++launch_counter();
+    to_bf16_k<<<grid_for(M->np), kT, 0, s>>>(M->theta, M->np, M->theta16);
+    ++launch_counter();
+    to_bf16_k<<<grid_for((long long)B * M->n_in), kT, 0, s>>>(M->X, (long long)B * M->n_in, M->Xb);
+    const __nv_bfloat16* t = M->theta16;
+    ++launch_counter();
+    dense_fwd_bf16_k<<<grid_for((long long)B * M->h), kT, 0, s>>>(M->Xb, B, M->n_in, t + o[0], t + o[1], M->h, 1, M->A1b, nullptr);
+    ++launch_counter();
+    dense_fwd_bf16_k<<<grid_for((long long)B * M->h), kT, 0, s>>>(M->A1b, B, M->h, t + o[2], t + o[3], M->h, 1, M->A2b, nullptr);
+    ++launch_counter();
+    dense_fwd_bf16_k<<<grid_for((long long)B * M->n_out), kT, 0, s>>>(M->A2b, B, M->h, t + o[4], t + o[5], M->n_out, 0, nullptr, M->Y);
+  } else {
+    forward_f32(M, B);
+  }
+  ++launch_counter();
+  normalize_k<<<grid_for((long long)B * M->n_out), kT, 0, s>>>(M->Y, (long long)B * M->n_out, M->n_out, M->ym, M->ys, 0, Y);
+  M_CUDA(cudaGetLastError());
+  return AD_OK;
+}
+
 }  // namespace
+
+namespace ad {
+
+int field_features(long long n, double dxmin, const double* Dxx, const double* Dxy,
+                   const double* Dyy, const double* ax, const double* ay, double max_a,
+                   cudaStream_t s, float* out21) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  const float init[19] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0.f, 3.0e38f, 0.f};
+  if (cudaMemcpyToSymbolAsync(g_feature_acc, init, sizeof(init), 0, cudaMemcpyHostToDevice, s) !=
+      cudaSuccess)
+    return 1;
+  float* d = nullptr;
+  if (cudaGetSymbolAddress((void**)&d, g_feature_acc) != cudaSuccess) return 1;
+  ++launch_counter();
+  field_features_k<<<grid_for(n), kT, 0, s>>>(Dxx, Dxy, Dyy, ax, ay, n, d);
+  float h[19];
+  if (cudaMemcpyFromSymbolAsync(h, g_feature_acc, sizeof(h), 0, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return 1;
+  double tot = 0.0;
+  for (int k = 0; k < 16; ++k) tot += h[k];
+  const double amax = (ax || ay) ? (double)h[18] : max_a;
+  out21[0] = (float)std::log(std::max((double)h[16], 1e-30));          // log D_par
+  out21[1] = (float)std::log(std::max((double)h[17], 1e-30));          // log D_perp
+  out21[2] = (float)std::log(amax + 1e-6);                              // log max|a|
+  out21[3] = (float)std::log(dxmin);                                    // log dx
+  out21[4] = 0.f;                                                       // log dt: per call
+  for (int k = 0; k < 16; ++k) out21[5 + k] = tot > 0 ? (float)(h[k] / tot) : 1.f / 16.f;
+  return 0;
+}
+
+int mlp_predict_host(ad_mlp* M, const float* X, int B, int bf16, float* Y) {
+  if (!M || !X || !Y || B < 1) return mfail(AD_ERR_INVALID, "bad arguments");
+  if (M->n_in != kFeatures || M->n_out != 2)
+    return mfail(AD_ERR_INVALID, "the bound model must have 21 inputs and 2 outputs");
+  {
+    const int r = ensure_cap(M, B);
+    if (r != AD_OK) return r;
+  }
+  cudaStream_t s = M->stream;
+  M_CUDA(cudaMemcpyAsync(M->Xin, X, sizeof(float) * B * M->n_in, cudaMemcpyHostToDevice, s));
+  {
+    const int r = predict_device(M, M->Xin, B, bf16, M->T);
+    if (r != AD_OK) return r;
+  }
+  M_CUDA(cudaMemcpyAsync(Y, M->T, sizeof(float) * B * M->n_out, cudaMemcpyDeviceToHost, s));
+  M_CUDA(cudaStreamSynchronize(s));
+  return AD_OK;
+}
+
+}  // namespace ad
 
 extern "C" {
 
@@ -416,7 +513,7 @@ int ad_mlp_destroy(ad_mlp* M) {
   if (!M) return AD_OK;
   if (M->stream) cudaStreamSynchronize(M->stream);
   for (float* p : {M->theta, M->grad, M->m, M->v, M->xm, M->xs, M->ym, M->ys, M->X, M->A1, M->A2,
-                   M->Y, M->T, M->dY, M->dA, M->dB, M->partial})
+                   M->Y, M->T, M->dY, M->dA, M->dB, M->partial, M->Xin})
     if (p) cudaFree(p);
   for (__nv_bfloat16* p : {M->theta16, M->Xb, M->A1b, M->A2b})
     if (p) cudaFree(p);
@@ -534,30 +631,11 @@ int ad_mlp_predict(ad_mlp* M, const float* X, int B, int bf16, float* Y) {
     const int r = ensure_cap(M, B);
     if (r != AD_OK) return r;
   }
-  cudaStream_t s = M->stream;
-  ++launch_counter();
-  normalize_k<<<grid_for((long long)B * M->n_in), kT, 0, s>>>(X, (long long)B * M->n_in, M->n_in, M->xm, M->xs, 1, M->X);
-  if (bf16) {
-    int o[6];
-    offsets(M, o);
-    ++launch_counter();
-    to_bf16_k<<<grid_for(M->np), kT, 0, s>>>(M->theta, M->np, M->theta16);
-    ++launch_counter();
-    to_bf16_k<<<grid_for((long long)B * M->n_in), kT, 0, s>>>(M->X, (long long)B * M->n_in, M->Xb);
-    const __nv_bfloat16* t = M->theta16;
-    ++launch_counter();
-    dense_fwd_bf16_k<<<grid_for((long long)B * M->h), kT, 0, s>>>(M->Xb, B, M->n_in, t + o[0], t + o[1], M->h, 1, M->A1b, nullptr);
-    ++launch_counter();
-    dense_fwd_bf16_k<<<grid_for((long long)B * M->h), kT, 0, s>>>(M->A1b, B, M->h, t + o[2], t + o[3], M->h, 1, M->A2b, nullptr);
-    ++launch_counter();
-    dense_fwd_bf16_k<<<grid_for((long long)B * M->n_out), kT, 0, s>>>(M->A2b, B, M->h, t + o[4], t + o[5], M->n_out, 0, nullptr, M->Y);
-  } else {
-    forward_f32(M, B);
+  {
+    const int r = predict_device(M, X, B, bf16, Y);
+    if (r != AD_OK) return r;
   }
-  ++launch_counter();
-  normalize_k<<<grid_for((long long)B * M->n_out), kT, 0, s>>>(M->Y, (long long)B * M->n_out, M->n_out, M->ym, M->ys, 0, Y);
-  M_CUDA(cudaGetLastError());
-  M_CUDA(cudaStreamSynchronize(s));
+  M_CUDA(cudaStreamSynchronize(M->stream));
   return AD_OK;
 }
 
@@ -566,31 +644,12 @@ int ad_field_features(const ad_grid* grid, const double* Dxx, const double* Dxy,
   set_error_message("");
   if (!grid || !Dxx || !Dxy || !Dyy || !out21 || grid->nx < 1 || grid->ny < 1 || !(dt > 0))
     return mfail(AD_ERR_INVALID, "bad arguments");
-  cudaStream_t s = (cudaStream_t)stream;
-  const long long n = (long long)grid->nx * grid->ny;
-  float* d = nullptr;
-  M_CUDA(cudaMalloc(&d, sizeof(float) * 18));
-  const float init[18] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0.f, 3.0e38f};
-  M_CUDA(cudaMemcpyAsync(d, init, sizeof(init), cudaMemcpyHostToDevice, s));
-  ++launch_counter();
-  field_features_k<<<grid_for(n), kT, 0, s>>>(Dxx, Dxy, Dyy, n, d, d + 16, d + 17);
-  float h[18];
-  cudaError_t e1 = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
-  cudaError_t e2 = cudaStreamSynchronize(s);
-  cudaFree(d);
-  if (e1 != cudaSuccess || e2 != cudaSuccess) {
-    cudaGetLastError();
-    return mfail(AD_ERR_CUDA, "field features kernel failed");
-  }
   const double dx = (grid->x1 - grid->x0) / grid->nx, dy = (grid->y1 - grid->y0) / grid->ny;
-  double tot = 0.0;
-  for (int k = 0; k < 16; ++k) tot += h[k];
-  out21[0] = (float)std::log(std::max((double)h[16], 1e-30));          // log D_par
-  out21[1] = (float)std::log(std::max((double)h[17], 1e-30));          // log D_perp
-  out21[2] = (float)std::log(max_a + 1e-6);                             // log max|a|
-  out21[3] = (float)std::log(std::min(dx, dy));                         // log dx
+  const long long n = (long long)grid->nx * grid->ny;
+  if (field_features(n, std::min(dx, dy), Dxx, Dxy, Dyy, nullptr, nullptr, max_a,
+                     (cudaStream_t)stream, out21) != 0)
+    return mfail(AD_ERR_CUDA, "field features kernel failed");
   out21[4] = (float)std::log(dt);                                       // log dt
-  for (int k = 0; k < 16; ++k) out21[5 + k] = tot > 0 ? (float)(h[k] / tot) : 1.f / 16.f;
   return AD_OK;
 }
 

@@ -22,13 +22,14 @@
 //   * every call shares the array and it keeps the previous call's contents:
 //     calls that overlap on the GPU (two streams, two host threads) race on
 //     it and must be serialised by the caller;
-//   * the first call on a device looks up the array's device address
-//     (cudaGetSymbolAddress, once per device, with that device current); make
-//     that first call before any stream capture.
+//   * every call looks up the array's device address on the current device
+//     (cudaGetSymbolAddress, which allocates nothing), so the address is
+//     never stale, even after the primary context was reset and the module
+//     reloaded at another address.  The first call on a device may load the
+//     module: make it before any stream capture.
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -43,7 +44,6 @@ using namespace ad;
 constexpr long long kNoAllocMaxCells = 1LL << 16;
 constexpr int kNoAllocMaxBlocks = 152 * 8;   // upper bound of stream_blocks()
 constexpr double kNoAllocRhoMax = 200.0;
-constexpr int kMaxDevices = 64;
 
 struct NoAllocScratch {
   double weights[9 * kNoAllocMaxCells];   // packed, then scaled in place to (W - c)/gamma
@@ -59,31 +59,21 @@ struct NoAllocScratch {
 // must use the address from cudaGetSymbolAddress (see scratch_on_device).
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
-std::mutex g_addr_mu;
-NoAllocScratch* g_addr[kMaxDevices] = {};
-
 int nfail(int code, const std::string& msg) {
   set_error_message(msg.c_str());   // reported by ad_last_error()
   return code;
 }
 
-// Device address of the scratch on the current device (looked up once per device).
+// Device address of the scratch on the current device, looked up on every
+// call: a saved address could outlive the context it belongs to.
 int scratch_on_device(NoAllocScratch** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) { cudaGetLastError(); return nfail(AD_ERR_CUDA, "cudaGetDevice failed"); }
-  if (dev < 0 || dev >= kMaxDevices) return nfail(AD_ERR_INVALID, "device index out of range");
-  std::lock_guard<std::mutex> lock(g_addr_mu);
-  if (!g_addr[dev]) {
-    void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess || !ptr) {
-      cudaGetLastError();
-      return nfail(AD_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    }
-    g_addr[dev] = static_cast<NoAllocScratch*>(ptr);
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess || !ptr) {
+    cudaGetLastError();
+    return nfail(AD_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   }
-  *out = g_addr[dev];
+  *out = static_cast<NoAllocScratch*>(ptr);
   return AD_OK;
 }
 
@@ -143,7 +133,9 @@ extern "C" int ad_leja_phi1_noalloc(const ad_grid* grid, const double* Dxx, cons
     double a = 0.0;
     NA_CUDA(cudaMemcpyAsync(&a, S->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
     NA_CUDA(cudaStreamSynchronize(s));
-    alpha = a < 0.0 ? a : -1.0;
+    // the same refusal as ad_spectral_bound: a bound >= 0 defines no Leja interval
+    if (!(a < 0.0)) return nfail(AD_ERR_INVALID, "spectral bound is not negative (A == 0?)");
+    alpha = a;
   }
   const double c = alpha / 2.0, gamma = -alpha / 4.0;
   if (gamma * dt > kNoAllocRhoMax)

@@ -10,6 +10,9 @@
 // direction; the host reads scal[3] only every few iterations to test
 // convergence.  A zero denominator gives a zero step (a converged residual
 // stays converged instead of turning into NaN).
+#include <cstring>
+#include <mutex>
+
 #include "ad_internal.h"
 
 namespace ad {
@@ -92,32 +95,58 @@ __global__ void pen_direction_k(long long n, const double* scal, const double* _
 }
 
 // -lambda_max(D) per cell, block minimum (the caller reduces with min)
-__global__ void neg_lambda_max_k(long long n, const double* __restrict__ Dxx,
-                                 const double* __restrict__ Dxy, const double* __restrict__ Dyy,
-                                 double* __restrict__ partials) {
+// Order-preserving map of doubles onto unsigned 64-bit integers (IEEE 754
+// bit patterns: flip all bits of negatives, the sign bit of the rest), so
+// that an integer atomicMax gives the largest double.
+__device__ __forceinline__ unsigned long long order_key(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// max over cells of lambda_max(D) = (Dxx + Dyy)/2 + sqrt(((Dxx - Dyy)/2)^2 + Dxy^2),
+// folded into one device word by atomicMax on its order key (no scratch).
+__device__ unsigned long long g_lambda_max_key;
+
+__global__ void lambda_max_k(long long n, const double* __restrict__ Dxx,
+                             const double* __restrict__ Dxy, const double* __restrict__ Dyy) {
   __shared__ double sm[kThreads];
-  double mn = 1e308;
+  double mx = -1e308;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x) {
     const double a = Dxx[idx], b = Dxy[idx], d = Dyy[idx];
     const double h = 0.5 * (a - d);
-    mn = fmin(mn, -(0.5 * (a + d) + sqrt(h * h + b * b)));
+    mx = fmax(mx, 0.5 * (a + d) + sqrt(h * h + b * b));
   }
-  sm[threadIdx.x] = mn;
+  sm[threadIdx.x] = mx;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sm[threadIdx.x] = fmin(sm[threadIdx.x], sm[threadIdx.x + s]);
+    if (threadIdx.x < s) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) partials[blockIdx.x] = sm[0];
+  if (threadIdx.x == 0) atomicMax(&g_lambda_max_key, order_key(sm[0]));
 }
 
 }  // namespace
 
-void neg_lambda_max_partials(long long n, const double* Dxx, const double* Dxy, const double* Dyy,
-                             double* partials, int nblocks, cudaStream_t s) {
+int lambda_max_reduce(long long n, const double* Dxx, const double* Dxy, const double* Dyy,
+                      int nblocks, cudaStream_t s, double* out) {
+  // one word of device state shared by every call: host threads are serialised
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  const unsigned long long lowest = 0ull;           // below the key of every double
+  if (cudaMemcpyToSymbolAsync(g_lambda_max_key, &lowest, sizeof(lowest), 0,
+                              cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return 1;
   ++launch_counter();
-  neg_lambda_max_k<<<nblocks, kThreads, 0, s>>>(n, Dxx, Dxy, Dyy, partials);
+  lambda_max_k<<<nblocks, kThreads, 0, s>>>(n, Dxx, Dxy, Dyy);
+  unsigned long long key = 0ull;
+  if (cudaMemcpyFromSymbolAsync(&key, g_lambda_max_key, sizeof(key), 0, cudaMemcpyDeviceToHost,
+                                s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return 1;
+  const unsigned long long b = (key >> 63) ? (key & 0x7fffffffffffffffull) : ~key;
+  std::memcpy(out, &b, sizeof(double));
+  return 0;
 }
 
 void penalty_cg_iteration(const GridDev& g, double dx, double dy, double c, double* x, double* r,

@@ -1,4 +1,4 @@
-"""Learned spectral bound for the batched form.
+"""Learned spectral bound for the batched form: the driver around the library.
 
 Section 2 of the paper bounds the spectrum with Gershgorin discs before every
 Leja series.  Here a small network (``MLP``, kernels in csrc/mlp.cu) predicts
@@ -7,30 +7,31 @@ spectra the method itself computes (power iteration on generated fields).
 Inside a batch the predicted bound replaces the power-iteration pass; a slice
 whose series does not converge falls back to power iteration.
 
-Targets are dimensionless so that a model trained on small generated grids
-serves large slices:  t0 = log(|alpha| dx^2 / D_par),  t1 = log(iterations).
-
-Every numerical step runs in the library's kernels; this module only drives
-them (field generation for training uses the seeded input generators).
+Every numerical step runs in the library: the features (recorded by
+ad_create_operator), the training labels (ad_bound_training_sample), training
+(ad_mlp_train), inference and the bound it implies (ad_learned_bounds).  This
+module only generates the seeded training fields (workloads) and sequences
+the calls.
 """
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass
-from typing import List, Optional, Sequence
+from typing import Sequence
 
 import numpy as np
 
-from . import (BC_DIRICHLET0, BC_PERIODIC, BOUND_POWER, FP64, MLP, NotConverged,
-               batch_midpoint_step, create_operator, expquad_step, field_features, leja_phi1,
-               set_spectral_bound, spectral_bound)
+from . import (BC_DIRICHLET0, BC_PERIODIC, BOUND_POWER, FP64, MLP, batch_midpoint_step,
+               bound_training_sample, create_operator, expquad_step, learned_bounds,
+               spectral_bound)
+
+# training-field sides and their weights: every side class contributes about
+# the same number of cells, so large grids are rare but present
+TRAIN_SIDES = (64, 128, 256, 512, 1024, 2048)
 
 
-@dataclass
-class FieldSample:
-    features: np.ndarray      # 21 inputs
-    targets: np.ndarray       # (t0, t1)
-    alpha: float              # power-iteration bound used as the label
+def draw_side(rng: np.random.Generator, sides: Sequence[int] = TRAIN_SIDES) -> int:
+    w = 1.0 / np.asarray(sides, dtype=np.float64)
+    return int(rng.choice(np.asarray(sides), p=w / w.sum()))
 
 
 def random_field(rng: np.random.Generator, side: int):
@@ -59,40 +60,46 @@ def random_field(rng: np.random.Generator, side: int):
     return g, Dxx, Dxy, Dyy, ax, ay, dt
 
 
-def label_field(g, Dxx, Dxy, Dyy, ax, ay, dt, device, seed=0, power_iters=60,
-                tol=1e-6) -> FieldSample:
-    """Features (GPU kernel), the power-iteration bound and the Leja iteration
-    count of phi_1(dt A) v at ``tol`` with alpha = 1.1 x the estimate."""
+def field_job(seed: int, k: int, sides: Sequence[int] = TRAIN_SIDES):
+    """Field k of the training set of ``seed`` (independent of every other k)."""
+    rng = np.random.default_rng([seed, k])
+    return random_field(rng, draw_side(rng, sides))
+
+
+def label_field(g, Dxx, Dxy, Dyy, ax, ay, dt, device, seed=0, power_iters=60, tol=1e-6):
+    """Inputs and targets of one field (ad_bound_training_sample on an FP64
+    operator of the field): returns (x[21], t[2], power-iteration |alpha|)."""
     import torch
     T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(), device=device)
-    dxx, dxy, dyy = T(Dxx), T(Dxy), T(Dyy)
-    amax = math.hypot(ax, ay)
-    f = field_features(g.nx, g.ny, g.bc, dxx, dxy, dyy, amax, dt)
-    op = create_operator(g.nx, g.ny, g.bc, dxx, dxy, dyy, ax, ay, FP64)
-    a_est = -spectral_bound(op, BOUND_POWER, seed=seed + 1, power_iters=power_iters, safety=1.0)
-    set_spectral_bound(op, -1.1 * a_est)
-    v = torch.as_tensor(np.random.default_rng(seed).standard_normal(g.n), device=device)
-    out = torch.empty_like(v)
+    op = create_operator(g.nx, g.ny, g.bc, T(Dxx), T(Dxy), T(Dyy), ax, ay, FP64)
     try:
-        st = leja_phi1(op, v, out, dt, tol=tol)
-        iters = st["iters"]
-    except NotConverged as e:
-        iters = e.stats["iters"] if e.stats else 500
-    op.close()
-    dx = min(g.dx, g.dy)
-    t0 = math.log(a_est * dx * dx / math.exp(f[0]))
-    return FieldSample(f, np.array([t0, math.log(max(iters, 1))], dtype=np.float32), -a_est)
+        return bound_training_sample(op, dt, seed, power_iters=power_iters, safety=1.1, tol=tol)
+    finally:
+        op.close()
 
 
-def build_dataset(n: int, seed: int, device, sides: Sequence[int] = (32, 48, 64, 96)):
-    rng = np.random.default_rng(seed)
-    samples = []
-    for k in range(n):
-        side = int(rng.choice(np.asarray(sides)))
-        samples.append(label_field(*random_field(rng, side), device=device, seed=seed * 100003 + k))
-    X = np.stack([s.features for s in samples]).astype(np.float32)
-    Y = np.stack([s.targets for s in samples]).astype(np.float32)
-    return X, Y, samples
+def build_dataset(n: int, seed: int, device, sides: Sequence[int] = TRAIN_SIDES,
+                  workers: int = 0):
+    """n labelled fields.  With workers > 1 the host-side field generation
+    runs in a spawned process pool beside the GPU labelling."""
+    xs, ts = [], []
+    if workers > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            futs = [ex.submit(field_job, seed, k, tuple(sides)) for k in range(n)]
+            for k, f in enumerate(futs):
+                x, t, _ = label_field(*f.result(), device=device, seed=seed * 100003 + k)
+                futs[k] = None
+                xs.append(x)
+                ts.append(t)
+    else:
+        for k in range(n):
+            x, t, _ = label_field(*field_job(seed, k, sides), device=device,
+                                  seed=seed * 100003 + k)
+            xs.append(x)
+            ts.append(t)
+    return np.stack(xs).astype(np.float32), np.stack(ts).astype(np.float32)
 
 
 def train_bound_model(X, Y, device, epochs=3000, lr=3e-3, seed=0, hidden=64) -> MLP:
@@ -103,16 +110,10 @@ def train_bound_model(X, Y, device, epochs=3000, lr=3e-3, seed=0, hidden=64) -> 
     return m
 
 
-def predict_bounds(m: MLP, feats, dxs: Sequence[float], device, margin=1.1, bf16=True):
-    """alpha_s = -margin * exp(t0) D_par / dx^2 and the predicted iterations.
-    ``feats``: (S, 21) float32 array or device tensor."""
-    import torch
-    X = torch.as_tensor(feats, device=device, dtype=torch.float32).contiguous()
-    pred = m.predict(X, bf16=bf16).double().cpu().numpy()
-    dpar = np.exp(X[:, 0].double().cpu().numpy())
-    dx = np.asarray(dxs, dtype=np.float64)
-    alpha = -margin * np.exp(pred[:, 0]) * dpar / (dx * dx)
-    return alpha, np.exp(pred[:, 1])
+def predict_bounds(model: MLP, ops, dt, margin=1.1, bf16=True):
+    """Every operator's bound from the model (ad_learned_bounds, which also
+    sets it); returns (alphas, predicted iterations)."""
+    return learned_bounds(model, ops, dt, margin=margin, bf16=bf16)
 
 
 def batched_step_with_fallback(batch, ops, us, t, dt, sources, tol, power_iters=40):

@@ -9,7 +9,7 @@ iteration totals must be equal and the results agree to the FP64 bar.
 import numpy as np
 import pytest
 
-from gpu_util import DEV, ad, dev64, devT, gpu_operator, gpu_source, need_gpu, oracle_operator, rel, torch
+from gpu_util import DEV, ad, dev64, devT, gpu_operator, gpu_source, need_gpu, oracle_operator, rel, torch, assert_close
 from oracle import integrators, leja
 from workloads import small_problem
 from workloads.fields import BC_DIRICHLET0, BC_PERIODIC
@@ -41,7 +41,7 @@ def test_adaptive_phi1_matches_oracle(case):
     st = ad().leja_phi1(op, dev64(v), out, p.dt, tol=1e-10)
     assert (st["substeps"], st["rejected"], st["iters"]) == (ost.substeps, ost.rejected, ost.iters)
     assert st["matvecs"] == ost.matvecs
-    assert rel(out.cpu().numpy(), ref) <= 1e-10
+    assert_close(out.cpu().numpy(), ref, 1e-10)
 
 
 def test_adaptive_growth_matches_oracle():
@@ -59,7 +59,7 @@ def test_adaptive_growth_matches_oracle():
     out = torch.empty(p.grid.n, dtype=torch.float64, device=DEV)
     st = ad().leja_phi1(op, dev64(v), out, p.dt, tol=1e-10)
     assert (st["substeps"], st["rejected"], st["iters"]) == (ost.substeps, ost.rejected, ost.iters)
-    assert rel(out.cpu().numpy(), ref) <= 1e-10
+    assert_close(out.cpu().numpy(), ref, 1e-10)
 
 
 @pytest.mark.parametrize("s,c", [(1, (0.5,)), (2, (1 / 3, 2 / 3))])
@@ -75,7 +75,7 @@ def test_adaptive_step_matches_oracle(s, c):
     u = dev64(p.u0)
     st = ad().expquad_step(op, u, 0.1, p.dt, s, c, gpu_source(p), tol=1e-10)
     assert (st["substeps"], st["rejected"], st["iters"]) == (ost.substeps, ost.rejected, ost.iters)
-    assert rel(u.cpu().numpy(), ref) <= 1e-10
+    assert_close(u.cpu().numpy(), ref, 1e-10)
 
 
 def test_adaptive_fp32_step_matches_oracle():
@@ -91,7 +91,7 @@ def test_adaptive_fp32_step_matches_oracle():
     u = devT(p.u0, 1)
     st = ad().expquad_step(op, u, 0.0, p.dt, 1, (0.5,), gpu_source(p, 1), tol=1e-6)
     assert st["converged"] == 1 and st["rejected"] >= 1
-    assert rel(u.cpu().numpy(), ref) <= 1e-5
+    assert_close(u.cpu().numpy(), ref, 1e-5)
 
 
 def test_adaptive_gives_up_and_leaves_u_unchanged():
@@ -129,4 +129,4 @@ def test_fixed_rule_unchanged_by_default():
     out = torch.empty(p.grid.n, dtype=torch.float64, device=DEV)
     st = ad().leja_phi1(op, dev64(v), out, p.dt, tol=1e-10)
     assert st["rejected"] == 0 and st["substeps"] == ost.substeps > 1
-    assert rel(out.cpu().numpy(), ref) <= 1e-10
+    assert_close(out.cpu().numpy(), ref, 1e-10)

@@ -12,7 +12,7 @@ applies it.
 import numpy as np
 import pytest
 
-from gpu_util import devT, gpu_operator, gpu_source, need_gpu, oracle_operator, rel, ad
+from gpu_util import devT, gpu_operator, gpu_source, need_gpu, oracle_operator, rel, ad, assert_close
 from oracle import integrators
 from workloads import small_problem
 from workloads.fields import BC_DIRICHLET0, BC_PERIODIC
@@ -76,7 +76,7 @@ def test_async_step_matches_oracle():
     ua, _, tot, _ = _run(p, 0, 2, (1 / 3, 2 / 3), 1, True, 1e-10,
                          setup=lambda op: ad().set_spectral_bound(op, alpha))
     assert tot["converged"] and tot["iters"] >= 2
-    assert rel(ua.cpu().numpy(), ref) <= 1e-9
+    assert_close(ua.cpu().numpy(), ref, 1e-9)
 
 
 def test_fallbacks_add_to_the_totals():

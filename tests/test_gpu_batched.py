@@ -12,7 +12,7 @@ import os
 import numpy as np
 import pytest
 
-from gpu_util import DEV, ad, devT, dev64, need_gpu, rel, torch
+from gpu_util import DEV, ad, devT, dev64, need_gpu, rel, torch, assert_close
 from oracle import integrators
 from oracle import operator as oop
 from oracle import spectral
@@ -68,7 +68,7 @@ def test_batched_forced_matches_oracle(force):
                                             lambda t, src=src: src.ravel(), alpha,
                                             force_iters=force)
         assert st[k]["iters"] == force
-        assert rel(us[k].cpu().numpy(), ref) <= 1e-5, (k, SIZES[k])
+        assert_close(us[k].cpu().numpy(), ref, 1e-5, str((k, SIZES[k])))
 
 
 def test_batched_adaptive_matches_oracle_per_slice():
@@ -86,14 +86,14 @@ def test_batched_adaptive_matches_oracle_per_slice():
         _, ost6 = integrators.expquad_step(A, u0.ravel(), 0.0, dt, 1, (0.5,),
                                            lambda t, src=src: src.ravel(), alpha, tol=1e-6)
         assert abs(st[k]["iters"] - ost6.iters) <= 2, (k, st[k]["iters"], ost6.iters)
-        assert rel(us[k].cpu().numpy(), ref) <= 1e-5, (k, SIZES[k])
+        assert_close(us[k].cpu().numpy(), ref, 1e-5, str((k, SIZES[k])))
     # a second step from the new state still matches (state reuse, cached scalars)
     u1 = [u.clone() for u in us]
     ad().batch_midpoint_step(batch, u1, dt, dt, srcs, tol=1e-6)
     for k, (g, A, alpha, src, u0) in enumerate(slices):
         ref, _ = integrators.expquad_step(A, us[k].cpu().numpy().astype(np.float64), dt, dt, 1,
                                           (0.5,), lambda t, src=src: src.ravel(), alpha, tol=1e-10)
-        assert rel(u1[k].cpu().numpy(), ref) <= 1e-5
+        assert_close(u1[k].cpu().numpy(), ref, 1e-5)
 
 
 def test_autotune_cache_round_trip(tmp_path, monkeypatch):
@@ -136,7 +136,7 @@ def test_unconverged_slice_keeps_its_state():
             continue
         ref, _ = integrators.expquad_step(A, u0.ravel(), 0.0, dt, 1, (0.5,),
                                           lambda t, src=src: src.ravel(), alpha, tol=1e-10)
-        assert rel(us[k].cpu().numpy(), ref) <= 1e-5, (k, SIZES[k])
+        assert_close(us[k].cpu().numpy(), ref, 1e-5, str((k, SIZES[k])))
     # the same call without raising gives the flag per slice
     us = states()
     st = ad().batch_midpoint_step(batch, us, 0.0, dt, srcs, tol=1e-6, raise_not_converged=False)
@@ -158,7 +158,7 @@ def test_ring_batch_forced_matches_oracle(force):
                                           lambda t, src=src: src.ravel(), alpha,
                                           force_iters=force)
         assert st[k]["iters"] == force
-        assert rel(us[k].cpu().numpy(), ref) <= 1e-5, (k, SIZES_RING[k])
+        assert_close(us[k].cpu().numpy(), ref, 1e-5, str((k, SIZES_RING[k])))
 
 
 def test_ring_batch_adaptive_and_tuned(tmp_path, monkeypatch):
@@ -177,7 +177,7 @@ def test_ring_batch_adaptive_and_tuned(tmp_path, monkeypatch):
         _, ost6 = integrators.expquad_step(A, u0.ravel(), 0.0, dt, 1, (0.5,),
                                            lambda t, src=src: src.ravel(), alpha, tol=1e-6)
         assert abs(st[k]["iters"] - ost6.iters) <= 2, (k, st[k]["iters"], ost6.iters)
-        assert rel(us[k].cpu().numpy(), ref) <= 1e-5, (k, SIZES_RING[k])
+        assert_close(us[k].cpu().numpy(), ref, 1e-5, str((k, SIZES_RING[k])))
 
 
 # every nx % 4 == 0 and ny >= 2: the two-iteration kernel (batch_pair_k)
@@ -199,7 +199,7 @@ def test_pair_batch_forced_matches_oracle(force):
                                           lambda t, src=src: src.ravel(), alpha,
                                           force_iters=force)
         assert st[k]["iters"] == force
-        assert rel(us[k].cpu().numpy(), ref) <= 1e-5, (k, SIZES_PAIR[k])
+        assert_close(us[k].cpu().numpy(), ref, 1e-5, str((k, SIZES_PAIR[k])))
 
 
 def test_pair_batch_adaptive_and_unconverged_slice():
@@ -215,7 +215,7 @@ def test_pair_batch_adaptive_and_unconverged_slice():
         _, ost6 = integrators.expquad_step(A, u0.ravel(), 0.0, dt, 1, (0.5,),
                                            lambda t, src=src: src.ravel(), alpha, tol=1e-6)
         assert abs(st[k]["iters"] - ost6.iters) <= 2, (k, st[k]["iters"], ost6.iters)
-        assert rel(us[k].cpu().numpy(), ref) <= 1e-5, (k, SIZES_PAIR[k])
+        assert_close(us[k].cpu().numpy(), ref, 1e-5, str((k, SIZES_PAIR[k])))
     bad = 1
     us = [devT(s[4], 1) for s in slices]
     us[bad][5] = float("nan")

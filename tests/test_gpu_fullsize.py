@@ -12,7 +12,9 @@ the FP32-storage form.
 import numpy as np
 import pytest
 
-from gpu_util import DEV, ad, need_gpu, rel, torch
+from gpu_util import DEV, ad, assert_close, need_gpu, oracle_at_gpu_count, rel, torch
+from oracle import integrators, spectral
+from oracle import operator as oop
 from window_oracle import alpha_from_fields, oracle_cell, sample_cells
 from workloads import config2, config3_slices, slice_problem
 
@@ -54,7 +56,7 @@ def test_config2_full_size_forced_step_sampled(c2, prec, k):
     got = np.array([out[j, i] for i, j in pts])
     ref = np.array([oracle_cell(p, i, j, k + 2, alpha, k, gsrc) for i, j in pts])
     bar = 1e-5 if prec == "fp32" else 1e-11
-    assert rel(got, ref) <= bar, (rel(got, ref), bar)
+    assert_close(got, ref, bar, str((rel(got, ref), bar)))
 
 
 def test_config3_full_batch_forced_step_sampled():
@@ -99,4 +101,64 @@ def test_config3_full_batch_forced_step_sampled():
         got = np.array([out[j, i] for i, j in pts])
         ref = np.array([oracle_cell(p, i, j, k + 2, alphas[s], k, p.source.g[0])
                         for i, j in pts])
-        assert rel(got, ref) <= 1e-5, (s, g.nx, rel(got, ref))
+        assert_close(got, ref, 1e-5, str((s, g.nx, rel(got, ref))))
+
+
+@pytest.fixture(scope="module")
+def c2_1024():
+    p = config2(nx=1024, tol=1e-10)
+    A = oop.assemble(p.grid, p.Dxx, p.Dxy, p.Dyy, p.ax_arr(), p.ay_arr())
+    return p, A, spectral.gershgorin(A)
+
+
+def test_config2_fp64_adaptive_steps_full_vector(c2_1024):
+    """The stream-function workload at 1024^2 (1 M cells: the large-grid
+    graph loop of per-iteration kernels that the 4096^2 FP64 path runs), three
+    adaptive exponential-midpoint steps at tol 1e-10, every cell against the
+    oracle: equal iteration counts per step, 1e-11 relative L2 and
+    element-wise per step (each step starts both sides from the same state)."""
+    need_gpu()
+    p, A, alpha = c2_1024
+    g = p.grid
+    D = [torch.as_tensor(np.ascontiguousarray(f).ravel(), device=DEV) for f in (p.Dxx, p.Dxy, p.Dyy)]
+    op = ad().create_operator(g.nx, g.ny, g.bc, D[0], D[1], D[2], 0.0, 0.0, ad().FP64)
+    ad().set_spectral_bound(op, alpha)
+    src = ad().Source([_dev(p.source.g[0], ad().FP64)], None)
+    S = lambda t: p.source_at(t).ravel()
+    u_ref = p.u0.ravel().copy()
+    for k in range(3):
+        t = k * p.dt
+        u = _dev(u_ref, ad().FP64)
+        st = ad().expquad_step(op, u, t, p.dt, 1, (0.5,), src, tol=1e-10)
+        ref, ost = integrators.expquad_step(A, u_ref, t, p.dt, 1, (0.5,), S, alpha, tol=1e-10)
+        assert st["substeps"] == ost.substeps == 1
+
+        def forced(m, u_ref=u_ref, t=t):
+            r, o = integrators.expquad_step(A, u_ref, t, p.dt, 1, (0.5,), S, alpha, force_iters=m)
+            return r, o.err_est
+        alt = oracle_at_gpu_count(st["iters"], ost.iters, forced, 1e-10)
+        assert_close(u.cpu().numpy(), ref if alt is None else alt, 1e-11, f"step {k}")
+        u_ref = ref
+    op.close()
+
+
+def test_config2_fp32_form_against_oracle_full_vector(c2_1024):
+    """The FP32-storage form of the same workload (tol 1e-6, two-iteration
+    kernel) against the FP64 oracle at tol 1e-10, every cell, three steps from
+    u0 on both sides: <= 1e-5 relative L2 and element-wise."""
+    need_gpu()
+    p, A, alpha = c2_1024
+    g = p.grid
+    D = [torch.as_tensor(np.ascontiguousarray(f).ravel(), device=DEV) for f in (p.Dxx, p.Dxy, p.Dyy)]
+    op = ad().create_operator(g.nx, g.ny, g.bc, D[0], D[1], D[2], 0.0, 0.0, ad().FP32_STORAGE)
+    ad().set_spectral_bound(op, alpha)
+    src = ad().Source([_dev(p.source.g[0], ad().FP32_STORAGE)], None)
+    S = lambda t: p.source_at(t).ravel()
+    u = _dev(p.u0, ad().FP32_STORAGE)
+    ref = p.u0.ravel().copy()
+    for k in range(3):
+        st = ad().expquad_step(op, u, k * p.dt, p.dt, 1, (0.5,), src, tol=1e-6)
+        assert st["converged"] == 1
+        ref, _ = integrators.expquad_step(A, ref, k * p.dt, p.dt, 1, (0.5,), S, alpha, tol=1e-10)
+        assert_close(u.double().cpu().numpy(), ref, 1e-5, f"step {k}")
+    op.close()

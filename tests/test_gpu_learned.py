@@ -6,7 +6,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_util import DEV, ad, dev64, devT, need_gpu, rel, torch
+from gpu_util import DEV, ad, dev64, devT, need_gpu, rel, torch, assert_close
 from oracle import integrators, mlp as omlp
 from oracle import operator as oop
 from oracle import spectral
@@ -68,18 +68,10 @@ def test_field_features_uniform_and_circular():
     assert hist.max() < 0.15                  # circular directions spread over all bins
 
 
-def test_learned_bound_in_batch_with_fallback():
-    need_gpu()
-    from paper_2307_12276_gb300 import learned
-    X, Y, samples = learned.build_dataset(240, seed=11, device=DEV, sides=(32, 48, 64))
-    model = learned.train_bound_model(X[:200], Y[:200], DEV, epochs=1500, lr=3e-3)
-    # relative error of the predicted dimensionless bound on held-out fields
-    pred = model.predict(torch.as_tensor(X[200:], device=DEV)).cpu().numpy()
-    err = np.abs(np.exp(pred[:, 0] - Y[200:, 0]) - 1.0)
-    assert np.median(err) < 0.15
-    # a small batch: learned bound, fallback where needed, parity with the oracle
-    slices, ops, us, srcs = [], [], [], []
-    feats, dxs = [], []
+def _small_batch(model, margin=1.2):
+    """Four FP32 slices of uneven size (circular field, constant advection)
+    and the shared step 100 / max gamma (Gershgorin)."""
+    slices, ops, us, srcs, fields = [], [], [], [], []
     for k, side in enumerate((40, 64, 96, 72)):
         g = Grid(side, side, BC_DIRICHLET0)
         Xc, Yc = cell_centres(g)
@@ -95,21 +87,99 @@ def test_learned_bound_in_batch_with_fallback():
         ops.append(op)
         us.append(devT(u0, 1))
         srcs.append(ad().Source([devT(src, 1)], None))
-        feats.append(ad().field_features(side, side, g.bc, dev64(Dxx), dev64(Dxy), dev64(Dyy), 0.05,
-                                         1.0))
-        dxs.append(g.dx)
+        fields.append((Dxx, Dxy, Dyy))
     gam = max(-spectral.gershgorin(s[1]) / 4 for s in slices)
-    dt = 100.0 / gam
-    feats = np.stack(feats)
-    feats[:, 4] = math.log(dt)
-    alpha, _ = learned.predict_bounds(model, feats, dxs, DEV, margin=1.2)
+    return slices, ops, us, srcs, fields, 100.0 / gam
+
+
+@pytest.fixture(scope="module")
+def bound_model():
+    need_gpu()
+    from paper_2307_12276_gb300 import learned
+    X, Y = learned.build_dataset(240, seed=11, device=DEV, sides=(32, 48, 64))
+    model = learned.train_bound_model(X[:200], Y[:200], DEV, epochs=1500, lr=3e-3)
+    return model, X, Y
+
+
+def test_learned_bound_heldout(bound_model):
+    """Relative error of the predicted dimensionless bound on held-out fields."""
+    model, X, Y = bound_model
+    pred = model.predict(torch.as_tensor(X[200:], device=DEV)).cpu().numpy()
+    err = np.abs(np.exp(pred[:, 0] - Y[200:, 0]) - 1.0)
+    assert np.median(err) < 0.15
+
+
+def test_training_sample_against_oracle():
+    """ad_bound_training_sample: its power estimate agrees with the oracle's
+    power iteration from the same SplitMix64 start, its features with
+    ad_field_features, and its targets follow from them."""
+    need_gpu()
+    from paper_2307_12276_gb300 import learned
+    g, Dxx, Dxy, Dyy, ax, ay, dt = learned.field_job(5, 3, sides=(48,))
+    op = ad().create_operator(g.nx, g.ny, g.bc, dev64(Dxx), dev64(Dxy), dev64(Dyy), ax, ay,
+                              ad().FP64)
+    x, t, est = ad().bound_training_sample(op, dt, seed=17, power_iters=60, safety=1.1, tol=1e-6)
+    A = oop.assemble(g, Dxx, Dxy, Dyy, ax, ay)
+    x0 = spectral.splitmix64_uniform(g.n, 18)
+    a_ref, _ = spectral.power_iteration(A, x0, iters=60, safety=1.0)
+    assert abs(est - (-a_ref)) <= 1e-10 * abs(a_ref)
+    f = ad().field_features(g.nx, g.ny, g.bc, dev64(Dxx), dev64(Dxy), dev64(Dyy),
+                            math.hypot(ax, ay), dt)
+    assert np.allclose(x, f, rtol=1e-5, atol=1e-6)
+    dx = min(g.dx, g.dy)
+    assert abs(t[0] - math.log(est * dx * dx / math.exp(float(x[0])))) <= 1e-5
+    assert ad().get_spectral_bound(op) == pytest.approx(-1.1 * est, rel=1e-15)
+    op.close()
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_learned_bounds_through_capi(bound_model, bf16):
+    """ad_learned_bounds against a NumPy restatement of its back-transform
+    alpha = -margin exp(t0) D_par / dx^2 on the model's own predictions; the
+    operators keep the bound; ad_spectral_bound(op, LEARNED) gives the same."""
+    model = bound_model[0]
+    slices, ops, us, srcs, fields, dt = _small_batch(model)
+    margin = 1.2
+    alpha, iters = ad().learned_bounds(model, ops, dt, margin=margin, bf16=bf16)
+    feats = np.stack([ad().field_features(g.nx, g.ny, g.bc, dev64(D[0]), dev64(D[1]), dev64(D[2]),
+                                          0.05, dt) for (g, _, _, _), D in zip(slices, fields)])
+    pred = model.predict(torch.as_tensor(feats, device=DEV), bf16=bf16).double().cpu().numpy()
+    dx = np.array([min(s[0].dx, s[0].dy) for s in slices])
+    ref = -margin * np.exp(pred[:, 0]) * np.exp(feats[:, 0].astype(np.float64)) / dx ** 2
+    tol = 2e-2 if bf16 else 1e-5
+    assert np.allclose(alpha, ref, rtol=tol), (alpha, ref)
+    assert np.allclose(iters, np.exp(pred[:, 1]), rtol=tol)
     for op, a in zip(ops, alpha):
-        ad().set_spectral_bound(op, float(a))
+        assert ad().get_spectral_bound(op) == a
+    # ad_spectral_bound's learned method runs the BF16 inference
+    a16, _ = ad().learned_bounds(model, [ops[1]], dt, margin=margin, bf16=True)
+    ad().set_bound_model(ops[1], model, margin=margin, dt=dt)
+    a1 = ad().spectral_bound(ops[1], ad().BOUND_LEARNED)
+    assert a1 == pytest.approx(a16[0], rel=1e-12)
+    ad().set_bound_model(ops[1], None)
+    with pytest.raises(ad().AdError):
+        ad().spectral_bound(ops[1], ad().BOUND_LEARNED)
+
+
+@pytest.mark.parametrize("force_bad", [False, True])
+def test_learned_bound_in_batch_with_fallback(bound_model, force_bad):
+    """The learned bounds drive a batched step; with force_bad one slice's
+    bound is cut to 0.3 x the prediction, so its series cannot converge (the
+    spectrum reaches far beyond the Leja interval): the fallback must list
+    exactly that slice and still leave it matching the oracle."""
+    from paper_2307_12276_gb300 import learned
+    model = bound_model[0]
+    slices, ops, us, srcs, fields, dt = _small_batch(model)
+    alpha, _ = learned.predict_bounds(model, ops, dt, margin=1.2)
+    bad = 2
+    if force_bad:
+        ad().set_spectral_bound(ops[bad], 0.3 * alpha[bad])
     batch = ad().create_batch(ops, autotune=False)
     st, fallback = learned.batched_step_with_fallback(batch, ops, us, 0.0, dt, srcs, tol=1e-6)
+    assert fallback == ([bad] if force_bad else [])
     assert all(s["converged"] for s in st)
     for k, (g, A, src, u0) in enumerate(slices):
         ref, _ = integrators.expquad_step(A, u0.ravel(), 0.0, dt, 1, (0.5,),
                                           lambda t, src=src: src.ravel(),
                                           spectral.gershgorin(A), tol=1e-10)
-        assert rel(us[k].cpu().numpy(), ref) <= 1e-5, (k, fallback)
+        assert_close(us[k].cpu().numpy(), ref, 1e-5, str((k, fallback)))

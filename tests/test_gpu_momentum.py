@@ -7,7 +7,7 @@ and without advection, and a 128^2 x 16 case (262k unknowns).
 import numpy as np
 import pytest
 
-from gpu_util import DEV, ad, dev64, need_gpu, rel, torch
+from gpu_util import DEV, ad, dev64, need_gpu, rel, torch, assert_close
 from oracle import integrators, leja, momentum, spectral
 from workloads.fields import BC_DIRICHLET0, BC_PERIODIC
 from workloads.momentum import momentum_problem
@@ -42,7 +42,7 @@ def test_apply_and_gershgorin_match_oracle(case):
     u = np.random.default_rng(4).standard_normal(A.shape[0])
     out = torch.empty(A.shape[0], dtype=torch.float64, device=DEV)
     ad().momentum_apply(op, dev64(u), out)
-    assert rel(out.cpu().numpy(), A @ u) <= 1e-13
+    assert_close(out.cpu().numpy(), A @ u, 1e-13)
     alpha = spectral.gershgorin(A)
     assert abs(ad().momentum_spectral_bound(op) - alpha) <= 1e-13 * abs(alpha)
 
@@ -57,11 +57,11 @@ def test_phi1_forced_and_adaptive_match_oracle(case):
     ref, _ = leja.leja_phi1(A, v, mp.dt, alpha, force_iters=25)
     st = ad().momentum_leja_phi1(op, dev64(v), out, mp.dt, force_iters=25)
     assert st["iters"] == 25
-    assert rel(out.cpu().numpy(), ref) <= 1e-12
+    assert_close(out.cpu().numpy(), ref, 1e-12)
     ref, ost = leja.leja_phi1(A, v, mp.dt, alpha, tol=1e-10)
     st = ad().momentum_leja_phi1(op, dev64(v), out, mp.dt, tol=1e-10)
     assert st["iters"] == ost.iters and st["converged"] == 1
-    assert rel(out.cpu().numpy(), ref) <= 1e-10
+    assert_close(out.cpu().numpy(), ref, 1e-10)
 
 
 def test_phi1_with_substeps_matches_oracle():
@@ -74,7 +74,7 @@ def test_phi1_with_substeps_matches_oracle():
     out = torch.empty(A.shape[0], dtype=torch.float64, device=DEV)
     st = ad().momentum_leja_phi1(op, dev64(v), out, mp.dt, tol=1e-10)
     assert st["substeps"] == ost.substeps > 1 and st["iters"] == ost.iters
-    assert rel(out.cpu().numpy(), ref) <= 1e-10
+    assert_close(out.cpu().numpy(), ref, 1e-10)
 
 
 @pytest.mark.parametrize("case", [CASES[0], CASES[2], (128, 128, 16, BC_DIRICHLET0, "circular",
@@ -93,7 +93,7 @@ def test_steps_match_oracle(case):
                                               alpha, tol=1e-10)
         st = ad().momentum_step(op, u, mp.dt, Sd, tol=1e-10)
         assert st["iters"] == ost.iters and st["matvecs"] == ost.matvecs
-    assert rel(u.cpu().numpy(), u_ref) <= 1e-10
+    assert_close(u.cpu().numpy(), u_ref, 1e-10)
 
 
 def test_invalid_arguments_raise():

@@ -8,7 +8,7 @@ problem set-up itself."""
 import numpy as np
 import pytest
 
-from gpu_util import ad, dev64, need_gpu, oracle_operator, rel, torch
+from gpu_util import ad, dev64, need_gpu, oracle_operator, rel, torch, assert_close
 from oracle import integrators
 from workloads.configs import paper_case
 
@@ -74,4 +74,4 @@ def test_case_II_step_matches_the_oracle():
     ad().expquad_step(op, u, 0.0, dt, 1, (0.5,), src, tol=1e-10)
     S = lambda t: p.source_at(t).ravel()
     ref, _ = integrators.expquad_step(A, p.u0.ravel(), 0.0, dt, 1, (0.5,), S, alpha, tol=1e-10)
-    assert rel(u.cpu().numpy(), ref) <= 1e-9
+    assert_close(u.cpu().numpy(), ref, 1e-9)

@@ -3,7 +3,7 @@ against the oracle's exact sparse solve, through the C ABI."""
 import numpy as np
 import pytest
 
-from gpu_util import ad, dev64, gpu_operator, gpu_source, need_gpu, oracle_operator, rel
+from gpu_util import ad, dev64, gpu_operator, gpu_source, need_gpu, oracle_operator, rel, assert_close
 from oracle import penalised
 from workloads import small_problem
 from workloads.fields import BC_DIRICHLET0, BC_PERIODIC
@@ -37,7 +37,7 @@ def test_penalised_steps_match_oracle(case):
         u_ref = penalised.imex_step(A, L, u_ref, t, p.dt, S, beta)
         st = ad().penalised_step(op, u, t, p.dt, gpu_source(p), beta=beta, cg_tol=1e-13)
         assert st["converged"] == 1 and st["iters"] > 0
-    assert rel(u.cpu().numpy(), u_ref) <= 1e-10
+    assert_close(u.cpu().numpy(), u_ref, 1e-10)
 
 
 def test_beta_zero_is_explicit_euler_and_cg_cap():
@@ -49,7 +49,7 @@ def test_beta_zero_is_explicit_euler_and_cg_cap():
     u = dev64(u0)
     st = ad().penalised_step(op, u, 0.0, p.dt, gpu_source(p), beta=0.0)
     want = u0 + p.dt * (A @ u0 + p.source_at(0.0).ravel())
-    assert rel(u.cpu().numpy(), want) <= 1e-12 and st["iters"] <= 8
+    assert_close(u.cpu().numpy(), want, 1e-12 and st["iters"] <= 8)
     # a CG budget that cannot reach the tolerance: error, u unchanged
     u = dev64(u0)
     with pytest.raises(ad().NotConverged):

@@ -11,7 +11,7 @@ time-dependent TDS source, evaluated at t + dt/2 = 0.3 + dt/2.
 import numpy as np
 import pytest
 
-from gpu_util import ad, devT, gpu_operator, need_gpu, oracle_operator, rel
+from gpu_util import ad, devT, gpu_operator, need_gpu, oracle_operator, rel, assert_close
 from oracle import integrators
 from workloads import small_problem
 from workloads.fields import BC_DIRICHLET0, BC_PERIODIC, SeparableSource
@@ -55,7 +55,7 @@ def test_fp32_midpoint_source_terms(nx, ny, bc, terms):
     st = ad().expquad_step(op, u, T0, p.dt, 1, (0.5,), _gpu_source(p), tol=1e-6,
                            force_iters=FORCE)
     assert st["iters"] == FORCE * st["substeps"]
-    assert rel(u.double().cpu().numpy(), ref) <= 1e-5
+    assert_close(u.double().cpu().numpy(), ref, 1e-5)
 
 
 @pytest.mark.parametrize("counts", [(0, 1, 2, 1), (2, 3, 0, 1)])
@@ -81,4 +81,4 @@ def test_batch_midpoint_source_terms(counts):
     stats = ad().batch_midpoint_step(batch, us, T0, dt, srcs, tol=1e-6, force_iters=FORCE)
     assert all(s["iters"] == FORCE for s in stats)
     for p, alpha, u in zip(probs, alphas, us):
-        assert rel(u.double().cpu().numpy(), _oracle_step(p, alpha)) <= 1e-5
+        assert_close(u.double().cpu().numpy(), _oracle_step(p, alpha), 1e-5)
