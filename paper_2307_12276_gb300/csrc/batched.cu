@@ -1158,8 +1158,14 @@ int ad_batch_midpoint_step(ad_batch* b, void* const* u, double t, double dt,
   // the one-pass series start serves the ring and pair modes with at most two
   // source terms per slice
   int max_src = 0;
-  for (const BatchSlice& hs : b->hs) max_src = std::max(max_src, hs.nsrc);
-  const int start_mode = (b->ring && max_src <= 2) ? (max_src > 0 ? 2 : 1) : 0;
+  uintptr_t bits = 0;       // the ring pass reads u and the sources with 16-byte copies
+  for (const BatchSlice& hs : b->hs) {
+    max_src = std::max(max_src, hs.nsrc);
+    bits |= reinterpret_cast<uintptr_t>(hs.u);
+    for (int k = 0; k < hs.nsrc; ++k) bits |= reinterpret_cast<uintptr_t>(hs.src_g[k]);
+  }
+  const bool aligned16 = (bits & 15u) == 0;
+  const int start_mode = (b->ring && max_src <= 2 && aligned16) ? (max_src > 0 ? 2 : 1) : 0;
   if (!b->exec || b->graph_force != force || b->graph_tol != tol ||
       b->graph_start != start_mode) {
     const int r = build_batch_graph(b, force, tol, start_mode);

@@ -981,6 +981,11 @@ void series_finish_pair_update(const SeriesArgs& a, void* u, double b, cudaStrea
 bool series_start_f32(const SeriesArgs& a, const void* u, const Sources& S, double d0, int force,
                       int max_iters, double tol, cudaStream_t s) {
   if (a.prec != 1 || a.aug || a.f32k != 3 || S.n > 2) return false;
+  // the ring pass reads u and the source fields with 16-byte copies: a caller
+  // vector on a weaker alignment takes the apply path instead
+  uintptr_t bits = reinterpret_cast<uintptr_t>(u);
+  for (int k = 0; k < S.n; ++k) bits |= reinterpret_cast<uintptr_t>(S.g[k]);
+  if (bits & 15u) return false;
   SeriesArgs b = a;
   b.w2 = S.n > 0 ? S.g[0] : nullptr;
   b.w1 = S.n > 1 ? S.g[1] : nullptr;
