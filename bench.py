@@ -279,6 +279,7 @@ F64_ITER_SOURCES = ("stencil_kernels.cu", "stencil9.cuh", "series_finish.cuh", "
 F32_ITER_SOURCES = ("stencil_kernels.cu", "tile_f32.cuh", "tile_f32_vec.cuh", "tile_f32_ring.cuh",
                     "ad_internal.h")
 F32_PAIR_SOURCES = F32_ITER_SOURCES + ("tile_f32_pair.cuh",)
+F32_TMA_SOURCES = F32_PAIR_SOURCES + ("tile_f32_bulk.cuh", "tile_f32_pair_tma.cuh")
 MOM_SOURCES = ("momentum.cu", "series_finish.cuh", "tile_f32.cuh", "ad_internal.h")
 
 # the FP64 series kernel behind each path that ad_series_timing reports
@@ -465,17 +466,25 @@ def measure_fp32_form(ad, dev, stream, flush, steps, p=None):
         iters.append(st["iters"])
         t += p.dt
     ms_iter = ad.profile_leja_iteration(op, aug=0, reps=100)
+    ad.time_series(op)
+    ad.expquad_step(op, u, t, p.dt, 1, (0.5,), src, tol=1e-6)
+    path = ad.series_timing(op)["kernel"] or ""
+    ad.time_series(op, False)
     kind = os.environ.get("AD_F32_KERNEL", "ring")[:1]
     kernel = {"b": "leja_iter_f32_bulk_k", "t": "leja_iter_f32_k",
               "v": "leja_iter_f32_vec_k"}.get(kind, "leja_iter_f32_ring_k")
-    pair = kernel == "leja_iter_f32_ring_k" and os.environ.get("AD_F32_PAIR", "1")[:1] != "0"
+    pair = "two-iteration" in path
+    tma = "TMA" in path
     # one launch: y, p read and written, 3 coefficient fields read, 4 B each;
     # the two-iteration kernel does this once for two iterations
     iters_per_launch = 2 if pair else 1
     ms_launch = ms_iter * iters_per_launch
     alg_bytes = 28.0 * g.n
     gbs = alg_bytes / (ms_launch * 1e-3) / 1e9
-    if pair:
+    if pair and tma:
+        kernel = "leja_iter2_f32_tma_k"
+        traffic = traffic_per_launch(F32_TMA_SOURCES, "leja_iter2_f32_tma_4096sq.md")
+    elif pair:
         kernel = "leja_iter2_f32_ring_k"
         traffic = traffic_per_launch(F32_PAIR_SOURCES, "leja_iter2_f32_ring_4096sq.md")
     elif kernel == "leja_iter_f32_ring_k":
@@ -490,6 +499,7 @@ def measure_fp32_form(ad, dev, stream, flush, steps, p=None):
             "value": round(value, 2), "unit": "Mcell-steps/s",
             "ms_per_step": round(ms / steps, 4), "leja_iters_per_step": statistics.mean(iters),
             "tol": 1e-6, "dtype": "f32 storage/arithmetic, f64 Leja scalars and norm sums",
+            "series_path": path,
             "roofline": {"bound": "hbm", "kernel": kernel + ("<0>" if pair else "<0,0>"),
                          "iterations_per_launch": iters_per_launch, "ms_per_launch":
                          round(ms_launch, 5), "achieved": round(gbs, 1), "peak": HBM_PEAK_GBS,

@@ -394,7 +394,8 @@ def time_series(op: Operator, enable: bool = True) -> None:
 SERIES_KERNELS = {0: None, 1: "leja_persistent_f64_k", 2: "leja_nsync_f64_k",
                   3: "graph loop of per-iteration kernels", 4: "host-driven per-iteration kernels",
                   5: "graph loop of two-iteration kernels", 6: "host-driven two-iteration kernels",
-                  7: "leja_tile_f64_k"}
+                  7: "leja_tile_f64_k", 8: "graph loop of two-iteration kernels, TMA rows",
+                  9: "host-driven two-iteration kernels, TMA rows"}
 
 
 def series_timing(op: Operator) -> dict:

@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 // Not part of the public ABI (that is include/anidiff.h).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -79,6 +80,17 @@ void apply_shifted_f64(const GridDev& g, const double* W, const double* u, doubl
                        double s1, cudaStream_t s);
 
 // ---------------------------------------------------------------- Leja series
+// Tensor maps of the FP32 two-iteration kernel's TMA row loader: the two
+// Newton-basis buffers, p and the three coefficient fields, each [ny][nx]
+// float32 with a box of 128 columns x 1 row (zero-Dirichlet grids, nx % 4 == 0).
+struct alignas(64) PairTmaMaps {
+  CUtensorMap y[2];
+  CUtensorMap p, xx, yy, xy;
+};
+// Encode the maps (false when the driver offers no encoder or refuses a map).
+bool encode_pair_tma(const GridDev& g, const void* y0, const void* y1, const void* p,
+                     const float* F, PairTmaMaps* out);
+
 struct SeriesArgs {
   GridDev g;
   int prec;                 // 0 fp64, 1 fp32
@@ -99,6 +111,8 @@ struct SeriesArgs {
   int has_handle;             // 1 when run inside the graph loop
   int f32k;                   // FP32 iteration kernel: 0 tile, 1 bulk-copy pipeline, 2 register
                             // marching, 3 register marching fed by cp.async rings
+  const PairTmaMaps* tma;     // host: the operator's TMA maps, or null (two-iteration
+                              // kernel on the cp.async ring)
 };
 // y[0] = src (or 0 if src == null), p = d0 * y[0]; resets ctrl.
 void series_init(const SeriesArgs& a, const void* src, double d0, int force, int max_iters,
@@ -116,6 +130,8 @@ void series_iteration(const SeriesArgs& a, cudaStream_t s);
 // (series_iteration then launches leja_iter2_f32_ring_k); after such a
 // series, series_flush_pair adds the pending last term to p.
 bool series_pair(const SeriesArgs& a);
+// ... and its row records come in by TMA (zero-Dirichlet grids with maps).
+bool series_pair_tma(const SeriesArgs& a);
 void series_flush_pair(const SeriesArgs& a, cudaStream_t s);
 // Pair mode, after the series: u += b (p + the pending term), FP32, one pass
 // (the flush and the update axpby together; p is not written).

@@ -65,7 +65,7 @@ __device__ int decide(Ctrl* ctrl, const LejaCoef& lc, int m, double ty, double t
   int stop = 0;
   if (ctrl->force > 0) {
     stop = terms >= ctrl->force;
-  } else if (!(ty == ty) || !(tp == tp)) {
+  } else if (!isfinite(ty) || !isfinite(tp)) {
     stop = 1;
     ctrl->status = 3;
   } else if (terms >= 2 && (lc.absd * lc.absd) * ty <= (tol * tol) * tp) {
@@ -344,6 +344,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     X.yout = static_cast<float*>(S.a.y[((m >> 1) + 1) & 1]);
     X.p = static_cast<float*>(S.a.p);
     X.ring = ring;
+    X.stages = PairLayout::STAGES;
     X.G.nx = S.a.g.nx;
     X.G.ny = S.a.g.ny;
     X.G.bc = S.a.g.bc;
@@ -365,7 +366,8 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     X.gx = X0 - 4 + 4 * lane;
     X.fix = X.G.bc != 0 && (X0 == 0 || X0 + kPairOwn >= X.G.nx);
     float ly1 = 0.f, lp1 = 0.f, ly2 = 0.f, lp2 = 0.f;
-    pair_run<ADV>(X, ly1, lp1, ly2, lp2);
+    CpAsyncLoader ldr;
+    pair_run<ADV>(X, ldr, ly1, lp1, ly2, lp2);
     double q[4] = {ly1, lp1, ly2, lp2};
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
@@ -523,6 +525,50 @@ __global__ void __launch_bounds__(kThreads) batch_finish_k(const BatchSlice* sli
       const long long idx = (long long)j * g.nx + i;
       const float pv = pending ? fmaf(d, y[idx], p[idx]) : p[idx];
       S.u[idx] = fmaf(S.dt, pv, S.u[idx]);
+    }
+  }
+}
+
+// batch_finish_k with 16-byte accesses, for batches whose rows and vectors
+// are 16-byte aligned (every nx % 4 == 0; the ring and pair modes with the
+// one-pass start): a thread updates four columns of every fourth row of its
+// tile, four rows in flight.  The same operations per element.
+__global__ void __launch_bounds__(kThreads) batch_finish_vec_k(const BatchSlice* slices,
+                                                              const int* tile_slice, int ntiles,
+                                                              int TY, int pair) {
+  const int cg = threadIdx.x & 63, rg = threadIdx.x >> 6;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const BatchSlice& S = slices[tile_slice[t]];
+    if (S.a.ctrl->status != 0) continue;      // not converged: keep the input state
+    const GridDev g = S.a.g;
+    const int local = t - S.tile_off;
+    const int x0 = (local % S.tiles_x) * kTileCols, y0 = (local / S.tiles_x) * TY;
+    const int i = x0 + 4 * cg;
+    if (i >= g.nx) continue;                  // nx % 4 == 0: the group is all inside
+    const int m = S.a.ctrl->m;
+    const bool pending = pair && m > 0 && !(m & 1);
+    const float d = pending ? (float)S.a.lc[m - 1].d : 0.0f;
+    const float* y = static_cast<const float*>(S.a.y[(m >> 1) & 1]);
+    const float* p = static_cast<const float*>(S.a.p);
+    const int y1 = min(g.ny, y0 + TY);
+    const float dt = S.dt;
+#pragma unroll 4
+    for (int j = y0 + rg; j < y1; j += 4) {
+      const long long idx = (long long)j * g.nx + i;
+      float4 pv = *reinterpret_cast<const float4*>(p + idx);
+      float4 uv = *reinterpret_cast<const float4*>(S.u + idx);
+      if (pending) {
+        const float4 yv = *reinterpret_cast<const float4*>(y + idx);
+        pv.x = fmaf(d, yv.x, pv.x);
+        pv.y = fmaf(d, yv.y, pv.y);
+        pv.z = fmaf(d, yv.z, pv.z);
+        pv.w = fmaf(d, yv.w, pv.w);
+      }
+      uv.x = fmaf(dt, pv.x, uv.x);
+      uv.y = fmaf(dt, pv.y, uv.y);
+      uv.z = fmaf(dt, pv.z, uv.z);
+      uv.w = fmaf(dt, pv.w, uv.w);
+      *reinterpret_cast<float4*>(S.u + idx) = uv;
     }
   }
 }
@@ -771,7 +817,8 @@ int build_batch_graph(ad_batch* b, int force, double tol, int start_mode) {
   {   // u += dt (p + the pending term of even pair-mode counts)
     int pr = b->pair ? 1 : 0;
     void* args[] = {&sl, &ts, &nt, &TY, &pr};
-    kp.func = (void*)batch_finish_k;
+    // the one-pass start certifies 16-byte aligned rows and vectors
+    kp.func = start_mode > 0 ? (void*)batch_finish_vec_k : (void*)batch_finish_k;
     kp.kernelParams = args;
     B_CUDA(cudaGraphAddKernelNode(&n_upd, g, &n_cond, 1, &kp));
   }

@@ -129,6 +129,8 @@ struct ad_operator {
   double* h_scal = nullptr;                    // [4 * (kMaxGmres + 2)]
   // learned bound: the model's inputs of this operator's fields (slot 4,
   // log dt, is filled per prediction), and the model ad_spectral_bound uses
+  PairTmaMaps tma{};                           // TMA maps of the FP32 two-iteration kernel
+  bool has_tma = false;
   float feat[kFeatures] = {};
   double dxmin = 0.0;
   ad_mlp* bound_model = nullptr;
@@ -194,6 +196,7 @@ SeriesArgs series_args(ad_operator* op, int aug) {
   a.adv = op->adv;
   a.abx = op->abx;
   a.aby = op->aby;
+  a.tma = op->has_tma ? &op->tma : nullptr;
   return a;
 }
 
@@ -499,7 +502,7 @@ int run_series(ad_operator* op, int aug, const void* src, double d0, int force, 
         ++launch_counter();
       }
       CUDA_TRY(cudaGetLastError());
-      if (op->time_series) op->t_path = persist ? pk : (graph_used ? 3 : 4) + (series_pair(a) ? 2 : 0);
+      if (op->time_series) op->t_path = persist ? pk : (graph_used ? 3 : 4) + (series_pair(a) ? (series_pair_tma(a) ? 5 : 2) : 0);
       *iters_out = -1;
       return AD_OK;
     }
@@ -512,7 +515,7 @@ int run_series(ad_operator* op, int aug, const void* src, double d0, int force, 
       op->t_ms += ms;
       op->t_series += 1;
       op->t_iters += iters;
-      op->t_path = persist ? pk : (graph_used ? 3 : 4) + (series_pair(a) ? 2 : 0);
+      op->t_path = persist ? pk : (graph_used ? 3 : 4) + (series_pair(a) ? (series_pair_tma(a) ? 5 : 2) : 0);
     }
     if (!op->h_ctrl->stop || op->h_ctrl->status == 4) op->ctrl_dirty = true;
     if (!op->h_ctrl->stop) return fail(AD_ERR_TIMEOUT, "Leja series did not reach its stop state");
@@ -841,6 +844,10 @@ int ad_create_operator(const ad_grid* grid, const double* Dxx, const double* Dxy
     ad_destroy_operator(op);
     return fail(AD_ERR_CUDA, std::string("pack kernel: ") + cudaGetErrorString(e));
   }
+  // FP32 zero-Dirichlet grids with nx % 4 == 0: the two-iteration kernel's
+  // rows come in by TMA (the maps cover this operator's own buffers)
+  if (precision != AD_FP64 && grid->bc == AD_BC_DIRICHLET0 && series_f32_kernel(1, grid->nx) == 3)
+    op->has_tma = encode_pair_tma(op->g, op->Y0, op->Y1, op->P, op->F, &op->tma);
   // inputs of the learned bound, from the fields while they are at hand
   op->dxmin = std::min(dx, dy);
   if (field_features(n, op->dxmin, Dxx, Dxy, Dyy, ax, ay, std::hypot(ax_c, ay_c), op->stream,

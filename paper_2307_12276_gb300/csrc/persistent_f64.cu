@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256) leja_persistent_f64_k(SeriesArgs a, unsig
         int stop = 0;
         if (ctrl->force > 0) {
           stop = terms >= ctrl->force;
-        } else if (!(ty == ty) || !(tp == tp)) {
+        } else if (!isfinite(ty) || !isfinite(tp)) {
           stop = 1;
           ctrl->status = 3;
         } else if (terms >= 2 && (absd * absd) * ty <= (tol * tol) * tp) {
@@ -406,7 +406,7 @@ __device__ bool nsync_read_norms(const double* slots, int k, int G, double& ty, 
 // 0 converged, 3 not finite, -1 keep going.
 __device__ __forceinline__ int nsync_test(const LejaCoef& lc, int terms, double tol, double ty,
                                           double tp) {
-  if (!(ty == ty) || !(tp == tp)) return 3;
+  if (!isfinite(ty) || !isfinite(tp)) return 3;
   if (terms >= 2 && (lc.absd * lc.absd) * ty <= (tol * tol) * tp) return 0;
   return -1;
 }

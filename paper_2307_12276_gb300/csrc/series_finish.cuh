@@ -44,7 +44,7 @@ __device__ void series_finish(const SeriesArgs& a, double sy, double sp) {
     int stop = 0;
     if (ctrl->force > 0) {
       stop = terms >= ctrl->force;
-    } else if (!(ty == ty) || !(tp == tp)) {       // NaN: give up
+    } else if (!isfinite(ty) || !isfinite(tp)) {   // NaN or overflow: give up
       stop = 1;
       ctrl->status = 3;
     } else if (terms >= 2 && (absd * absd) * ty <= (tol * tol) * tp) {   // squared test

@@ -28,6 +28,7 @@
 #include "tile_f32_vec.cuh"
 #include "tile_f32_ring.cuh"
 #include "tile_f32_pair.cuh"
+#include "tile_f32_pair_tma.cuh"
 
 namespace ad {
 
@@ -76,7 +77,7 @@ __device__ void series_finish2(const SeriesArgs& a, double y1, double p1, double
       bool stop = false;
       if (ctrl->force > 0) {
         stop = terms >= ctrl->force;
-      } else if (!(ty == ty) || !(tp == tp)) {
+      } else if (!isfinite(ty) || !isfinite(tp)) {
         stop = true;
         status = 3;
       } else if (terms >= 2 && (absd * absd) * ty <= (tol * tol) * tp) {
@@ -568,6 +569,7 @@ __global__ void __launch_bounds__(kPairWarps * 32, 1) leja_iter2_f32_ring_k(Seri
   X.yout = static_cast<float*>(a.y[((m >> 1) + 1) & 1]);
   X.p = static_cast<float*>(a.p);
   X.ring = pair_smem + (size_t)(threadIdx.x >> 5) * PairLayout::STAGES * PairLayout::SIZE;
+  X.stages = PairLayout::STAGES;
   X.G.nx = a.g.nx;
   X.G.ny = a.g.ny;
   X.G.bc = a.g.bc;
@@ -600,13 +602,99 @@ __global__ void __launch_bounds__(kPairWarps * 32, 1) leja_iter2_f32_ring_k(Seri
     X.L = pair_lane(X0, X.G.lane, X.G.nx, X.G.bc);
     X.gx = X0 - 4 + 4 * X.G.lane;
     X.fix = X.G.bc != 0 && (X0 == 0 || X0 + kPairOwn >= X.G.nx);
-    pair_run<ADV>(X, ly1, lp1, ly2, lp2);
+    CpAsyncLoader ldr;
+    pair_run<ADV>(X, ldr, ly1, lp1, ly2, lp2);
   }
   series_finish2(a, (double)ly1, (double)lp1, (double)ly2, (double)lp2);
 }
 
 size_t pair_smem_bytes() {
   return sizeof(float) * (size_t)kPairWarps * PairLayout::STAGES * PairLayout::SIZE;
+}
+
+// The same two iterations with the row records brought in by TMA
+// (tile_f32_pair_tma.cuh): zero-Dirichlet grids.  Dynamic shared memory: the
+// rings (aligned to 128 bytes for the copies), then each warp's STAGES
+// mbarriers.
+template <int ADV>
+__global__ void __launch_bounds__(kPairWarps * 32, 1)
+    leja_iter2_f32_tma_k(SeriesArgs a, const __grid_constant__ PairTmaMaps maps) {
+  extern __shared__ __align__(16) unsigned char pair_tma_smem[];
+  const volatile Ctrl* vc = a.ctrl;
+  if (vc->stop) return;
+  const int m = vc->m;                                 // even in pair mode
+  const LejaCoef lc1 = a.lc[m], lc2 = a.lc[m + 1];
+  float* rings = reinterpret_cast<float*>(
+      (reinterpret_cast<uintptr_t>(pair_tma_smem) + 127) & ~uintptr_t(127));
+  const int warp = threadIdx.x >> 5;
+  constexpr int stages = PairLayout::STAGES;   // a constant: the slot index is a cheap modulo
+  uint64_t* bars = reinterpret_cast<uint64_t*>(
+                       rings + (size_t)kPairWarps * stages * PairLayout::SIZE) +
+                   warp * stages;
+  PairCtx X;
+  X.a = &a;
+  X.stages = stages;
+  X.yin = static_cast<const float*>(a.y[(m >> 1) & 1]);
+  X.yout = static_cast<float*>(a.y[((m >> 1) + 1) & 1]);
+  X.p = static_cast<float*>(a.p);
+  X.ring = rings + (size_t)warp * stages * PairLayout::SIZE;
+  X.G.nx = a.g.nx;
+  X.G.ny = a.g.ny;
+  X.G.bc = a.g.bc;
+  X.G.n = a.g.n;
+  X.G.lane = threadIdx.x & 31;
+  X.ig = (float)(1.0 / a.gamma);
+  X.sh1 = (float)(a.c / a.gamma + lc1.xi);
+  X.sh2 = (float)(a.c / a.gamma + lc2.xi);
+  X.d0 = m > 0 ? (float)a.lc[m - 1].d : 0.0f;          // pending d_m y_m
+  X.d1 = (float)lc1.d;
+  X.d2 = (float)lc2.d;
+  X.abx = a.abx;
+  X.aby = a.aby;
+  if (X.G.lane == 0) {
+    for (int s = 0; s < stages; ++s) mbar_init(bars + s, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  TmaLoader ldr{&maps, &maps.y[(m >> 1) & 1], bars, a.ctrl, 0u, 0u, false};
+  // bands of rows, one per warp of each strip (at least 8 rows each)
+  const int strips = (X.G.nx + kPairOwn - 1) / kPairOwn;
+  const long long warps = (long long)gridDim.x * kPairWarps;
+  long long bands = warps / strips;
+  if (bands > X.G.ny / 8) bands = X.G.ny / 8;
+  if (bands < 1) bands = 1;
+  const long long units = bands * strips;
+  const long long w = (long long)blockIdx.x * kPairWarps + warp;
+  long long u0, u1;
+  vec_range(units, warps, w, u0, u1);
+  float ly1 = 0.f, lp1 = 0.f, ly2 = 0.f, lp2 = 0.f;
+  for (long long u = u0; u < u1; ++u) {
+    const long long b = u / strips;
+    const int X0 = (int)(u - b * strips) * kPairOwn;
+    X.y0 = (int)(X.G.ny * b / bands);
+    X.y1 = (int)(X.G.ny * (b + 1) / bands);
+    X.L = pair_lane(X0, X.G.lane, X.G.nx, X.G.bc);
+    X.gx = X0 - 4 + 4 * X.G.lane;
+    X.fix = X.G.bc != 0 && (X0 == 0 || X0 + kPairOwn >= X.G.nx);
+    pair_run<ADV>(X, ldr, ly1, lp1, ly2, lp2);
+  }
+  series_finish2(a, (double)ly1, (double)lp1, (double)ly2, (double)lp2);
+}
+
+size_t pair_tma_smem_bytes() {
+  return pair_smem_bytes() + 128 + sizeof(uint64_t) * kPairWarps * PairLayout::STAGES;
+}
+
+// The TMA row loader is measured slower than the cp.async rings on this
+// kernel (116 vs 95 us per 4096^2 launch: the marching is bound by issue
+// latency, and lane 0's copy issue sits on the warp's critical path), so it
+// runs only when asked for: AD_F32_TMA=1.
+bool pair_tma_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("AD_F32_TMA");
+    return e && e[0] == '1';
+  }();
+  return on;
 }
 
 // After a pair-mode series: add the pending d_m y_m when it stopped after an
@@ -777,6 +865,10 @@ int series_blocks_grid(int prec, int nx, int ny) {
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem_bytes());
       cudaFuncSetAttribute((void*)leja_iter2_f32_ring_k<1>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem_bytes());
+      cudaFuncSetAttribute((void*)leja_iter2_f32_tma_k<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)pair_tma_smem_bytes());
+      cudaFuncSetAttribute((void*)leja_iter2_f32_tma_k<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)pair_tma_smem_bytes());
       attr = true;
     }
     // one block of 8 warps per SM; fewer for small grids (>= 16 rows per warp)
@@ -880,8 +972,17 @@ void series_iteration(const SeriesArgs& a, cudaStream_t s) {
     }
   } else if (series_pair(a)) {
     ++launch_counter();
-    if (a.adv == 0) leja_iter2_f32_ring_k<0><<<a.nblocks, kPairWarps * 32, pair_smem_bytes(), s>>>(a);
-    else leja_iter2_f32_ring_k<1><<<a.nblocks, kPairWarps * 32, pair_smem_bytes(), s>>>(a);
+    if (series_pair_tma(a)) {
+      const size_t smem = pair_tma_smem_bytes();
+      if (a.adv == 0)
+        leja_iter2_f32_tma_k<0><<<a.nblocks, kPairWarps * 32, smem, s>>>(a, *a.tma);
+      else
+        leja_iter2_f32_tma_k<1><<<a.nblocks, kPairWarps * 32, smem, s>>>(a, *a.tma);
+    } else if (a.adv == 0) {
+      leja_iter2_f32_ring_k<0><<<a.nblocks, kPairWarps * 32, pair_smem_bytes(), s>>>(a);
+    } else {
+      leja_iter2_f32_ring_k<1><<<a.nblocks, kPairWarps * 32, pair_smem_bytes(), s>>>(a);
+    }
   } else if (a.f32k == 3) {
     ++launch_counter();
 #define AD_F32R_LAUNCH(AUGV, ADVV)                                                  \
@@ -943,12 +1044,50 @@ void series_iteration(const SeriesArgs& a, cudaStream_t s) {
   }
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool encode_pair_tma(const GridDev& g, const void* y0, const void* y1, const void* p,
+                     const float* F, PairTmaMaps* out) {
+  static const EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (EncodeTiledFn) nullptr;
+    }
+    return (EncodeTiledFn)f;
+  }();
+  if (!fn || g.nx % 4 != 0) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny};
+  const cuuint64_t strides[1] = {(cuuint64_t)g.nx * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)PairLayout::XY, 1};    // 128 columns, one row
+  const cuuint32_t step[2] = {1, 1};
+  auto enc = [&](CUtensorMap* m, const void* base) {
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box,
+              step, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;   // out of range: zeros
+  };
+  const long long n = g.n;
+  return enc(&out->y[0], y0) && enc(&out->y[1], y1) && enc(&out->p, p) && enc(&out->xx, F) &&
+         enc(&out->yy, F + n) && enc(&out->xy, F + 2 * n);
+}
+
 bool series_pair(const SeriesArgs& a) {
   static const bool off = [] {
     const char* e = getenv("AD_F32_PAIR");        // tuning override: 0 = one iteration per launch
     return e && e[0] == '0';
   }();
   return !off && a.prec == 1 && a.f32k == 3 && !a.aug && a.adv != 2 && a.g.ny >= 2;
+}
+
+bool series_pair_tma(const SeriesArgs& a) {
+  return series_pair(a) && a.tma && a.g.bc != 0 && pair_tma_enabled();
 }
 
 void series_flush_pair(const SeriesArgs& a, cudaStream_t s) {

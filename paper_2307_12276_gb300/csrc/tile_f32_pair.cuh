@@ -93,6 +93,7 @@ struct PRow {          // one row around the lane's group, columns gx - 1 .. gx 
 
 struct PairCtx {       // per-run constants
   const SeriesArgs* a;
+  int stages;          // ring depth (records per warp)
   const float* yin;
   float* yout;
   float* p;
@@ -117,7 +118,7 @@ __device__ __forceinline__ void pair_spread(float* v, float4 q, const PairCtx& X
 }
 
 __device__ __forceinline__ float* pair_slot(const PairCtx& X, int r) {
-  return X.ring + (size_t)((r - (X.y0 - 2)) % PairLayout::STAGES) * PairLayout::SIZE;
+  return X.ring + (size_t)((r - (X.y0 - 2)) % X.stages) * PairLayout::SIZE;
 }
 
 // Copies of row r (rows y0 - 2 .. y1 + 1; one commit group per row, empty past
@@ -141,15 +142,30 @@ __device__ __forceinline__ void pair_issue(const PairCtx& X, int r) {
   cp_async_commit();
 }
 
-// Read row r into registers, then refill its record with row r + S.  Row r is
-// the oldest pending group: the S - 1 younger ones stay in flight.
-__device__ __forceinline__ void pair_consume(const PairCtx& X, int r, PRow& R) {
+// The row copies of a warp's ring: 16-byte cp.async per lane, one commit
+// group per row.  A lane that copies nothing for its group leaves zeros.
+struct CpAsyncLoader {
+  static constexpr bool kReadAll = false;   // records hold data only where a lane copied
+  __device__ __forceinline__ void issue(const PairCtx& X, int r) { pair_issue(X, r); }
+  // row r (the oldest pending group: the S - 1 younger ones stay in flight)
+  __device__ __forceinline__ const float* wait(const PairCtx& X, int r) {
+    cp_async_wait_group<PairLayout::STAGES - 1>();
+    __syncwarp();
+    return pair_slot(X, r);
+  }
+  __device__ __forceinline__ void drain(const PairCtx&) {
+    cp_async_wait_group<0>();          // nothing may land in the ring after the run
+    __syncwarp();
+  }
+};
+
+// Read row r into registers, then refill its record with row r + S.
+template <class Ld>
+__device__ __forceinline__ void pair_consume(const PairCtx& X, Ld& ldr, int r, PRow& R) {
   using PL = PairLayout;
-  cp_async_wait_group<PL::STAGES - 1>();
-  __syncwarp();
-  const float* S = pair_slot(X, r);
+  const float* S = ldr.wait(X, r);
   const int c = 4 * X.G.lane;
-  const bool ld = X.L.load;
+  const bool ld = Ld::kReadAll || X.L.load;
   float4 y4 = make_float4(0.f, 0.f, 0.f, 0.f), q4 = y4, b4 = y4, x4 = y4, p4 = y4;
   if (ld) {
     y4 = *reinterpret_cast<const float4*>(S + PL::Y + c);
@@ -167,7 +183,7 @@ __device__ __forceinline__ void pair_consume(const PairCtx& X, int r, PRow& R) {
   R.yy[0] = b4.x; R.yy[1] = b4.y; R.yy[2] = b4.z; R.yy[3] = b4.w;
   R.p[0] = p4.x; R.p[1] = p4.y; R.p[2] = p4.z; R.p[3] = p4.w;
   __syncwarp();
-  pair_issue(X, r + PL::STAGES);
+  ldr.issue(X, r + X.stages);
 }
 
 // North-face fluxes of row B towards row N (the expressions of vnorth).
@@ -259,12 +275,12 @@ __device__ __forceinline__ void pair_level1(const PairCtx& X, int r, const PRow&
 // j, j + 1 (B.p: p_m of row j + 1; A.p: p_{m+1} of row j) and Ua, Ub the
 // y_{m+1} rows j - 1, j; N and Un are free.  The next step's roles are
 // (B, N, A) and (Ub, Un, Ua).
-template <int ADV>
-__device__ __forceinline__ void pair_step(const PairCtx& X, int j, PRow& A, PRow& B, PRow& N,
-                                          const float* Ua, const float* Ub, float* Un,
+template <int ADV, class Ld>
+__device__ __forceinline__ void pair_step(const PairCtx& X, Ld& ldr, int j, PRow& A, PRow& B,
+                                          PRow& N, const float* Ua, const float* Ub, float* Un,
                                           float* fs1, float* fs2, float& ly1, float& lp1,
                                           float& ly2, float& lp2) {
-  pair_consume(X, j + 2, N);
+  pair_consume(X, ldr, j + 2, N);
   pair_level1<ADV>(X, j + 1, A, B, N, fs1, Un, ly1, lp1);
   if (X.G.bc != 0 && j + 1 == X.G.ny) {     // y_{m+1} row ny = -(row ny - 1)
 #pragma unroll
@@ -285,22 +301,23 @@ __device__ __forceinline__ void pair_step(const PairCtx& X, int j, PRow& A, PRow
   }
 }
 
-// One marching run of rows [y0, y1) (X.y0, X.y1) of the strip of X.
-template <int ADV>
-__device__ __forceinline__ void pair_run(const PairCtx& X, float& ly1, float& lp1, float& ly2,
-                                         float& lp2) {
+// One marching run of rows [y0, y1) (X.y0, X.y1) of the strip of X, its rows
+// brought into the warp's ring by the loader ldr.
+template <int ADV, class Ld>
+__device__ __forceinline__ void pair_run(const PairCtx& X, Ld& ldr, float& ly1, float& lp1,
+                                         float& ly2, float& lp2) {
   const int y0 = X.y0, y1 = X.y1;
   __syncwarp();
 #pragma unroll 1
-  for (int q = 0; q < PairLayout::STAGES; ++q) pair_issue(X, y0 - 2 + q);
+  for (int q = 0; q < X.stages; ++q) ldr.issue(X, y0 - 2 + q);
   PRow r0, r1, r2;
   float u0[6], u1[6], u2[6], fs1[4], fs2[4];
-  pair_consume(X, y0 - 2, r0);
-  pair_consume(X, y0 - 1, r1);
+  pair_consume(X, ldr, y0 - 2, r0);
+  pair_consume(X, ldr, y0 - 1, r1);
   pair_north<ADV>(r0.y, r1.y, r0.xy, r1.xy, r0.yy, r1.yy, X.aby, fs1);   // south faces, row y0 - 1
-  pair_consume(X, y0, r2);
+  pair_consume(X, ldr, y0, r2);
   pair_level1<ADV>(X, y0 - 1, r0, r1, r2, fs1, u1, ly1, lp1);
-  pair_consume(X, y0 + 1, r0);
+  pair_consume(X, ldr, y0 + 1, r0);
   pair_level1<ADV>(X, y0, r1, r2, r0, fs1, u2, ly1, lp1);
   if (X.G.bc != 0 && y0 == 0) {               // y_{m+1} row -1 = -(row 0)
 #pragma unroll
@@ -312,14 +329,14 @@ __device__ __forceinline__ void pair_run(const PairCtx& X, float& ly1, float& lp
   int j = y0;
 #pragma unroll 1
   for (; j + 3 <= y1; j += 3) {
-    pair_step<ADV>(X, j, r2, r0, r1, u1, u2, u0, fs1, fs2, ly1, lp1, ly2, lp2);
-    pair_step<ADV>(X, j + 1, r0, r1, r2, u2, u0, u1, fs1, fs2, ly1, lp1, ly2, lp2);
-    pair_step<ADV>(X, j + 2, r1, r2, r0, u0, u1, u2, fs1, fs2, ly1, lp1, ly2, lp2);
+    pair_step<ADV>(X, ldr, j, r2, r0, r1, u1, u2, u0, fs1, fs2, ly1, lp1, ly2, lp2);
+    pair_step<ADV>(X, ldr, j + 1, r0, r1, r2, u2, u0, u1, fs1, fs2, ly1, lp1, ly2, lp2);
+    pair_step<ADV>(X, ldr, j + 2, r1, r2, r0, u0, u1, u2, fs1, fs2, ly1, lp1, ly2, lp2);
   }
-  if (j < y1) pair_step<ADV>(X, j, r2, r0, r1, u1, u2, u0, fs1, fs2, ly1, lp1, ly2, lp2);
-  if (j + 1 < y1) pair_step<ADV>(X, j + 1, r0, r1, r2, u2, u0, u1, fs1, fs2, ly1, lp1, ly2, lp2);
-  cp_async_wait_group<0>();          // nothing may land in the ring after the run
-  __syncwarp();
+  if (j < y1) pair_step<ADV>(X, ldr, j, r2, r0, r1, u1, u2, u0, fs1, fs2, ly1, lp1, ly2, lp2);
+  if (j + 1 < y1)
+    pair_step<ADV>(X, ldr, j + 1, r0, r1, r2, u2, u0, u1, fs1, fs2, ly1, lp1, ly2, lp2);
+  ldr.drain(X);
 }
 
 }  // namespace

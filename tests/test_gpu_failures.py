@@ -39,3 +39,24 @@ def test_nan_input_stops_series(precision):
     vd = torch.as_tensor(np.nan_to_num(v), device=DEV).to(dtype)
     st = ad().leja_phi1(op, vd, out, p.dt, tol=1e-6)
     assert st["converged"] == 1
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("nx", [48, 600])            # persistent FP64 kernels / graph loop
+def test_overflowing_series_is_not_converged(precision, nx):
+    """A bound far too small (0.02 x Gershgorin) leaves most of the spectrum
+    outside the Leja interval: the series' terms grow until the norms
+    overflow.  Infinite norms must end the series as not converged (they
+    would otherwise pass the stopping test inf <= inf)."""
+    need_gpu()
+    p = small_problem(nx, 40, BC_DIRICHLET0, "random", dt_factor=100)
+    A, alpha = oracle_operator(p)
+    op = gpu_operator(p, precision)
+    ad().set_spectral_bound(op, 0.02 * alpha)
+    v = np.random.default_rng(4).standard_normal(p.grid.n)
+    dtype = torch.float64 if precision == 0 else torch.float32
+    vd = torch.as_tensor(v, device=DEV).to(dtype)
+    out = torch.empty_like(vd)
+    with pytest.raises(ad().NotConverged) as e:
+        ad().leja_phi1(op, vd, out, p.dt, tol=1e-8)
+    assert e.value.stats["converged"] == 0

@@ -105,6 +105,23 @@ def test_two_iteration_kernel_equals_one_iteration_kernel(case, tmp_path):
         assert s2["f%d" % m]["iters"] == m
 
 
+@pytest.mark.parametrize("case", [c for c in CASES if c[2] == BC_DIRICHLET0])
+def test_tma_rows_equal_cp_async_rows(case, tmp_path):
+    """The two-iteration kernel with its row records brought in by TMA
+    (cp.async.bulk.tensor boxes, zero fill outside the grid; AD_F32_TMA=1)
+    against the same kernel on per-lane cp.async rings: every record holds the
+    same values, so vectors, counts and error estimates are identical."""
+    need_gpu()
+    st, at = _run(case, str(tmp_path / "tma"), {"AD_F32_TMA": "1"})
+    sc, ac = _run(case, str(tmp_path / "cp"), {})
+    assert st["path"] == "graph loop of two-iteration kernels, TMA rows"
+    assert sc["path"] == "graph loop of two-iteration kernels"
+    for key in ac.files:
+        assert st[key]["iters"] == sc[key]["iters"], key
+        assert st[key]["err_est"] == sc[key]["err_est"], key
+        assert np.array_equal(at[key], ac[key]), key
+
+
 @pytest.mark.parametrize("case", CASES[:4])
 @pytest.mark.parametrize("m", FORCED)
 def test_forced_counts_of_either_parity_match_oracle(case, m):
