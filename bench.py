@@ -935,14 +935,15 @@ def measure_batched_form(ad, dev, stream, steps, nslices=128, sides=(256, 512, 1
         out["cpu_baseline"] = batched_oracle_baseline(config3_slices(nslices, sides=sides), dt)
     if learned_fields:
         out["learned"] = measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, fields,
-                                         dt, batch, steps, ms_batch, power_s, learned_fields)
+                                         dt, batch, steps, ms_batch, power_s, learned_fields,
+                                         ms_fp64=ms_fp64)
     for op in ops:
         op.close()
     return out
 
 
 def measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, fields, dt, batch, steps,
-                    ms_batch, power_s, nfields, margin=1.1):
+                    ms_batch, power_s, nfields, margin=1.1, ms_fp64=None):
     """Train the bound network on generated fields (inputs and labels from
     ad_bound_training_sample: power-iteration spectra and Leja iteration
     counts; sides 64..2048, D_par in [1, 100], dt in [10, 1000] Delta t_CFL),
@@ -1014,6 +1015,11 @@ def measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, fields, dt, 
                                       "min": round(float(ratio.min()), 3),
                                       "max": round(float(ratio.max()), 3)},
             "speedup_vs_power_iteration_bounds": round(plain_total / learned_total, 3),
+            "speedup_over_plain_fp64_gpu": (
+                round((power_s + steps * ms_fp64 * 1e-3) / learned_total, 3)
+                if ms_fp64 else None),
+            "speedup_note": "bound time plus the steps; plain FP64 GPU: power-iteration bounds "
+                            "and one FP64 call per slice at tol 1e-6",
             "steps_in_comparison": steps}
 
 
