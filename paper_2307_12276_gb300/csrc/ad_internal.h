@@ -132,6 +132,8 @@ void series_iteration(const SeriesArgs& a, cudaStream_t s);
 bool series_pair(const SeriesArgs& a);
 // ... and its row records come in by TMA (zero-Dirichlet grids with maps).
 bool series_pair_tma(const SeriesArgs& a);
+// The two-iteration marching keeps one row of lookahead in registers.
+bool pair_prefetch();
 void series_flush_pair(const SeriesArgs& a, cudaStream_t s);
 // Pair mode, after the series: u += b (p + the pending term), FP32, one pass
 // (the flush and the update axpby together; p is not written).

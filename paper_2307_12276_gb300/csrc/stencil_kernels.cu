@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) leja_iter_f32_ring_k(SeriesAr
 // Two fused FP32 iterations per launch by register marching over overlapped
 // 120-column strips fed by per-warp cp.async rings (tile_f32_pair.cuh); one
 // block of 8 warps per SM.
-template <int ADV>
+template <int ADV, bool PF>
 __global__ void __launch_bounds__(kPairWarps * 32, 1) leja_iter2_f32_ring_k(SeriesArgs a) {
   extern __shared__ __align__(16) float pair_smem[];
   const volatile Ctrl* vc = a.ctrl;
@@ -603,7 +603,8 @@ __global__ void __launch_bounds__(kPairWarps * 32, 1) leja_iter2_f32_ring_k(Seri
     X.gx = X0 - 4 + 4 * X.G.lane;
     X.fix = X.G.bc != 0 && (X0 == 0 || X0 + kPairOwn >= X.G.nx);
     CpAsyncLoader ldr;
-    pair_run<ADV>(X, ldr, ly1, lp1, ly2, lp2);
+    if (PF) pair_run_pf<ADV>(X, ldr, ly1, lp1, ly2, lp2);
+    else pair_run<ADV>(X, ldr, ly1, lp1, ly2, lp2);
   }
   series_finish2(a, (double)ly1, (double)lp1, (double)ly2, (double)lp2);
 }
@@ -798,6 +799,16 @@ __global__ void __launch_bounds__(kThreads) leja_iter_f32_k(SeriesArgs a) {
 
 }  // namespace
 
+// Row lookahead in registers for the two-iteration kernels (pair_run_pf):
+// AD_F32_PREFETCH=0 runs the marching without it.
+bool pair_prefetch() {
+  static const bool off = [] {
+    const char* e = getenv("AD_F32_PREFETCH");
+    return e && e[0] == '0';
+  }();
+  return !off;
+}
+
 // Failure-detection check of the bounded waits: one block waits on an
 // mbarrier whose phase never completes (two arrivals expected, one made) and
 // must give up after timeout_ns, recording 4 (timeout) in *status.
@@ -861,10 +872,10 @@ int series_blocks_grid(int prec, int nx, int ny) {
       AD_RING_ATTR(false, 0); AD_RING_ATTR(false, 1); AD_RING_ATTR(false, 2);
       AD_RING_ATTR(true, 0); AD_RING_ATTR(true, 1); AD_RING_ATTR(true, 2);
 #undef AD_RING_ATTR
-      cudaFuncSetAttribute((void*)leja_iter2_f32_ring_k<0>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem_bytes());
-      cudaFuncSetAttribute((void*)leja_iter2_f32_ring_k<1>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem_bytes());
+      for (void* fn : {(void*)leja_iter2_f32_ring_k<0, false>, (void*)leja_iter2_f32_ring_k<1, false>,
+                       (void*)leja_iter2_f32_ring_k<0, true>, (void*)leja_iter2_f32_ring_k<1, true>})
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pair_smem_bytes());
       cudaFuncSetAttribute((void*)leja_iter2_f32_tma_k<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)pair_tma_smem_bytes());
       cudaFuncSetAttribute((void*)leja_iter2_f32_tma_k<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -978,10 +989,12 @@ void series_iteration(const SeriesArgs& a, cudaStream_t s) {
         leja_iter2_f32_tma_k<0><<<a.nblocks, kPairWarps * 32, smem, s>>>(a, *a.tma);
       else
         leja_iter2_f32_tma_k<1><<<a.nblocks, kPairWarps * 32, smem, s>>>(a, *a.tma);
-    } else if (a.adv == 0) {
-      leja_iter2_f32_ring_k<0><<<a.nblocks, kPairWarps * 32, pair_smem_bytes(), s>>>(a);
+    } else if (pair_prefetch()) {
+      if (a.adv == 0) leja_iter2_f32_ring_k<0, true><<<a.nblocks, kPairWarps * 32, pair_smem_bytes(), s>>>(a);
+      else leja_iter2_f32_ring_k<1, true><<<a.nblocks, kPairWarps * 32, pair_smem_bytes(), s>>>(a);
     } else {
-      leja_iter2_f32_ring_k<1><<<a.nblocks, kPairWarps * 32, pair_smem_bytes(), s>>>(a);
+      if (a.adv == 0) leja_iter2_f32_ring_k<0, false><<<a.nblocks, kPairWarps * 32, pair_smem_bytes(), s>>>(a);
+      else leja_iter2_f32_ring_k<1, false><<<a.nblocks, kPairWarps * 32, pair_smem_bytes(), s>>>(a);
     }
   } else if (a.f32k == 3) {
     ++launch_counter();

@@ -339,5 +339,79 @@ __device__ __forceinline__ void pair_run(const PairCtx& X, Ld& ldr, float& ly1, 
   ldr.drain(X);
 }
 
+// Step j with the next row prefetched: on entry A, B, N hold rows j, j + 1,
+// j + 2 (N was read by the previous step) and Q is free; Q receives row
+// j + 3 first, so its shared-memory loads and shuffles overlap this step's
+// arithmetic instead of heading its dependency chain.  Otherwise pair_step.
+// The next step's roles are (B, N, Q, A) and (Ub, Un, Ua's successor).
+template <int ADV, class Ld>
+__device__ __forceinline__ void pair_step_pf(const PairCtx& X, Ld& ldr, int j, PRow& A, PRow& B,
+                                             PRow& N, PRow& Q, const float* Ua, const float* Ub,
+                                             float* Un, float* fs1, float* fs2, float& ly1,
+                                             float& lp1, float& ly2, float& lp2) {
+  if (j + 3 <= X.y1 + 1) pair_consume(X, ldr, j + 3, Q);   // rows are issued up to y1 + 1
+  pair_level1<ADV>(X, j + 1, A, B, N, fs1, Un, ly1, lp1);
+  if (X.G.bc != 0 && j + 1 == X.G.ny) {     // y_{m+1} row ny = -(row ny - 1)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Un[k] = -Ub[k];
+  }
+  float z[4];
+  pair_level<ADV>(Ua, Ub, Un, A.xx, A.xy, B.xy, A.yy, B.yy, X.abx, X.aby, fs2, X.ig, X.sh2, z);
+  if (X.L.own) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float p2 = fmaf(X.d2, z[k], A.p[k]);
+      ly2 = fmaf(z[k], z[k], ly2);
+      lp2 = fmaf(p2, p2, lp2);
+    }
+    const long long idx = (long long)j * X.G.nx + X.gx;
+    *reinterpret_cast<float4*>(X.yout + idx) = make_float4(z[0], z[1], z[2], z[3]);
+  }
+}
+
+// pair_run with one row of lookahead in registers: four row records and four
+// y_{m+1} rows rotate with period 4 (the loop is unrolled four times, so no
+// row is copied).  The same operations in the same order as pair_run.
+template <int ADV, class Ld>
+__device__ __forceinline__ void pair_run_pf(const PairCtx& X, Ld& ldr, float& ly1, float& lp1,
+                                            float& ly2, float& lp2) {
+  const int y0 = X.y0, y1 = X.y1;
+  __syncwarp();
+#pragma unroll 1
+  for (int q = 0; q < X.stages; ++q) ldr.issue(X, y0 - 2 + q);
+  PRow R0, R1, R2, R3;
+  float U0[6], U1[6], U2[6], U3[6], fs1[4], fs2[4];
+  pair_consume(X, ldr, y0 - 2, R0);
+  pair_consume(X, ldr, y0 - 1, R1);
+  pair_north<ADV>(R0.y, R1.y, R0.xy, R1.xy, R0.yy, R1.yy, X.aby, fs1);   // south faces, row y0 - 1
+  pair_consume(X, ldr, y0, R2);
+  pair_level1<ADV>(X, y0 - 1, R0, R1, R2, fs1, U1, ly1, lp1);
+  pair_consume(X, ldr, y0 + 1, R3);
+  pair_level1<ADV>(X, y0, R1, R2, R3, fs1, U2, ly1, lp1);
+  if (X.G.bc != 0 && y0 == 0) {               // y_{m+1} row -1 = -(row 0)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) U1[k] = -U2[k];
+  }
+  // south faces of level 2 on row y0: coefficient rows y0 - 1 (R1) and y0 (R2)
+  pair_north<ADV>(U1, U2, R1.xy, R2.xy, R1.yy, R2.yy, X.aby, fs2);
+  pair_consume(X, ldr, y0 + 2, R0);           // y0 + 2 <= y1 + 1: always issued
+  // rows: R2 = y0, R3 = y0 + 1, R0 = y0 + 2, R1 free; y_{m+1}: U1 = y0 - 1, U2 = y0
+  int j = y0;
+#pragma unroll 1
+  for (; j + 4 <= y1; j += 4) {
+    pair_step_pf<ADV>(X, ldr, j, R2, R3, R0, R1, U1, U2, U3, fs1, fs2, ly1, lp1, ly2, lp2);
+    pair_step_pf<ADV>(X, ldr, j + 1, R3, R0, R1, R2, U2, U3, U0, fs1, fs2, ly1, lp1, ly2, lp2);
+    pair_step_pf<ADV>(X, ldr, j + 2, R0, R1, R2, R3, U3, U0, U1, fs1, fs2, ly1, lp1, ly2, lp2);
+    pair_step_pf<ADV>(X, ldr, j + 3, R1, R2, R3, R0, U0, U1, U2, fs1, fs2, ly1, lp1, ly2, lp2);
+  }
+  if (j < y1)
+    pair_step_pf<ADV>(X, ldr, j, R2, R3, R0, R1, U1, U2, U3, fs1, fs2, ly1, lp1, ly2, lp2);
+  if (j + 1 < y1)
+    pair_step_pf<ADV>(X, ldr, j + 1, R3, R0, R1, R2, U2, U3, U0, fs1, fs2, ly1, lp1, ly2, lp2);
+  if (j + 2 < y1)
+    pair_step_pf<ADV>(X, ldr, j + 2, R0, R1, R2, R3, U3, U0, U1, fs1, fs2, ly1, lp1, ly2, lp2);
+  ldr.drain(X);
+}
+
 }  // namespace
 }  // namespace ad
