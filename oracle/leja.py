@@ -19,7 +19,9 @@ Readings where the paper is silent (each is listed in the design notes):
     full precision; ties (relative 1e-12 in the log-product) go to the larger xi.
   * Stopping rule: after term m+1 (m+1 >= 2), stop when
         |d_{m+1}| ||y_{m+1}||_2 <= tol ||p_{m+1}||_2 ;
-    fail (not converged) after ``max_iters`` terms.  ``force_iters`` runs an
+    fail (not converged) after ``max_iters`` terms, or at once when either
+    norm is not finite (NaN input, or terms that overflow because the bound
+    leaves part of the spectrum far outside the interpolation interval).  ``force_iters`` runs an
     exact number of terms with no test.
   * Substepping: if rho = gamma dt exceeds rho_max, the step is split into K
     equal substeps (K = ceil(rho / rho_max)).
@@ -204,11 +206,14 @@ def _newton_series(matvec_shifted, y0, d, xi, tol, force_iters, max_iters, top=N
     for m in range(max_iters):
         y = matvec_shifted(y, m) - xi[m] * y
         p = p + d[m + 1] * y
-        if m + 1 >= 2:
-            ny, np_ = np.linalg.norm(sel(y)), np.linalg.norm(sel(p))
-            if abs(d[m + 1]) * ny <= tol * np_:
-                est = abs(d[m + 1]) * ny / np_ if np_ > 0 else 0.0
-                return p, m + 1, est, True
+        ny, np_ = np.linalg.norm(sel(y)), np.linalg.norm(sel(p))
+        if not (np.isfinite(ny) and np.isfinite(np_)):
+            # a NaN, or terms that overflowed: the series has failed (without
+            # this, inf <= inf would pass the test below as converged)
+            return p, m + 1, float("inf"), False
+        if m + 1 >= 2 and abs(d[m + 1]) * ny <= tol * np_:
+            est = abs(d[m + 1]) * ny / np_ if np_ > 0 else 0.0
+            return p, m + 1, est, True
     ny, np_ = np.linalg.norm(sel(y)), np.linalg.norm(sel(p))
     est = abs(d[max_iters]) * ny / np_ if np_ > 0 else float("inf")
     return p, max_iters, est, False

@@ -227,3 +227,25 @@ def test_adaptive_with_ample_budget_is_the_fixed_step():
     adapt, st_a = leja.leja_phi1(A, v, p.dt, alpha, tol=1e-10, adaptive=True)
     assert st_f.substeps == 1 and st_a.rejected == 0 and st_a.substeps == 1
     assert np.array_equal(fixed, adapt) and st_a.iters == st_f.iters
+
+
+def test_non_finite_norms_end_the_series_unconverged():
+    """A NaN input stops the series at its first term; a bound far too small
+    (0.02 x Gershgorin: most of the spectrum lies far outside the Leja
+    interval) makes the terms grow until the norms overflow, and the series
+    must then report failure, not pass inf <= inf as converged.  With the
+    true bound the same series converges."""
+    p = small_problem(12, 10, BC_DIRICHLET0, "random", dt_factor=100)
+    A = op.assemble(p.grid, p.Dxx, p.Dxy, p.Dyy, p.ax_arr(), p.ay_arr())
+    alpha = spectral.gershgorin(A)
+    v = np.random.default_rng(4).standard_normal(p.grid.n)
+    _, st = leja.leja_phi1(A, v, p.dt, alpha, tol=1e-8)
+    assert st.converged
+    with np.errstate(over="ignore", invalid="ignore"):
+        out, st = leja.leja_phi1(A, v, p.dt, 0.02 * alpha, tol=1e-8)
+    assert not st.converged and st.iters < leja.MAX_ITERS
+    assert np.max(np.abs(out)) > 1e100          # the terms diverged until a norm overflowed
+    w = v.copy()
+    w[5] = np.nan
+    _, st = leja.leja_phi1(A, w, p.dt, alpha, tol=1e-8)
+    assert not st.converged and st.iters == 1
