@@ -380,6 +380,7 @@ def measure_workload(ad, dev, stream, p, flush, steps, warmup, e2e_steps, world=
     achieved = ((flops * series_t["iters"] + step_flops * series_t["series"])
                 / (series_t["ms"] * 1e-3) / 1e12)
     ms_forced = ad.profile_leja_iteration(op, aug=int(aug), reps=300 if g.n < 10 ** 6 else 60)
+    fma_peak = ad.fp64_fma_rate(2, 1 << 16, stream=stream)    # this device's DFMA loop, live
     traffic = None
     if kernel == "leja_nsync_f64_k" and g.nx == 512:
         traffic = traffic_per_launch(F64_SERIES_SOURCES, "leja_nsync_f64_512sq.md")
@@ -409,8 +410,11 @@ def measure_workload(ad, dev, stream, p, flush, steps, warmup, e2e_steps, world=
                     "frac": round(hbm_gbs / HBM_PEAK_GBS, 4),
                     "note": "algorithmic bytes per iteration / iteration time, of measured copy "
                             "bandwidth (the FP64 pipe, not HBM, bounds this kernel)"},
-            "peak_note": "of derived FP64 peak: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz "
-                         "(a DFMA loop on every SM measured 1.68 DFMA/clk/SM = 1.06 TFLOP/s)"}
+            "measured_fp64_fma_tflops": round(fma_peak, 4),
+            "frac_of_measured_fp64_fma": round(achieved / fma_peak, 4),
+            "peak_note": "of derived FP64 peak: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz; "
+                         "measured_fp64_fma_tflops is a DFMA loop on every SM timed in this "
+                         "run (ad_fp64_fma_rate)"}
     res = {"workload": label or p.name, "nx": g.nx, "ny": g.ny, "cells": g.n,
            "value": value, "dev_ms": dev_ms, "ms_per_step": dev_ms / steps,
            "leja_iters_per_step": tot["iters"] / steps, "gpu_launches": launches,

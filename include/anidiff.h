@@ -461,6 +461,14 @@ AD_API int ad_leja_phi1_noalloc(const ad_grid* grid, const double* Dxx, const do
                                 const double* v, double* out, double dt, double tol,
                                 int force_iters, void* cuda_stream, ad_stats* stats);
 
+/* Measurement helper (no counterpart in the paper): the FP64 FMA rate this
+ * device sustains, in TFLOP/s (2 flops per FMA), from one timed launch (after
+ * one untimed) of blocks_per_sm (1..8) blocks of 256 threads per SM, each
+ * thread running four independent fused multiply-add chains of iters steps
+ * (1024..2^24).  The FP64 kernels of this library are bound by this rate;
+ * it is reported beside the nominal peak of their roofline. */
+AD_API int ad_fp64_fma_rate(int blocks_per_sm, int iters, void* cuda_stream, double* tflops);
+
 /* Failure-detection check (no counterpart in the paper): one block waits on a
  * device barrier that nothing releases, with the library's bounded-wait
  * machinery and a bound of timeout_ms (0 < timeout_ms <= 1000).  Returns

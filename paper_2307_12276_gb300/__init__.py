@@ -96,6 +96,7 @@ _sig = {
     "ad_learned_bounds": (_i, [_vp, C.POINTER(_vp), _i, C.POINTER(_d), _d, _i, C.POINTER(_d),
                                C.POINTER(_d)]),
     "ad_set_bound_model": (_i, [_vp, _vp, _d, _d]),
+    "ad_fp64_fma_rate": (_i, [_i, _i, _vp, C.POINTER(_d)]),
     "ad_bound_training_sample": (_i, [_vp, _d, C.c_ulonglong, _i, _d, _d, C.POINTER(C.c_float),
                                       C.POINTER(C.c_float), C.POINTER(_d)]),
     "ad_create_momentum_operator": (_i, [C.POINTER(_Grid), C.POINTER(_Momentum), _vp, _vp, _vp,
@@ -559,6 +560,13 @@ class MLP:
         Y = torch.empty((B, self.n_out), dtype=torch.float32, device=X.device)
         _check(_lib.ad_mlp_predict(self.handle, X.data_ptr(), B, 1 if bf16 else 0, Y.data_ptr()))
         return Y
+
+
+def fp64_fma_rate(blocks_per_sm: int = 2, iters: int = 1 << 16, stream=None) -> float:
+    """ad_fp64_fma_rate: the FP64 FMA rate of the device in TFLOP/s."""
+    r = _d()
+    _check(_lib.ad_fp64_fma_rate(int(blocks_per_sm), int(iters), _stream_ptr(stream), C.byref(r)))
+    return r.value
 
 
 def learned_bounds(model: "MLP", ops: Sequence[Operator], dts, margin: float = 1.1,

@@ -132,8 +132,9 @@ void series_iteration(const SeriesArgs& a, cudaStream_t s);
 bool series_pair(const SeriesArgs& a);
 // ... and its row records come in by TMA (zero-Dirichlet grids with maps).
 bool series_pair_tma(const SeriesArgs& a);
-// The two-iteration marching keeps one row of lookahead in registers.
-bool pair_prefetch();
+// Marching of the two-iteration kernels: 1 one row of lookahead in registers
+// (default), 0 without.
+int pair_march();
 void series_flush_pair(const SeriesArgs& a, cudaStream_t s);
 // Pair mode, after the series: u += b (p + the pending term), FP32, one pass
 // (the flush and the update axpby together; p is not written).
@@ -238,6 +239,10 @@ struct ad_operator;
 struct ad_mlp;
 namespace ad {
 bool operator_view(const ad_operator* op, OperatorView* v);
+
+// FP64 FMA rate of the device (TFLOP/s) from a timed launch of `blocks` blocks of
+// independent DFMA chains, `iters` per chain; 0, or 2 on a CUDA error.
+int fp64_fma_rate(int blocks, int iters, cudaStream_t s, double* tflops);
 
 // One-block kernel whose bounded wait must run out (failure-detection test).
 int wait_timeout_probe(unsigned long long timeout_ns, int* status_dev, cudaStream_t s);

@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
 // iterations in tile order and applies the stopping rule after iteration m
 // and, if it does not fire, after iteration m + 1.  Eligible batches: every
 // slice with nx % 4 == 0 and ny >= 2, constant or no advection.
-template <int ADV, bool PF>
+template <int ADV, int MODE>
 __global__ void __launch_bounds__(kRingThreads, 1)
     batch_pair_k(const BatchSlice* slices, const int* rtile_slice, int nrtiles, int nslices,
                  int R, double* tile_partials, unsigned int* bticket, unsigned long long handle,
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     X.fix = X.G.bc != 0 && (X0 == 0 || X0 + kPairOwn >= X.G.nx);
     float ly1 = 0.f, lp1 = 0.f, ly2 = 0.f, lp2 = 0.f;
     CpAsyncLoader ldr;
-    if (PF) pair_run_pf<ADV>(X, ldr, ly1, lp1, ly2, lp2);
+    if (MODE == 1) pair_run_pf<ADV>(X, ldr, ly1, lp1, ly2, lp2);
     else pair_run<ADV>(X, ldr, ly1, lp1, ly2, lp2);
     double q[4] = {ly1, lp1, ly2, lp2};
 #pragma unroll
@@ -579,9 +579,9 @@ size_t batch_pair_smem() {
 }
 
 void* pick_pair(int adv) {
-  if (pair_prefetch())
-    return adv == 0 ? (void*)batch_pair_k<0, true> : (void*)batch_pair_k<1, true>;
-  return adv == 0 ? (void*)batch_pair_k<0, false> : (void*)batch_pair_k<1, false>;
+  static void* const fn[2][2] = {{(void*)batch_pair_k<0, 0>, (void*)batch_pair_k<1, 0>},
+                                 {(void*)batch_pair_k<0, 1>, (void*)batch_pair_k<1, 1>}};
+  return fn[pair_march()][adv == 0 ? 0 : 1];
 }
 
 template <int ADV>

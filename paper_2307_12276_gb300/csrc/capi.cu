@@ -1566,6 +1566,20 @@ int ad_cn_step(ad_operator* op, void* u, double t, double dt, const ad_source* s
   return AD_OK;
 }
 
+int ad_fp64_fma_rate(int blocks_per_sm, int iters, void* cuda_stream, double* tflops) {
+  g_err.clear();
+  if (!tflops || blocks_per_sm < 1 || blocks_per_sm > 8 || iters < 1024 || iters > (1 << 24))
+    return fail(AD_ERR_INVALID, "blocks_per_sm in [1, 8], iters in [1024, 2^24]");
+  int dev = 0, sms = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (fp64_fma_rate(blocks_per_sm * sms, iters, (cudaStream_t)cuda_stream, tflops) != 0) {
+    cudaGetLastError();
+    return fail(AD_ERR_CUDA, "FP64 rate probe failed");
+  }
+  return AD_OK;
+}
+
 int ad_check_wait_timeout(double timeout_ms, void* cuda_stream) {
   g_err.clear();
   if (!(timeout_ms > 0) || timeout_ms > 1000.0) return fail(AD_ERR_INVALID, "timeout_ms in (0, 1000]");

@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) leja_iter_f32_ring_k(SeriesAr
 // Two fused FP32 iterations per launch by register marching over overlapped
 // 120-column strips fed by per-warp cp.async rings (tile_f32_pair.cuh); one
 // block of 8 warps per SM.
-template <int ADV, bool PF>
+template <int ADV, int MODE>
 __global__ void __launch_bounds__(kPairWarps * 32, 1) leja_iter2_f32_ring_k(SeriesArgs a) {
   extern __shared__ __align__(16) float pair_smem[];
   const volatile Ctrl* vc = a.ctrl;
@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(kPairWarps * 32, 1) leja_iter2_f32_ring_k(Seri
     X.gx = X0 - 4 + 4 * X.G.lane;
     X.fix = X.G.bc != 0 && (X0 == 0 || X0 + kPairOwn >= X.G.nx);
     CpAsyncLoader ldr;
-    if (PF) pair_run_pf<ADV>(X, ldr, ly1, lp1, ly2, lp2);
+    if (MODE == 1) pair_run_pf<ADV>(X, ldr, ly1, lp1, ly2, lp2);
     else pair_run<ADV>(X, ldr, ly1, lp1, ly2, lp2);
   }
   series_finish2(a, (double)ly1, (double)lp1, (double)ly2, (double)lp2);
@@ -799,14 +799,17 @@ __global__ void __launch_bounds__(kThreads) leja_iter_f32_k(SeriesArgs a) {
 
 }  // namespace
 
-// Row lookahead in registers for the two-iteration kernels (pair_run_pf):
-// AD_F32_PREFETCH=0 runs the marching without it.
-bool pair_prefetch() {
-  static const bool off = [] {
-    const char* e = getenv("AD_F32_PREFETCH");
-    return e && e[0] == '0';
+// Marching of the two-iteration kernels: 1 pair_run_pf (one row of
+// lookahead in registers, the default), 0 pair_run (tuning override
+// AD_F32_MARCH=0).  Measured at 4096^2: 91.8 against 94.6 us per launch; a
+// third marching with level 2 one row further behind level 1 (two
+// independent chains per step) took 98.9 us and was dropped.
+int pair_march() {
+  static const int mode = [] {
+    const char* e = getenv("AD_F32_MARCH");
+    return e && e[0] == '0' ? 0 : 1;
   }();
-  return !off;
+  return mode;
 }
 
 // Failure-detection check of the bounded waits: one block waits on an
@@ -832,6 +835,42 @@ int wait_timeout_probe(unsigned long long timeout_ns, int* status_dev, cudaStrea
   ++launch_counter();
   wait_timeout_probe_k<<<1, 32, 0, s>>>(timeout_ns, status_dev);
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+// FP64 FMA rate probe: every thread runs four independent chains
+// a <- a * b + c (b just below 1, so the chains stay finite); the result is
+// stored only under a condition that never holds, which keeps the chains
+// live without a memory stream.
+__global__ void __launch_bounds__(kThreads) dfma_rate_k(int iters, double* sink) {
+  double a0 = 1.0 + 1e-3 * threadIdx.x, a1 = a0 + 0.25, a2 = a0 + 0.5, a3 = a0 + 0.75;
+  const double b = 0.99999999, c = 1e-9;
+#pragma unroll 4
+  for (int k = 0; k < iters; ++k) {
+    a0 = fma(a0, b, c);
+    a1 = fma(a1, b, c);
+    a2 = fma(a2, b, c);
+    a3 = fma(a3, b, c);
+  }
+  if (a0 + a1 + a2 + a3 < -1.0) sink[blockIdx.x] = a0;
+}
+
+int fp64_fma_rate(int blocks, int iters, cudaStream_t s, double* tflops) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return 2;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return 2; }
+  launch_counter() += 2;
+  dfma_rate_k<<<blocks, kThreads, 0, s>>>(iters, nullptr);      // warm-up (clocks up)
+  cudaEventRecord(e0, s);
+  dfma_rate_k<<<blocks, kThreads, 0, s>>>(iters, nullptr);
+  cudaEventRecord(e1, s);
+  float ms = 0.f;
+  const bool ok = cudaEventSynchronize(e1) == cudaSuccess &&
+                  cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0.f;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok) return 2;
+  *tflops = 2.0 * 4.0 * iters * (double)kThreads * blocks / (ms * 1e-3) / 1e12;
+  return 0;
 }
 
 int series_blocks(int prec, long long n) {
@@ -872,8 +911,8 @@ int series_blocks_grid(int prec, int nx, int ny) {
       AD_RING_ATTR(false, 0); AD_RING_ATTR(false, 1); AD_RING_ATTR(false, 2);
       AD_RING_ATTR(true, 0); AD_RING_ATTR(true, 1); AD_RING_ATTR(true, 2);
 #undef AD_RING_ATTR
-      for (void* fn : {(void*)leja_iter2_f32_ring_k<0, false>, (void*)leja_iter2_f32_ring_k<1, false>,
-                       (void*)leja_iter2_f32_ring_k<0, true>, (void*)leja_iter2_f32_ring_k<1, true>})
+      for (void* fn : {(void*)leja_iter2_f32_ring_k<0, 0>, (void*)leja_iter2_f32_ring_k<1, 0>,
+                       (void*)leja_iter2_f32_ring_k<0, 1>, (void*)leja_iter2_f32_ring_k<1, 1>})
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)pair_smem_bytes());
       cudaFuncSetAttribute((void*)leja_iter2_f32_tma_k<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -989,12 +1028,13 @@ void series_iteration(const SeriesArgs& a, cudaStream_t s) {
         leja_iter2_f32_tma_k<0><<<a.nblocks, kPairWarps * 32, smem, s>>>(a, *a.tma);
       else
         leja_iter2_f32_tma_k<1><<<a.nblocks, kPairWarps * 32, smem, s>>>(a, *a.tma);
-    } else if (pair_prefetch()) {
-      if (a.adv == 0) leja_iter2_f32_ring_k<0, true><<<a.nblocks, kPairWarps * 32, pair_smem_bytes(), s>>>(a);
-      else leja_iter2_f32_ring_k<1, true><<<a.nblocks, kPairWarps * 32, pair_smem_bytes(), s>>>(a);
     } else {
-      if (a.adv == 0) leja_iter2_f32_ring_k<0, false><<<a.nblocks, kPairWarps * 32, pair_smem_bytes(), s>>>(a);
-      else leja_iter2_f32_ring_k<1, false><<<a.nblocks, kPairWarps * 32, pair_smem_bytes(), s>>>(a);
+      static void* const fn[2][2] = {
+          {(void*)leja_iter2_f32_ring_k<0, 0>, (void*)leja_iter2_f32_ring_k<1, 0>},
+          {(void*)leja_iter2_f32_ring_k<0, 1>, (void*)leja_iter2_f32_ring_k<1, 1>}};
+      void* args[] = {const_cast<SeriesArgs*>(&a)};
+      cudaLaunchKernel(fn[pair_march()][a.adv == 0 ? 0 : 1], dim3(a.nblocks), dim3(kPairWarps * 32),
+                       args, pair_smem_bytes(), s);
     }
   } else if (a.f32k == 3) {
     ++launch_counter();

@@ -90,9 +90,13 @@ def _run(case, prefix, env_extra):
 
 
 @pytest.mark.parametrize("case", CASES)
-def test_two_iteration_kernel_equals_one_iteration_kernel(case, tmp_path):
+@pytest.mark.parametrize("march", ["0", "1"])
+def test_two_iteration_kernel_equals_one_iteration_kernel(case, march, tmp_path):
+    """Both marchings of the two-iteration kernel (0 plain, 1 with one row of
+    lookahead in registers) form the same values in the same order as the
+    one-iteration kernel."""
     need_gpu()
-    s2, a2 = _run(case, str(tmp_path / "pair"), {})
+    s2, a2 = _run(case, str(tmp_path / "pair"), {"AD_F32_MARCH": march})
     s1, a1 = _run(case, str(tmp_path / "single"), {"AD_F32_PAIR": "0"})
     assert s2["path"] == "graph loop of two-iteration kernels"
     assert s1["path"] == "graph loop of per-iteration kernels"
