@@ -228,9 +228,15 @@ AD_API int ad_cn_step(ad_operator* op, void* u, double t, double dt, const ad_so
  * of a cosmic-ray grid: with the momentum terms of the full transport
  * equation dropped, each momentum only sets its own coefficients) advanced by
  * one exponential-midpoint step each (Eq. exp_midpoint) in ONE CUDA graph
- * launch.  Each slice keeps its own spectral bound, Leja scalars and stopping
- * rule; the fused iteration kernel strides over one flat list of 256 x TY
- * tiles of every active slice, and slices that have converged drop out. */
+ * launch: the series start of every slice in one pass, the Newton series of
+ * every slice in ONE persistent cooperative kernel (two iterations per pass
+ * over warp tiles; a slice's next pass waits only for its own previous pass,
+ * so slices at different passes overlap; converged slices drop out), and the
+ * update in one pass.  Each slice keeps its own spectral bound, Leja scalars
+ * and stopping rule.  Where the persistent kernel does not apply (slices with
+ * nx % 4 != 0 or an advection field, unaligned vectors, more than two source
+ * terms, AD_BATCH_PERSIST=0) the series runs as a graph loop of iteration
+ * launches instead. */
 typedef struct ad_batch ad_batch;
 
 /* Group nslices AD_FP32_STORAGE operators (same advection mode, same stream;
@@ -250,7 +256,8 @@ AD_API int ad_destroy_batch(ad_batch* b);
  * count in every entry).  AD_ERR_NOT_CONVERGED if any slice hit max_iters
  * (or produced a non-finite norm); such a slice keeps its input state, so the
  * caller can repeat it alone with a safer bound, while every converged slice
- * has been advanced. */
+ * has been advanced.  AD_ERR_TIMEOUT if a bounded wait of the persistent
+ * kernel gave up (the context stays usable). */
 AD_API int ad_batch_midpoint_step(ad_batch* b, void* const* u, double t, double dt,
                                   const ad_source* src, double tol, int force_iters,
                                   ad_stats* per_slice);

@@ -33,7 +33,8 @@ struct Ctrl {
   int force;      // > 0: exact iteration count, no stopping test
   int max_iters;
   unsigned int ticket;  // blocks of the running iteration that have finished
-  unsigned int gen;     // grid-barrier generation of the persistent series kernel
+  unsigned int gen;     // grid-barrier generation of the persistent series kernel;
+                        // batched persistent iteration: passes the slice has completed
   double tol;
   double err_est;
   double ynorm2;  // last ||y_{m+1}||^2

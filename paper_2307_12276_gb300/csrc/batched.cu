@@ -40,6 +40,22 @@ namespace {
 
 constexpr int kBatchSources = 4;
 constexpr int kBatchUnroll = 4;
+constexpr unsigned long long kPersistTimeoutNs = 2000000000ULL;   // bound of every wait
+
+// Device words of a batched step (the kernels take a pointer to `ticket`).
+struct BatchSync {
+  unsigned int ticket;        // launches of the graph loop: warps of the launch done
+  int active;                 // persistent iteration: slices still iterating
+  int abort;                  // persistent iteration: a bounded wait gave up
+  int pad;
+  unsigned long long next;    // persistent iteration: next (pass, tile) item
+};
+
+__device__ __forceinline__ unsigned long long batch_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 struct BatchSlice {
   SeriesArgs a;                     // operator buffers, batch-owned lc/ctrl
@@ -119,8 +135,15 @@ __global__ void __launch_bounds__(kThreads) batch_init_k(const BatchSlice* slice
       c->err_est = 0.0;
       c->ynorm2 = 0.0;
       c->pnorm2 = 0.0;
+      c->gen = 0u;                // passes completed (persistent iteration)
     }
-    if (threadIdx.x == 0) *bticket = 0u;
+    if (threadIdx.x == 0) {
+      BatchSync* bs = reinterpret_cast<BatchSync*>(bticket);
+      bs->ticket = 0u;
+      bs->active = nslices;
+      bs->abort = 0;
+      bs->next = 0ull;
+    }
   }
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const BatchSlice& S = slices[tile_slice[t]];
@@ -423,6 +446,143 @@ __global__ void __launch_bounds__(kRingThreads, 1)
   }
 }
 
+// The whole Newton series of every slice in ONE persistent (cooperative)
+// launch: warps take (pass, tile) items in order from a global counter, an
+// item being one two-iteration pass (pair_run, as batch_pair_k) of one warp
+// tile.  A tile of pass k waits only for pass k - 1 of its own slice (the
+// slice's completed-pass counter, set by the warp that applies the slice's
+// stopping rule), so slices at different passes overlap and no launch
+// boundary separates the passes.  Items are taken in pass order, so every
+// item of pass k - 1 is taken, and running on a resident warp, before any
+// warp waits on it; each wait is bounded (kPersistTimeoutNs of global time:
+// on expiry the kernel records status 4 and every warp leaves).  Items of a
+// slice that has stopped are skipped; the warps leave once no slice is
+// iterating.
+template <int ADV, int MODE>
+__global__ void __launch_bounds__(kRingThreads, 1)
+    batch_persist_k(const BatchSlice* slices, const int* rtile_slice, int nrtiles, int nslices,
+                    int R, double* tile_partials, unsigned int* bticket) {
+  extern __shared__ __align__(16) float pair_smem[];
+  BatchSync* bs = reinterpret_cast<BatchSync*>(bticket);
+  const int lane = threadIdx.x & 31;
+  float* ring = pair_smem + (size_t)(threadIdx.x >> 5) * PairLayout::STAGES * PairLayout::SIZE;
+  const unsigned long long limit = (unsigned long long)(kMaxIters / 2 + 1) * nrtiles;
+  for (;;) {
+    unsigned long long it = 0ull;
+    if (lane == 0) it = atomicAdd(&bs->next, 1ull);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= limit) break;                    // no series runs past kMaxIters
+    const int k = (int)(it / (unsigned long long)nrtiles);
+    const int tile = (int)(it - (unsigned long long)k * nrtiles);
+    const BatchSlice& S = slices[rtile_slice[tile]];
+    Ctrl* ctrl = S.a.ctrl;
+    int state = 0;                             // 0 run, 1 slice stopped, 2 leave
+    if (lane == 0) {
+      const unsigned long long t0 = batch_ns();
+      for (;;) {
+        if (*(volatile int*)&bs->abort) { state = 2; break; }
+        if (*(volatile int*)&ctrl->stop) { state = 1; break; }
+        if (*(volatile unsigned int*)&ctrl->gen >= (unsigned int)k) {
+          // the slice's flags are written stop first, then (after a fence) the
+          // pass count: a stop that came with this count must be seen here
+          __threadfence();
+          if (*(volatile int*)&ctrl->stop) state = 1;
+          break;
+        }
+        if (batch_ns() - t0 > kPersistTimeoutNs) {
+          *(volatile int*)&ctrl->status = 4;
+          *(volatile int*)&bs->abort = 1;
+          state = 2;
+          break;
+        }
+        __nanosleep(256);                      // back off: the polls share L2 with the work
+      }
+      if (state == 1 && *(volatile int*)&bs->active == 0) state = 2;   // nothing iterates
+      __threadfence();
+    }
+    state = __shfl_sync(0xffffffffu, state, 0);
+    if (state == 2) break;
+    if (state == 1) continue;
+    const int m = *(volatile int*)&ctrl->m;    // 2 k
+    const LejaCoef lc1 = S.a.lc[m], lc2 = S.a.lc[m + 1];
+    PairCtx X;
+    X.a = &S.a;
+    X.yin = static_cast<const float*>(S.a.y[(m >> 1) & 1]);
+    X.yout = static_cast<float*>(S.a.y[((m >> 1) + 1) & 1]);
+    X.p = static_cast<float*>(S.a.p);
+    X.ring = ring;
+    X.stages = PairLayout::STAGES;
+    X.G.nx = S.a.g.nx;
+    X.G.ny = S.a.g.ny;
+    X.G.bc = S.a.g.bc;
+    X.G.n = S.a.g.n;
+    X.G.lane = lane;
+    X.ig = (float)(1.0 / S.a.gamma);
+    X.sh1 = (float)(S.a.c / S.a.gamma + lc1.xi);
+    X.sh2 = (float)(S.a.c / S.a.gamma + lc2.xi);
+    X.d0 = m > 0 ? (float)S.a.lc[m - 1].d : 0.0f;
+    X.d1 = (float)lc1.d;
+    X.d2 = (float)lc2.d;
+    X.abx = S.a.abx;
+    X.aby = S.a.aby;
+    const int local = tile - S.rt_off;
+    const int X0 = (local % S.rt_x) * kPairOwn;
+    X.y0 = (local / S.rt_x) * R;
+    X.y1 = min(S.a.g.ny, X.y0 + R);
+    X.L = pair_lane(X0, lane, X.G.nx, X.G.bc);
+    X.gx = X0 - 4 + 4 * lane;
+    X.fix = X.G.bc != 0 && (X0 == 0 || X0 + kPairOwn >= X.G.nx);
+    float ly1 = 0.f, lp1 = 0.f, ly2 = 0.f, lp2 = 0.f;
+    CpAsyncLoader ldr;
+    if (MODE == 1) pair_run_pf<ADV>(X, ldr, ly1, lp1, ly2, lp2);
+    else pair_run<ADV>(X, ldr, ly1, lp1, ly2, lp2);
+    double q[4] = {ly1, lp1, ly2, lp2};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) q[kk] += __shfl_down_sync(0xffffffffu, q[kk], o);
+    int last = 0;
+    if (lane == 0) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) tile_partials[4 * tile + kk] = q[kk];
+      __threadfence();
+      const unsigned int t = atomicAdd(&ctrl->ticket, 1u);
+      last = (t == (unsigned int)S.rt_n - 1u) ? 1 : 0;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {                                // the slice's last tile of pass k: decide
+      __threadfence();
+      double t4[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int r = lane; r < S.rt_n; r += 32)
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) t4[kk] += __ldcg(&tile_partials[4 * (S.rt_off + r) + kk]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) t4[kk] += __shfl_down_sync(0xffffffffu, t4[kk], o);
+      if (lane == 0) {
+        int stop = decide(ctrl, lc1, m, t4[0], t4[1]);
+        if (stop) {
+          ctrl->m = m + 1;                     // p is complete (no pending term)
+        } else {
+          stop = decide(ctrl, lc2, m + 1, t4[2], t4[3]);
+          ctrl->m = m + 2;
+        }
+        if (*(volatile int*)&bs->abort) stop = 1;
+        ctrl->ticket = 0u;
+        __threadfence();                       // the pass's data and scalars before its flags
+        if (stop) {
+          *(volatile int*)&ctrl->stop = 1;
+          atomicSub(&bs->active, 1);
+          __threadfence();                     // stop before the pass count that reveals it
+        }
+        *(volatile unsigned int*)&ctrl->gen = (unsigned int)(k + 1);
+        __threadfence();
+      }
+    }
+  }
+}
+
 // Series start of every slice in one marching pass (the ring kernels'
 // run with scale 1, shift 0 and p taken as 0): y_0 = A u + c0 g0 + c1 g1,
 // p_0 = d0 y_0, over 128-column x TY-row units (the two halves of each
@@ -450,8 +610,15 @@ __global__ void __launch_bounds__(kRingThreads, 1)
       c->err_est = 0.0;
       c->ynorm2 = 0.0;
       c->pnorm2 = 0.0;
+      c->gen = 0u;                // passes completed (persistent iteration)
     }
-    if (threadIdx.x == 0) *bticket = 0u;
+    if (threadIdx.x == 0) {
+      BatchSync* bs = reinterpret_cast<BatchSync*>(bticket);
+      bs->ticket = 0u;
+      bs->active = nslices;
+      bs->abort = 0;
+      bs->next = 0ull;
+    }
   }
   using L = RingLayout<SRC, ADV>;
   float* ring = ring_smem + (size_t)(threadIdx.x >> 5) * L::STAGES * L::SIZE;
@@ -654,6 +821,8 @@ struct ad_batch {
   int graph_force = -2;
   double graph_tol = -1.0;
   int graph_start = -1;               // start_mode the graph was built with
+  bool persist = false;               // the graph runs the persistent iteration kernel
+  bool persist_off = false;           // the persistent kernel could not be built here
 };
 
 namespace {
@@ -738,6 +907,35 @@ int upload_ring_tiles(ad_batch* b, int R) {
 
 int ring_grid(const ad_batch* b) { return std::max(1, std::min(152, (b->nrtiles + 7) / 8)); }
 
+void* pick_persist(int adv) {
+  static void* const fn[2][2] = {{(void*)batch_persist_k<0, 0>, (void*)batch_persist_k<1, 0>},
+                                 {(void*)batch_persist_k<0, 1>, (void*)batch_persist_k<1, 1>}};
+  return fn[pair_march()][adv == 0 ? 0 : 1];
+}
+
+// Blocks of the persistent iteration kernel: one per SM when a block fits on
+// every SM at once (co-residency of all blocks is what its waits rely on);
+// 0 to keep the graph loop (also with AD_BATCH_PERSIST=0).
+int persist_grid(const ad_batch* b) {
+  static const bool off = [] {
+    const char* e = getenv("AD_BATCH_PERSIST");
+    return e && e[0] == '0';
+  }();
+  if (off || !b->pair || b->persist_off) return 0;
+  int dev = 0, sms = 0, per_sm = 0;
+  void* fn = pick_persist(b->adv);
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)batch_pair_smem()) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRingThreads,
+                                                    batch_pair_smem()) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm >= 1 ? sms : 0;
+}
+
 void destroy_batch_graph(ad_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
@@ -751,8 +949,12 @@ int build_batch_graph(ad_batch* b, int force, double tol, int start_mode) {
   cudaGraph_t g;
   B_CUDA(cudaGraphCreate(&g, 0));
   b->graph = g;
-  cudaGraphConditionalHandle h;
-  B_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  // the two-iteration passes as ONE persistent cooperative launch (one block
+  // per SM, every block resident) instead of the graph loop
+  const int pgrid = persist_grid(b);
+  b->persist = b->pair && start_mode > 0 && pgrid > 0;
+  cudaGraphConditionalHandle h{};
+  if (!b->persist) B_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
   int TY = b->TY, nt = b->ntiles, S = b->S, maxit = kMaxIters;
   const BatchSlice* sl = b->d_slices;
   const int* ts = b->d_tile_slice;
@@ -788,6 +990,27 @@ int build_batch_graph(ad_batch* b, int force, double tol, int start_mode) {
       B_CUDA(cudaGraphAddKernelNode(&n_init, g, &n_apply, 1, &kp));
     }
   }
+  const int* rts = b->d_rtile_slice;
+  int nrt = b->nrtiles, R = b->R;
+  double* rparts = b->d_rpartials;
+  if (b->persist) {
+    void* pargs[] = {&sl, &rts, &nrt, &S, &R, &rparts, &bt};
+    cudaKernelNodeParams pp = kp;
+    pp.func = pick_persist(b->adv);
+    pp.kernelParams = pargs;
+    pp.blockDim = dim3(kRingThreads);
+    pp.gridDim = dim3(pgrid);
+    pp.sharedMemBytes = (unsigned)batch_pair_smem();
+    B_CUDA(cudaGraphAddKernelNode(&n_cond, g, &n_init, 1, &pp));
+    cudaKernelNodeAttrValue coop{};
+    coop.cooperative = 1;
+    if (cudaGraphKernelNodeSetAttribute(n_cond, cudaKernelNodeAttributeCooperative, &coop) !=
+        cudaSuccess) {             // no cooperative graph nodes here: build the graph loop
+      cudaGetLastError();
+      b->persist_off = true;
+      return build_batch_graph(b, force, tol, start_mode);
+    }
+  } else {
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = h;
@@ -795,9 +1018,6 @@ int build_batch_graph(ad_batch* b, int force, double tol, int start_mode) {
   cp.conditional.size = 1;
   B_CUDA(cudaGraphAddNode(&n_cond, g, &n_init, nullptr, 1, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  const int* rts = b->d_rtile_slice;
-  int nrt = b->nrtiles, R = b->R;
-  double* rparts = b->d_rpartials;
   {
     void* args[] = {&sl, &ts, &nt, &S, &parts, &bt, &hv, &one};
     void* rargs[] = {&sl, &rts, &nrt, &S, &R, &rparts, &bt, &hv, &one};
@@ -819,6 +1039,7 @@ int build_batch_graph(ad_batch* b, int force, double tol, int start_mode) {
       prev = nn;
     }
   }
+  }
   {   // u += dt (p + the pending term of even pair-mode counts)
     int pr = b->pair ? 1 : 0;
     void* args[] = {&sl, &ts, &nt, &TY, &pr};
@@ -827,7 +1048,12 @@ int build_batch_graph(ad_batch* b, int force, double tol, int start_mode) {
     kp.kernelParams = args;
     B_CUDA(cudaGraphAddKernelNode(&n_upd, g, &n_cond, 1, &kp));
   }
-  B_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
+  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    if (!b->persist) return bfail(AD_ERR_CUDA, "cudaGraphInstantiate failed");
+    b->persist_off = true;         // the cooperative node was refused: build the graph loop
+    return build_batch_graph(b, force, tol, start_mode);
+  }
   b->graph_force = force;
   b->graph_tol = tol;
   b->graph_start = start_mode;
@@ -1012,14 +1238,14 @@ int ad_create_batch(ad_operator* const* ops, int nslices, int autotune, ad_batch
   bool ok = cudaMalloc(&b->d_slices, sizeof(BatchSlice) * nslices) == cudaSuccess &&
             cudaMalloc(&b->d_lc, sizeof(LejaCoef) * kMaxIters * nslices) == cudaSuccess &&
             cudaMalloc(&b->d_ctrl, sizeof(Ctrl) * nslices) == cudaSuccess &&
-            cudaMalloc(&b->d_bticket, sizeof(unsigned int)) == cudaSuccess;
+            cudaMalloc(&b->d_bticket, sizeof(BatchSync)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     ad_destroy_batch(b);
     return bfail(AD_ERR_NOMEM, "batch allocation failed");
   }
   cudaMemsetAsync(b->d_ctrl, 0, sizeof(Ctrl) * nslices, b->stream);
-  cudaMemsetAsync(b->d_bticket, 0, sizeof(unsigned int), b->stream);
+  cudaMemsetAsync(b->d_bticket, 0, sizeof(BatchSync), b->stream);
   for (int s = 0; s < nslices; ++s) {
     b->hs[s].a.lc = b->d_lc + (size_t)s * kMaxIters;
     b->hs[s].a.ctrl = b->d_ctrl + s;
@@ -1068,7 +1294,15 @@ int ad_create_batch(ad_operator* const* ops, int nslices, int autotune, ad_batch
   const std::string key = tune_key(b);
   auto cache = read_cache();
   auto it = cache.find(key);
-  if (it != cache.end()) {
+  static const int rows_override = [] {
+    const char* e = getenv("AD_BATCH_ROWS");          // tuning override: rows per warp tile
+    const int v = e ? atoi(e) : 0;
+    return (v == 16 || v == 32 || v == 64 || v == 128) ? v : 0;
+  }();
+  if (rows_override && b->ring) {
+    TY = rows_override;
+    bps = 1;
+  } else if (it != cache.end()) {
     TY = it->second.ty;
     bps = it->second.bps;
     tuned = it->second.ms;
@@ -1233,7 +1467,8 @@ int ad_batch_midpoint_step(ad_batch* b, void* const* u, double t, double dt,
   for (int s = 0; s < b->S; ++s) {
     const Ctrl& c = b->h_ctrl[s];
     total_iters += c.iters;
-    if (c.status != 0) status = AD_ERR_NOT_CONVERGED;
+    if (c.status == 4) status = AD_ERR_TIMEOUT;
+    else if (c.status != 0 && status != AD_ERR_TIMEOUT) status = AD_ERR_NOT_CONVERGED;
     if (per_slice) {
       ad_stats& st = per_slice[s];
       st = ad_stats{};
@@ -1251,10 +1486,13 @@ int ad_batch_midpoint_step(ad_batch* b, void* const* u, double t, double dt,
     int max_it = 0;
     for (int s = 0; s < b->S; ++s) max_it = std::max(max_it, b->h_ctrl[s].iters);
     const int per_run = kBatchUnroll * (b->pair ? 2 : 1);     // iterations per body run
-    const int launches = (int)(launch_counter() - l0) + 3 + (b->pair ? 1 : 0) +
+    const int launches =
+        b->persist ? (int)(launch_counter() - l0) + 3          // start, persistent, finish
+                   : (int)(launch_counter() - l0) + 3 + (b->pair ? 1 : 0) +
                          kBatchUnroll * ((max_it + per_run - 1) / per_run);
     for (int s = 0; s < b->S; ++s) per_slice[s].kernel_launches = launches;
   }
+  if (status == AD_ERR_TIMEOUT) return bfail(status, "a bounded wait of the batched series gave up");
   if (status != AD_OK) return bfail(status, "a slice's Leja series reached max_iters");
   return AD_OK;
 }

@@ -240,6 +240,7 @@ for key, kw in (("f7", dict(force_iters=7)), ("f8", dict(force_iters=8)), ("tol"
     us = [devT(s[4], 1) for s in slices]
     st = ad().batch_midpoint_step(batch, us, 0.0, dt, srcs, **kw)
     stats[key] = [s["iters"] for s in st]
+    stats["launches_" + key] = st[0]["kernel_launches"]
     for k, u in enumerate(us):
         out["%s_%d" % (key, k)] = u.cpu().numpy()
 np.savez({prefix!r}, **out)
@@ -266,6 +267,36 @@ def test_pair_batch_equals_ring_batch(tmp_path):
         assert r.returncode == 0, r.stderr[-2000:]
         res[tag] = (json.loads(r.stdout.strip().splitlines()[-1]), np.load(prefix + ".npz"))
     (sp, ap), (sr, ar) = res["pair"], res["ring"]
-    assert sp == sr
+    assert {k: v for k, v in sp.items() if not k.startswith("launches")} == \
+        {k: v for k, v in sr.items() if not k.startswith("launches")}
     for key in ar.files:
         assert np.array_equal(ap[key], ar[key]), key
+
+
+def test_persistent_batch_equals_graph_loop(tmp_path):
+    """The whole series of every slice in one persistent cooperative launch
+    (each slice's pass waiting only for its own previous pass) against the
+    graph loop of two-iteration launches (AD_BATCH_PERSIST=0): the same tiles
+    and the same order of every sum, so identical counts and results; the
+    persistent step is three kernels (start, series, finish)."""
+    need_gpu()
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = {}
+    for tag, env_extra in (("persist", {}), ("loop", {"AD_BATCH_PERSIST": "0"})):
+        env = dict(os.environ)
+        env.update(env_extra)
+        env["AD_AUTOTUNE_CACHE"] = str(tmp_path / f"tune_{tag}.json")
+        prefix = str(tmp_path / tag)
+        code = PAIR_CHILD.format(root=root, tests=os.path.join(root, "tests"), prefix=prefix)
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        res[tag] = (json.loads(r.stdout.strip().splitlines()[-1]), np.load(prefix + ".npz"))
+    (sp, ap), (sl, al) = res["persist"], res["loop"]
+    for key in ("f7", "f8", "tol"):
+        assert sp[key] == sl[key], key
+        assert sp["launches_" + key] == 3 < sl["launches_" + key], key
+    for key in al.files:
+        assert np.array_equal(ap[key], al[key]), key
