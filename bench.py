@@ -860,12 +860,14 @@ def measure_batched_form(ad, dev, stream, steps, nslices=128, sides=(256, 512, 1
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     iters = []
+    torch.cuda.profiler.start()       # the range a profiler started with capture off records
     ev0.record(stream)
     for k in range(steps):
         st = ad.batch_midpoint_step(batch, us, (k + 1) * dt, dt, srcs, tol=1e-6)
         iters.append(sum(s["iters"] for s in st))
     ev1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     ms_batch = ev0.elapsed_time(ev1) / steps
     # the same slices, one operator call each
     u2 = [u.clone() for u in u_start]
@@ -1108,7 +1110,8 @@ def run_ours(args):
     if "batched" in wanted:
         forms["batched"] = measure_batched_form(
             ad, dev, stream, args.form_steps,
-            learned_fields=args.learned_fields if "learned" in wanted else 0)
+            learned_fields=args.learned_fields if "learned" in wanted else 0,
+            cpu_baseline=not args.no_cpu_baseline)
 
     cpu, err, err32 = None, None, None
     if oracle_proc is not None:
