@@ -504,7 +504,10 @@ def measure_fp32_form(ad, dev, stream, flush, steps, p=None):
             "ms_per_step": round(ms / steps, 4), "leja_iters_per_step": statistics.mean(iters),
             "tol": 1e-6, "dtype": "f32 storage/arithmetic, f64 Leja scalars and norm sums",
             "series_path": path,
-            "roofline": {"bound": "hbm", "kernel": kernel + ("<0>" if pair else "<0,0>"),
+            "roofline": {"bound": "hbm",
+                         "kernel": kernel + (("<0, %d>" % (0 if os.environ.get("AD_F32_MARCH", "1")
+                                                           [:1] == "0" else 1)) if pair and not tma
+                                             else ("<0>" if pair else "<0,0>")),
                          "iterations_per_launch": iters_per_launch, "ms_per_launch":
                          round(ms_launch, 5), "achieved": round(gbs, 1), "peak": HBM_PEAK_GBS,
                          "unit": "GB/s", "frac": round(gbs / HBM_PEAK_GBS, 4),

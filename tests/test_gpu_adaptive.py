@@ -9,7 +9,7 @@ iteration totals must be equal and the results agree to the FP64 bar.
 import numpy as np
 import pytest
 
-from gpu_util import DEV, ad, dev64, devT, gpu_operator, gpu_source, need_gpu, oracle_operator, rel, torch, assert_close
+from gpu_util import DEV, ad, dev64, devT, gpu_operator, gpu_source, need_gpu, oracle_operator, torch, assert_close
 from oracle import integrators, leja
 from workloads import small_problem
 from workloads.fields import BC_DIRICHLET0, BC_PERIODIC

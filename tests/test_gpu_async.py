@@ -12,7 +12,7 @@ applies it.
 import numpy as np
 import pytest
 
-from gpu_util import devT, gpu_operator, gpu_source, need_gpu, oracle_operator, rel, ad, assert_close
+from gpu_util import devT, gpu_operator, gpu_source, need_gpu, oracle_operator, ad, assert_close
 from oracle import integrators
 from workloads import small_problem
 from workloads.fields import BC_DIRICHLET0, BC_PERIODIC

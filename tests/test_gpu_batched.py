@@ -12,12 +12,12 @@ import os
 import numpy as np
 import pytest
 
-from gpu_util import DEV, ad, devT, dev64, need_gpu, rel, torch, assert_close
+from gpu_util import ad, devT, dev64, need_gpu, torch, assert_close
 from oracle import integrators
 from oracle import operator as oop
 from oracle import spectral
 from workloads import Grid, cell_centres, gaussian, tensor_from_b, b_circular
-from workloads.fields import BC_DIRICHLET0, SeparableSource
+from workloads.fields import BC_DIRICHLET0
 
 pytestmark = pytest.mark.gpu
 

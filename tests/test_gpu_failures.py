@@ -4,7 +4,7 @@ NOT_CONVERGED; the context stays usable afterwards."""
 import numpy as np
 import pytest
 
-from gpu_util import DEV, ad, dev64, gpu_operator, need_gpu, oracle_operator, torch
+from gpu_util import DEV, ad, gpu_operator, need_gpu, oracle_operator, torch
 from workloads import small_problem
 from workloads.fields import BC_DIRICHLET0
 

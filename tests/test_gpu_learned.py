@@ -6,7 +6,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_util import DEV, ad, dev64, devT, need_gpu, rel, torch, assert_close
+from gpu_util import DEV, ad, dev64, devT, need_gpu, torch, assert_close
 from oracle import integrators, mlp as omlp
 from oracle import operator as oop
 from oracle import spectral

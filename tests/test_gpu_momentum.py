@@ -7,7 +7,7 @@ and without advection, and a 128^2 x 16 case (262k unknowns).
 import numpy as np
 import pytest
 
-from gpu_util import DEV, ad, dev64, need_gpu, rel, torch, assert_close
+from gpu_util import DEV, ad, dev64, need_gpu, torch, assert_close
 from oracle import integrators, leja, momentum, spectral
 from workloads.fields import BC_DIRICHLET0, BC_PERIODIC
 from workloads.momentum import momentum_problem

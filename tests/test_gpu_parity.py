@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from gpu_util import (DEV, ad, assert_close, dev64, devT, gpu_operator, gpu_source, need_gpu,
-                      oracle_at_gpu_count, oracle_operator, rel, torch)
+                      oracle_at_gpu_count, oracle_operator, torch)
 from oracle import cn as ocn
 from oracle import integrators, leja, spectral
 from workloads import config0, config1, small_problem

@@ -3,7 +3,7 @@ against the oracle's exact sparse solve, through the C ABI."""
 import numpy as np
 import pytest
 
-from gpu_util import ad, dev64, gpu_operator, gpu_source, need_gpu, oracle_operator, rel, assert_close
+from gpu_util import ad, dev64, gpu_operator, gpu_source, need_gpu, oracle_operator, assert_close
 from oracle import penalised
 from workloads import small_problem
 from workloads.fields import BC_DIRICHLET0, BC_PERIODIC

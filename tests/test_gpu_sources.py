@@ -11,7 +11,7 @@ time-dependent TDS source, evaluated at t + dt/2 = 0.3 + dt/2.
 import numpy as np
 import pytest
 
-from gpu_util import ad, devT, gpu_operator, need_gpu, oracle_operator, rel, assert_close
+from gpu_util import ad, devT, gpu_operator, need_gpu, oracle_operator, assert_close
 from oracle import integrators
 from workloads import small_problem
 from workloads.fields import BC_DIRICHLET0, BC_PERIODIC, SeparableSource

@@ -8,7 +8,6 @@ scratch buffer.  After one warm-up call of each kind (the first step of a
 kind instantiates its CUDA graph), ten more of each must leave the device's
 free memory exactly unchanged.
 """
-import numpy as np
 import pytest
 
 from gpu_util import ad, dev64, devT, gpu_operator, gpu_source, need_gpu, torch
