@@ -464,6 +464,43 @@ def batch_info(b: Batch) -> dict:
     return {"tile_rows": ty.value, "blocks": nb.value, "tiles": nt.value, "tuned_ms": ms.value}
 
 
+_SOURCE_FIELDS = ("nterms", "g", "h", "ctx")
+
+
+def _batch_sources(ops, sources):
+    """ad_source[S] of a batch built in one buffer: every slice's term pointers
+    packed into one void* array, the records written column by column (the
+    batched step is called once per time step for every slice, so this avoids
+    one ctypes array and callback object per slice).  Returns (pointer, objects
+    to keep alive during the call)."""
+    import numpy as np
+    S = len(ops)
+    counts = np.zeros(S, dtype=np.int64)
+    ptrs, hcalls = [], []
+    for s, src in enumerate(sources):
+        if src is None or len(src.g) == 0:
+            continue
+        if len(src.g) > MAX_SOURCES:
+            raise ValueError("at most 16 source terms")
+        counts[s] = len(src.g)
+        ptrs.extend(ops[s].vec(gk, "source term") for gk in src.g)
+        if src.h is not None:
+            hs = list(src.h)
+            hcalls.append((s, _PROFILE(lambda k, t, ctx, hs=hs: float(hs[k](t)))))
+    flat = (C.c_void_p * max(1, len(ptrs)))(*ptrs)
+    buf = (C.c_byte * (C.sizeof(_Source) * S))()
+    dt = np.dtype({"names": list(_SOURCE_FIELDS), "formats": ["i4", "u8", "u8", "u8"],
+                   "offsets": [getattr(_Source, f).offset for f in _SOURCE_FIELDS],
+                   "itemsize": C.sizeof(_Source)})
+    rec = np.frombuffer(buf, dtype=dt)
+    first = np.concatenate(([0], np.cumsum(counts)[:-1]))
+    rec["nterms"] = counts
+    rec["g"] = np.where(counts > 0, C.addressof(flat) + C.sizeof(C.c_void_p) * first, 0)
+    for s, cb in hcalls:
+        rec["h"][s] = C.cast(cb, C.c_void_p).value
+    return C.cast(buf, _vp), (flat, buf, hcalls)
+
+
 def batch_midpoint_step(b: Batch, us, t: float, dt: float, sources=None, tol: float = 1e-6,
                         force_iters: int = -1, raise_not_converged: bool = True):
     """ad_batch_midpoint_step: us = list of float32 device tensors (one per slice),
@@ -472,18 +509,14 @@ def batch_midpoint_step(b: Batch, us, t: float, dt: float, sources=None, tol: fl
     S = len(b.ops)
     if len(us) != S:
         raise ValueError("one state vector per slice")
-    uptr = (_vp * S)(*[b.ops[s].vec(us[s], f"u[{s}]") for s in range(S)])
-    keep = []
+    ops = b.ops
+    uptr = (_vp * S)(*[ops[s].vec(us[s], "u") for s in range(S)])
+    keep = ()
     srcp = None
     if sources is not None:
-        arr = (_Source * S)()
-        for s, src in enumerate(sources):
-            st_, k = _source_struct(b.ops[s], src)
-            keep.append(k)
-            if st_ is not None:
-                arr[s] = st_
-        srcp = C.cast(arr, _vp)
-        keep.append(arr)
+        if len(sources) != S:
+            raise ValueError("one Source (or None) per slice")
+        srcp, keep = _batch_sources(ops, sources)
     stats = (Stats * S)()
     status = _lib.ad_batch_midpoint_step(b.handle, uptr, t, dt, srcp, tol, force_iters, stats)
     if not (status == AD_ERR_NOT_CONVERGED and not raise_not_converged):

@@ -121,13 +121,12 @@ __device__ __forceinline__ float* pair_slot(const PairCtx& X, int r) {
   return X.ring + (size_t)((r - (X.y0 - 2)) % X.stages) * PairLayout::SIZE;
 }
 
-// Copies of row r (rows y0 - 2 .. y1 + 1; one commit group per row, empty past
-// the end): y, Dxy, Dyy always; Dxx for the rows level 1 computes; p for own
-// rows on own lanes.
-__device__ __forceinline__ void pair_issue(const PairCtx& X, int r) {
+// Copies of row r into record S (rows y0 - 2 .. y1 + 1; one commit group per
+// row, empty past the end): y, Dxy, Dyy always; Dxx for the rows level 1
+// computes; p for own rows on own lanes.
+__device__ __forceinline__ void pair_issue(const PairCtx& X, int r, float* S) {
   using PL = PairLayout;
   if (r <= X.y1 + 1 && X.L.load) {
-    float* S = pair_slot(X, r);
     const long long n = X.G.n;
     const float* F = static_cast<const float*>(X.a->coef);
     const long long off = map_row(r, X.G.nx, X.G.ny, X.G.bc).off + X.L.src;
@@ -144,14 +143,27 @@ __device__ __forceinline__ void pair_issue(const PairCtx& X, int r) {
 
 // The row copies of a warp's ring: 16-byte cp.async per lane, one commit
 // group per row.  A lane that copies nothing for its group leaves zeros.
+// Every lane reads back only the 16 bytes per field that it copied itself
+// (neighbouring columns come by shuffles), so neither the wait nor the refill
+// of a record needs a warp barrier: cp.async.wait_group makes a thread's own
+// copies visible to it, and the refill of a record is issued after the
+// thread's reads of it.  The records are used in row order, so the slot is
+// a rolling counter: the initial fill writes records 0 .. S - 1, and each
+// refill writes the record just read.
 struct CpAsyncLoader {
   static constexpr bool kReadAll = false;   // records hold data only where a lane copied
-  __device__ __forceinline__ void issue(const PairCtx& X, int r) { pair_issue(X, r); }
+  int slot = 0;                             // record of the next row read (and refilled)
+  __device__ __forceinline__ float* rec(const PairCtx& X) const {
+    return X.ring + slot * PairLayout::SIZE;
+  }
+  __device__ __forceinline__ void issue(const PairCtx& X, int r) {
+    pair_issue(X, r, rec(X));
+    slot = slot + 1 == PairLayout::STAGES ? 0 : slot + 1;
+  }
   // row r (the oldest pending group: the S - 1 younger ones stay in flight)
-  __device__ __forceinline__ const float* wait(const PairCtx& X, int r) {
+  __device__ __forceinline__ const float* wait(const PairCtx& X, int) {
     cp_async_wait_group<PairLayout::STAGES - 1>();
-    __syncwarp();
-    return pair_slot(X, r);
+    return rec(X);
   }
   __device__ __forceinline__ void drain(const PairCtx&) {
     cp_async_wait_group<0>();          // nothing may land in the ring after the run
@@ -182,7 +194,6 @@ __device__ __forceinline__ void pair_consume(const PairCtx& X, Ld& ldr, int r, P
   pair_spread(R.xx, x4, X, 1.0f);
   R.yy[0] = b4.x; R.yy[1] = b4.y; R.yy[2] = b4.z; R.yy[3] = b4.w;
   R.p[0] = p4.x; R.p[1] = p4.y; R.p[2] = p4.z; R.p[3] = p4.w;
-  __syncwarp();
   ldr.issue(X, r + X.stages);
 }
 

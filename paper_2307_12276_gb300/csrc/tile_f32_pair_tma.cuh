@@ -24,7 +24,7 @@
 // (AD_F32_TMA=1); the GPU tests hold the two bit for bit.
 //
 // Ordering: a slot is refilled by the warp that just read it; after
-// __syncwarp, lane 0 fences the generic-proxy reads against the copy
+// __syncwarp (in issue), lane 0 fences the generic-proxy reads against the copy
 // engine's writes (fence.proxy.async) before it issues the next copies.
 // Every wait is bounded (kBulkTimeoutNs of global time): on a timeout the
 // warp records status 4 in the control block, stops issuing and waiting, and
@@ -66,7 +66,10 @@ struct TmaLoader {
     return (r - (X.y0 - 2)) % X.stages;
   }
 
+  // (called by the whole warp: the barrier orders every lane's reads of the
+  // record before lane 0 hands it to the copy engine)
   __device__ __forceinline__ void issue(const PairCtx& X, int r) {
+    __syncwarp();
     if (failed || r > X.y1 + 1) return;
     using PL = PairLayout;
     const int s = slot_of(X, r);
