@@ -262,9 +262,13 @@ AD_API int ad_batch_midpoint_step(ad_batch* b, void* const* u, double t, double 
                                   const ad_source* src, double tol, int force_iters,
                                   ad_stats* per_slice);
 
-/* Chosen tile height, launch blocks, tile count and the autotuned kernel time. */
+/* Chosen tile height, launch blocks, tile count, the autotuned kernel time
+ * and the marching of the two-iteration kernels (0 plain, 1 one row of
+ * lookahead in registers, 2 the same with packed FP32 pair arithmetic; the
+ * autotuner times 1 and 2 on the persistent kernel).  Any pointer may be
+ * NULL. */
 AD_API int ad_batch_info(const ad_batch* b, int* tile_rows, int* blocks, int* ntiles,
-                         double* tuned_ms);
+                         double* tuned_ms, int* marching);
 
 /* ---------------------------------------------------------------- learned bound
  * A small network predicting, from per-field features, the spectral bound

@@ -83,7 +83,8 @@ _sig = {
     "ad_create_batch": (_i, [C.POINTER(_vp), _i, _i, C.POINTER(_vp)]),
     "ad_destroy_batch": (_i, [_vp]),
     "ad_batch_midpoint_step": (_i, [_vp, C.POINTER(_vp), _d, _d, _vp, _d, _i, C.POINTER(Stats)]),
-    "ad_batch_info": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_d)]),
+    "ad_batch_info": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_d),
+                          C.POINTER(_i)]),
     "ad_mlp_create": (_i, [_i, _i, _i, C.c_ulonglong, _vp, C.POINTER(_vp)]),
     "ad_mlp_destroy": (_i, [_vp]),
     "ad_mlp_num_params": (_i, [_vp, C.POINTER(_i)]),
@@ -459,9 +460,11 @@ def destroy_batch(b: Batch):
 
 
 def batch_info(b: Batch) -> dict:
-    ty, nb, nt, ms = _i(), _i(), _i(), _d()
-    _check(_lib.ad_batch_info(b.handle, C.byref(ty), C.byref(nb), C.byref(nt), C.byref(ms)))
-    return {"tile_rows": ty.value, "blocks": nb.value, "tiles": nt.value, "tuned_ms": ms.value}
+    ty, nb, nt, ms, mr = _i(), _i(), _i(), _d(), _i()
+    _check(_lib.ad_batch_info(b.handle, C.byref(ty), C.byref(nb), C.byref(nt), C.byref(ms),
+                              C.byref(mr)))
+    return {"tile_rows": ty.value, "blocks": nb.value, "tiles": nt.value, "tuned_ms": ms.value,
+            "marching": mr.value}
 
 
 _SOURCE_FIELDS = ("nterms", "g", "h", "ctx")

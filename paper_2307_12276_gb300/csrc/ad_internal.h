@@ -84,7 +84,7 @@ void apply_shifted_f64(const GridDev& g, const double* W, const double* u, doubl
 // Tensor maps of the FP32 two-iteration kernel's TMA row loader: the two
 // Newton-basis buffers, p and the three coefficient fields, each [ny][nx]
 // float32 with a box of 128 columns x 1 row (zero-Dirichlet grids, nx % 4 == 0).
-struct alignas(64) PairTmaMaps {
+struct PairTmaMaps {     // aligned as CUtensorMap
   CUtensorMap y[2];
   CUtensorMap p, xx, yy, xy;
 };
@@ -134,8 +134,10 @@ bool series_pair(const SeriesArgs& a);
 // ... and its row records come in by TMA (zero-Dirichlet grids with maps).
 bool series_pair_tma(const SeriesArgs& a);
 // Marching of the two-iteration kernels: 1 one row of lookahead in registers
-// (default), 0 without.
+// (default), 0 without, 2 as 1 with packed FP32 pair arithmetic.
 int pair_march();
+// The marching set by AD_F32_MARCH (0, 1 or 2), -1 when it is not set.
+int pair_march_env();
 void series_flush_pair(const SeriesArgs& a, cudaStream_t s);
 // Pair mode, after the series: u += b (p + the pending term), FP32, one pass
 // (the flush and the update axpby together; p is not written).

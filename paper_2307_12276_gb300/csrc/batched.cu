@@ -390,7 +390,8 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     X.fix = X.G.bc != 0 && (X0 == 0 || X0 + kPairOwn >= X.G.nx);
     float ly1 = 0.f, lp1 = 0.f, ly2 = 0.f, lp2 = 0.f;
     CpAsyncLoader ldr;
-    if (MODE == 1) pair_run_pf<ADV>(X, ldr, ly1, lp1, ly2, lp2);
+    if (MODE == 2) pair_run_pf<ADV, true>(X, ldr, ly1, lp1, ly2, lp2);
+    else if (MODE == 1) pair_run_pf<ADV>(X, ldr, ly1, lp1, ly2, lp2);
     else pair_run<ADV>(X, ldr, ly1, lp1, ly2, lp2);
     double q[4] = {ly1, lp1, ly2, lp2};
 #pragma unroll
@@ -534,7 +535,8 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     X.fix = X.G.bc != 0 && (X0 == 0 || X0 + kPairOwn >= X.G.nx);
     float ly1 = 0.f, lp1 = 0.f, ly2 = 0.f, lp2 = 0.f;
     CpAsyncLoader ldr;
-    if (MODE == 1) pair_run_pf<ADV>(X, ldr, ly1, lp1, ly2, lp2);
+    if (MODE == 2) pair_run_pf<ADV, true>(X, ldr, ly1, lp1, ly2, lp2);
+    else if (MODE == 1) pair_run_pf<ADV>(X, ldr, ly1, lp1, ly2, lp2);
     else pair_run<ADV>(X, ldr, ly1, lp1, ly2, lp2);
     double q[4] = {ly1, lp1, ly2, lp2};
 #pragma unroll
@@ -745,10 +747,11 @@ size_t batch_pair_smem() {
   return sizeof(float) * (size_t)kRingWarps * PairLayout::STAGES * PairLayout::SIZE;
 }
 
-void* pick_pair(int adv) {
-  static void* const fn[2][2] = {{(void*)batch_pair_k<0, 0>, (void*)batch_pair_k<1, 0>},
-                                 {(void*)batch_pair_k<0, 1>, (void*)batch_pair_k<1, 1>}};
-  return fn[pair_march()][adv == 0 ? 0 : 1];
+void* pick_pair(int adv, int march) {
+  static void* const fn[3][2] = {{(void*)batch_pair_k<0, 0>, (void*)batch_pair_k<1, 0>},
+                                 {(void*)batch_pair_k<0, 1>, (void*)batch_pair_k<1, 1>},
+                                 {(void*)batch_pair_k<0, 2>, (void*)batch_pair_k<1, 2>}};
+  return fn[march][adv == 0 ? 0 : 1];
 }
 
 template <int ADV>
@@ -823,6 +826,7 @@ struct ad_batch {
   int graph_start = -1;               // start_mode the graph was built with
   bool persist = false;               // the graph runs the persistent iteration kernel
   bool persist_off = false;           // the persistent kernel could not be built here
+  int march = 1;                      // marching of the two-iteration kernels (pair_march)
 };
 
 namespace {
@@ -907,10 +911,11 @@ int upload_ring_tiles(ad_batch* b, int R) {
 
 int ring_grid(const ad_batch* b) { return std::max(1, std::min(152, (b->nrtiles + 7) / 8)); }
 
-void* pick_persist(int adv) {
-  static void* const fn[2][2] = {{(void*)batch_persist_k<0, 0>, (void*)batch_persist_k<1, 0>},
-                                 {(void*)batch_persist_k<0, 1>, (void*)batch_persist_k<1, 1>}};
-  return fn[pair_march()][adv == 0 ? 0 : 1];
+void* pick_persist(int adv, int march) {
+  static void* const fn[3][2] = {{(void*)batch_persist_k<0, 0>, (void*)batch_persist_k<1, 0>},
+                                 {(void*)batch_persist_k<0, 1>, (void*)batch_persist_k<1, 1>},
+                                 {(void*)batch_persist_k<0, 2>, (void*)batch_persist_k<1, 2>}};
+  return fn[march][adv == 0 ? 0 : 1];
 }
 
 // Blocks of the persistent iteration kernel: one per SM when a block fits on
@@ -923,17 +928,23 @@ int persist_grid(const ad_batch* b) {
   }();
   if (off || !b->pair || b->persist_off) return 0;
   int dev = 0, sms = 0, per_sm = 0;
-  void* fn = pick_persist(b->adv);
   if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)batch_pair_smem()) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRingThreads,
-                                                    batch_pair_smem()) != cudaSuccess) {
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  return per_sm >= 1 ? sms : 0;
+  for (int march = 0; march <= 2; ++march) {    // every marching a batch may run
+    void* fn = pick_persist(b->adv, march);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)batch_pair_smem()) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRingThreads,
+                                                      batch_pair_smem()) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      return 0;
+    }
+  }
+  return sms;
 }
 
 void destroy_batch_graph(ad_batch* b) {
@@ -996,7 +1007,7 @@ int build_batch_graph(ad_batch* b, int force, double tol, int start_mode) {
   if (b->persist) {
     void* pargs[] = {&sl, &rts, &nrt, &S, &R, &rparts, &bt};
     cudaKernelNodeParams pp = kp;
-    pp.func = pick_persist(b->adv);
+    pp.func = pick_persist(b->adv, b->march);
     pp.kernelParams = pargs;
     pp.blockDim = dim3(kRingThreads);
     pp.gridDim = dim3(pgrid);
@@ -1023,7 +1034,7 @@ int build_batch_graph(ad_batch* b, int force, double tol, int start_mode) {
     void* rargs[] = {&sl, &rts, &nrt, &S, &R, &rparts, &bt, &hv, &one};
     cudaKernelNodeParams ip = kp;
     if (b->ring) {
-      ip.func = b->pair ? pick_pair(b->adv) : pick_ring(b->adv);
+      ip.func = b->pair ? pick_pair(b->adv, b->march) : pick_ring(b->adv);
       ip.kernelParams = rargs;
       ip.blockDim = dim3(kRingThreads);
       ip.gridDim = dim3(ring_grid(b));
@@ -1075,10 +1086,11 @@ std::string cache_path() {
 struct TuneEntry {
   int ty, bps;
   double ms;
+  int march;       // marching of the two-iteration kernels (1 where not tuned)
 };
 
 // The cache is a JSON object with one entry per line:
-//   "key": {"ty": 16, "bps": 4, "ms": 0.1234},
+//   "key": {"ty": 16, "bps": 4, "ms": 0.1234, "march": 1},
 std::map<std::string, TuneEntry> read_cache() {
   std::map<std::string, TuneEntry> m;
   FILE* f = fopen(cache_path().c_str(), "r");
@@ -1087,9 +1099,10 @@ std::map<std::string, TuneEntry> read_cache() {
   while (fgets(line, sizeof line, f)) {
     char key[512];
     TuneEntry e{};
-    if (sscanf(line, " \"%511[^\"]\": {\"ty\": %d, \"bps\": %d, \"ms\": %lf", key, &e.ty, &e.bps,
-               &e.ms) == 4)
-      m[key] = e;
+    e.march = 1;
+    const int got = sscanf(line, " \"%511[^\"]\": {\"ty\": %d, \"bps\": %d, \"ms\": %lf, \"march\": %d",
+                           key, &e.ty, &e.bps, &e.ms, &e.march);
+    if (got >= 4 && e.march >= 0 && e.march <= 2) m[key] = e;
   }
   fclose(f);
   return m;
@@ -1103,8 +1116,9 @@ void write_cache(const std::map<std::string, TuneEntry>& m) {
   fprintf(f, "{\n");
   size_t k = 0;
   for (const auto& kv : m) {
-    fprintf(f, "  \"%s\": {\"ty\": %d, \"bps\": %d, \"ms\": %.6f}%s\n", kv.first.c_str(), kv.second.ty,
-            kv.second.bps, kv.second.ms, (++k < m.size()) ? "," : "");
+    fprintf(f, "  \"%s\": {\"ty\": %d, \"bps\": %d, \"ms\": %.6f, \"march\": %d}%s\n",
+            kv.first.c_str(), kv.second.ty, kv.second.bps, kv.second.ms, kv.second.march,
+            (++k < m.size()) ? "," : "");
   }
   fprintf(f, "}\n");
   fclose(f);
@@ -1136,7 +1150,7 @@ int time_ring(ad_batch* b, int R, int reps, double* ms_out) {
   const int sgrid = std::min(b->ntiles, b->nblocks);
   batch_init_k<<<sgrid, kThreads, 0, b->stream>>>(b->d_slices, b->d_tile_slice, b->ntiles, b->TY,
                                                   b->S, force, maxit, tol, b->d_bticket);
-  void* fn = b->pair ? pick_pair(b->adv) : pick_ring(b->adv);
+  void* fn = b->pair ? pick_pair(b->adv, b->march) : pick_ring(b->adv);
   const size_t smem = b->pair ? batch_pair_smem() : ring_smem_for(b->adv);
   const int grid = ring_grid(b);
   cudaEvent_t e0, e1;
@@ -1185,7 +1199,7 @@ int time_persist(ad_batch* b, int R, int reps, int grid, double* ms_out) {
   unsigned int* bt = b->d_bticket;
   void* args[] = {&sl, &rts, &nrt, &S, &R, &rparts, &bt};
   B_CUDA(cudaEventRecord(e0, b->stream));
-  const cudaError_t le = cudaLaunchCooperativeKernel(pick_persist(b->adv), dim3(grid),
+  const cudaError_t le = cudaLaunchCooperativeKernel(pick_persist(b->adv, b->march), dim3(grid),
                                                      dim3(kRingThreads), args,
                                                      batch_pair_smem(), b->stream);
   B_CUDA(cudaEventRecord(e1, b->stream));
@@ -1319,8 +1333,10 @@ int ad_create_batch(ad_operator* const* ops, int nslices, int autotune, ad_batch
           cudaFuncSetAttribute(pick_ring(adv), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)ring_smem_for(adv));
         for (int adv = 0; adv < 2; ++adv)
-          cudaFuncSetAttribute(pick_pair(adv), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)batch_pair_smem());
+          for (int march = 0; march <= 2; ++march)
+            cudaFuncSetAttribute(pick_pair(adv, march),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)batch_pair_smem());
         for (int src = 0; src < 2; ++src)
           for (int adv = 0; adv < 3; ++adv)
             cudaFuncSetAttribute(pick_start(src != 0, adv),
@@ -1331,7 +1347,7 @@ int ad_create_batch(ad_operator* const* ops, int nslices, int autotune, ad_batch
     }
   }
   // tile shape: cached autotune result, a fresh autotune, or the default
-  int TY = 32, bps = 4;
+  int TY = 32, bps = 4, march = pair_march();
   double tuned = 0.0;
   const std::string key = tune_key(b);
   auto cache = read_cache();
@@ -1348,6 +1364,7 @@ int ad_create_batch(ad_operator* const* ops, int nslices, int autotune, ad_batch
     TY = it->second.ty;
     bps = it->second.bps;
     tuned = it->second.ms;
+    if (pair_march_env() < 0) march = it->second.march;
   } else if (autotune && b->ring) {
     // streaming kernels keep 256 x 32 tiles; tune the rows per warp tile
     {
@@ -1359,32 +1376,40 @@ int ad_create_batch(ad_operator* const* ops, int nslices, int autotune, ad_batch
       }
     }
     double best = 1e30;
-    // The persistent series kernel (pair mode) is tuned on itself.  Its
-    // adaptive steps end with passes over few slices, where small tiles
-    // spread the work over more warps: it takes the smallest R whose full
-    // pass is within 10 % of the fastest (on the 128-slice workload R = 64:
-    // 7.96 ms per step against 8.39 ms with the fastest full pass, R = 128).
+    // The persistent series kernel (pair mode) is tuned on itself, over the
+    // rows per warp tile and the marching of its two stencil levels (scalar
+    // or packed FP32 pairs, unless AD_F32_MARCH fixes it).  Its adaptive
+    // steps end with passes over few slices, where small tiles spread the
+    // work over more warps: it takes the smallest R whose full pass is within
+    // 10 % of the fastest (on the 128-slice workload R = 64: 7.96 ms per step
+    // against 8.39 ms with the fastest full pass, R = 128).
     const int pgrid = b->pair ? persist_grid(b) : 0;
+    const bool tune_march = pgrid > 0 && pair_march_env() < 0;
     double tr[4] = {0.0, 0.0, 0.0, 0.0};
+    int tm[4] = {march, march, march, march};
     const int rows[4] = {16, 32, 64, 128};
     for (int q = 0; q < 4; ++q) {
-      double ms = 0.0;
-      const int r = pgrid > 0 ? time_persist(b, rows[q], 6, pgrid, &ms)
-                              : time_ring(b, rows[q], 6, &ms);
-      if (r != AD_OK) {
-        std::string msg = ad_last_error();
-        ad_destroy_batch(b);
-        return bfail(r, msg);
+      tr[q] = 1e30;
+      for (int m = tune_march ? 1 : march; m <= (tune_march ? 2 : march); ++m) {
+        b->march = m;
+        double ms = 0.0;
+        const int r = pgrid > 0 ? time_persist(b, rows[q], 6, pgrid, &ms)
+                                : time_ring(b, rows[q], 6, &ms);
+        if (r != AD_OK) {
+          std::string msg = ad_last_error();
+          ad_destroy_batch(b);
+          return bfail(r, msg);
+        }
+        if (ms < tr[q]) { tr[q] = ms; tm[q] = m; }
       }
-      tr[q] = ms;
-      if (ms < best) { best = ms; TY = rows[q]; }
+      if (tr[q] < best) { best = tr[q]; TY = rows[q]; march = tm[q]; }
     }
     if (pgrid > 0)
       for (int q = 0; q < 4; ++q)
-        if (tr[q] <= 1.1 * best) { TY = rows[q]; best = tr[q]; break; }
+        if (tr[q] <= 1.1 * best) { TY = rows[q]; best = tr[q]; march = tm[q]; break; }
     bps = 1;
     tuned = best;
-    cache[key] = TuneEntry{TY, bps, best};
+    cache[key] = TuneEntry{TY, bps, best, march};
     write_cache(cache);
   } else if (autotune) {
     double best = 1e30;
@@ -1400,10 +1425,11 @@ int ad_create_batch(ad_operator* const* ops, int nslices, int autotune, ad_batch
         if (ms < best) { best = ms; TY = ty; bps = bp; }
       }
     tuned = best;
-    cache[key] = TuneEntry{TY, bps, best};
+    cache[key] = TuneEntry{TY, bps, best, march};
     write_cache(cache);
   }
   b->tuned_ms = tuned;
+  b->march = march;
   int r;
   if (b->ring) {
     b->nblocks = 152 * 4;                 // streaming kernels: 4 blocks of 256 per SM
@@ -1434,12 +1460,14 @@ int ad_destroy_batch(ad_batch* b) {
   return AD_OK;
 }
 
-int ad_batch_info(const ad_batch* b, int* tile_rows, int* blocks, int* ntiles, double* tuned_ms) {
+int ad_batch_info(const ad_batch* b, int* tile_rows, int* blocks, int* ntiles, double* tuned_ms,
+                  int* marching) {
   if (!b) return bfail(AD_ERR_INVALID, "NULL batch");
   if (tile_rows) *tile_rows = b->ring ? b->R : b->TY;
   if (blocks) *blocks = b->ring ? ring_grid(b) : std::min(b->ntiles, b->nblocks);
   if (ntiles) *ntiles = b->ring ? b->nrtiles : b->ntiles;
   if (tuned_ms) *tuned_ms = b->tuned_ms;
+  if (marching) *marching = b->march;
   return AD_OK;
 }
 

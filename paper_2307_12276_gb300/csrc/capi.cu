@@ -253,8 +253,16 @@ bool build_graph(ad_operator* op, int aug) {
   a.handle = (unsigned long long)handle;
   a.has_handle = 1;
   for (int u = 0; u < kGraphUnroll; ++u) series_iteration(a, op->cap_stream);
+  // A launch the runtime refused during capture adds no node: a loop body
+  // without its iteration kernels would never clear the loop condition, so
+  // the graph is only kept when every launch was taken.
+  const cudaError_t launched = cudaGetLastError();
   cudaGraph_t captured = nullptr;
-  if (cudaStreamEndCapture(op->cap_stream, &captured) != cudaSuccess) {
+  const cudaError_t ended = cudaStreamEndCapture(op->cap_stream, &captured);
+  size_t body_nodes = 0;
+  if (launched != cudaSuccess || ended != cudaSuccess ||
+      cudaGraphGetNodes(body, nullptr, &body_nodes) != cudaSuccess ||
+      body_nodes < (size_t)kGraphUnroll) {
     cudaGetLastError();
     cudaGraphDestroy(graph);
     return false;

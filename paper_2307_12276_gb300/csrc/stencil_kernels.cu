@@ -603,7 +603,8 @@ __global__ void __launch_bounds__(kPairWarps * 32, 1) leja_iter2_f32_ring_k(Seri
     X.gx = X0 - 4 + 4 * X.G.lane;
     X.fix = X.G.bc != 0 && (X0 == 0 || X0 + kPairOwn >= X.G.nx);
     CpAsyncLoader ldr;
-    if (MODE == 1) pair_run_pf<ADV>(X, ldr, ly1, lp1, ly2, lp2);
+    if (MODE == 2) pair_run_pf<ADV, true>(X, ldr, ly1, lp1, ly2, lp2);
+    else if (MODE == 1) pair_run_pf<ADV>(X, ldr, ly1, lp1, ly2, lp2);
     else pair_run<ADV>(X, ldr, ly1, lp1, ly2, lp2);
   }
   series_finish2(a, (double)ly1, (double)lp1, (double)ly2, (double)lp2);
@@ -800,17 +801,36 @@ __global__ void __launch_bounds__(kThreads) leja_iter_f32_k(SeriesArgs a) {
 }  // namespace
 
 // Marching of the two-iteration kernels: 1 pair_run_pf (one row of
-// lookahead in registers, the default), 0 pair_run (tuning override
-// AD_F32_MARCH=0).  Measured at 4096^2: 91.8 against 94.6 us per launch; a
-// third marching with level 2 one row further behind level 1 (two
-// independent chains per step) took 98.9 us and was dropped.
-int pair_march() {
+// lookahead in registers, the default of single series), 0 pair_run, 2
+// pair_run_pf with the stencil levels in packed FP32 pairs (AD_F32_MARCH
+// selects; batches tune 1 against 2 on their persistent kernel).  Measured
+// at 4096^2 without advection: 0: 94.6, 1: 90.7, 2: 93.5 us per launch; on the
+// 128-slice batch (constant advection) a full pass of the persistent kernel
+// takes 0.859 ms with 1 and 0.814 ms with 2.  A marching with level 2 one row
+// further behind level 1 (two independent chains per step) took 98.9 us and
+// was dropped.
+int pair_march_env() {
   static const int mode = [] {
     const char* e = getenv("AD_F32_MARCH");
-    return e && e[0] == '0' ? 0 : 1;
+    return e && e[0] >= '0' && e[0] <= '2' && e[1] == 0 ? e[0] - '0' : -1;
   }();
   return mode;
 }
+
+int pair_march() {
+  const int m = pair_march_env();
+  return m < 0 ? 1 : m;
+}
+
+namespace {
+// The two-iteration kernels by marching (pair_march) and advection (none,
+// constant): the launch picks from this table, and the shared-memory opt-in
+// runs over all of it.
+void* const kPairKernels[3][2] = {
+    {(void*)leja_iter2_f32_ring_k<0, 0>, (void*)leja_iter2_f32_ring_k<1, 0>},
+    {(void*)leja_iter2_f32_ring_k<0, 1>, (void*)leja_iter2_f32_ring_k<1, 1>},
+    {(void*)leja_iter2_f32_ring_k<0, 2>, (void*)leja_iter2_f32_ring_k<1, 2>}};
+}  // namespace
 
 // Failure-detection check of the bounded waits: one block waits on an
 // mbarrier whose phase never completes (two arrivals expected, one made) and
@@ -911,10 +931,10 @@ int series_blocks_grid(int prec, int nx, int ny) {
       AD_RING_ATTR(false, 0); AD_RING_ATTR(false, 1); AD_RING_ATTR(false, 2);
       AD_RING_ATTR(true, 0); AD_RING_ATTR(true, 1); AD_RING_ATTR(true, 2);
 #undef AD_RING_ATTR
-      for (void* fn : {(void*)leja_iter2_f32_ring_k<0, 0>, (void*)leja_iter2_f32_ring_k<1, 0>,
-                       (void*)leja_iter2_f32_ring_k<0, 1>, (void*)leja_iter2_f32_ring_k<1, 1>})
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)pair_smem_bytes());
+      for (const auto& row : kPairKernels)      // every marching the launches can pick
+        for (void* fn : row)
+          cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)pair_smem_bytes());
       cudaFuncSetAttribute((void*)leja_iter2_f32_tma_k<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)pair_tma_smem_bytes());
       cudaFuncSetAttribute((void*)leja_iter2_f32_tma_k<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1029,12 +1049,9 @@ void series_iteration(const SeriesArgs& a, cudaStream_t s) {
       else
         leja_iter2_f32_tma_k<1><<<a.nblocks, kPairWarps * 32, smem, s>>>(a, *a.tma);
     } else {
-      static void* const fn[2][2] = {
-          {(void*)leja_iter2_f32_ring_k<0, 0>, (void*)leja_iter2_f32_ring_k<1, 0>},
-          {(void*)leja_iter2_f32_ring_k<0, 1>, (void*)leja_iter2_f32_ring_k<1, 1>}};
       void* args[] = {const_cast<SeriesArgs*>(&a)};
-      cudaLaunchKernel(fn[pair_march()][a.adv == 0 ? 0 : 1], dim3(a.nblocks), dim3(kPairWarps * 32),
-                       args, pair_smem_bytes(), s);
+      cudaLaunchKernel(kPairKernels[pair_march()][a.adv == 0 ? 0 : 1], dim3(a.nblocks),
+                       dim3(kPairWarps * 32), args, pair_smem_bytes(), s);
     }
   } else if (a.f32k == 3) {
     ++launch_counter();

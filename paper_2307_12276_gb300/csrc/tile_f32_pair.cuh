@@ -42,6 +42,8 @@
 // Eligible: the phi_1 form (no augmented couplings), no advection or constant
 // advection, nx % 4 == 0, ny >= 2.
 #pragma once
+#include <type_traits>
+
 #include "tile_f32_ring.cuh"
 
 namespace ad {
@@ -243,6 +245,116 @@ __device__ __forceinline__ void pair_level(const float* uA, const float* uB, con
   }
 }
 
+// Packed FP32 pairs (the f32x2 arithmetic of sm_100 and later): each half is
+// rounded exactly as the scalar operation, so a packed expression gives the
+// scalar expression's results bit for bit with half the instructions.  Pairs
+// are formed only where both halves sit in one aligned register pair or come
+// straight from scalar results; sums across neighbouring columns of another
+// alignment stay scalar.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+      "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+
+// pair_north with packed pairs: columns (1, 2) and (3, 4) of the lane's six.
+template <int ADV>
+__device__ __forceinline__ void pair_north_x2(const float* uB, const float* uN, const float* xyB,
+                                              const float* xyN, const float* yyB, const float* yyN,
+                                              float aby, float* fn) {
+  float s[6];                           // uN + uB, the sums of both dd terms
+  s[0] = uN[0] + uB[0];
+  s[5] = uN[5] + uB[5];
+#pragma unroll
+  for (int h = 1; h < 5; h += 2) {
+    const float2 t = add2(f2(uN[h], uN[h + 1]), f2(uB[h], uB[h + 1]));
+    s[h] = t.x;
+    s[h + 1] = t.y;
+  }
+#pragma unroll
+  for (int h = 1; h < 5; h += 2) {      // columns h, h + 1
+    const int k = h - 1;
+    const float2 ayn = add2(f2(yyB[k], yyB[k + 1]), f2(yyN[k], yyN[k + 1]));
+    const float2 qn = add2(f2(xyB[h], xyB[h + 1]), f2(xyN[h], xyN[h + 1]));
+    const float2 du = sub2(f2(uN[h], uN[h + 1]), f2(uB[h], uB[h + 1]));
+    const float2 dd = f2(s[h + 1] - s[h - 1], s[h + 2] - s[h]);
+    float2 f = fma2(ayn, du, mul2(qn, dd));
+    if (ADV == 1) f = fma2(f2(aby, aby), f2(s[h], s[h + 1]), f);
+    fn[k] = f.x;
+    fn[k + 1] = f.y;
+  }
+}
+
+// pair_level with packed pairs: faces (0, 1) and (2, 3) and columns (1, 2),
+// (3, 4); face 4 scalar.
+template <int ADV>
+__device__ __forceinline__ void pair_level_x2(const float* uA, const float* uB, const float* uN,
+                                              const float* xx, const float* xyB, const float* xyN,
+                                              const float* yyB, const float* yyN, float abx,
+                                              float aby, float* fs, float ig, float sh, float* z) {
+  float fn[4];
+  pair_north_x2<ADV>(uB, uN, xyB, xyN, yyB, yyN, aby, fn);
+  float fx[5];
+#pragma unroll
+  for (int f = 0; f < 4; f += 2) {      // faces f, f + 1
+    const float2 axf = f2(xx[f] + xx[f + 1], xx[f + 1] + xx[f + 2]);
+    const float2 qf = f2(xyB[f] + xyB[f + 1], xyB[f + 1] + xyB[f + 2]);
+    const float2 du = f2(uB[f + 1] - uB[f], uB[f + 2] - uB[f + 1]);
+    const float2 sn = f2(uN[f + 1] + uN[f], uN[f + 2] + uN[f + 1]);
+    const float2 sa = f2(uA[f + 1] + uA[f], uA[f + 2] + uA[f + 1]);
+    float2 v = fma2(axf, du, mul2(qf, sub2(sn, sa)));
+    if (ADV == 1) v = fma2(f2(abx, abx), f2(uB[f] + uB[f + 1], uB[f + 1] + uB[f + 2]), v);
+    fx[f] = v.x;
+    fx[f + 1] = v.y;
+  }
+  {
+    const float axf = xx[4] + xx[5];
+    const float qf = xyB[4] + xyB[5];
+    float v = face_flux(axf, uB[5] - uB[4], qf, (uN[5] + uN[4]) - (uA[5] + uA[4]));
+    if (ADV == 1) v = fmaf(abx, uB[4] + uB[5], v);
+    fx[4] = v;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; k += 2) {      // columns k + 1, k + 2
+    const float2 au = add2(f2(fx[k + 1] - fx[k], fx[k + 2] - fx[k + 1]),
+                           sub2(f2(fn[k], fn[k + 1]), f2(fs[k], fs[k + 1])));
+    const float2 zz = fma2(au, f2(ig, ig), mul2(f2(-sh, -sh), f2(uB[k + 1], uB[k + 2])));
+    z[k] = zz.x;
+    z[k + 1] = zz.y;
+    fs[k] = fn[k];
+    fs[k + 1] = fn[k + 1];
+  }
+}
+
+// Norm-sum accumulators: one float (scalar marching) or a packed pair.
+__device__ __forceinline__ void acc_sq4(float& a, const float* v) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) a = fmaf(v[k], v[k], a);
+}
+__device__ __forceinline__ void acc_sq4(float2& a, const float* v) {
+  const float2 lo = f2(v[0], v[1]), hi = f2(v[2], v[3]);
+  a = fma2(lo, lo, a);
+  a = fma2(hi, hi, a);
+}
+__device__ __forceinline__ float acc_total(float a) { return a; }
+__device__ __forceinline__ float acc_total(float2 a) { return a.x + a.y; }
+
+template <int ADV, bool X2>
+__device__ __forceinline__ void pair_north_any(const float* uB, const float* uN, const float* xyB,
+                                               const float* xyN, const float* yyB,
+                                               const float* yyN, float aby, float* fn) {
+  if constexpr (X2) pair_north_x2<ADV>(uB, uN, xyB, xyN, yyB, yyN, aby, fn);
+  else pair_north<ADV>(uB, uN, xyB, xyN, yyB, yyN, aby, fn);
+}
+
 // A row of y_{m+1} from the level-1 values z of the lane's group: with zero
 // Dirichlet, column -1 (in the group left of column 0) and column nx (in the
 // group right of nx - 1) become the odd reflection of their mirror; then the
@@ -259,26 +371,57 @@ __device__ __forceinline__ void pair_y1(float* u, const float* z, const PairCtx&
   u[5] = __shfl_down_sync(0xffffffffu, u[1], 1);
 }
 
-// Level 1 on row r (A, B, N: rows r - 1 .. r + 1 of y_m) into u1; on an own
-// row also p_{m+1} = p_m + d_m y_m + d_{m+1} y_{m+1} (stored, and kept in B.p
-// for level 2) and the level-1 norm terms.
-template <int ADV>
+// Level 1 on row r (A, B, N: rows r - 1 .. r + 1 of y_m) into u1; on a row of
+// the run also p_{m+1} = p_m + d_m y_m + d_{m+1} y_{m+1} (stored by own lanes,
+// and kept in B.p for level 2) and the level-1 norm terms.  Every lane forms
+// the terms (no divergent branch); the run's sums of lanes that own no group
+// are dropped when the run ends (pair_run_sums).
+template <int ADV, bool X2 = false, class Acc>
 __device__ __forceinline__ void pair_level1(const PairCtx& X, int r, const PRow& A, PRow& B,
-                                            const PRow& N, float* fs1, float* u1, float& ly1,
-                                            float& lp1) {
+                                            const PRow& N, float* fs1, float* u1, Acc& ly1,
+                                            Acc& lp1) {
   float z[4];
-  pair_level<ADV>(A.y, B.y, N.y, B.xx, B.xy, N.xy, B.yy, N.yy, X.abx, X.aby, fs1, X.ig, X.sh1, z);
+  if constexpr (X2)
+    pair_level_x2<ADV>(A.y, B.y, N.y, B.xx, B.xy, N.xy, B.yy, N.yy, X.abx, X.aby, fs1, X.ig,
+                       X.sh1, z);
+  else
+    pair_level<ADV>(A.y, B.y, N.y, B.xx, B.xy, N.xy, B.yy, N.yy, X.abx, X.aby, fs1, X.ig, X.sh1, z);
   pair_y1(u1, z, X);
-  if (X.L.own && r >= X.y0 && r < X.y1) {
+  if (r >= X.y0 && r < X.y1) {               // uniform over the warp
+    if constexpr (X2) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float pm = fmaf(X.d0, B.y[k + 1], B.p[k]);   // the pending d_m y_m
-      B.p[k] = fmaf(X.d1, z[k], pm);
-      ly1 = fmaf(z[k], z[k], ly1);
-      lp1 = fmaf(B.p[k], B.p[k], lp1);
+      for (int k = 0; k < 4; k += 2) {
+        const float2 pm = fma2(f2(X.d0, X.d0), f2(B.y[k + 1], B.y[k + 2]), f2(B.p[k], B.p[k + 1]));
+        const float2 pn = fma2(f2(X.d1, X.d1), f2(z[k], z[k + 1]), pm);
+        B.p[k] = pn.x;
+        B.p[k + 1] = pn.y;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float pm = fmaf(X.d0, B.y[k + 1], B.p[k]);   // the pending d_m y_m
+        B.p[k] = fmaf(X.d1, z[k], pm);
+      }
     }
+    acc_sq4(ly1, z);
+    acc_sq4(lp1, B.p);
     const long long idx = (long long)r * X.G.nx + X.gx;
-    *reinterpret_cast<float4*>(X.p + idx) = make_float4(B.p[0], B.p[1], B.p[2], B.p[3]);
+    if (X.L.own)
+      *reinterpret_cast<float4*>(X.p + idx) = make_float4(B.p[0], B.p[1], B.p[2], B.p[3]);
+  }
+}
+
+// The norm sums of one run added to the thread's totals: only lanes that own
+// their group contribute (the others' terms may come from records they never
+// filled).
+template <class Acc>
+__device__ __forceinline__ void pair_run_sums(const PairCtx& X, const Acc* r, float& ly1,
+                                              float& lp1, float& ly2, float& lp2) {
+  if (X.L.own) {
+    ly1 += acc_total(r[0]);
+    lp1 += acc_total(r[1]);
+    ly2 += acc_total(r[2]);
+    lp2 += acc_total(r[3]);
   }
 }
 
@@ -300,16 +443,14 @@ __device__ __forceinline__ void pair_step(const PairCtx& X, Ld& ldr, int j, PRow
   // level 2 on row j: coefficient rows j (A) and j + 1 (B)
   float z[4];
   pair_level<ADV>(Ua, Ub, Un, A.xx, A.xy, B.xy, A.yy, B.yy, X.abx, X.aby, fs2, X.ig, X.sh2, z);
-  if (X.L.own) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float p2 = fmaf(X.d2, z[k], A.p[k]);
-      ly2 = fmaf(z[k], z[k], ly2);
-      lp2 = fmaf(p2, p2, lp2);
-    }
-    const long long idx = (long long)j * X.G.nx + X.gx;
-    *reinterpret_cast<float4*>(X.yout + idx) = make_float4(z[0], z[1], z[2], z[3]);
+  for (int k = 0; k < 4; ++k) {
+    const float p2 = fmaf(X.d2, z[k], A.p[k]);
+    ly2 = fmaf(z[k], z[k], ly2);
+    lp2 = fmaf(p2, p2, lp2);
   }
+  const long long idx = (long long)j * X.G.nx + X.gx;
+  if (X.L.own) *reinterpret_cast<float4*>(X.yout + idx) = make_float4(z[0], z[1], z[2], z[3]);
 }
 
 // One marching run of rows [y0, y1) (X.y0, X.y1) of the strip of X, its rows
@@ -317,6 +458,7 @@ __device__ __forceinline__ void pair_step(const PairCtx& X, Ld& ldr, int j, PRow
 template <int ADV, class Ld>
 __device__ __forceinline__ void pair_run(const PairCtx& X, Ld& ldr, float& ly1, float& lp1,
                                          float& ly2, float& lp2) {
+  float rs[4] = {0.f, 0.f, 0.f, 0.f};   // this run's norm sums
   const int y0 = X.y0, y1 = X.y1;
   __syncwarp();
 #pragma unroll 1
@@ -327,9 +469,9 @@ __device__ __forceinline__ void pair_run(const PairCtx& X, Ld& ldr, float& ly1, 
   pair_consume(X, ldr, y0 - 1, r1);
   pair_north<ADV>(r0.y, r1.y, r0.xy, r1.xy, r0.yy, r1.yy, X.aby, fs1);   // south faces, row y0 - 1
   pair_consume(X, ldr, y0, r2);
-  pair_level1<ADV>(X, y0 - 1, r0, r1, r2, fs1, u1, ly1, lp1);
+  pair_level1<ADV>(X, y0 - 1, r0, r1, r2, fs1, u1, rs[0], rs[1]);
   pair_consume(X, ldr, y0 + 1, r0);
-  pair_level1<ADV>(X, y0, r1, r2, r0, fs1, u2, ly1, lp1);
+  pair_level1<ADV>(X, y0, r1, r2, r0, fs1, u2, rs[0], rs[1]);
   if (X.G.bc != 0 && y0 == 0) {               // y_{m+1} row -1 = -(row 0)
 #pragma unroll
     for (int k = 0; k < 6; ++k) u1[k] = -u2[k];
@@ -340,52 +482,65 @@ __device__ __forceinline__ void pair_run(const PairCtx& X, Ld& ldr, float& ly1, 
   int j = y0;
 #pragma unroll 1
   for (; j + 3 <= y1; j += 3) {
-    pair_step<ADV>(X, ldr, j, r2, r0, r1, u1, u2, u0, fs1, fs2, ly1, lp1, ly2, lp2);
-    pair_step<ADV>(X, ldr, j + 1, r0, r1, r2, u2, u0, u1, fs1, fs2, ly1, lp1, ly2, lp2);
-    pair_step<ADV>(X, ldr, j + 2, r1, r2, r0, u0, u1, u2, fs1, fs2, ly1, lp1, ly2, lp2);
+    pair_step<ADV>(X, ldr, j, r2, r0, r1, u1, u2, u0, fs1, fs2, rs[0], rs[1], rs[2], rs[3]);
+    pair_step<ADV>(X, ldr, j + 1, r0, r1, r2, u2, u0, u1, fs1, fs2, rs[0], rs[1], rs[2], rs[3]);
+    pair_step<ADV>(X, ldr, j + 2, r1, r2, r0, u0, u1, u2, fs1, fs2, rs[0], rs[1], rs[2], rs[3]);
   }
-  if (j < y1) pair_step<ADV>(X, ldr, j, r2, r0, r1, u1, u2, u0, fs1, fs2, ly1, lp1, ly2, lp2);
+  if (j < y1) pair_step<ADV>(X, ldr, j, r2, r0, r1, u1, u2, u0, fs1, fs2, rs[0], rs[1], rs[2], rs[3]);
   if (j + 1 < y1)
-    pair_step<ADV>(X, ldr, j + 1, r0, r1, r2, u2, u0, u1, fs1, fs2, ly1, lp1, ly2, lp2);
+    pair_step<ADV>(X, ldr, j + 1, r0, r1, r2, u2, u0, u1, fs1, fs2, rs[0], rs[1], rs[2], rs[3]);
   ldr.drain(X);
+  pair_run_sums(X, rs, ly1, lp1, ly2, lp2);
 }
 
 // Step j with the next row prefetched: on entry A, B, N hold rows j, j + 1,
 // j + 2 (N was read by the previous step) and Q is free; Q receives row
 // j + 3 first, so its shared-memory loads and shuffles overlap this step's
 // arithmetic instead of heading its dependency chain.  Otherwise pair_step.
-// The next step's roles are (B, N, Q, A) and (Ub, Un, Ua's successor).
-template <int ADV, class Ld>
+// The next step's roles are (B, N, Q, A) and (Ub, Un, Ua's successor).  X2:
+// the levels in packed pairs (same results).
+template <int ADV, bool X2, class Ld, class Acc>
 __device__ __forceinline__ void pair_step_pf(const PairCtx& X, Ld& ldr, int j, PRow& A, PRow& B,
                                              PRow& N, PRow& Q, const float* Ua, const float* Ub,
-                                             float* Un, float* fs1, float* fs2, float& ly1,
-                                             float& lp1, float& ly2, float& lp2) {
+                                             float* Un, float* fs1, float* fs2, Acc& ly1,
+                                             Acc& lp1, Acc& ly2, Acc& lp2) {
   if (j + 3 <= X.y1 + 1) pair_consume(X, ldr, j + 3, Q);   // rows are issued up to y1 + 1
-  pair_level1<ADV>(X, j + 1, A, B, N, fs1, Un, ly1, lp1);
+  pair_level1<ADV, X2>(X, j + 1, A, B, N, fs1, Un, ly1, lp1);
   if (X.G.bc != 0 && j + 1 == X.G.ny) {     // y_{m+1} row ny = -(row ny - 1)
 #pragma unroll
     for (int k = 0; k < 6; ++k) Un[k] = -Ub[k];
   }
-  float z[4];
-  pair_level<ADV>(Ua, Ub, Un, A.xx, A.xy, B.xy, A.yy, B.yy, X.abx, X.aby, fs2, X.ig, X.sh2, z);
-  if (X.L.own) {
+  float z[4], p2[4];
+  if constexpr (X2) {
+    pair_level_x2<ADV>(Ua, Ub, Un, A.xx, A.xy, B.xy, A.yy, B.yy, X.abx, X.aby, fs2, X.ig, X.sh2,
+                       z);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float p2 = fmaf(X.d2, z[k], A.p[k]);
-      ly2 = fmaf(z[k], z[k], ly2);
-      lp2 = fmaf(p2, p2, lp2);
+    for (int k = 0; k < 4; k += 2) {
+      const float2 t = fma2(f2(X.d2, X.d2), f2(z[k], z[k + 1]), f2(A.p[k], A.p[k + 1]));
+      p2[k] = t.x;
+      p2[k + 1] = t.y;
     }
-    const long long idx = (long long)j * X.G.nx + X.gx;
-    *reinterpret_cast<float4*>(X.yout + idx) = make_float4(z[0], z[1], z[2], z[3]);
+  } else {
+    pair_level<ADV>(Ua, Ub, Un, A.xx, A.xy, B.xy, A.yy, B.yy, X.abx, X.aby, fs2, X.ig, X.sh2, z);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) p2[k] = fmaf(X.d2, z[k], A.p[k]);
   }
+  acc_sq4(ly2, z);
+  acc_sq4(lp2, p2);
+  const long long idx = (long long)j * X.G.nx + X.gx;
+  if (X.L.own) *reinterpret_cast<float4*>(X.yout + idx) = make_float4(z[0], z[1], z[2], z[3]);
 }
 
 // pair_run with one row of lookahead in registers: four row records and four
 // y_{m+1} rows rotate with period 4 (the loop is unrolled four times, so no
-// row is copied).  The same operations in the same order as pair_run.
-template <int ADV, class Ld>
+// row is copied).  The same operations in the same order as pair_run; with
+// X2 the levels run in packed pairs and each norm sum is kept as two
+// interleaved partial sums.
+template <int ADV, bool X2 = false, class Ld>
 __device__ __forceinline__ void pair_run_pf(const PairCtx& X, Ld& ldr, float& ly1, float& lp1,
                                             float& ly2, float& lp2) {
+  using Acc = std::conditional_t<X2, float2, float>;
+  Acc rs[4] = {};                       // this run's norm sums
   const int y0 = X.y0, y1 = X.y1;
   __syncwarp();
 #pragma unroll 1
@@ -394,34 +549,35 @@ __device__ __forceinline__ void pair_run_pf(const PairCtx& X, Ld& ldr, float& ly
   float U0[6], U1[6], U2[6], U3[6], fs1[4], fs2[4];
   pair_consume(X, ldr, y0 - 2, R0);
   pair_consume(X, ldr, y0 - 1, R1);
-  pair_north<ADV>(R0.y, R1.y, R0.xy, R1.xy, R0.yy, R1.yy, X.aby, fs1);   // south faces, row y0 - 1
+  pair_north_any<ADV, X2>(R0.y, R1.y, R0.xy, R1.xy, R0.yy, R1.yy, X.aby, fs1);   // south faces, row y0 - 1
   pair_consume(X, ldr, y0, R2);
-  pair_level1<ADV>(X, y0 - 1, R0, R1, R2, fs1, U1, ly1, lp1);
+  pair_level1<ADV, X2>(X, y0 - 1, R0, R1, R2, fs1, U1, rs[0], rs[1]);
   pair_consume(X, ldr, y0 + 1, R3);
-  pair_level1<ADV>(X, y0, R1, R2, R3, fs1, U2, ly1, lp1);
+  pair_level1<ADV, X2>(X, y0, R1, R2, R3, fs1, U2, rs[0], rs[1]);
   if (X.G.bc != 0 && y0 == 0) {               // y_{m+1} row -1 = -(row 0)
 #pragma unroll
     for (int k = 0; k < 6; ++k) U1[k] = -U2[k];
   }
   // south faces of level 2 on row y0: coefficient rows y0 - 1 (R1) and y0 (R2)
-  pair_north<ADV>(U1, U2, R1.xy, R2.xy, R1.yy, R2.yy, X.aby, fs2);
+  pair_north_any<ADV, X2>(U1, U2, R1.xy, R2.xy, R1.yy, R2.yy, X.aby, fs2);
   pair_consume(X, ldr, y0 + 2, R0);           // y0 + 2 <= y1 + 1: always issued
   // rows: R2 = y0, R3 = y0 + 1, R0 = y0 + 2, R1 free; y_{m+1}: U1 = y0 - 1, U2 = y0
   int j = y0;
 #pragma unroll 1
   for (; j + 4 <= y1; j += 4) {
-    pair_step_pf<ADV>(X, ldr, j, R2, R3, R0, R1, U1, U2, U3, fs1, fs2, ly1, lp1, ly2, lp2);
-    pair_step_pf<ADV>(X, ldr, j + 1, R3, R0, R1, R2, U2, U3, U0, fs1, fs2, ly1, lp1, ly2, lp2);
-    pair_step_pf<ADV>(X, ldr, j + 2, R0, R1, R2, R3, U3, U0, U1, fs1, fs2, ly1, lp1, ly2, lp2);
-    pair_step_pf<ADV>(X, ldr, j + 3, R1, R2, R3, R0, U0, U1, U2, fs1, fs2, ly1, lp1, ly2, lp2);
+    pair_step_pf<ADV, X2>(X, ldr, j, R2, R3, R0, R1, U1, U2, U3, fs1, fs2, rs[0], rs[1], rs[2], rs[3]);
+    pair_step_pf<ADV, X2>(X, ldr, j + 1, R3, R0, R1, R2, U2, U3, U0, fs1, fs2, rs[0], rs[1], rs[2], rs[3]);
+    pair_step_pf<ADV, X2>(X, ldr, j + 2, R0, R1, R2, R3, U3, U0, U1, fs1, fs2, rs[0], rs[1], rs[2], rs[3]);
+    pair_step_pf<ADV, X2>(X, ldr, j + 3, R1, R2, R3, R0, U0, U1, U2, fs1, fs2, rs[0], rs[1], rs[2], rs[3]);
   }
   if (j < y1)
-    pair_step_pf<ADV>(X, ldr, j, R2, R3, R0, R1, U1, U2, U3, fs1, fs2, ly1, lp1, ly2, lp2);
+    pair_step_pf<ADV, X2>(X, ldr, j, R2, R3, R0, R1, U1, U2, U3, fs1, fs2, rs[0], rs[1], rs[2], rs[3]);
   if (j + 1 < y1)
-    pair_step_pf<ADV>(X, ldr, j + 1, R3, R0, R1, R2, U2, U3, U0, fs1, fs2, ly1, lp1, ly2, lp2);
+    pair_step_pf<ADV, X2>(X, ldr, j + 1, R3, R0, R1, R2, U2, U3, U0, fs1, fs2, rs[0], rs[1], rs[2], rs[3]);
   if (j + 2 < y1)
-    pair_step_pf<ADV>(X, ldr, j + 2, R0, R1, R2, R3, U3, U0, U1, fs1, fs2, ly1, lp1, ly2, lp2);
+    pair_step_pf<ADV, X2>(X, ldr, j + 2, R0, R1, R2, R3, U3, U0, U1, fs1, fs2, rs[0], rs[1], rs[2], rs[3]);
   ldr.drain(X);
+  pair_run_sums(X, rs, ly1, lp1, ly2, lp2);
 }
 
 }  // namespace

@@ -106,9 +106,12 @@ def test_autotune_cache_round_trip(tmp_path, monkeypatch):
     assert len(data) == 1
     entry = next(iter(data.values()))
     assert entry["ty"] == info1["tile_rows"] and entry["ty"] in (8, 16, 32, 64, 128)
+    assert entry["march"] == info1["marching"] and entry["march"] in (0, 1, 2)
     _, _, b2 = _build(autotune=True)            # served from the cache
-    assert ad().batch_info(b2)["tile_rows"] == info1["tile_rows"]
-    assert abs(ad().batch_info(b2)["tuned_ms"] - entry["ms"]) < 1e-6
+    info2 = ad().batch_info(b2)
+    assert info2["tile_rows"] == info1["tile_rows"]
+    assert info2["marching"] == info1["marching"]
+    assert abs(info2["tuned_ms"] - entry["ms"]) < 1e-6
 
 
 def test_unconverged_slice_keeps_its_state():
@@ -248,15 +251,18 @@ print(json.dumps(stats))
 """
 
 
-def test_pair_batch_equals_ring_batch(tmp_path):
-    """The two-iteration batch kernel forms every entry as the one-iteration
-    ring kernel does (AD_F32_PAIR=0): with equal counts, identical results."""
+@pytest.mark.parametrize("march", ["1", "2"])
+def test_pair_batch_equals_ring_batch(tmp_path, march):
+    """The two-iteration batch kernel, with either marching the autotuner
+    chooses from (scalar or packed FP32 pair arithmetic), forms every entry
+    as the one-iteration ring kernel does (AD_F32_PAIR=0): with equal counts,
+    identical results."""
     need_gpu()
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     res = {}
-    for tag, env_extra in (("pair", {}), ("ring", {"AD_F32_PAIR": "0"})):
+    for tag, env_extra in (("pair", {"AD_F32_MARCH": march}), ("ring", {"AD_F32_PAIR": "0"})):
         env = dict(os.environ)
         env.update(env_extra)
         env["AD_AUTOTUNE_CACHE"] = str(tmp_path / f"tune_{tag}.json")

@@ -90,11 +90,12 @@ def _run(case, prefix, env_extra):
 
 
 @pytest.mark.parametrize("case", CASES)
-@pytest.mark.parametrize("march", ["0", "1"])
+@pytest.mark.parametrize("march", ["0", "1", "2"])
 def test_two_iteration_kernel_equals_one_iteration_kernel(case, march, tmp_path):
-    """Both marchings of the two-iteration kernel (0 plain, 1 with one row of
-    lookahead in registers) form the same values in the same order as the
-    one-iteration kernel."""
+    """Every marching of the two-iteration kernel (0 plain, 1 with one row of
+    lookahead in registers, 2 the same with the stencil levels in packed FP32
+    pairs) forms the same values in the same order as the one-iteration
+    kernel."""
     need_gpu()
     s2, a2 = _run(case, str(tmp_path / "pair"), {"AD_F32_MARCH": march})
     s1, a1 = _run(case, str(tmp_path / "single"), {"AD_F32_PAIR": "0"})
