@@ -1133,6 +1133,8 @@ std::string tune_key(const ad_batch* b) {
                                       : (b->ring ? "ring" : "tile")) + "-f32-adv" +
                   std::to_string(b->adv) +
                   "-S" + std::to_string(b->S);
+  if (b->pair && pair_march_env() >= 0)       // a marching fixed by AD_F32_MARCH is not tuned
+    k += "-march" + std::to_string(pair_march_env());
   for (const auto& kv : sizes)
     k += "-" + std::to_string(kv.first.first) + "x" + std::to_string(kv.first.second) + "*" +
          std::to_string(kv.second);
