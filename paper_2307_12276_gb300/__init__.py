@@ -151,25 +151,36 @@ def _check(status: int, stats: Optional[Stats] = None):
     raise cls(status, last_error(), d)
 
 
+_TORCH = None
+
+
+def _torch_types():
+    """(torch.Tensor, {dtype name: torch dtype}) once torch is importable, else None."""
+    global _TORCH
+    if _TORCH is None:
+        try:
+            import torch
+            _TORCH = (torch.Tensor, {"float64": torch.float64, "float32": torch.float32})
+        except ImportError:
+            _TORCH = False
+    return _TORCH
+
+
 def _ptr(x, dtype_name: str, n: int, what: str):
     """Pointer of a contiguous tensor/array with n elements of the given dtype."""
     if x is None:
         return None
     if isinstance(x, int):
         return x
-    try:
-        import torch
-        if isinstance(x, torch.Tensor):
-            want = {"float64": torch.float64, "float32": torch.float32}[dtype_name]
-            if x.dtype != want:
-                raise TypeError(f"{what}: expected {dtype_name}, got {x.dtype}")
-            if not x.is_contiguous():
-                raise ValueError(f"{what}: tensor must be contiguous")
-            if x.numel() != n:
-                raise ValueError(f"{what}: expected {n} elements, got {x.numel()}")
-            return x.data_ptr()
-    except ImportError:
-        pass
+    tt = _torch_types()
+    if tt and isinstance(x, tt[0]):
+        if x.dtype != tt[1][dtype_name]:
+            raise TypeError(f"{what}: expected {dtype_name}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError(f"{what}: tensor must be contiguous")
+        if x.numel() != n:
+            raise ValueError(f"{what}: expected {n} elements, got {x.numel()}")
+        return x.data_ptr()
     import numpy as np
     if isinstance(x, np.ndarray):
         if x.dtype != np.dtype(dtype_name):
