@@ -981,7 +981,7 @@ def measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, fields, dt, 
     # operators recorded at creation
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    alpha, it_pred = learned.predict_bounds(model, ops, dt, margin=margin)
+    alpha, it_pred = learned.predict_bounds(model, ops, dt, margin=margin, batch=batch)
     torch.cuda.synchronize()
     predict_s = time.perf_counter() - t0
     for s in range(len(us)):

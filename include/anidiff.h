@@ -262,6 +262,21 @@ AD_API int ad_batch_midpoint_step(ad_batch* b, void* const* u, double t, double 
                                   const ad_source* src, double tol, int force_iters,
                                   ad_stats* per_slice);
 
+/* Queue order of the slices' warp tiles.  In every pass of the batched
+ * series the tiles of the slices expected to iterate longest are handed out
+ * first, so that the longest series, which bound the step, do not wait behind
+ * slices that stop earlier.  iters: nslices expected Leja iteration counts
+ * (e.g. the learned model's predictions from ad_learned_bounds), or NULL for
+ * slice order.  After every step the batch re-queues the slices by the counts
+ * that step took (AD_BATCH_ORDER=0 keeps the order set here).  The order
+ * changes no result: each slice's tile sums keep their order.  Takes effect
+ * at the next ad_batch_midpoint_step; AD_ERR_INVALID for a non-finite count. */
+AD_API int ad_batch_iteration_hint(ad_batch* b, const double* iters);
+
+/* The current queue order: order[q] is the slice queued q-th (nslices ints,
+ * caller memory). */
+AD_API int ad_batch_order(const ad_batch* b, int* order);
+
 /* Chosen tile height, launch blocks, tile count, the autotuned kernel time
  * and the marching of the two-iteration kernels (0 plain, 1 one row of
  * lookahead in registers, 2 the same with packed FP32 pair arithmetic; the

@@ -83,6 +83,8 @@ _sig = {
     "ad_create_batch": (_i, [C.POINTER(_vp), _i, _i, C.POINTER(_vp)]),
     "ad_destroy_batch": (_i, [_vp]),
     "ad_batch_midpoint_step": (_i, [_vp, C.POINTER(_vp), _d, _d, _vp, _d, _i, C.POINTER(Stats)]),
+    "ad_batch_iteration_hint": (_i, [_vp, _vp]),
+    "ad_batch_order": (_i, [_vp, _vp]),
     "ad_batch_info": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_d),
                           C.POINTER(_i)]),
     "ad_mlp_create": (_i, [_i, _i, _i, C.c_ulonglong, _vp, C.POINTER(_vp)]),
@@ -468,6 +470,27 @@ def create_batch(ops, autotune: bool = True) -> Batch:
 
 def destroy_batch(b: Batch):
     b.close()
+
+
+def batch_iteration_hint(b: Batch, iters=None) -> None:
+    """ad_batch_iteration_hint: expected Leja iterations per slice (the longest
+    series are queued first in every pass), or None for slice order."""
+    import numpy as np
+    if iters is None:
+        _check(_lib.ad_batch_iteration_hint(b.handle, None))
+        return
+    arr = np.ascontiguousarray(np.asarray(iters, dtype=np.float64))
+    if arr.size != len(b.ops):
+        raise ValueError("one iteration hint per slice")
+    _check(_lib.ad_batch_iteration_hint(b.handle, arr.ctypes.data))
+
+
+def batch_order(b: Batch) -> list:
+    """ad_batch_order: the slices in the queue order of their warp tiles."""
+    import numpy as np
+    out = np.zeros(len(b.ops), dtype=np.int32)
+    _check(_lib.ad_batch_order(b.handle, out.ctypes.data))
+    return out.tolist()
 
 
 def batch_info(b: Batch) -> dict:

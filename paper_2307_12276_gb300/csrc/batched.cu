@@ -827,6 +827,11 @@ struct ad_batch {
   bool persist = false;               // the graph runs the persistent iteration kernel
   bool persist_off = false;           // the persistent kernel could not be built here
   int march = 1;                      // marching of the two-iteration kernels (pair_march)
+  // Queue order of the slices' warp tiles (empty: slice order): slices expected
+  // to iterate longest first, from ad_batch_iteration_hint and then from the
+  // counts of each step; order_dirty asks the next step to rebuild the list.
+  std::vector<int> order;
+  bool order_dirty = false;
 };
 
 namespace {
@@ -881,9 +886,10 @@ int upload_tiles(ad_batch* b, int TY) {
 }
 
 // Warp-tile table for rows per tile R: slice s owns ring tiles [rt_off, rt_off + rt_n).
-int upload_ring_tiles(ad_batch* b, int R) {
+int upload_ring_tiles(ad_batch* b, int R, bool sync = true) {
   std::vector<int> ts;
-  for (int s = 0; s < b->S; ++s) {
+  for (int q = 0; q < b->S; ++q) {
+    const int s = b->order.empty() ? q : b->order[q];
     BatchSlice& hs = b->hs[s];
     const int cols = b->pair ? kPairOwn : kVecCols;
     hs.rt_x = (hs.a.g.nx + cols - 1) / cols;
@@ -905,8 +911,32 @@ int upload_ring_tiles(ad_batch* b, int R) {
                          cudaMemcpyHostToDevice, b->stream));
   B_CUDA(cudaMemcpyAsync(b->d_slices, b->hs.data(), sizeof(BatchSlice) * b->S,
                          cudaMemcpyHostToDevice, b->stream));
-  B_CUDA(cudaStreamSynchronize(b->stream));
+  if (sync) B_CUDA(cudaStreamSynchronize(b->stream));
   return AD_OK;
+}
+
+// Queue the slices' warp tiles by decreasing expected iteration count (ties in
+// slice order).  In every pass the series that run longest are then handed
+// out first, so their next pass is not held behind the tiles of slices that
+// stop earlier; the tile sums of each slice keep their order, so results do
+// not depend on the queue order.
+void order_by_iterations(ad_batch* b, const double* iters) {
+  std::vector<int> o(b->S);
+  for (int s = 0; s < b->S; ++s) o[s] = s;
+  if (iters)
+    std::stable_sort(o.begin(), o.end(), [&](int x, int y) { return iters[x] > iters[y]; });
+  if (o != b->order) {
+    b->order = o;
+    b->order_dirty = true;
+  }
+}
+
+bool order_auto() {
+  static const bool on = [] {
+    const char* e = getenv("AD_BATCH_ORDER");         // tuning override: 0 keeps slice order
+    return !(e && e[0] == '0');
+  }();
+  return on;
 }
 
 int ring_grid(const ad_batch* b) { return std::max(1, std::min(152, (b->nrtiles + 7) / 8)); }
@@ -1473,6 +1503,23 @@ int ad_batch_info(const ad_batch* b, int* tile_rows, int* blocks, int* ntiles, d
   return AD_OK;
 }
 
+int ad_batch_iteration_hint(ad_batch* b, const double* iters) {
+  set_error_message("");
+  if (!b) return bfail(AD_ERR_INVALID, "NULL batch");
+  if (iters)
+    for (int s = 0; s < b->S; ++s)
+      if (!std::isfinite(iters[s])) return bfail(AD_ERR_INVALID, "iteration hints must be finite");
+  order_by_iterations(b, iters);
+  return AD_OK;
+}
+
+int ad_batch_order(const ad_batch* b, int* order) {
+  set_error_message("");
+  if (!b || !order) return bfail(AD_ERR_INVALID, "NULL argument");
+  for (int q = 0; q < b->S; ++q) order[q] = b->order.empty() ? q : b->order[q];
+  return AD_OK;
+}
+
 int ad_batch_midpoint_step(ad_batch* b, void* const* u, double t, double dt,
                            const ad_source* src, double tol, int force_iters,
                            ad_stats* per_slice) {
@@ -1520,6 +1567,11 @@ int ad_batch_midpoint_step(ad_batch* b, void* const* u, double t, double dt,
       lc_dirty = true;
     }
   }
+  if (b->ring && b->order_dirty) {         // a new queue order of the warp tiles
+    const int r = upload_ring_tiles(b, b->R, false);
+    if (r != AD_OK) return r;
+    b->order_dirty = false;
+  }
   if (lc_dirty)
     B_CUDA(cudaMemcpyAsync(b->d_lc, b->h_lc.data(), sizeof(LejaCoef) * b->h_lc.size(),
                            cudaMemcpyHostToDevice, b->stream));
@@ -1564,6 +1616,11 @@ int ad_batch_midpoint_step(ad_batch* b, void* const* u, double t, double dt,
       st.err_est = c.pnorm2 > 0.0 ? c.err_est * std::sqrt(c.ynorm2 / c.pnorm2) : 0.0;
       st.alpha = b->lc_alpha[s];
     }
+  }
+  if (b->ring && order_auto()) {           // the next step queues the longest series first
+    std::vector<double> it(b->S);
+    for (int s = 0; s < b->S; ++s) it[s] = b->h_ctrl[s].iters;
+    order_by_iterations(b, it.data());
   }
   if (per_slice) {
     // kernels of the whole batched step: apply, init, update and every kernel of

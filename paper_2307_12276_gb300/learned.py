@@ -20,9 +20,9 @@ from typing import Sequence
 
 import numpy as np
 
-from . import (BC_DIRICHLET0, BC_PERIODIC, BOUND_POWER, FP64, MLP, batch_midpoint_step,
-               bound_training_sample, create_operator, expquad_step, learned_bounds,
-               spectral_bound)
+from . import (BC_DIRICHLET0, BC_PERIODIC, BOUND_POWER, FP64, MLP, batch_iteration_hint,
+               batch_midpoint_step, bound_training_sample, create_operator, expquad_step,
+               learned_bounds, spectral_bound)
 
 # training-field sides and their weights: every side class contributes about
 # the same number of cells, so large grids are rare but present
@@ -110,10 +110,15 @@ def train_bound_model(X, Y, device, epochs=3000, lr=3e-3, seed=0, hidden=64) -> 
     return m
 
 
-def predict_bounds(model: MLP, ops, dt, margin=1.1, bf16=True):
+def predict_bounds(model: MLP, ops, dt, margin=1.1, bf16=True, batch=None):
     """Every operator's bound from the model (ad_learned_bounds, which also
-    sets it); returns (alphas, predicted iterations)."""
-    return learned_bounds(model, ops, dt, margin=margin, bf16=bf16)
+    sets it); returns (alphas, predicted iterations).  With a batch of these
+    operators, the predicted iteration counts also set its queue order
+    (ad_batch_iteration_hint: the longest series first in every pass)."""
+    alpha, iters = learned_bounds(model, ops, dt, margin=margin, bf16=bf16)
+    if batch is not None:
+        batch_iteration_hint(batch, iters)
+    return alpha, iters
 
 
 def batched_step_with_fallback(batch, ops, us, t, dt, sources, tol, power_iters=40):

@@ -306,3 +306,34 @@ def test_persistent_batch_equals_graph_loop(tmp_path):
         assert sp["launches_" + key] == 3 < sl["launches_" + key], key
     for key in al.files:
         assert np.array_equal(ap[key], al[key]), key
+
+
+def test_queue_order_follows_iterations_and_changes_no_result():
+    """ad_batch_iteration_hint queues the slices expected to iterate longest
+    first; after each step the batch re-queues them by that step's counts
+    (decreasing, ties in slice order); the queue order changes no result (each
+    slice's tile sums keep their order), whatever it is."""
+    need_gpu()
+    slices, ops, batch = _build(sizes=SIZES_PAIR)
+    dt = _dt(slices)
+    srcs = [ad().Source([devT(s[3], 1)], None) for s in slices]
+    S = len(slices)
+    ad().batch_iteration_hint(batch, None)
+    assert ad().batch_order(batch) == list(range(S))
+    us0 = [devT(s[4], 1) for s in slices]
+    st0 = ad().batch_midpoint_step(batch, us0, 0.0, dt, srcs, tol=1e-6)
+    iters = [s["iters"] for s in st0]
+    assert len(set(iters)) > 1                  # the slices need different counts
+    assert ad().batch_order(batch) == sorted(range(S), key=lambda k: -iters[k])
+    for hint in (list(range(S)), [float((7 * k) % S) for k in range(S)]):
+        ad().batch_iteration_hint(batch, hint)
+        assert ad().batch_order(batch) == sorted(range(S), key=lambda k: -hint[k])
+        us = [devT(s[4], 1) for s in slices]
+        st = ad().batch_midpoint_step(batch, us, 0.0, dt, srcs, tol=1e-6)
+        assert [s["iters"] for s in st] == iters
+        for k in range(S):
+            assert torch.equal(us[k].view(torch.int32), us0[k].view(torch.int32)), (hint, k)
+    with pytest.raises(ad().AdError):
+        ad().batch_iteration_hint(batch, [float("nan")] * S)
+    with pytest.raises(ValueError):
+        ad().batch_iteration_hint(batch, [1.0] * (S + 1))

@@ -163,7 +163,8 @@ def test_learned_bounds_through_capi(bound_model, bf16):
 
 @pytest.mark.parametrize("force_bad", [False, True])
 def test_learned_bound_in_batch_with_fallback(bound_model, force_bad):
-    """The learned bounds drive a batched step; with force_bad one slice's
+    """The learned bounds drive a batched step (and their iteration counts its
+    queue order); with force_bad one slice's
     bound is cut to 0.02 x its Gershgorin bound, so the spectrum reaches far
     beyond the Leja interval and the series diverges (its FP32 terms overflow
     long before the stopping rule could hold): the fallback must list exactly
@@ -171,11 +172,13 @@ def test_learned_bound_in_batch_with_fallback(bound_model, force_bad):
     from paper_2307_12276_gb300 import learned
     model = bound_model[0]
     slices, ops, us, srcs, fields, dt = _small_batch(model)
-    alpha, _ = learned.predict_bounds(model, ops, dt, margin=1.2)
+    batch = ad().create_batch(ops, autotune=False)
+    alpha, it_pred = learned.predict_bounds(model, ops, dt, margin=1.2, batch=batch)
+    # the predicted counts set the batch's queue order (longest series first)
+    assert ad().batch_order(batch) == sorted(range(len(ops)), key=lambda k: -it_pred[k])
     bad = 2
     if force_bad:
         ad().set_spectral_bound(ops[bad], 0.02 * spectral.gershgorin(slices[bad][1]))
-    batch = ad().create_batch(ops, autotune=False)
     st, fallback = learned.batched_step_with_fallback(batch, ops, us, 0.0, dt, srcs, tol=1e-6)
     assert fallback == ([bad] if force_bad else [])
     assert all(s["converged"] for s in st)
