@@ -275,7 +275,7 @@ def traffic_per_launch(files, summary: str):
 # sources that define each profiled kernel (the digest in its summary covers these)
 F64_SERIES_SOURCES = ("persistent_f64.cu", "stencil9.cuh", "ad_internal.h")
 F64_ITER_SOURCES = ("stencil_kernels.cu", "stencil9.cuh", "series_finish.cuh", "tile_f32.cuh",
-                    "ad_internal.h")
+                    "ad_internal.h", "sqsum.cuh")
 F32_ITER_SOURCES = ("stencil_kernels.cu", "tile_f32.cuh", "tile_f32_vec.cuh", "tile_f32_ring.cuh",
                     "ad_internal.h")
 F32_PAIR_SOURCES = F32_ITER_SOURCES + ("tile_f32_pair.cuh",)
@@ -415,6 +415,17 @@ def measure_workload(ad, dev, stream, p, flush, steps, warmup, e2e_steps, world=
             "peak_note": "of derived FP64 peak: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz; "
                          "measured_fp64_fma_tflops is a DFMA loop on every SM timed in this "
                          "run (ad_fp64_fma_rate)"}
+    if kernel == "leja_iter_f64_k":
+        # the library's rule: the large-grid iteration forms the norms' two
+        # squares per cell on the integer and FP32 pipes unless AD_F64_NORMS=fp64
+        off_pipe = not os.environ.get("AD_F64_NORMS", "").startswith("f")
+        pipe_ops = fma - 2 if off_pipe else fma
+        roof["fp64_pipe_ops_per_cell"] = pipe_ops
+        roof["frac_of_measured_fp64_fma_pipe_ops"] = round(achieved * pipe_ops / fma / fma_peak, 4)
+        roof["fp64_pipe_note"] = ("achieved counts the method's FP64 FMA-class operations per cell "
+                                  f"({fma}); {fma - pipe_ops} of them (the norms' squares) run off "
+                                  "the FP64 pipe, so the pipe itself executes "
+                                  f"{pipe_ops} per cell")
     res = {"workload": label or p.name, "nx": g.nx, "ny": g.ny, "cells": g.n,
            "value": value, "dev_ms": dev_ms, "ms_per_step": dev_ms / steps,
            "leja_iters_per_step": tot["iters"] / steps, "gpu_launches": launches,

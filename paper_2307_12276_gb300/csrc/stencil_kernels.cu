@@ -24,6 +24,7 @@
 
 #include "tile_f32.cuh"
 #include "series_finish.cuh"
+#include "sqsum.cuh"
 #include "tile_f32_bulk.cuh"
 #include "tile_f32_vec.cuh"
 #include "tile_f32_ring.cuh"
@@ -268,8 +269,11 @@ __global__ void apply_f64_k(GridDev g, const double* __restrict__ W, const doubl
 
 // Fused Leja iteration m: y_{m+1} = Ws y_m - xi_m y_m [+ e1 w2 + e2 w1],
 // p += d_{m+1} y_{m+1}, norm partials; each block owns a contiguous chunk of
-// cells (equal FP64 work per block: the kernel is FP64-pipe bound).
-template <bool AUG>
+// cells (equal FP64 work per block: the kernel is FP64-pipe bound).  SQ: the
+// norms' sums of squares on the integer and FP32 pipes (sqsum.cuh), which
+// leaves the FP64 pipe 11 instructions per cell instead of 13; otherwise two
+// FP64 FMAs per cell.
+template <bool AUG, bool SQ>
 __global__ void __launch_bounds__(kThreads) leja_iter_f64_k(SeriesArgs a) {
   const volatile Ctrl* vc = a.ctrl;
   if (vc->stop) return;
@@ -288,6 +292,7 @@ __global__ void __launch_bounds__(kThreads) leja_iter_f64_k(SeriesArgs a) {
   const unsigned int c1 = min(n, c0 + chunk);
   const bool use_w2 = AUG && lc.e1 != 0.0, use_w1 = AUG && lc.e2 != 0.0;
   double sy = 0.0, sp = 0.0;
+  SqSum qy, qp;
   // two cells per thread and loop trip, computed side by side (independent
   // FP64 chains and loads in flight)
   for (unsigned int base = c0 + threadIdx.x; base < c1; base += 2 * blockDim.x) {
@@ -317,9 +322,18 @@ __global__ void __launch_bounds__(kThreads) leja_iter_f64_k(SeriesArgs a) {
       yout[idx] = z[q];
       const double pn = fma(lc.d, z[q], p[idx]);
       p[idx] = pn;
-      sy = fma(z[q], z[q], sy);
-      sp = fma(pn, pn, sp);
+      if (SQ) {
+        qy.add(z[q]);
+        qp.add(pn);
+      } else {
+        sy = fma(z[q], z[q], sy);
+        sp = fma(pn, pn, sp);
+      }
     }
+  }
+  if (SQ) {
+    sy = qy.value();
+    sp = qp.value();
   }
   series_finish(a, sy, sp);
 }
@@ -1030,15 +1044,29 @@ void apply_f32(const GridDev& g, const float* F, int adv, float abx, float aby, 
                                                        0.0f, 1.0f);
 }
 
+// The large-grid FP64 iteration forms its norms' sums of squares off the FP64
+// pipe (SqSum) unless AD_F64_NORMS=fp64 asks for FP64 FMAs.  Measured on the
+// 4096^2 workload: 0.397 against 0.428 ms per iteration (the FP64 pipe is fed
+// 11 instructions per cell instead of 13, at 89 % of a plain DFMA loop's rate
+// against 96 %); with one cell per thread and 6 blocks per SM 0.394 ms, with
+// four cells per thread 0.399 ms.
+static bool f64_int_squares() {
+  static const bool on = [] {
+    const char* e = getenv("AD_F64_NORMS");
+    return !(e && e[0] == 'f');
+  }();
+  return on;
+}
+
 void series_iteration(const SeriesArgs& a, cudaStream_t s) {
   if (a.prec == 0) {
-    if (a.aug) {
-      ++launch_counter();
-      leja_iter_f64_k<true><<<a.nblocks, kThreads, 0, s>>>(a);
-    }
-    else {
-      ++launch_counter();
-      leja_iter_f64_k<false><<<a.nblocks, kThreads, 0, s>>>(a);
+    ++launch_counter();
+    if (f64_int_squares()) {
+      if (a.aug) leja_iter_f64_k<true, true><<<a.nblocks, kThreads, 0, s>>>(a);
+      else leja_iter_f64_k<false, true><<<a.nblocks, kThreads, 0, s>>>(a);
+    } else {
+      if (a.aug) leja_iter_f64_k<true, false><<<a.nblocks, kThreads, 0, s>>>(a);
+      else leja_iter_f64_k<false, false><<<a.nblocks, kThreads, 0, s>>>(a);
     }
   } else if (series_pair(a)) {
     ++launch_counter();
