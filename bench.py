@@ -280,7 +280,7 @@ F32_ITER_SOURCES = ("stencil_kernels.cu", "tile_f32.cuh", "tile_f32_vec.cuh", "t
                     "ad_internal.h")
 F32_PAIR_SOURCES = F32_ITER_SOURCES + ("tile_f32_pair.cuh",)
 F32_TMA_SOURCES = F32_PAIR_SOURCES + ("tile_f32_bulk.cuh", "tile_f32_pair_tma.cuh")
-MOM_SOURCES = ("momentum.cu", "series_finish.cuh", "tile_f32.cuh", "ad_internal.h")
+MOM_SOURCES = ("momentum.cu", "series_finish.cuh", "tile_f32.cuh", "ad_internal.h", "sqsum.cuh")
 
 # the FP64 series kernel behind each path that ad_series_timing reports
 SERIES_KERNEL_NAMES = {"graph loop of per-iteration kernels": "leja_iter_f64_k",
@@ -570,8 +570,12 @@ def measure_momentum_form(ad, dev, stream, steps=3):
             "value": round(N / (ms * 1e-3) / 1e6, 2), "unit": "Munknown-steps/s",
             "ms_per_step": round(ms, 4), "leja_iters_per_step": float(np.mean(iters)),
             "tol": mp.tol, "dt_over_cfl": 100.0,
-            "roofline": {"bound": "alu", "kernel": "mom_iter_k<true>",
+            "roofline": {"bound": "alu", "kernel": "mom_iter_k<true, true>",
                          "ms_per_iteration": round(ms_iter, 5),
+                         # the library's rule: the norms' two squares per unknown run off
+                         # the FP64 pipe unless AD_F64_NORMS=fp64
+                         "fp64_pipe_ops_per_unknown":
+                             21 if os.environ.get("AD_F64_NORMS", "").startswith("f") else 19,
                          "alg_flops_per_iteration": flops, "achieved": round(tf, 4),
                          "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
                          "frac": round(tf / FP64_PEAK_TFLOPS, 4),

@@ -42,6 +42,7 @@
 #include "ad_internal.h"
 #include "leja_host.h"
 #include "series_finish.cuh"
+#include "sqsum.cuh"
 
 struct ad_momentum_operator;
 
@@ -164,7 +165,9 @@ __global__ void mom_apply_k(GridDev g, int np, const double* __restrict__ WD,
 
 // One fused Newton iteration on all slices: y_{m+1} = ((A - c)/gamma - xi_m) y_m,
 // p += d_{m+1} y_{m+1}, norm partials; then the stopping rule (series_finish).
-template <bool ADV>
+// SQ: the norms' sums of squares on the integer and FP32 pipes (sqsum.cuh),
+// two FP64 instructions per unknown fewer; otherwise FP64 FMAs.
+template <bool ADV, bool SQ>
 __global__ void __launch_bounds__(kThreads) mom_iter_k(SeriesArgs a, int np,
                                                        const double* __restrict__ sWD,
                                                        const double* __restrict__ sWA,
@@ -190,6 +193,7 @@ __global__ void __launch_bounds__(kThreads) mom_iter_k(SeriesArgs a, int np,
   double* __restrict__ p = static_cast<double*>(a.p);
   const long long n = a.g.n;
   double sy = 0.0, sp = 0.0;
+  SqSum qy, qp;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(idx % a.g.nx), j = (int)(idx / a.g.nx);
@@ -212,14 +216,34 @@ __global__ void __launch_bounds__(kThreads) mom_iter_k(SeriesArgs a, int np,
       yout[base + idx] = z;
       const double pv = fma(d, z, p[base + idx]);
       p[base + idx] = pv;
-      sy = fma(z, z, sy);
-      sp = fma(pv, pv, sp);
+      if (SQ) {
+        qy.add(z);
+        qp.add(pv);
+      } else {
+        sy = fma(z, z, sy);
+        sp = fma(pv, pv, sp);
+      }
       yp = yc;
       yc = yn;
       yn = k + 2 < np ? yin[base + 2 * n + idx] : 0.0;
     }
   }
+  if (SQ) {
+    sy = qy.value();
+    sp = qp.value();
+  }
   series_finish(a, sy, sp);
+}
+
+// The momentum iteration forms its norms' sums of squares off the FP64 pipe
+// unless AD_F64_NORMS=fp64 asks for FP64 FMAs (the rule of the large-grid
+// FP64 iteration).
+bool mom_int_squares() {
+  static const bool on = [] {
+    const char* e = getenv("AD_F64_NORMS");
+    return !(e && e[0] == 'f');
+  }();
+  return on;
 }
 
 // Gershgorin bound of the coupled operator: min over rows of
@@ -434,12 +458,22 @@ int mop_series(ad_momentum_operator* op, const double* src, double d0, int force
   for (;;) {
     for (int q = 0; q < kMomChunk; ++q) {
       ++launch_counter();
-      if (op->adv)
-        mom_iter_k<true><<<op->nblocks, kThreads, smem, op->stream>>>(a, op->np, op->sWD,
-                                                                      op->sWA, op->mc);
-      else
-        mom_iter_k<false><<<op->nblocks, kThreads, smem, op->stream>>>(a, op->np, op->sWD,
-                                                                       nullptr, op->mc);
+      const double* wa = op->adv ? op->sWA : nullptr;
+      if (mom_int_squares()) {
+        if (op->adv)
+          mom_iter_k<true, true><<<op->nblocks, kThreads, smem, op->stream>>>(a, op->np, op->sWD,
+                                                                              wa, op->mc);
+        else
+          mom_iter_k<false, true><<<op->nblocks, kThreads, smem, op->stream>>>(a, op->np,
+                                                                               op->sWD, wa, op->mc);
+      } else {
+        if (op->adv)
+          mom_iter_k<true, false><<<op->nblocks, kThreads, smem, op->stream>>>(a, op->np,
+                                                                               op->sWD, wa, op->mc);
+        else
+          mom_iter_k<false, false><<<op->nblocks, kThreads, smem, op->stream>>>(a, op->np,
+                                                                                op->sWD, wa, op->mc);
+      }
     }
     launched += kMomChunk;
     M_CUDA(cudaGetLastError());

@@ -129,3 +129,50 @@ def test_power_of_two_scaling_and_oracle_estimate():
     assert_close(out, ref if alt is None else alt, 1e-11)
     if alt is None:
         assert st["err_est"] == pytest.approx(ost.err_est, rel=1e-12)
+
+
+MOM_CHILD = r"""
+import json, sys
+import numpy as np, torch
+sys.path.insert(0, {root!r})
+sys.path.insert(0, {tests!r})
+import paper_2307_12276_gb300 as ad
+from workloads.fields import BC_DIRICHLET0
+from workloads.momentum import momentum_problem
+D = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(), device="cuda:0")
+mp = momentum_problem(96, 80, 8, BC_DIRICHLET0, "circular", adv=(0.1, 0.05), dt_factor=100.0)
+s = mp.spatial
+op = ad.create_momentum_operator(96, 80, BC_DIRICHLET0, D(s.Dxx), D(s.Dxy), D(s.Dyy), mp.mom.P,
+                                 mp.mom.beta, mp.mom.dpp, mp.mom.b, mp.mom.loss, ax=s.ax, ay=s.ay)
+ad.momentum_spectral_bound(op)
+v = D(mp.S.ravel() + 0.1 * np.random.default_rng(5).standard_normal(mp.S.size))
+stats, arrays = {{}}, {{}}
+for key, kw in (("f17", dict(force_iters=17)), ("tol", dict(tol=1e-10))):
+    out = torch.empty_like(v)
+    stats[key] = ad.momentum_leja_phi1(op, v, out, mp.dt, **kw)
+    arrays[key] = out.cpu().numpy()
+np.savez({prefix!r}, **arrays)
+print(json.dumps(stats))
+"""
+
+
+def test_momentum_norm_squares_equal_fp64_fma_sums(tmp_path):
+    """The momentum-coupled iteration with both ways of forming the norms:
+    identical vectors and counts, error estimates to 1e-12."""
+    need_gpu()
+    res = {}
+    for tag, env_extra in (("sq", {}), ("fma", {"AD_F64_NORMS": "fp64"})):
+        env = dict(os.environ)
+        env.pop("AD_F64_NORMS", None)
+        env.update(env_extra)
+        prefix = str(tmp_path / tag)
+        code = MOM_CHILD.format(root=ROOT, tests=os.path.join(ROOT, "tests"), prefix=prefix)
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        res[tag] = (json.loads(r.stdout.strip().splitlines()[-1]), np.load(prefix + ".npz"))
+    (sq, a_sq), (fm, a_fm) = res["sq"], res["fma"]
+    for key in a_fm.files:
+        assert sq[key]["iters"] == fm[key]["iters"] and sq[key]["converged"], key
+        assert sq[key]["err_est"] == pytest.approx(fm[key]["err_est"], rel=1e-12), key
+        assert np.array_equal(a_sq[key], a_fm[key]), key
