@@ -809,7 +809,9 @@ def _slice_operators(ad, dev, stream, nslices, sides):
 def _batched_oracle_slice(spec):
     """One slice of the batch on the CPU oracle (worker of a spawned pool):
     the operator, a 30-step power-iteration bound from the SplitMix64 start
-    of the GPU side, then one exponential-midpoint step at tol 1e-6, timed."""
+    of the GPU side, then one exponential-midpoint step at tol 1e-6, timed;
+    untimed, the same step at tol 1e-10 from the FP32-rounded initial field
+    the GPU starts from (the reference its first step is compared with)."""
     import numpy as np
     sys.path.insert(0, ROOT)
     from oracle import integrators, spectral
@@ -823,7 +825,11 @@ def _batched_oracle_slice(spec):
     S = lambda t: p.source_at(t).ravel()
     t0 = time.perf_counter()
     integrators.expquad_step(A, p.u0.ravel(), 0.0, dt, 1, (0.5,), S, alpha, tol=1e-6)
-    return p.grid.n, time.perf_counter() - t0
+    secs = time.perf_counter() - t0
+    u32 = p.u0.ravel().astype(np.float32).astype(np.float64)
+    S32 = lambda t: p.source_at(t).ravel().astype(np.float32).astype(np.float64)
+    ref, _ = integrators.expquad_step(A, u32, 0.0, dt, 1, (0.5,), S32, alpha, tol=1e-10)
+    return p.grid.n, secs, seed - 1, ref
 
 
 def batched_oracle_baseline(specs, dt, max_side=512):
@@ -842,9 +848,10 @@ def batched_oracle_baseline(specs, dt, max_side=512):
     with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
         res = list(ex.map(_batched_oracle_slice, jobs))
     wall = time.perf_counter() - t0
-    cells = sum(c for c, _ in res)
-    secs = sum(t for _, t in res)
-    return {"value": round(cells / (secs / workers) / 1e6, 4), "unit": "Mcell-steps/s",
+    cells = sum(r[0] for r in res)
+    secs = sum(r[1] for r in res)
+    refs = {r[2]: r[3] for r in res}
+    return refs, {"value": round(cells / (secs / workers) / 1e6, 4), "unit": "Mcell-steps/s",
             "cores": workers, "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{len(jobs)} of {len(specs)} slices (sides <= {max_side}), one "
                       f"exponential-midpoint step each at tol 1e-6, {workers} spawned workers "
@@ -876,6 +883,8 @@ def measure_batched_form(ad, dev, stream, steps, nslices=128, sides=(256, 512, 1
     u_start = [u.clone() for u in us]
     ad.batch_midpoint_step(batch, us, 0.0, dt, srcs, tol=1e-6)      # warm-up
     torch.cuda.synchronize()
+    # the first step of the slices the CPU baseline also steps, for its error
+    step1 = {k: us[k].double().cpu().numpy() for k, p in enumerate(probs) if p.grid.nx <= 512}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     iters = []
     torch.cuda.profiler.start()       # the range a profiler started with capture off records
@@ -956,7 +965,16 @@ def measure_batched_form(ad, dev, stream, steps, nslices=128, sides=(256, 512, 1
            "setup_s": round(setup_s, 1), "tol": 1e-6}
     if cpu_baseline:
         from workloads import config3_slices
-        out["cpu_baseline"] = batched_oracle_baseline(config3_slices(nslices, sides=sides), dt)
+        refs, out["cpu_baseline"] = batched_oracle_baseline(config3_slices(nslices, sides=sides),
+                                                            dt)
+        errs = [float(np.linalg.norm(step1[k] - r) / np.linalg.norm(r)) for k, r in refs.items()]
+        mx = [float(np.max(np.abs(step1[k] - r)) / np.max(np.abs(r))) for k, r in refs.items()]
+        out["err_vs_oracle_step1"] = {
+            "slices": len(errs), "max_rel_l2": max(errs), "median_rel_l2": float(np.median(errs)),
+            "max_rel_max": max(mx),
+            "note": "the batch's first step (FP32 storage, tol 1e-6) of every slice of side "
+                    "<= 512 against the FP64 oracle's step at tol 1e-10 from the same "
+                    "FP32-rounded field, same power-iteration start"}
     if learned_fields:
         out["learned"] = measure_learned(ad, dev, stream, ops, us, u_start, srcs, probs, fields,
                                          dt, batch, steps, ms_batch, power_s, learned_fields,
