@@ -204,9 +204,12 @@ __global__ void __launch_bounds__(kThreads) batch_iter_k(const BatchSlice* slice
     if (s_last) {                              // this slice's last tile: decide for it
       __threadfence();
       double ay = 0.0, ap = 0.0;
+      // unrolled: the loads of several tiles in flight, the sums still in tile order
+#pragma unroll 8
       for (int q = threadIdx.x; q < S.ntiles; q += blockDim.x) {
-        ay += __ldcg(&tile_partials[2 * (S.tile_off + q)]);
-        ap += __ldcg(&tile_partials[2 * (S.tile_off + q) + 1]);
+        const double2 v = __ldcg(reinterpret_cast<const double2*>(tile_partials) + S.tile_off + q);
+        ay += v.x;
+        ap += v.y;
       }
       block_sum2(ay, ap);
       if (threadIdx.x == 0) {
@@ -301,9 +304,12 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     if (last) {                                // this slice's last tile: decide for it
       __threadfence();
       double ay = 0.0, ap = 0.0;
+      // unrolled: the loads of several tiles in flight, the sums still in tile order
+#pragma unroll 8
       for (int q = lane; q < S.rt_n; q += 32) {
-        ay += __ldcg(&tile_partials[2 * (S.rt_off + q)]);
-        ap += __ldcg(&tile_partials[2 * (S.rt_off + q) + 1]);
+        const double2 v = __ldcg(reinterpret_cast<const double2*>(tile_partials) + S.rt_off + q);
+        ay += v.x;
+        ap += v.y;
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -362,7 +368,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     const int m = vc->m;                       // even
     const LejaCoef lc1 = S.a.lc[m], lc2 = S.a.lc[m + 1];
     PairCtx X;
-    X.a = &S.a;
+    X.F = static_cast<const float*>(S.a.coef);
     X.yin = static_cast<const float*>(S.a.y[(m >> 1) & 1]);
     X.yout = static_cast<float*>(S.a.y[((m >> 1) + 1) & 1]);
     X.p = static_cast<float*>(S.a.p);
@@ -410,9 +416,16 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     if (last) {                                // this slice's last tile: decide for it
       __threadfence();
       double t4[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int r = lane; r < S.rt_n; r += 32)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) t4[k] += __ldcg(&tile_partials[4 * (S.rt_off + r) + k]);
+      // unrolled: the loads of several tiles in flight, the sums still in tile order
+#pragma unroll 8
+      for (int r = lane; r < S.rt_n; r += 32) {
+        const double2* tp = reinterpret_cast<const double2*>(tile_partials) + 2 * (S.rt_off + r);
+        const double2 v0 = __ldcg(tp), v1 = __ldcg(tp + 1);
+        t4[0] += v0.x;
+        t4[1] += v0.y;
+        t4[2] += v1.x;
+        t4[3] += v1.y;
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
@@ -507,7 +520,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     const int m = *(volatile int*)&ctrl->m;    // 2 k
     const LejaCoef lc1 = S.a.lc[m], lc2 = S.a.lc[m + 1];
     PairCtx X;
-    X.a = &S.a;
+    X.F = static_cast<const float*>(S.a.coef);
     X.yin = static_cast<const float*>(S.a.y[(m >> 1) & 1]);
     X.yout = static_cast<float*>(S.a.y[((m >> 1) + 1) & 1]);
     X.p = static_cast<float*>(S.a.p);
@@ -555,9 +568,16 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     if (last) {                                // the slice's last tile of pass k: decide
       __threadfence();
       double t4[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int r = lane; r < S.rt_n; r += 32)
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) t4[kk] += __ldcg(&tile_partials[4 * (S.rt_off + r) + kk]);
+      // unrolled: the loads of several tiles in flight, the sums still in tile order
+#pragma unroll 8
+      for (int r = lane; r < S.rt_n; r += 32) {
+        const double2* tp = reinterpret_cast<const double2*>(tile_partials) + 2 * (S.rt_off + r);
+        const double2 v0 = __ldcg(tp), v1 = __ldcg(tp + 1);
+        t4[0] += v0.x;
+        t4[1] += v0.y;
+        t4[2] += v1.x;
+        t4[3] += v1.y;
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1)
 #pragma unroll

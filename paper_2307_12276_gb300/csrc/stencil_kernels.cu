@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(kPairWarps * 32, 1) leja_iter2_f32_ring_k(Seri
   const int m = vc->m;                                 // even in pair mode
   const LejaCoef lc1 = a.lc[m], lc2 = a.lc[m + 1];
   PairCtx X;
-  X.a = &a;
+  X.F = static_cast<const float*>(a.coef);
   X.yin = static_cast<const float*>(a.y[(m >> 1) & 1]);
   X.yout = static_cast<float*>(a.y[((m >> 1) + 1) & 1]);
   X.p = static_cast<float*>(a.p);
@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(kPairWarps * 32, 1)
                        rings + (size_t)kPairWarps * stages * PairLayout::SIZE) +
                    warp * stages;
   PairCtx X;
-  X.a = &a;
+  X.F = static_cast<const float*>(a.coef);
   X.stages = stages;
   X.yin = static_cast<const float*>(a.y[(m >> 1) & 1]);
   X.yout = static_cast<float*>(a.y[((m >> 1) + 1) & 1]);

@@ -93,8 +93,8 @@ struct PRow {          // one row around the lane's group, columns gx - 1 .. gx 
   float p[4];          // p_m; after level 1 on an own row, p_{m+1}
 };
 
-struct PairCtx {       // per-run constants
-  const SeriesArgs* a;
+struct PairCtx {       // per-run constants (registers: no per-row loads through a struct in memory)
+  const float* F;      // the coefficient fields [3][n]
   int stages;          // ring depth (records per warp)
   const float* yin;
   float* yout;
@@ -130,7 +130,7 @@ __device__ __forceinline__ void pair_issue(const PairCtx& X, int r, float* S) {
   using PL = PairLayout;
   if (r <= X.y1 + 1 && X.L.load) {
     const long long n = X.G.n;
-    const float* F = static_cast<const float*>(X.a->coef);
+    const float* F = X.F;
     const long long off = map_row(r, X.G.nx, X.G.ny, X.G.bc).off + X.L.src;
     const int c = 4 * X.G.lane;
     cp_async16(S + PL::Y + c, X.yin + off);
@@ -138,7 +138,7 @@ __device__ __forceinline__ void pair_issue(const PairCtx& X, int r, float* S) {
     cp_async16(S + PL::YY + c, F + n + off);
     if (r >= X.y0 - 1 && r <= X.y1) cp_async16(S + PL::XX + c, F + off);
     if (r >= X.y0 && r < X.y1 && X.L.own)
-      cp_async16(S + PL::P + c, static_cast<const float*>(X.a->p) + off);
+      cp_async16(S + PL::P + c, X.p + off);
   }
   cp_async_commit();
 }
