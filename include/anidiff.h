@@ -262,6 +262,20 @@ AD_API int ad_batch_midpoint_step(ad_batch* b, void* const* u, double t, double 
                                   const ad_source* src, double tol, int force_iters,
                                   ad_stats* per_slice);
 
+/* Binds the batch to state vectors and sources held by the caller, for
+ * repeated steps with ad_batch_step (no per-call arrays to pass or check):
+ * u and src as for ad_batch_midpoint_step.  The pointers to the vectors and
+ * to the source fields are copied (the arrays u, src and src[s].g need not
+ * outlive the call); the vectors, the fields and any h context must stay
+ * valid until the batch is rebound or destroyed.  AD_ERR_INVALID as
+ * ad_batch_midpoint_step. */
+AD_API int ad_batch_bind(ad_batch* b, void* const* u, const ad_source* src);
+
+/* One exponential-midpoint step of the bound vectors: ad_batch_midpoint_step
+ * with the arguments of the last ad_batch_bind (AD_ERR_INVALID if none). */
+AD_API int ad_batch_step(ad_batch* b, double t, double dt, double tol, int force_iters,
+                         ad_stats* per_slice);
+
 /* Queue order of the slices' warp tiles.  In every pass of the batched
  * series the tiles of the slices expected to iterate longest are handed out
  * first, so that the longest series, which bound the step, do not wait behind

@@ -84,6 +84,8 @@ _sig = {
     "ad_destroy_batch": (_i, [_vp]),
     "ad_batch_midpoint_step": (_i, [_vp, C.POINTER(_vp), _d, _d, _vp, _d, _i, C.POINTER(Stats)]),
     "ad_batch_iteration_hint": (_i, [_vp, _vp]),
+    "ad_batch_bind": (_i, [_vp, _vp, _vp]),
+    "ad_batch_step": (_i, [_vp, _d, _d, _d, _i, _vp]),
     "ad_batch_order": (_i, [_vp, _vp]),
     "ad_batch_info": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_d),
                           C.POINTER(_i)]),
@@ -470,6 +472,35 @@ def create_batch(ops, autotune: bool = True) -> Batch:
 
 def destroy_batch(b: Batch):
     b.close()
+
+
+def batch_bind(b: Batch, us, sources=None) -> None:
+    """ad_batch_bind: the state vectors (float32 device tensors, one per slice)
+    and sources that ad_batch_step advances.  The tensors and the callables of
+    the sources are kept referenced by the batch."""
+    S = len(b.ops)
+    if len(us) != S:
+        raise ValueError("one state vector per slice")
+    uptr = (_vp * S)(*[b.ops[s].vec(us[s], "u") for s in range(S)])
+    srcp, keep = None, ()
+    if sources is not None:
+        if len(sources) != S:
+            raise ValueError("one Source (or None) per slice")
+        srcp, keep = _batch_sources(b.ops, sources)
+    _check(_lib.ad_batch_bind(b.handle, uptr, srcp))
+    b._bound = (us, sources, keep)
+
+
+def batch_step(b: Batch, t: float, dt: float, tol: float = 1e-6, force_iters: int = -1,
+               raise_not_converged: bool = True):
+    """ad_batch_step: one exponential-midpoint step of the vectors bound by
+    batch_bind.  Returns the per-slice stats."""
+    S = len(b.ops)
+    stats = (Stats * S)()
+    status = _lib.ad_batch_step(b.handle, t, dt, tol, force_iters, stats)
+    if not (status == AD_ERR_NOT_CONVERGED and not raise_not_converged):
+        _check(status, stats[0])
+    return [stats[s].as_dict() for s in range(S)]
 
 
 def batch_iteration_hint(b: Batch, iters=None) -> None:

@@ -847,6 +847,11 @@ struct ad_batch {
   bool persist = false;               // the graph runs the persistent iteration kernel
   bool persist_off = false;           // the persistent kernel could not be built here
   int march = 1;                      // marching of the two-iteration kernels (pair_march)
+  // vectors and sources bound by ad_batch_bind (caller memory), for ad_batch_step
+  std::vector<void*> bound_u;
+  std::vector<ad_source> bound_src;
+  std::vector<std::vector<const void*>> bound_g;
+  bool bound_has_src = false;
   // Queue order of the slices' warp tiles (empty: slice order): slices expected
   // to iterate longest first, from ad_batch_iteration_hint and then from the
   // counts of each step; order_dirty asks the next step to rebuild the list.
@@ -1657,6 +1662,38 @@ int ad_batch_midpoint_step(ad_batch* b, void* const* u, double t, double dt,
   if (status == AD_ERR_TIMEOUT) return bfail(status, "a bounded wait of the batched series gave up");
   if (status != AD_OK) return bfail(status, "a slice's Leja series reached max_iters");
   return AD_OK;
+}
+
+int ad_batch_bind(ad_batch* b, void* const* u, const ad_source* src) {
+  set_error_message("");
+  if (!b || !u) return bfail(AD_ERR_INVALID, "NULL argument");
+  for (int s = 0; s < b->S; ++s) {
+    if (!u[s]) return bfail(AD_ERR_INVALID, "u[s] is NULL");
+    if (src && (src[s].nterms < 0 || src[s].nterms > kBatchSources))
+      return bfail(AD_ERR_INVALID, "batched sources: at most 4 terms per slice");
+    if (src && src[s].nterms > 0 && !src[s].g) return bfail(AD_ERR_INVALID, "source: g is NULL");
+  }
+  b->bound_u.assign(u, u + b->S);
+  b->bound_has_src = src != nullptr;
+  b->bound_src.assign(b->S, ad_source{});
+  b->bound_g.assign(b->S, {});
+  if (src)
+    for (int s = 0; s < b->S; ++s) {       // the term pointers are copied; the fields are not
+      b->bound_g[s].assign(src[s].g, src[s].g + src[s].nterms);
+      b->bound_src[s] = src[s];
+      b->bound_src[s].g = b->bound_g[s].data();
+    }
+  return AD_OK;
+}
+
+int ad_batch_step(ad_batch* b, double t, double dt, double tol, int force_iters,
+                  ad_stats* per_slice) {
+  set_error_message("");
+  if (!b) return bfail(AD_ERR_INVALID, "NULL batch");
+  if ((int)b->bound_u.size() != b->S) return bfail(AD_ERR_INVALID, "no vectors bound (ad_batch_bind)");
+  return ad_batch_midpoint_step(b, b->bound_u.data(), t, dt,
+                                b->bound_has_src ? b->bound_src.data() : nullptr, tol, force_iters,
+                                per_slice);
 }
 
 }  // extern "C"

@@ -20,9 +20,9 @@ from typing import Sequence
 
 import numpy as np
 
-from . import (BC_DIRICHLET0, BC_PERIODIC, BOUND_POWER, FP64, MLP, batch_iteration_hint,
-               batch_midpoint_step, bound_training_sample, create_operator, expquad_step,
-               learned_bounds, spectral_bound)
+from . import (BC_DIRICHLET0, BC_PERIODIC, BOUND_POWER, FP64, MLP, batch_bind,
+               batch_iteration_hint, batch_step, bound_training_sample, create_operator,
+               expquad_step, learned_bounds, spectral_bound)
 
 # training-field sides and their weights: every side class contributes about
 # the same number of cells, so large grids are rare but present
@@ -124,9 +124,14 @@ def predict_bounds(model: MLP, ops, dt, margin=1.1, bf16=True, batch=None):
 def batched_step_with_fallback(batch, ops, us, t, dt, sources, tol, power_iters=40):
     """One batched midpoint step.  A slice whose series did not converge keeps
     its input state (the batched step leaves it untouched); it then gets a
-    power-iteration bound and repeats its step alone.  Returns (per-slice
-    stats, list of fallback slice indices)."""
-    st = batch_midpoint_step(batch, us, t, dt, sources, tol=tol, raise_not_converged=False)
+    power-iteration bound and repeats its step alone.  The batch is bound to
+    the lists us and sources (ad_batch_bind) the first time they are passed,
+    and stepped through the binding.  Returns (per-slice stats, list of
+    fallback slice indices)."""
+    bound = getattr(batch, "_bound", None)
+    if bound is None or bound[0] is not us or bound[1] is not sources:
+        batch_bind(batch, us, sources)
+    st = batch_step(batch, t, dt, tol=tol, raise_not_converged=False)
     bad = [s for s in range(len(us)) if not st[s]["converged"]]
     for s in bad:
         spectral_bound(ops[s], BOUND_POWER, seed=s + 1, power_iters=power_iters, safety=1.1)

@@ -337,3 +337,33 @@ def test_queue_order_follows_iterations_and_changes_no_result():
         ad().batch_iteration_hint(batch, [float("nan")] * S)
     with pytest.raises(ValueError):
         ad().batch_iteration_hint(batch, [1.0] * (S + 1))
+
+
+def test_bound_step_equals_midpoint_step():
+    """ad_batch_bind + ad_batch_step give ad_batch_midpoint_step's results bit
+    for bit (time-dependent sources included, their profiles evaluated at each
+    step's midpoint); stepping an unbound batch is refused; a rebind moves the
+    step to other vectors."""
+    need_gpu()
+    slices, ops, batch = _build(sizes=SIZES_PAIR)
+    dt = _dt(slices)
+    prof = [lambda t: 1.0 + 0.5 * np.sin(2.0 * np.pi * t)]
+    srcs = [ad().Source([devT(s[3], 1)], prof) for s in slices]
+    with pytest.raises(ad().AdError):
+        ad().batch_step(batch, 0.0, dt)
+    ua = [devT(s[4], 1) for s in slices]
+    ub = [devT(s[4], 1) for s in slices]
+    sa, sb = [], []
+    for k in range(3):
+        sa.append(ad().batch_midpoint_step(batch, ua, k * dt, dt, srcs, tol=1e-6))
+    ad().batch_bind(batch, ub, srcs)
+    for k in range(3):
+        sb.append(ad().batch_step(batch, k * dt, dt, tol=1e-6))
+    assert [[s["iters"] for s in st] for st in sa] == [[s["iters"] for s in st] for st in sb]
+    for x, y in zip(ua, ub):
+        assert torch.equal(x.view(torch.int32), y.view(torch.int32))
+    uc = [devT(s[4], 1) for s in slices]
+    ad().batch_bind(batch, uc, srcs)
+    ad().batch_step(batch, 0.0, dt, tol=1e-6)
+    assert not torch.equal(uc[0], devT(slices[0][4], 1))
+    assert torch.equal(ub[0].view(torch.int32), ua[0].view(torch.int32))   # untouched by the rebind
