@@ -466,7 +466,8 @@ AD_API int ad_profile_leja_iteration(ad_operator* op, int aug, int reps, double*
  * on 2-D tiles, 3 graph loop of
  * per-iteration kernels, 4 host-driven per-iteration launches, 5 and 6 the
  * same with the FP32 two-iteration kernel, 8 and 9 the same with its rows
- * brought in by TMA, 0 none yet.
+ * brought in by TMA, 10 the FP64 series of a small grid in one thread-block
+ * cluster, 0 none yet.
  * Recording adds two event records and no synchronisation (each series
  * already ends with one). */
 AD_API int ad_time_series(ad_operator* op, int enable);

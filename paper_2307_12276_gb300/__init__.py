@@ -412,7 +412,7 @@ SERIES_KERNELS = {0: None, 1: "leja_persistent_f64_k", 2: "leja_nsync_f64_k",
                   3: "graph loop of per-iteration kernels", 4: "host-driven per-iteration kernels",
                   5: "graph loop of two-iteration kernels", 6: "host-driven two-iteration kernels",
                   7: "leja_tile_f64_k", 8: "graph loop of two-iteration kernels, TMA rows",
-                  9: "host-driven two-iteration kernels, TMA rows"}
+                  9: "host-driven two-iteration kernels, TMA rows", 10: "leja_cluster_f64_k"}
 
 
 def series_timing(op: Operator) -> dict:

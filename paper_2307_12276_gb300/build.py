@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libanidiff.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["stencil_kernels.cu", "persistent_f64.cu", "vec_kernels.cu", "capi.cu", "leja_host.cpp", "noalloc.cu", "batched.cu", "mlp.cu", "momentum.cu", "penalised.cu"]
+SOURCES = ["stencil_kernels.cu", "persistent_f64.cu", "cluster_f64.cu", "vec_kernels.cu", "capi.cu", "leja_host.cpp", "noalloc.cu", "batched.cu", "mlp.cu", "momentum.cu", "penalised.cu"]
 
 
 def nvcc() -> str:

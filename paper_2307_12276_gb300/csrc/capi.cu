@@ -23,6 +23,7 @@
 
 #include "anidiff.h"
 #include "ad_internal.h"
+#include "cluster_f64.h"
 #include "leja_host.h"
 
 using namespace ad;
@@ -469,9 +470,11 @@ int run_series(ad_operator* op, int aug, const void* src, double d0, int force, 
       ++op->atev_used;
     }
     if (op->time_series) CUDA_TRY(cudaEventRecord(ev[0], op->stream));
-    // small and medium FP64 grids: the whole series in one cooperative launch
-    const int pk = getenv("AD_NO_PERSIST") ? 0
-                   : series_run_persistent(a, &op->ctrl->gen, &op->nsync, op->stream, fuse);
+    // small FP64 grids: the whole series in one thread-block cluster; small and
+    // medium ones: in one cooperative launch
+    int pk = getenv("AD_NO_PERSIST") ? 0 : series_run_cluster(a, op->stream, fuse);
+    if (!pk && !getenv("AD_NO_PERSIST"))
+      pk = series_run_persistent(a, &op->ctrl->gen, &op->nsync, op->stream, fuse);
     if (fuse && !pk) {
       if (op->time_series && async) --op->atev_used;   // the event pair is reused
       return kNotFused;

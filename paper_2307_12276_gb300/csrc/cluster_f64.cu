@@ -1,0 +1,349 @@
+// FP64 Newton series (Section 2) of a small grid in ONE thread-block cluster.
+//
+// For grids of a few thousand cells the series is a chain of short
+// dependent iterations: at 64^2 a Leja iteration is 4096 cells of a 9-point
+// stencil, and the cost of the persistent tile kernel (152 blocks of 27-32
+// cells, neighbours synchronised through flags in global memory, the stopping
+// rule two iterations late) is its synchronisation latency, about 6 us per
+// iteration.  Here the grid lives in the distributed shared memory of one
+// cluster of K <= 16 CTAs (one per SM): CTA r owns the row band
+// [r ny / K, (r + 1) ny / K) -- its 9 scaled weights, its part of p and a
+// window of y with one halo row above and below and one halo column on each
+// side.  Per iteration m:
+//   1. every thread forms z = y_{m+1} and p_{m+1} on its cells (the cell
+//      arithmetic of the persistent kernels, operation for operation) and
+//      its two squared-norm partials; warp 0 adds the block's partials;
+//   2. one hardware cluster barrier (release / acquire) publishes the new
+//      rows and the block sums to the whole cluster;
+//   3. each CTA copies its two halo rows of y_{m+1} from the neighbouring
+//      CTAs' shared memory, and warp 0 of every CTA adds the K block sums in
+//      rank order and applies the stopping rule -- the same values in the
+//      same order everywhere, so every CTA takes the same decision and runs
+//      the same number of barriers.
+// Double buffering (y windows and block sums by parity) makes one barrier
+// per iteration enough: a buffer is overwritten only one barrier after the
+// last remote read of it.  A final barrier keeps every CTA's shared memory
+// alive until the others have stopped reading it.  The waits are the
+// hardware barrier's own (no spin loop, nothing to time out).
+//
+// With a StepFuse of one stage (exponential midpoint, Eq. exp_midpoint) the
+// launch also forms the step's right-hand side w1 = A u + S (prologue, the
+// apply kernel's arithmetic) and the update u += dt P (epilogue), as the
+// tile kernel does: one launch per step.
+#include "cluster_f64.h"
+#include "stencil9.cuh"
+
+#include <cooperative_groups.h>
+
+#include <cstdlib>
+#include <mutex>
+#include <vector>
+
+namespace cg = cooperative_groups;
+
+namespace ad {
+namespace {
+
+constexpr int kClusterThreads = 256;
+constexpr int kClusterMaxCtas = 16;          // non-portable cluster size (GB300 allows 16)
+// Measured per Leja iteration (64^2-workload fields, cluster vs tile kernel):
+// 32^2 3.1 vs 5.7 us, 64^2 3.4 vs 5.6, 96^2 4.9 vs 6.0, 128^2 6.3 vs 5.3.
+constexpr long long kClusterMaxCells = 96 * 96;
+
+struct ClusterGeom {
+  int K;        // CTAs in the cluster
+  int rows;     // largest row band (shared-memory plane stride: rows * nx cells)
+  int S;        // window row stride, nx + 2
+};
+
+template <bool FUSED>
+__global__ void __launch_bounds__(kClusterThreads)
+    leja_cluster_f64_k(SeriesArgs a, ClusterGeom geo, StepFuse F) {
+  extern __shared__ __align__(16) double csm[];
+  __shared__ double s_red[2][kClusterThreads];    // per-thread norm partials
+  __shared__ double s_part[2][2];                 // this CTA's (y, p) sums, by parity of m
+  __shared__ int s_stop, s_status;
+  __shared__ double s_ty, s_tp;
+  cg::cluster_group cl = cg::this_cluster();
+  const int K = geo.K, rank = (int)cl.block_rank();
+  const int t = threadIdx.x, T = blockDim.x, lane = t & 31, warp = t >> 5;
+  const GridDev g = a.g;
+  const int nx = g.nx, ny = g.ny, S = geo.S;
+  const long long n = g.n;
+  const bool periodic = g.bc == 0;
+  const int r0 = (int)((long long)ny * rank / K), r1 = (int)((long long)ny * (rank + 1) / K);
+  const int rows = r1 - r0, nc = rows * nx;
+  const int cpb = geo.rows * nx;
+  const int WB = (geo.rows + 2) * S;
+  double* sW = csm;                    // [9][cpb] scaled weights
+  double* sP = sW + 9 * cpb;           // [cpb] p
+  double* win = sP + cpb;              // [2][WB]: y_m in buffer m & 1
+  const double* __restrict__ Ws = static_cast<const double*>(a.coef);
+  Ctrl* ctrl = a.ctrl;
+  const int force = FUSED ? F.force : ctrl->force;
+  const int max_it = min(FUSED ? F.max_iters : ctrl->max_iters, kMaxIters);
+  const double tol = FUSED ? F.tol : ctrl->tol;
+  auto widx = [&](int li, int lj) { return (lj + 1) * S + li + 1; };
+  // periodic: the halo columns of a row hold the wrapped values
+  auto put = [&](double* wb, int li, int lj, double v) {
+    wb[widx(li, lj)] = v;
+    if (periodic) {
+      if (li == 0) wb[widx(nx, lj)] = v;
+      if (li == nx - 1) wb[widx(-1, lj)] = v;
+    }
+  };
+  // the neighbouring bands (periodic wrap; -1: zero Dirichlet, the halo row stays 0)
+  const int up_rank = rank > 0 ? rank - 1 : (periodic ? K - 1 : -1);
+  const int dn_rank = rank < K - 1 ? rank + 1 : (periodic ? 0 : -1);
+  const double* up_win = nullptr;
+  const double* dn_win = nullptr;
+  int up_row = 0;
+  if (up_rank >= 0) {
+    up_win = cl.map_shared_rank(win, (unsigned)up_rank);
+    const int ur0 = (int)((long long)ny * up_rank / K), ur1 = (int)((long long)ny * (up_rank + 1) / K);
+    up_row = ur1 - ur0 - 1;            // its last row
+  }
+  if (dn_rank >= 0) dn_win = cl.map_shared_rank(win, (unsigned)dn_rank);
+  // halo rows of buffer buf from the neighbours' shared memory
+  auto fill_halo = [&](int buf) {
+    double* wb = win + buf * WB;
+    for (int q = t; q < 2 * S; q += T) {
+      if (q < S) {
+        if (up_win) wb[q] = up_win[buf * WB + (up_row + 1) * S + q];
+      } else if (dn_win) {
+        wb[(rows + 1) * S + (q - S)] = dn_win[buf * WB + S + (q - S)];
+      }
+    }
+  };
+
+  for (int q = t; q < 2 * WB; q += T) win[q] = 0.0;   // zero Dirichlet halo
+  __syncthreads();
+  const double* __restrict__ Wu = F.W;
+  const double* __restrict__ uu = F.u;
+  for (int k = t; k < nc; k += T) {
+    const int li = k % nx, lj = k / nx;
+    const long long idx = (long long)(r0 + lj) * nx + li;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) sW[q * cpb + k] = Ws[(long long)q * n + idx];
+    if (FUSED) {   // w1 = A u + sum a_k g_k, as the apply kernel forms it; y_0 = w1
+      const double au = stencil9(Wu, n, uu, li, r0 + lj, nx, ny, g.bc, idx);
+      double r = 1.0 * au;
+      for (int q = 0; q < F.src.n; ++q)
+        r = fma(F.src.a[q], static_cast<const double*>(F.src.g[q])[idx], r);
+      F.w1[idx] = r;
+      put(win, li, lj, r);
+      sP[k] = F.d0 * r;
+    } else {
+      put(win, li, lj, static_cast<const double*>(a.y[0])[idx]);
+      sP[k] = static_cast<const double*>(a.p)[idx];
+    }
+  }
+  cl.sync();            // every band's y_0 is in place
+  fill_halo(0);
+  __syncthreads();
+
+  int m = 0;
+  for (;;) {
+    const LejaCoef lc = a.lc[m];
+    const double* wy = win + (m & 1) * WB;
+    double* wz = win + ((m + 1) & 1) * WB;
+    double sy = 0.0, sp = 0.0;
+    for (int k = t; k < nc; k += T) {
+      const int li = k % nx, lj = k / nx;
+      const double* yc = wy + widx(li, lj);
+      // the cell arithmetic of the persistent kernels, in their order
+      double z = sW[4 * cpb + k] * yc[0];
+      z = fma(sW[0 * cpb + k], yc[-S - 1], z);
+      z = fma(sW[1 * cpb + k], yc[-S], z);
+      z = fma(sW[2 * cpb + k], yc[-S + 1], z);
+      z = fma(sW[3 * cpb + k], yc[-1], z);
+      z = fma(sW[5 * cpb + k], yc[1], z);
+      z = fma(sW[6 * cpb + k], yc[S - 1], z);
+      z = fma(sW[7 * cpb + k], yc[S], z);
+      z = fma(sW[8 * cpb + k], yc[S + 1], z);
+      z = fma(-lc.xi, yc[0], z);
+      put(wz, li, lj, z);
+      const double pn = fma(lc.d, z, sP[k]);
+      sP[k] = pn;
+      sy = fma(z, z, sy);
+      sp = fma(pn, pn, sp);
+    }
+    s_red[0][t] = sy;
+    s_red[1][t] = sp;
+    __syncthreads();
+    if (warp == 0) {   // the block's sums: thread order per lane, one shuffle tree for both
+      double ty = 0.0, tp = 0.0;
+      for (int q = lane; q < T; q += 32) {
+        ty += s_red[0][q];
+        tp += s_red[1][q];
+      }
+      const bool lo = lane < 16;
+      double v = (lo ? ty : tp) + __shfl_xor_sync(0xffffffffu, lo ? tp : ty, 16);
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) s_part[m & 1][0] = v;
+      if (lane == 16) s_part[m & 1][1] = v;
+    }
+    cl.sync();          // y_{m+1} bands and the block sums, cluster-wide
+    fill_halo((m + 1) & 1);
+    if (warp == 0) {   // the K block sums in rank order, identical in every CTA
+      const int q = lane & 15;
+      double v = 0.0;
+      if (q < K) v = cl.map_shared_rank(&s_part[m & 1][0], (unsigned)q)[lane < 16 ? 0 : 1];
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      const double ty = __shfl_sync(0xffffffffu, v, 0);
+      const double tp = __shfl_sync(0xffffffffu, v, 16);
+      if (lane == 0) {   // the rule of series_finish after terms = m + 1
+        const int terms = m + 1;
+        int stop = 0, st = 0;
+        if (force > 0) {
+          stop = terms >= force;
+        } else if (!isfinite(ty) || !isfinite(tp)) {
+          stop = 1;
+          st = 3;
+        } else if (terms >= 2 && (lc.absd * lc.absd) * ty <= (tol * tol) * tp) {
+          stop = 1;
+        } else if (terms >= max_it) {
+          stop = 1;
+          st = 3;
+        }
+        if (terms >= kMaxIters) stop = 1;
+        s_stop = stop;
+        s_status = st;
+        s_ty = ty;
+        s_tp = tp;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    ++m;
+  }
+  if (FUSED) {   // u = 1 u + b P, as the axpby kernel forms it
+    for (int k = t; k < nc; k += T) {
+      const long long idx = (long long)(r0 + k / nx) * nx + k % nx;
+      F.u[idx] = fma(F.b, sP[k], 1.0 * F.u[idx]);
+    }
+  } else {
+    double* p = static_cast<double*>(a.p);
+    for (int k = t; k < nc; k += T) p[(long long)(r0 + k / nx) * nx + k % nx] = sP[k];
+  }
+  cl.sync();            // no CTA leaves while another may still read its shared memory
+  if (rank == 0 && t == 0) {
+    const int fin = m;
+    ctrl->iters = fin + 1;
+    ctrl->m = fin + 1;
+    ctrl->ynorm2 = s_ty;
+    ctrl->pnorm2 = s_tp;
+    ctrl->err_est = a.lc[fin].absd;
+    ctrl->status = s_status;
+    ctrl->stop = 1;
+    if (FUSED && F.totals) {   // the asynchronous step's report
+      AsyncTotals* tt = F.totals;
+      const int it = fin + 1;
+      tt->iters += it;
+      if (F.timed) tt->timed_iters += it;
+      tt->series += 1;
+      if (s_status > tt->status) tt->status = s_status;
+      const double e = s_tp > 0.0 ? a.lc[fin].absd * sqrt(s_ty / s_tp)
+                                  : (s_ty > 0.0 ? INFINITY : 0.0);
+      if (e > tt->err_est) tt->err_est = e;
+    }
+  }
+}
+
+// Off with AD_F64_CLUSTER=0, and whenever AD_F64_KERNEL or AD_NO_NSYNC asks
+// for one of the persistent kernels by name.
+bool cluster_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("AD_F64_CLUSTER");
+    return !(e && e[0] == '0') && !getenv("AD_F64_KERNEL") && !getenv("AD_NO_NSYNC");
+  }();
+  return on;
+}
+
+}  // namespace
+
+int series_run_cluster(const SeriesArgs& a, cudaStream_t s, const StepFuse* fuse) {
+  if (!cluster_enabled() || a.prec != 0 || a.aug || a.g.n > kClusterMaxCells) return 0;
+  if (fuse && fuse->s != 1) return 0;
+  const int nx = a.g.nx, ny = a.g.ny;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 0; }
+  void* fn = fuse ? (void*)leja_cluster_f64_k<true> : (void*)leja_cluster_f64_k<false>;
+  // once per (device, kernel): all the dynamic shared memory the device
+  // offers, and clusters of 16; then per (K, smem): whether one such cluster
+  // can be resident (cached: a series is launched on every step)
+  struct FnInfo { int dev; const void* fn; size_t max_dyn; bool ok; };
+  struct Fit { int dev; const void* fn; int K; size_t smem; bool ok; };
+  static std::mutex mu;
+  static std::vector<FnInfo> fns;
+  static std::vector<Fit> fits;
+  std::lock_guard<std::mutex> lock(mu);
+  const FnInfo* fi = nullptr;
+  for (const FnInfo& f : fns)
+    if (f.dev == dev && f.fn == fn) fi = &f;
+  if (!fi) {
+    FnInfo f{dev, fn, 0, false};
+    int optin = 0;
+    cudaFuncAttributes fa{};
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+        cudaFuncGetAttributes(&fa, fn) == cudaSuccess && fa.sharedSizeBytes < (size_t)optin) {
+      f.max_dyn = (size_t)optin - fa.sharedSizeBytes;
+      f.ok = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)f.max_dyn) == cudaSuccess &&
+             cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                 cudaSuccess;
+    }
+    cudaGetLastError();
+    fns.push_back(f);
+    fi = &fns.back();
+  }
+  if (!fi->ok) return 0;
+  for (int K = std::min(kClusterMaxCtas, ny); K >= 1;
+       K = K > 8 ? std::min(8, ny) : (K > 4 ? std::min(4, ny) : 0)) {
+    const ClusterGeom geo{K, (ny + K - 1) / K, nx + 2};
+    const size_t smem =
+        sizeof(double) * ((size_t)10 * geo.rows * nx + 2 * (size_t)(geo.rows + 2) * geo.S);
+    if (smem > fi->max_dyn) continue;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)K;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)K);
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int known = -1;
+    for (const Fit& f : fits)
+      if (f.dev == dev && f.fn == fn && f.K == K && f.smem == smem) known = f.ok ? 1 : 0;
+    if (known < 0) {
+      int clusters = 0;
+      const bool ok = cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg) == cudaSuccess &&
+                      clusters >= 1;
+      cudaGetLastError();
+      fits.push_back(Fit{dev, fn, K, smem, ok});
+      known = ok ? 1 : 0;
+    }
+    if (!known) continue;
+    StepFuse F{};
+    if (fuse) F = *fuse;
+    SeriesArgs args = a;
+    args.nblocks = K;
+    ClusterGeom g = geo;
+    void* params[] = {&args, &g, &F};
+    if (cudaLaunchKernelExC(&cfg, fn, params) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    ++launch_counter();
+    return 10;
+  }
+  return 0;
+}
+
+}  // namespace ad
