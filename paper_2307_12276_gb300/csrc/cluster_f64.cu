@@ -3,28 +3,33 @@
 // For grids of a few thousand cells the series is a chain of short
 // dependent iterations: at 64^2 a Leja iteration is 4096 cells of a 9-point
 // stencil, and the cost of the persistent tile kernel (152 blocks of 27-32
-// cells, neighbours synchronised through flags in global memory, the stopping
-// rule two iterations late) is its synchronisation latency, about 6 us per
-// iteration.  Here the grid lives in the distributed shared memory of one
-// cluster of K <= 16 CTAs (one per SM): CTA r owns the row band
-// [r ny / K, (r + 1) ny / K) -- its 9 scaled weights, its part of p and a
-// window of y with one halo row above and below and one halo column on each
-// side.  Per iteration m:
-//   1. every thread forms z = y_{m+1} and p_{m+1} on its cells (the cell
-//      arithmetic of the persistent kernels, operation for operation) and
-//      its two squared-norm partials; warp 0 adds the block's partials;
-//   2. one hardware cluster barrier (release / acquire) publishes the new
-//      rows and the block sums to the whole cluster;
-//   3. each CTA copies its two halo rows of y_{m+1} from the neighbouring
-//      CTAs' shared memory, and warp 0 of every CTA adds the K block sums in
-//      rank order and applies the stopping rule -- the same values in the
-//      same order everywhere, so every CTA takes the same decision and runs
-//      the same number of barriers.
-// Double buffering (y windows and block sums by parity) makes one barrier
-// per iteration enough: a buffer is overwritten only one barrier after the
-// last remote read of it.  A final barrier keeps every CTA's shared memory
-// alive until the others have stopped reading it.  The waits are the
-// hardware barrier's own (no spin loop, nothing to time out).
+// cells, neighbours synchronised through flags in global memory) is its
+// synchronisation latency, about 6 us per iteration.  Here the grid lives in
+// the distributed shared memory of one cluster of K <= 16 CTAs (one per SM):
+// CTA r owns the row band [r ny / K, (r + 1) ny / K) -- its 9 scaled
+// weights, three p buffers and two windows of y with one halo row above and
+// below and one halo column on each side.  Per iteration m:
+//   phase A: warps 2-9 form z = y_{m+1} and p_{m+1} on the band (the cell
+//     arithmetic of the persistent kernels, operation for operation) and
+//     their squared-norm terms; meanwhile control warp 1 adds the block's
+//     terms of iteration m - 1, and control warp 0 adds the K block sums of
+//     iteration m - 2 (published one barrier earlier) and applies the
+//     stopping rule to iteration m - 2;
+//   one hardware cluster barrier (release / acquire) publishes the new rows
+//     and the block sums to the whole cluster;
+//   each CTA copies its two halo rows of y_{m+1} from the neighbouring CTAs'
+//     shared memory.
+// The norms and the decision stay off the critical path: the rule runs two
+// iterations late (p after iteration m - 2 survives in the third p buffer)
+// and the K sums are added in rank order by every CTA, so every CTA takes the
+// same decision and runs the same number of barriers.  Count limits (forced
+// counts, max_iters) stop before the iteration they exclude, and a drain
+// then tests the two iterations still pending.  Double buffering (y windows
+// and block sums by parity) makes one barrier per iteration enough: a buffer
+// is overwritten only one barrier after the last remote read of it.  A final
+// barrier keeps every CTA's shared memory alive until the others have
+// stopped reading it.  The waits are the hardware barrier's own (no spin
+// loop, nothing to time out).
 //
 // With a StepFuse of one stage (exponential midpoint, Eq. exp_midpoint) the
 // launch also forms the step's right-hand side w1 = A u + S (prologue, the
@@ -44,11 +49,14 @@ namespace cg = cooperative_groups;
 namespace ad {
 namespace {
 
-constexpr int kClusterThreads = 256;
+constexpr int kClusterCompute = 256;                  // threads of warps 2-9
+constexpr int kClusterThreads = 64 + kClusterCompute;  // + the two control warps
 constexpr int kClusterMaxCtas = 16;          // non-portable cluster size (GB300 allows 16)
-// Measured per Leja iteration (64^2-workload fields, cluster vs tile kernel):
-// 32^2 3.1 vs 5.7 us, 64^2 3.4 vs 5.6, 96^2 4.9 vs 6.0, 128^2 6.3 vs 5.3.
-constexpr long long kClusterMaxCells = 96 * 96;
+// Measured per Leja iteration (the 64^2 workload's fields at other sizes,
+// this kernel vs the tile kernel): 32^2 1.9 vs 5.1 us, 64^2 2.5 vs 5.4,
+// 96^2 3.7 vs 5.5, 112^2 5.2 vs 5.8, 128^2 5.4 vs 5.3, 160^2 7.3 vs 5.7:
+// beyond 112^2 the 16 SMs' FP64 pipes, not synchronisation, bound it.
+constexpr long long kClusterMaxCells = 112 * 112;
 
 struct ClusterGeom {
   int K;        // CTAs in the cluster
@@ -60,13 +68,14 @@ template <bool FUSED>
 __global__ void __launch_bounds__(kClusterThreads)
     leja_cluster_f64_k(SeriesArgs a, ClusterGeom geo, StepFuse F) {
   extern __shared__ __align__(16) double csm[];
-  __shared__ double s_red[2][kClusterThreads];    // per-thread norm partials
-  __shared__ double s_part[2][2];                 // this CTA's (y, p) sums, by parity of m
-  __shared__ int s_stop, s_status;
+  __shared__ double s_red[2][2][kClusterCompute];  // per-thread norm terms, by parity of m
+  __shared__ double s_part[2][2];                  // this CTA's (y, p) sums, by parity of m
+  __shared__ int s_fin, s_status;
   __shared__ double s_ty, s_tp;
   cg::cluster_group cl = cg::this_cluster();
   const int K = geo.K, rank = (int)cl.block_rank();
   const int t = threadIdx.x, T = blockDim.x, lane = t & 31, warp = t >> 5;
+  const int ct = t - 64;                             // compute thread index (warps 2-9)
   const GridDev g = a.g;
   const int nx = g.nx, ny = g.ny, S = geo.S;
   const long long n = g.n;
@@ -76,13 +85,15 @@ __global__ void __launch_bounds__(kClusterThreads)
   const int cpb = geo.rows * nx;
   const int WB = (geo.rows + 2) * S;
   double* sW = csm;                    // [9][cpb] scaled weights
-  double* sP = sW + 9 * cpb;           // [cpb] p
-  double* win = sP + cpb;              // [2][WB]: y_m in buffer m & 1
+  double* sP = sW + 9 * cpb;           // [3][cpb]: p after iteration k in buffer (k + 1) % 3
+  double* win = sP + 3 * cpb;          // [2][WB]: y_m in buffer m & 1
   const double* __restrict__ Ws = static_cast<const double*>(a.coef);
   Ctrl* ctrl = a.ctrl;
   const int force = FUSED ? F.force : ctrl->force;
   const int max_it = min(FUSED ? F.max_iters : ctrl->max_iters, kMaxIters);
   const double tol = FUSED ? F.tol : ctrl->tol;
+  // iterations 0 .. limit - 1 at most (terms <= limit)
+  const int limit = max(1, force > 0 ? min(force, kMaxIters) : max_it);
   auto widx = [&](int li, int lj) { return (lj + 1) * S + li + 1; };
   // periodic: the halo columns of a row hold the wrapped values
   auto put = [&](double* wb, int li, int lj, double v) {
@@ -115,8 +126,49 @@ __global__ void __launch_bounds__(kClusterThreads)
       }
     }
   };
+  // control warp 1: the block's sums of the terms of parity par -- lanes
+  // 0-15 the y terms, 16-31 the p terms, 16 terms per lane (q = lane mod 16
+  // + 16 j) added as a
+  // pairwise tree, then a shuffle tree over the half-warp (FP64 adds are
+  // slow to issue from one warp, so the dependent chain is kept short)
+  auto block_sums = [&](int par) {
+    static_assert(kClusterCompute == 256, "16 lanes x 16 terms per norm");
+    const double* src = &s_red[par][lane >> 4][lane & 15];
+    double v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = src[16 * j];   // lanes on consecutive words
+#pragma unroll
+    for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+      for (int j = 0; j < w; ++j) v[j] = v[j] + v[j + w];
+    double r = v[0];
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (lane == 0) s_part[par][0] = r;
+    if (lane == 16) s_part[par][1] = r;
+  };
+  // control warp: the K block sums of parity par in rank order (identical in
+  // every CTA), in every lane
+  auto cluster_sums = [&](int par, double& ty, double& tp) {
+    const int q = lane & 15;
+    double v = 0.0;
+    if (q < K) v = cl.map_shared_rank(&s_part[par][0], (unsigned)q)[lane < 16 ? 0 : 1];
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    ty = __shfl_sync(0xffffffffu, v, 0);
+    tp = __shfl_sync(0xffffffffu, v, 16);
+  };
+  // the norm test of series_finish on iteration k (terms = k + 1) with
+  // absd = |d_{k+1}|: 0 converged, 3 not finite, -1 go on
+  const double tol2 = tol * tol;
+  auto norm_test = [&](int k, double absd, double ty, double tp) -> int {
+    if (!isfinite(ty) || !isfinite(tp)) return 3;
+    if (k + 1 >= 2 && (absd * absd) * ty <= tol2 * tp) return 0;
+    return -1;
+  };
 
   for (int q = t; q < 2 * WB; q += T) win[q] = 0.0;   // zero Dirichlet halo
+  if (t == 0) s_fin = -1;
   __syncthreads();
   const double* __restrict__ Wu = F.W;
   const double* __restrict__ uu = F.u;
@@ -143,94 +195,107 @@ __global__ void __launch_bounds__(kClusterThreads)
   __syncthreads();
 
   int m = 0;
+  // Leja scalars one iteration ahead (their loads stay off the critical path):
+  // xi_m, d_{m+1} for the compute warps, |d| of the iteration warp 0 tests next
+  double xi_m = a.lc[0].xi, d_m = a.lc[0].d;
+  double absd_next = a.lc[0].absd;
   for (;;) {
-    const LejaCoef lc = a.lc[m];
-    const double* wy = win + (m & 1) * WB;
-    double* wz = win + ((m + 1) & 1) * WB;
-    double sy = 0.0, sp = 0.0;
-    for (int k = t; k < nc; k += T) {
-      const int li = k % nx, lj = k / nx;
-      const double* yc = wy + widx(li, lj);
-      // the cell arithmetic of the persistent kernels, in their order
-      double z = sW[4 * cpb + k] * yc[0];
-      z = fma(sW[0 * cpb + k], yc[-S - 1], z);
-      z = fma(sW[1 * cpb + k], yc[-S], z);
-      z = fma(sW[2 * cpb + k], yc[-S + 1], z);
-      z = fma(sW[3 * cpb + k], yc[-1], z);
-      z = fma(sW[5 * cpb + k], yc[1], z);
-      z = fma(sW[6 * cpb + k], yc[S - 1], z);
-      z = fma(sW[7 * cpb + k], yc[S], z);
-      z = fma(sW[8 * cpb + k], yc[S + 1], z);
-      z = fma(-lc.xi, yc[0], z);
-      put(wz, li, lj, z);
-      const double pn = fma(lc.d, z, sP[k]);
-      sP[k] = pn;
-      sy = fma(z, z, sy);
-      sp = fma(pn, pn, sp);
-    }
-    s_red[0][t] = sy;
-    s_red[1][t] = sp;
-    __syncthreads();
-    if (warp == 0) {   // the block's sums: thread order per lane, one shuffle tree for both
-      double ty = 0.0, tp = 0.0;
-      for (int q = lane; q < T; q += 32) {
-        ty += s_red[0][q];
-        tp += s_red[1][q];
+    if (m >= limit) break;          // count limit: the drain below decides
+    if (warp >= 2) {                // phase A: iteration m
+      const double xi = xi_m, dd = d_m;
+      if (m + 1 < kMaxIters) {
+        xi_m = a.lc[m + 1].xi;
+        d_m = a.lc[m + 1].d;
       }
-      const bool lo = lane < 16;
-      double v = (lo ? ty : tp) + __shfl_xor_sync(0xffffffffu, lo ? tp : ty, 16);
-#pragma unroll
-      for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) s_part[m & 1][0] = v;
-      if (lane == 16) s_part[m & 1][1] = v;
-    }
-    cl.sync();          // y_{m+1} bands and the block sums, cluster-wide
-    fill_halo((m + 1) & 1);
-    if (warp == 0) {   // the K block sums in rank order, identical in every CTA
-      const int q = lane & 15;
-      double v = 0.0;
-      if (q < K) v = cl.map_shared_rank(&s_part[m & 1][0], (unsigned)q)[lane < 16 ? 0 : 1];
-#pragma unroll
-      for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      const double ty = __shfl_sync(0xffffffffu, v, 0);
-      const double tp = __shfl_sync(0xffffffffu, v, 16);
-      if (lane == 0) {   // the rule of series_finish after terms = m + 1
-        const int terms = m + 1;
-        int stop = 0, st = 0;
-        if (force > 0) {
-          stop = terms >= force;
-        } else if (!isfinite(ty) || !isfinite(tp)) {
-          stop = 1;
-          st = 3;
-        } else if (terms >= 2 && (lc.absd * lc.absd) * ty <= (tol * tol) * tp) {
-          stop = 1;
-        } else if (terms >= max_it) {
-          stop = 1;
-          st = 3;
+      const double* wy = win + (m & 1) * WB;
+      double* wz = win + ((m + 1) & 1) * WB;
+      const double* Pin = sP + (m % 3) * cpb;
+      double* Pout = sP + ((m + 1) % 3) * cpb;
+      double sy = 0.0, sp = 0.0;
+      for (int k = ct; k < nc; k += kClusterCompute) {
+        const int li = k % nx, lj = k / nx;
+        const double* yc = wy + widx(li, lj);
+        // the cell arithmetic of the persistent kernels, in their order
+        double z = sW[4 * cpb + k] * yc[0];
+        z = fma(sW[0 * cpb + k], yc[-S - 1], z);
+        z = fma(sW[1 * cpb + k], yc[-S], z);
+        z = fma(sW[2 * cpb + k], yc[-S + 1], z);
+        z = fma(sW[3 * cpb + k], yc[-1], z);
+        z = fma(sW[5 * cpb + k], yc[1], z);
+        z = fma(sW[6 * cpb + k], yc[S - 1], z);
+        z = fma(sW[7 * cpb + k], yc[S], z);
+        z = fma(sW[8 * cpb + k], yc[S + 1], z);
+        z = fma(-xi, yc[0], z);
+        put(wz, li, lj, z);
+        const double pn = fma(dd, z, Pin[k]);
+        Pout[k] = pn;
+        sy = fma(z, z, sy);
+        sp = fma(pn, pn, sp);
+      }
+      s_red[m & 1][0][ct] = sy;
+      s_red[m & 1][1][ct] = sp;
+    } else if (warp == 1) {         // phase A: the block's sums of iteration m - 1
+      if (m >= 1) block_sums((m - 1) & 1);
+    } else if (m >= 2) {            // phase A: the rule on iteration m - 2
+      const double absd = absd_next;
+      absd_next = a.lc[m - 1].absd;
+      if (force <= 0) {
+        double ty, tp;
+        cluster_sums((m - 2) & 1, ty, tp);
+        const int r = norm_test(m - 2, absd, ty, tp);
+        if (lane == 0 && r >= 0) {
+          s_fin = m - 2;
+          s_status = r;
+          s_ty = ty;
+          s_tp = tp;
         }
-        if (terms >= kMaxIters) stop = 1;
-        s_stop = stop;
+      }
+    }
+    __syncthreads();
+    if (s_fin >= 0) break;          // the same decision in every CTA
+    cl.sync();                      // y_{m+1} bands and the block sums of m - 1, cluster-wide
+    fill_halo((m + 1) & 1);
+    __syncthreads();
+    ++m;
+  }
+  if (s_fin < 0) {   // stopped by a count before iteration m: iterations m - 2, m - 1 pending
+    if (warp == 1) block_sums((m - 1) & 1);
+    __syncthreads();
+    cl.sync();
+    if (warp == 0) {
+      int fin = m - 1, st = 0;
+      double ty = 0.0, tp = 0.0;
+      if (force <= 0 && m >= 2) {
+        cluster_sums((m - 2) & 1, ty, tp);
+        const int r = norm_test(m - 2, a.lc[m - 2].absd, ty, tp);
+        if (r >= 0) { fin = m - 2; st = r; }
+      }
+      if (fin == m - 1) {
+        cluster_sums((m - 1) & 1, ty, tp);
+        if (force <= 0) st = norm_test(m - 1, a.lc[m - 1].absd, ty, tp) == 0 ? 0 : 3;
+      }
+      if (lane == 0) {
+        s_fin = fin;
         s_status = st;
         s_ty = ty;
         s_tp = tp;
       }
     }
     __syncthreads();
-    if (s_stop) break;
-    ++m;
   }
+  const int fin = s_fin;
+  const double* Pf = sP + ((fin + 1) % 3) * cpb;
   if (FUSED) {   // u = 1 u + b P, as the axpby kernel forms it
     for (int k = t; k < nc; k += T) {
       const long long idx = (long long)(r0 + k / nx) * nx + k % nx;
-      F.u[idx] = fma(F.b, sP[k], 1.0 * F.u[idx]);
+      F.u[idx] = fma(F.b, Pf[k], 1.0 * F.u[idx]);
     }
   } else {
     double* p = static_cast<double*>(a.p);
-    for (int k = t; k < nc; k += T) p[(long long)(r0 + k / nx) * nx + k % nx] = sP[k];
+    for (int k = t; k < nc; k += T) p[(long long)(r0 + k / nx) * nx + k % nx] = Pf[k];
   }
   cl.sync();            // no CTA leaves while another may still read its shared memory
   if (rank == 0 && t == 0) {
-    const int fin = m;
     ctrl->iters = fin + 1;
     ctrl->m = fin + 1;
     ctrl->ynorm2 = s_ty;
@@ -304,7 +369,7 @@ int series_run_cluster(const SeriesArgs& a, cudaStream_t s, const StepFuse* fuse
        K = K > 8 ? std::min(8, ny) : (K > 4 ? std::min(4, ny) : 0)) {
     const ClusterGeom geo{K, (ny + K - 1) / K, nx + 2};
     const size_t smem =
-        sizeof(double) * ((size_t)10 * geo.rows * nx + 2 * (size_t)(geo.rows + 2) * geo.S);
+        sizeof(double) * ((size_t)12 * geo.rows * nx + 2 * (size_t)(geo.rows + 2) * geo.S);
     if (smem > fi->max_dyn) continue;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -1,7 +1,7 @@
 """The FP64 series of small grids in one thread-block cluster
 (leja_cluster_f64_k) against the persistent tile kernel and the oracle.
 
-Grids of up to 96^2 cells run their phi_1 series -- and a midpoint step of
+Grids of up to 112^2 cells run their phi_1 series -- and a midpoint step of
 one substep, prologue and update included -- in one cluster of up to 16 CTAs
 that keeps the grid in distributed shared memory.  Every entry is formed by
 the operations of the tile kernel in the same order, so with the same
@@ -28,7 +28,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 CASES = [  # (nx, ny, bc, kind, adv, adv_field, dt_factor)
     (64, 64, 0, "uniform", (0.0, 0.0), False, 100.0),      # the 64^2 workload's shape
-    (96, 96, 1, "stream", (0.0, 0.0), False, 200.0),       # the largest cluster grid
+    (96, 96, 1, "stream", (0.0, 0.0), False, 200.0),
+    (112, 112, 0, "stream", (0.0, 0.0), False, 200.0),    # the largest cluster grid
     (100, 37, 1, "circular", (0.1, 0.05), False, 150.0),   # uneven bands (37 rows / 16)
     (17, 23, 0, "random", (0.5, -0.3), True, 50.0),        # advection field, periodic
     (4, 3, 0, "uniform", (0.1, 0.0), False, 80.0),         # three CTAs of one row
