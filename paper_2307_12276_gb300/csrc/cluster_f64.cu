@@ -15,8 +15,8 @@
 //     terms of iteration m - 1, and control warp 0 adds the K block sums of
 //     iteration m - 2 (published one barrier earlier) and applies the
 //     stopping rule to iteration m - 2;
-//   one hardware cluster barrier (release / acquire) publishes the new rows
-//     and the block sums to the whole cluster;
+//   one hardware cluster barrier (release / acquire, every thread of the
+//     cluster) publishes the new rows, the block sums and the decision;
 //   each CTA copies its two halo rows of y_{m+1} from the neighbouring CTAs'
 //     shared memory.
 // The norms and the decision stay off the critical path: the rule runs two
@@ -128,9 +128,9 @@ __global__ void __launch_bounds__(kClusterThreads)
   };
   // control warp 1: the block's sums of the terms of parity par -- lanes
   // 0-15 the y terms, 16-31 the p terms, 16 terms per lane (q = lane mod 16
-  // + 16 j) added as a
-  // pairwise tree, then a shuffle tree over the half-warp (FP64 adds are
-  // slow to issue from one warp, so the dependent chain is kept short)
+  // + 16 j) added as a pairwise tree, then a shuffle tree over the half-warp
+  // (FP64 adds are slow to issue from one warp, so the dependent chain is
+  // kept short)
   auto block_sums = [&](int par) {
     static_assert(kClusterCompute == 256, "16 lanes x 16 terms per norm");
     const double* src = &s_red[par][lane >> 4][lane & 15];
@@ -251,9 +251,11 @@ __global__ void __launch_bounds__(kClusterThreads)
         }
       }
     }
-    __syncthreads();
-    if (s_fin >= 0) break;          // the same decision in every CTA
-    cl.sync();                      // y_{m+1} bands and the block sums of m - 1, cluster-wide
+    // y_{m+1} bands and the block sums of m - 1, cluster-wide; a release /
+    // acquire barrier over every thread of the cluster, so it also orders
+    // this block's shared memory (the decision s_fin, the terms in s_red)
+    cl.sync();
+    if (s_fin >= 0) break;          // the same decision in every CTA, after the same barrier
     fill_halo((m + 1) & 1);
     __syncthreads();
     ++m;
