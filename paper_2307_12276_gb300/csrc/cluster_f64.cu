@@ -31,10 +31,13 @@
 // stopped reading it.  The waits are the hardware barrier's own (no spin
 // loop, nothing to time out).
 //
-// With a StepFuse of one stage (exponential midpoint, Eq. exp_midpoint) the
-// launch also forms the step's right-hand side w1 = A u + S (prologue, the
-// apply kernel's arithmetic) and the update u += dt P (epilogue), as the
-// tile kernel does: one launch per step.
+// The augmented series of two-stage quadrature (Eq. exp_quad) adds the
+// couplings e1 w2 + e2 w1 per cell, w1 and w2 held in shared memory beside
+// the weights.  With a StepFuse the launch also forms the step's right-hand
+// sides w1 = A u + sum a_k g_k and w2 = sum b_k g_k (prologue, the apply
+// kernel's arithmetic; y_0 = w1 for the midpoint rule, Eq. exp_midpoint,
+// y_0 = 0 for two stages) and the update u += P (epilogue), as the tile
+// kernel does: one launch per step.
 #include "cluster_f64.h"
 #include "stencil9.cuh"
 
@@ -64,7 +67,7 @@ struct ClusterGeom {
   int S;        // window row stride, nx + 2
 };
 
-template <bool FUSED>
+template <bool FUSED, bool AUG>
 __global__ void __launch_bounds__(kClusterThreads)
     leja_cluster_f64_k(SeriesArgs a, ClusterGeom geo, StepFuse F) {
   extern __shared__ __align__(16) double csm[];
@@ -86,7 +89,9 @@ __global__ void __launch_bounds__(kClusterThreads)
   const int WB = (geo.rows + 2) * S;
   double* sW = csm;                    // [9][cpb] scaled weights
   double* sP = sW + 9 * cpb;           // [3][cpb]: p after iteration k in buffer (k + 1) % 3
-  double* win = sP + 3 * cpb;          // [2][WB]: y_m in buffer m & 1
+  double* sW1 = sP + 3 * cpb;          // [cpb] w1, [cpb] w2: the augmented couplings (AUG)
+  double* sW2 = sW1 + cpb;
+  double* win = sP + (AUG ? 5 : 3) * cpb;   // [2][WB]: y_m in buffer m & 1
   const double* __restrict__ Ws = static_cast<const double*>(a.coef);
   Ctrl* ctrl = a.ctrl;
   const int force = FUSED ? F.force : ctrl->force;
@@ -177,17 +182,30 @@ __global__ void __launch_bounds__(kClusterThreads)
     const long long idx = (long long)(r0 + lj) * nx + li;
 #pragma unroll
     for (int q = 0; q < 9; ++q) sW[q * cpb + k] = Ws[(long long)q * n + idx];
-    if (FUSED) {   // w1 = A u + sum a_k g_k, as the apply kernel forms it; y_0 = w1
+    if (FUSED) {   // w1 = A u + sum a_k g_k, w2 = sum b_k g_k, as the apply kernel forms them
       const double au = stencil9(Wu, n, uu, li, r0 + lj, nx, ny, g.bc, idx);
-      double r = 1.0 * au;
-      for (int q = 0; q < F.src.n; ++q)
-        r = fma(F.src.a[q], static_cast<const double*>(F.src.g[q])[idx], r);
+      double r = 1.0 * au, r2 = 0.0;
+      for (int q = 0; q < F.src.n; ++q) {
+        const double gq = static_cast<const double*>(F.src.g[q])[idx];
+        r = fma(F.src.a[q], gq, r);
+        r2 = fma(F.src.b[q], gq, r2);
+      }
       F.w1[idx] = r;
-      put(win, li, lj, r);
-      sP[k] = F.d0 * r;
+      if (AUG) {                   // two stages: y_0 = 0 (the window stays 0)
+        sW1[k] = r;
+        sW2[k] = r2;
+        sP[k] = F.d0 * 0.0;
+      } else {                     // midpoint: y_0 = w1
+        put(win, li, lj, r);
+        sP[k] = F.d0 * r;
+      }
     } else {
       put(win, li, lj, static_cast<const double*>(a.y[0])[idx]);
       sP[k] = static_cast<const double*>(a.p)[idx];
+      if (AUG) {
+        sW1[k] = static_cast<const double*>(a.w1)[idx];
+        sW2[k] = static_cast<const double*>(a.w2)[idx];
+      }
     }
   }
   cl.sync();            // every band's y_0 is in place
@@ -196,16 +214,22 @@ __global__ void __launch_bounds__(kClusterThreads)
 
   int m = 0;
   // Leja scalars one iteration ahead (their loads stay off the critical path):
-  // xi_m, d_{m+1} for the compute warps, |d| of the iteration warp 0 tests next
+  // xi_m, d_{m+1} (and the coupling scalars e1, e2) for the compute warps,
+  // |d| of the iteration warp 0 tests next
   double xi_m = a.lc[0].xi, d_m = a.lc[0].d;
+  double e1_m = AUG ? a.lc[0].e1 : 0.0, e2_m = AUG ? a.lc[0].e2 : 0.0;
   double absd_next = a.lc[0].absd;
   for (;;) {
     if (m >= limit) break;          // count limit: the drain below decides
     if (warp >= 2) {                // phase A: iteration m
-      const double xi = xi_m, dd = d_m;
+      const double xi = xi_m, dd = d_m, e1 = e1_m, e2 = e2_m;
       if (m + 1 < kMaxIters) {
         xi_m = a.lc[m + 1].xi;
         d_m = a.lc[m + 1].d;
+        if (AUG) {
+          e1_m = a.lc[m + 1].e1;
+          e2_m = a.lc[m + 1].e2;
+        }
       }
       const double* wy = win + (m & 1) * WB;
       double* wz = win + ((m + 1) & 1) * WB;
@@ -226,6 +250,10 @@ __global__ void __launch_bounds__(kClusterThreads)
         z = fma(sW[7 * cpb + k], yc[S], z);
         z = fma(sW[8 * cpb + k], yc[S + 1], z);
         z = fma(-xi, yc[0], z);
+        if (AUG) {                 // the augmented couplings, as the persistent kernels add them
+          if (e1 != 0.0) z = fma(e1, sW2[k], z);
+          if (e2 != 0.0) z = fma(e2, sW1[k], z);
+        }
         put(wz, li, lj, z);
         const double pn = fma(dd, z, Pin[k]);
         Pout[k] = pn;
@@ -332,12 +360,15 @@ bool cluster_enabled() {
 }  // namespace
 
 int series_run_cluster(const SeriesArgs& a, cudaStream_t s, const StepFuse* fuse) {
-  if (!cluster_enabled() || a.prec != 0 || a.aug || a.g.n > kClusterMaxCells) return 0;
-  if (fuse && fuse->s != 1) return 0;
+  if (!cluster_enabled() || a.prec != 0 || a.g.n > kClusterMaxCells) return 0;
+  if (fuse && (fuse->s == 2) != (a.aug != 0)) return 0;
   const int nx = a.g.nx, ny = a.g.ny;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 0; }
-  void* fn = fuse ? (void*)leja_cluster_f64_k<true> : (void*)leja_cluster_f64_k<false>;
+  void* fn = fuse ? (a.aug ? (void*)leja_cluster_f64_k<true, true>
+                           : (void*)leja_cluster_f64_k<true, false>)
+                  : (a.aug ? (void*)leja_cluster_f64_k<false, true>
+                           : (void*)leja_cluster_f64_k<false, false>);
   // once per (device, kernel): all the dynamic shared memory the device
   // offers, and clusters of 16; then per (K, smem): whether one such cluster
   // can be resident (cached: a series is launched on every step)
@@ -371,7 +402,8 @@ int series_run_cluster(const SeriesArgs& a, cudaStream_t s, const StepFuse* fuse
        K = K > 8 ? std::min(8, ny) : (K > 4 ? std::min(4, ny) : 0)) {
     const ClusterGeom geo{K, (ny + K - 1) / K, nx + 2};
     const size_t smem =
-        sizeof(double) * ((size_t)12 * geo.rows * nx + 2 * (size_t)(geo.rows + 2) * geo.S);
+        sizeof(double) * ((size_t)(a.aug ? 14 : 12) * geo.rows * nx +
+                          2 * (size_t)(geo.rows + 2) * geo.S);
     if (smem > fi->max_dyn) continue;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;

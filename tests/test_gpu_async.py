@@ -148,5 +148,5 @@ def test_series_timing_covers_async_series():
     assert t["series"] == 3
     assert t["iters"] == tot["iters"]
     assert t["ms"] > 0.0
-    assert t["kernel"] == "leja_tile_f64_k"
+    assert t["kernel"] == "leja_cluster_f64_k"      # 96 x 80: one thread-block cluster
     ad().time_series(op, False)

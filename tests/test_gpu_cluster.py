@@ -1,8 +1,9 @@
 """The FP64 series of small grids in one thread-block cluster
 (leja_cluster_f64_k) against the persistent tile kernel and the oracle.
 
-Grids of up to 112^2 cells run their phi_1 series -- and a midpoint step of
-one substep, prologue and update included -- in one cluster of up to 16 CTAs
+Grids of up to 112^2 cells run their Newton series (the phi_1 form and the
+augmented form of two-stage quadrature) -- and an exponential step of one
+substep, prologue and update included -- in one cluster of up to 16 CTAs
 that keeps the grid in distributed shared memory.  Every entry is formed by
 the operations of the tile kernel in the same order, so with the same
 iteration count the vectors are identical; the norm sums run over another
@@ -37,8 +38,9 @@ CASES = [  # (nx, ny, bc, kind, adv, adv_field, dt_factor)
 ]
 FORCED = [1, 2, 9, 40]
 
-# One case: forced and adaptive phi_1 actions, two midpoint steps (one launch
-# each) and the series path; prints JSON stats, saves the vectors.
+# One case: forced and adaptive phi_1 actions, two midpoint and two two-stage
+# steps (one launch each) and the series path; prints JSON stats, saves the
+# vectors.
 CHILD = r"""
 import json, sys
 import numpy as np, torch
@@ -68,6 +70,12 @@ for k in range(2):
     stats["step%d" % k] = ad.expquad_step(op, u, k * p.dt, p.dt, 1, (0.5,), src, tol=1e-10)
     arrays["step%d" % k] = u.cpu().numpy()
 stats["step_path"] = ad.series_timing(op)["kernel"]
+u = T(p.u0)
+for k in range(2):
+    stats["stepq%d" % k] = ad.expquad_step(op, u, k * p.dt, p.dt, 2, (1 / 3, 2 / 3), src,
+                                           tol=1e-10)
+    arrays["stepq%d" % k] = u.cpu().numpy()
+stats["stepq_path"] = ad.series_timing(op)["kernel"]
 np.savez({prefix!r}, **arrays)
 print(json.dumps(stats))
 """
@@ -88,7 +96,7 @@ def test_cluster_kernel_equals_tile_kernel(case, tmp_path):
     need_gpu()
     sc, ac = _run(case, str(tmp_path / "cluster"), {})
     st, at = _run(case, str(tmp_path / "tile"), {"AD_F64_CLUSTER": "0"})
-    assert sc["path"] == "leja_cluster_f64_k" and sc["step_path"] == "leja_cluster_f64_k"
+    assert sc["path"] == sc["step_path"] == sc["stepq_path"] == "leja_cluster_f64_k"
     assert st["path"] == "leja_tile_f64_k"
     for key in at.files:
         assert sc[key]["iters"] == st[key]["iters"], (key, sc[key], st[key])
@@ -99,6 +107,7 @@ def test_cluster_kernel_equals_tile_kernel(case, tmp_path):
         assert sc["f%d" % m]["iters"] == m
     for k in range(2):   # the whole step in one launch
         assert sc["step%d" % k]["kernel_launches"] == 1
+        assert sc["stepq%d" % k]["kernel_launches"] == 1
 
 
 @pytest.mark.parametrize("case", [CASES[0], CASES[2], CASES[3]])
@@ -137,4 +146,19 @@ def test_cluster_kernel_matches_oracle(case):
         return r, o.err_est
     alt2 = oracle_at_gpu_count(st2["iters"], ost2.iters, forced_step, 1e-10)
     assert_close(u.cpu().numpy(), ref2 if alt2 is None else alt2, 1e-11, "midpoint step")
+
+    # a two-stage step (the augmented series) from t = 0.1
+    c = (1 / 3, 2 / 3)
+    u = dev64(p.u0)
+    st3 = ad().expquad_step(op, u, 0.1, p.dt, 2, c, gpu_source(p), tol=1e-10)
+    assert ad().series_timing(op)["kernel"] == "leja_cluster_f64_k"
+    ref3, ost3 = integrators.expquad_step(A, p.u0.ravel(), 0.1, p.dt, 2, c, S, alpha, 1e-10)
+    assert st3["substeps"] == ost3.substeps == 1
+
+    def forced_q(k):
+        r, o = integrators.expquad_step(A, p.u0.ravel(), 0.1, p.dt, 2, c, S, alpha,
+                                        force_iters=k)
+        return r, o.err_est
+    alt3 = oracle_at_gpu_count(st3["iters"], ost3.iters, forced_q, 1e-10)
+    assert_close(u.cpu().numpy(), ref3 if alt3 is None else alt3, 1e-11, "two-stage step")
     op.close()

@@ -180,7 +180,7 @@ def test_series_timing_counts_every_series():
     assert t["series"] == st["substeps"]
     assert t["iters"] == st["iters"]
     assert t["ms"] > 0.0
-    assert t["kernel"] in ("leja_tile_f64_k", "leja_nsync_f64_k")
+    assert t["kernel"] in ("leja_cluster_f64_k", "leja_tile_f64_k", "leja_nsync_f64_k")
     ad().time_series(op, False)
     ad().expquad_step(op, u, p.dt, p.dt, 2, (1 / 3, 2 / 3), src, tol=1e-10)
     assert ad().series_timing(op) == t
