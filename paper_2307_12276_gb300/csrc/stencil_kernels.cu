@@ -35,6 +35,44 @@ namespace ad {
 
 namespace {
 
+// Deterministic block sum of four values of an NT-thread block; results valid
+// in thread 0.  Warp w < 4 adds the w-th value of every thread: eight per lane
+// as a pairwise tree, then a butterfly.  The four sums run in parallel, so no
+// warp issues more than 12 dependent FP64 additions (one warp issues one FP64
+// instruction per 64 cycles on this GPU; two block_sum2 calls on warp 0 took
+// 52).
+template <int NT>
+__device__ __forceinline__ void block_sum4(double& a, double& b, double& c, double& d) {
+  static_assert(NT == 256, "eight values per lane of four warps");
+  __shared__ double s4[4][NT];
+  __shared__ double r4[4];
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  __syncthreads();
+  s4[0][t] = a;
+  s4[1][t] = b;
+  s4[2][t] = c;
+  s4[3][t] = d;
+  __syncthreads();
+  if (w < 4) {
+    double x[NT / 32];
+#pragma unroll
+    for (int j = 0; j < NT / 32; ++j) x[j] = s4[w][lane + 32 * j];
+#pragma unroll
+    for (int h = NT / 64; h >= 1; h >>= 1)
+#pragma unroll
+      for (int j = 0; j < h; ++j) x[j] += x[j + h];
+    const double v = warp_sum(x[0]);
+    if (lane == 0) r4[w] = v;
+  }
+  __syncthreads();
+  if (t == 0) {
+    a = r4[0];
+    b = r4[1];
+    c = r4[2];
+    d = r4[3];
+  }
+}
+
 // Epilogue of a pair launch (two iterations, m and m + 1, m even): publish the
 // block's four norm partials; the last block sums them in block order and
 // applies the stopping rule after term m + 1, then after term m + 2.  A stop
@@ -43,14 +81,12 @@ namespace {
 // next pair launch, or by pair_flush_k after the series).
 __device__ void series_finish2(const SeriesArgs& a, double y1, double p1, double y2, double p2) {
   __shared__ unsigned int s_last;
-  block_sum2<kPairWarps * 32>(y1, p1);
-  const double by1 = y1, bp1 = p1;
-  block_sum2<kPairWarps * 32>(y2, p2);
+  block_sum4<kPairWarps * 32>(y1, p1, y2, p2);
   Ctrl* ctrl = a.ctrl;
   if (threadIdx.x == 0) {
     double* q = a.partials + 4 * blockIdx.x;
-    q[0] = by1;
-    q[1] = bp1;
+    q[0] = y1;
+    q[1] = p1;
     q[2] = y2;
     q[3] = p2;
     __threadfence();
@@ -67,8 +103,7 @@ __device__ void series_finish2(const SeriesArgs& a, double y1, double p1, double
     t2y += __ldcg(&a.partials[4 * b + 2]);
     t2p += __ldcg(&a.partials[4 * b + 3]);
   }
-  block_sum2<kPairWarps * 32>(t1y, t1p);
-  block_sum2<kPairWarps * 32>(t2y, t2p);
+  block_sum4<kPairWarps * 32>(t1y, t1p, t2y, t2p);
   if (threadIdx.x == 0) {
     const int m = ctrl->m;
     const double tol = ctrl->tol;
